@@ -1,0 +1,155 @@
+/*
+ * libbsct - pixel-basis (box-spline) Gram filtering for parallel-beam X-ray CT on one
+ * GB300 GPU (sm_103a).  C ABI: plain pointers and sizes, no C++ or torch types.
+ *
+ * Method: Shu & Entezari, "Gram Filtering and Sinogram Interpolation for Pixel-basis
+ * in Parallel-beam X-ray CT Reconstruction" (arXiv 2005.13471).  The reconstruction
+ * solves the normal equations  G c = b  of the least-squares problem of Sec. 2, where
+ *   G = H^T H is applied as a (2N-1) x (2N-1) Gram filter (Sec. 4), and
+ *   b = H^T g_hat is the back projection of the B-spline-interpolated sinogram (Sec. 5).
+ *
+ * Conventions used by every entry point:
+ *   - coefficient images are N x N, row-major, element [k2][k1]; unit pixels; pixel
+ *     centre x_k = (k1 - (N-1)/2, k2 - (N-1)/2);
+ *   - view theta projects x onto y = x . (cos theta, sin theta);
+ *   - detector sample m (0 <= m < n_bins) sits at y_m = (m - (n_bins-1)/2) * lambda_y;
+ *   - angles are given in half turns (theta / pi) so that 0 and 1/2 are exact;
+ *   - the detector blur is a unit-mass box of width zeta_blur (0 = no blur);
+ *   - Gram filter taps G[d], d = (d1, d2) in [-(N-1), N-1]^2, stored [d2+N-1][d1+N-1].
+ *
+ * Memory: every device buffer passed in (d_*) is allocated and owned by the caller
+ * and must stay valid until the stream reaches the end of the call.  Handles
+ * (bsct_gram) own their device memory and free it in bsct_gram_free.  All calls are
+ * asynchronous on the given stream (a cudaStream_t passed as void*, NULL = legacy
+ * default stream) except where stated.
+ *
+ * Errors: every int-returning call returns BSCT_OK (0) on success, a negative
+ * BSCT_ERR_* code on failure (nothing was launched, or a CUDA call failed), or a
+ * positive BSCT_WARN_* code.  bsct_status_string / bsct_last_error_string describe
+ * the code and the last failure.  No exception crosses the ABI.
+ */
+#ifndef BSCT_H
+#define BSCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BSCT_OK 0
+#define BSCT_ERR_INVALID_ARG (-1)
+#define BSCT_ERR_UNSUPPORTED_SIZE (-2)
+#define BSCT_ERR_CUDA (-3)
+#define BSCT_ERR_TIMEOUT (-4)
+#define BSCT_ERR_NONFINITE (-5)
+#define BSCT_WARN_NOT_CONVERGED 1
+
+#define BSCT_F32 0 /* FP32 data path */
+#define BSCT_F64 1 /* FP64 data path */
+
+#define BSCT_APPLY_FFT32 0         /* FP32 zero-padded 2N x 2N FFT convolution */
+#define BSCT_APPLY_F64 1           /* FP64 zero-padded FFT convolution */
+
+/* Problem geometry (Sec. 2: coefficients c_k on an N x N grid, n_angles views, a
+ * detector of n_bins samples with step lambda_y, blur width zeta_blur).
+ * angles_pi: HOST array of n_angles values theta_j / pi (any real values; theta and
+ * theta + pi are distinct views).  Read during the call only. */
+typedef struct bsct_geom {
+  int32_t N;
+  int32_t n_angles;
+  int32_t n_bins;
+  int32_t reserved;
+  const double* angles_pi;
+  double lambda_y;
+  double zeta_blur;
+} bsct_geom;
+
+typedef struct bsct_gram bsct_gram; /* opaque, library-owned */
+
+typedef struct bsct_cg_report {
+  int32_t iterations;        /* CG iterations run */
+  int32_t converged;         /* 1 if the recursive residual reached rel_tol */
+  double rel_residual;       /* recursive ||r|| / ||b|| at exit */
+  double true_rel_residual;  /* ||b - G x|| / ||b|| recomputed at exit (or -1 if not computed) */
+} bsct_cg_report;
+
+/* Supported image sizes N (the FFT lengths are N and 2N). */
+int bsct_supported_size(int32_t N);
+
+/* Build the Gram filter of a geometry (Sec. 4): for every offset d,
+ *   G[d] = sum_theta M_[c, c, s, s, zeta, zeta](d . u_theta)
+ * (the unit-mass box spline of the Gram entry; zeta terms only when zeta > 0), then
+ * its 2N x 2N circulant spectrum for the FFT apply (Sec. 4, Toeplitz-block-Toeplitz
+ * remark).  Taps and spectrum are computed in FP64 on the GPU; precision selects the
+ * stored spectrum (BSCT_F32 or BSCT_F64) and the data path of gram_apply / cg_solve.
+ * The handle keeps the scratch for gram_apply and cg_solve, so calls sharing one
+ * handle must be serialised on one stream.
+ * Errors: INVALID_ARG (null pointers, n_angles < 1, lambda_y <= 0, zeta_blur < 0 or
+ * 0 < zeta_blur < 0.2), UNSUPPORTED_SIZE (N not supported), CUDA. */
+int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram** out, void* stream);
+
+/* Release a handle (synchronises its stream first).  NULL is a no-op. */
+void bsct_gram_free(bsct_gram* g);
+
+/* Copy the (2N-1)^2 FP64 taps, layout [d2+N-1][d1+N-1], into d_out (device). */
+int bsct_gram_taps(const bsct_gram* g, double* d_out, void* stream);
+
+/* Copy the real spectrum of the circulant embedding, [2N][N+1] FP64, entry [u][v] =
+ * sum_d G[d] exp(-2 pi i (d2 u + d1 v) / 2N) (device). */
+int bsct_gram_spectrum(const bsct_gram* g, double* d_out, void* stream);
+
+/* y = G x: y[i] = sum_j G[i - j] x[j] on the N x N grid (Sec. 4), computed as a
+ * zero-padded 2N x 2N FFT convolution.  mode BSCT_APPLY_FFT32 needs a BSCT_F32
+ * handle and float buffers, BSCT_APPLY_F64 a BSCT_F64 handle and double buffers.
+ * d_x and d_y: N*N elements, may not alias. */
+int bsct_gram_apply(const bsct_gram* g, const void* d_x, void* d_y, int mode, void* stream);
+
+/* Bytes of device workspace bsct_backproject needs for this geometry/precision. */
+int bsct_backproject_workspace(const bsct_geom* geom, int precision, size_t* bytes);
+
+/* b = H^T g_hat (Sec. 5): per view the sinogram row is prefiltered by the correction
+ * filter q of Eq. 5 (degree-2 views only; q[m] = sqrt(2)(2 sqrt(2) - 3)^|m|, |m| <= 40),
+ * interpolated with the B-spline of degree d = (#non-zero of |cos|, |sin|, zeta) - 1,
+ * and integrated against the blurred pixel footprint, i.e.
+ *   b_k = sum_theta sum_m c~[m] lambda_y M_[c, s, zeta, lambda_y x (d+1)](y_m - x_k . u).
+ * d_sino: [n_angles][n_bins] in view order of geom->angles_pi; d_b: [N][N] (output,
+ * overwritten).  float for BSCT_F32, double for BSCT_F64.  d_work: workspace of at
+ * least the size bsct_backproject_workspace reports.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE (N > 16384 or too many detector samples per
+ * view), CUDA. */
+int bsct_backproject(const bsct_geom* geom, const void* d_sino, void* d_b, int precision,
+                     void* d_work, size_t work_bytes, void* stream);
+
+/* Conjugate gradients on G x = b (normal equations of Sec. 2) with the handle's data
+ * precision; inner products and step scalars in FP64 on the device.
+ * d_b: right-hand side [N][N]; d_x: in = initial guess (ignored if x0_is_zero),
+ * out = solution.  Runs max_iter iterations, or stops early once the recursive
+ * relative residual <= rel_tol (checked every check_every iterations; rel_tol <= 0
+ * disables the check and the host never waits inside the loop).  Synchronous: returns
+ * after the stream has finished, with *report filled (report may be NULL).
+ * Returns BSCT_OK, BSCT_WARN_NOT_CONVERGED (rel_tol > 0 not reached), or an error. */
+int bsct_cg_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero, int max_iter,
+                  double rel_tol, int check_every, bsct_cg_report* report, void* stream);
+
+/* Run exactly n_iter CG iterations without any host synchronisation (the body every
+ * CG step of bsct_cg_solve runs; suitable for timing and CUDA-graph capture).  The
+ * state (x, r, p and the scalars) lives in the handle: call bsct_cg_begin first. */
+int bsct_cg_begin(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero, void* stream);
+int bsct_cg_iterate(bsct_gram* g, void* d_x, int n_iter, void* stream);
+/* Copy the current recursive squared residual ||r||^2 and ||b||^2 to host (synchronous). */
+int bsct_cg_residual(const bsct_gram* g, double* rr, double* bb, void* stream);
+
+/* Human-readable text of a status code, and of the last failure on this thread. */
+const char* bsct_status_string(int status);
+const char* bsct_last_error_string(void);
+
+/* Number of kernel launches issued by this library since load (all threads). */
+uint64_t bsct_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSCT_H */

@@ -1,0 +1,284 @@
+"""GB300-native pixel-basis (box-spline) Gram filtering for parallel-beam X-ray CT.
+
+Thin Python binding of ``libbsct.so`` (include/bsct.h): argument marshalling only.
+Every step of the method runs in the library's CUDA kernels; torch provides device
+memory and the current CUDA stream.  The binding raises if the library is missing
+or a tensor is not a contiguous CUDA tensor of the expected dtype and shape -
+there is no CPU fallback.
+
+Entry points (same names as the C ABI):
+    gram_build(geom, precision)          -> GramFilter   (Sec. 4 Gram filter + spectrum)
+    gram_apply(gram, x, out=None)        -> y = G x      (zero-padded FFT convolution)
+    backproject(geom, sino, precision)   -> b = H^T g    (Sec. 5)
+    cg_solve(gram, b, x0=None, ...)      -> (x, report)  (normal equations of Sec. 2)
+"""
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "F32", "F64", "Geometry", "GramFilter", "gram_build", "gram_apply", "backproject", "cg_solve",
+    "library_path", "lib", "supported_size", "launch_count",
+]
+
+F32 = 0
+F64 = 1
+APPLY_FFT32 = 0
+APPLY_F64 = 1
+OK = 0
+WARN_NOT_CONVERGED = 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+def library_path():
+    return os.path.join(_HERE, "libbsct.so")
+
+
+class _Geom(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int32),
+        ("n_angles", ctypes.c_int32),
+        ("n_bins", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("angles_pi", ctypes.POINTER(ctypes.c_double)),
+        ("lambda_y", ctypes.c_double),
+        ("zeta_blur", ctypes.c_double),
+    ]
+
+
+class _CGReport(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int32),
+        ("converged", ctypes.c_int32),
+        ("rel_residual", ctypes.c_double),
+        ("true_rel_residual", ctypes.c_double),
+    ]
+
+
+def _declare(L):
+    vp, i32, dbl, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_size_t
+    gp = ctypes.POINTER(_Geom)
+    L.bsct_supported_size.argtypes = [i32]
+    L.bsct_supported_size.restype = ctypes.c_int
+    L.bsct_gram_build.argtypes = [gp, ctypes.c_int, ctypes.POINTER(vp), vp]
+    L.bsct_gram_free.argtypes = [vp]
+    L.bsct_gram_free.restype = None
+    L.bsct_gram_taps.argtypes = [vp, vp, vp]
+    L.bsct_gram_spectrum.argtypes = [vp, vp, vp]
+    L.bsct_gram_apply.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+    L.bsct_backproject_workspace.argtypes = [gp, ctypes.c_int, ctypes.POINTER(sz)]
+    L.bsct_backproject.argtypes = [gp, vp, vp, ctypes.c_int, vp, sz, vp]
+    L.bsct_cg_solve.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, dbl, ctypes.c_int,
+                                ctypes.POINTER(_CGReport), vp]
+    L.bsct_cg_begin.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+    L.bsct_cg_iterate.argtypes = [vp, vp, ctypes.c_int, vp]
+    L.bsct_cg_residual.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp]
+    L.bsct_status_string.argtypes = [ctypes.c_int]
+    L.bsct_status_string.restype = ctypes.c_char_p
+    L.bsct_last_error_string.argtypes = []
+    L.bsct_last_error_string.restype = ctypes.c_char_p
+    L.bsct_launch_count.argtypes = []
+    L.bsct_launch_count.restype = ctypes.c_uint64
+    for name in ("bsct_gram_build", "bsct_gram_taps", "bsct_gram_spectrum", "bsct_gram_apply",
+                 "bsct_backproject_workspace", "bsct_backproject", "bsct_cg_solve", "bsct_cg_begin",
+                 "bsct_cg_iterate", "bsct_cg_residual"):
+        getattr(L, name).restype = ctypes.c_int
+
+
+def lib():
+    """Load libbsct.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(path)
+        _declare(L)
+        _LIB = L
+    return _LIB
+
+
+def _check(rc, what):
+    if rc < 0:
+        L = lib()
+        raise RuntimeError(f"{what} failed: {L.bsct_status_string(rc).decode()} "
+                           f"({L.bsct_last_error_string().decode()})")
+    return rc
+
+
+def supported_size(N):
+    return bool(lib().bsct_supported_size(int(N)))
+
+
+def launch_count():
+    return int(lib().bsct_launch_count())
+
+
+def _stream():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dtype(precision):
+    import torch
+
+    return torch.float32 if precision == F32 else torch.float64
+
+
+def _dev(t, shape, dtype, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Geometry:
+    """Problem geometry of Sec. 2: N x N unit-pixel grid, views, detector of n_bins samples.
+
+    angles_pi: view angles in half turns (theta / pi), e.g. ``np.arange(n) / n``.
+    """
+
+    def __init__(self, N, angles_pi, n_bins, lambda_y=1.0, zeta_blur=0.0):
+        self.N = int(N)
+        self.angles_pi = np.ascontiguousarray(np.asarray(angles_pi, dtype=np.float64).reshape(-1))
+        self.n_angles = int(self.angles_pi.size)
+        self.n_bins = int(n_bins)
+        self.lambda_y = float(lambda_y)
+        self.zeta_blur = float(zeta_blur)
+        self._c = _Geom(self.N, self.n_angles, self.n_bins, 0,
+                        self.angles_pi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        self.lambda_y, self.zeta_blur)
+
+    @classmethod
+    def uniform(cls, N, n_angles, n_bins, lambda_y=1.0, zeta_blur=0.0):
+        return cls(N, np.arange(n_angles, dtype=np.float64) / n_angles, n_bins, lambda_y, zeta_blur)
+
+    def cptr(self):
+        return ctypes.byref(self._c)
+
+
+class GramFilter:
+    """Library-owned Gram filter of one geometry (taps, spectrum, apply/CG scratch)."""
+
+    def __init__(self, geom, precision=F32):
+        self.geom = geom
+        self.N = geom.N
+        self.precision = precision
+        self._h = ctypes.c_void_p()
+        _check(lib().bsct_gram_build(geom.cptr(), precision, ctypes.byref(self._h), _stream()), "bsct_gram_build")
+
+    def close(self):
+        if self._h:
+            lib().bsct_gram_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def dtype(self):
+        return _dtype(self.precision)
+
+    def taps(self):
+        import torch
+
+        out = torch.empty((2 * self.N - 1, 2 * self.N - 1), dtype=torch.float64, device="cuda")
+        _check(lib().bsct_gram_taps(self._h, ctypes.c_void_p(out.data_ptr()), _stream()), "bsct_gram_taps")
+        return out
+
+    def spectrum(self):
+        import torch
+
+        out = torch.empty((2 * self.N, self.N + 1), dtype=torch.float64, device="cuda")
+        _check(lib().bsct_gram_spectrum(self._h, ctypes.c_void_p(out.data_ptr()), _stream()), "bsct_gram_spectrum")
+        return out
+
+    def apply(self, x, out=None):
+        import torch
+
+        n = self.N
+        px = _dev(x, (n, n), self.dtype, "x")
+        if out is None:
+            out = torch.empty((n, n), dtype=self.dtype, device=x.device)
+        py = _dev(out, (n, n), self.dtype, "out")
+        mode = APPLY_FFT32 if self.precision == F32 else APPLY_F64
+        _check(lib().bsct_gram_apply(self._h, px, py, mode, _stream()), "bsct_gram_apply")
+        return out
+
+    def cg_solve(self, b, x0=None, max_iter=100, rel_tol=0.0, check_every=10):
+        import torch
+
+        n = self.N
+        pb = _dev(b, (n, n), self.dtype, "b")
+        x = torch.empty((n, n), dtype=self.dtype, device=b.device) if x0 is None else x0.clone()
+        px = _dev(x, (n, n), self.dtype, "x")
+        rep = _CGReport()
+        rc = _check(lib().bsct_cg_solve(self._h, pb, px, 1 if x0 is None else 0, int(max_iter), float(rel_tol),
+                                        int(check_every), ctypes.byref(rep), _stream()), "bsct_cg_solve")
+        report = dict(iterations=rep.iterations, converged=bool(rep.converged), rel_residual=rep.rel_residual,
+                      true_rel_residual=rep.true_rel_residual, status=rc)
+        return x, report
+
+    def cg_begin(self, b, x, x0_is_zero=True):
+        n = self.N
+        _check(lib().bsct_cg_begin(self._h, _dev(b, (n, n), self.dtype, "b"), _dev(x, (n, n), self.dtype, "x"),
+                                   1 if x0_is_zero else 0, _stream()), "bsct_cg_begin")
+
+    def cg_iterate(self, x, n_iter):
+        n = self.N
+        _check(lib().bsct_cg_iterate(self._h, _dev(x, (n, n), self.dtype, "x"), int(n_iter), _stream()),
+               "bsct_cg_iterate")
+
+    def cg_residual(self):
+        rr, bb = ctypes.c_double(), ctypes.c_double()
+        _check(lib().bsct_cg_residual(self._h, ctypes.byref(rr), ctypes.byref(bb), _stream()), "bsct_cg_residual")
+        return rr.value, bb.value
+
+
+def gram_build(geom, precision=F32):
+    return GramFilter(geom, precision)
+
+
+def gram_apply(gram, x, out=None):
+    return gram.apply(x, out)
+
+
+def backproject_workspace(geom, precision=F32):
+    n = ctypes.c_size_t()
+    _check(lib().bsct_backproject_workspace(geom.cptr(), precision, ctypes.byref(n)), "bsct_backproject_workspace")
+    return int(n.value)
+
+
+def backproject(geom, sino, precision=F32, out=None, work=None):
+    """b = H^T g_hat (Sec. 5) for a device sinogram [n_angles, n_bins]."""
+    import torch
+
+    dt = _dtype(precision)
+    ps = _dev(sino, (geom.n_angles, geom.n_bins), dt, "sino")
+    if out is None:
+        out = torch.empty((geom.N, geom.N), dtype=dt, device=sino.device)
+    pb = _dev(out, (geom.N, geom.N), dt, "out")
+    nbytes = backproject_workspace(geom, precision)
+    if work is None or work.numel() < nbytes:
+        work = torch.empty(nbytes, dtype=torch.uint8, device=sino.device)
+    _check(lib().bsct_backproject(geom.cptr(), ps, pb, precision, ctypes.c_void_p(work.data_ptr()),
+                                  ctypes.c_size_t(work.numel()), _stream()), "bsct_backproject")
+    return out
+
+
+def cg_solve(gram, b, x0=None, max_iter=100, rel_tol=0.0, check_every=10):
+    return gram.cg_solve(b, x0, max_iter, rel_tol, check_every)

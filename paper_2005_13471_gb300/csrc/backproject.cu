@@ -1,0 +1,328 @@
+// Back projection b = H^T g_hat with B-spline sinogram interpolation (Sec. 5).
+//
+// For view theta with footprint directions [|c|, |s|, zeta] and interpolation degree
+// d (Sec. 5 degree rule), sample m contributes to pixel k with weight
+//     K(y_m - t_k),  K(u) = lambda * M_[|c|, |s|, zeta, lambda x (d+1)](u),  t_k = x_k . u
+// (beta_d((y - y_m)/lambda) = lambda M_[lambda^(d+1)](y - y_m), correlated with the
+// footprint M_[c, s, zeta]).  Write p = (t_k - y_0)/lambda = m0 + f with m0 integer and
+// f in [0, 1); then y_{m0+j} - t_k = (j - f) lambda and the weight of sample m0 + j is
+// phi_j(f) = K((j - f) lambda).  Each phi_j is a piecewise polynomial in f whose kinks
+// all sit in one set {0} U {frac(-kink(K) / lambda)}, so per view:
+//
+//   k_bp_tables (FP64): kinks sigma_0 = 0 < ... < sigma_Q = 1, and for every piece q and
+//       offset j the degree-<=5 polynomial of phi_j on piece q, by Chebyshev interpolation
+//       at 6 nodes of exact FP64 kernel values (the kernel is evaluated with the
+//       short-direction split of bsct_boxspline.cuh, so views near the axes lose no
+//       digits), stored as monomials in v = (f - mid_q) / halfwidth_q in [-1, 1];
+//   k_prefilter: c~ = g_s * q for degree-2 views (Eq. 5 correction filter,
+//       q[m] = sqrt(2) (2 sqrt(2) - 3)^|m|, |m| <= 40, zero outside the detector);
+//   k_bp_gather: one thread per pixel, loop over views: locate f's piece, then
+//       b_k += sum_j c~[m0 + j] * poly_{q,j}(v).  The detector coordinate of each warp's
+//       8 x 4 pixel sub-tile is computed once per view in FP64 and the pixel offsets are
+//       added in T, so FP32 keeps ~1e-6 absolute accuracy in f.
+#include <math.h>
+
+#include "bsct_boxspline.cuh"
+#include "bsct_internal.h"
+
+namespace bsct {
+
+constexpr int BP_QMAX = 12;   // pieces per view (<= 9 occur)
+constexpr int BP_NJMAX = 16;  // samples touching one pixel (lambda_y >= ~0.2)
+constexpr int BP_HDR = 8;
+constexpr int BP_SIG = BP_HDR;                      // sigma[QMAX+1]
+constexpr int BP_MID = BP_SIG + BP_QMAX + 1;        // mid[QMAX]
+constexpr int BP_IHW = BP_MID + BP_QMAX;            // 1/halfwidth[QMAX]
+constexpr int BP_COEF = 48;                         // coef[QMAX][NJMAX][8], aligned
+constexpr int BP_STRIDE = BP_COEF + BP_QMAX * BP_NJMAX * 8;
+constexpr int BP_TX = 32, BP_TY = 8, BP_CHUNK = 64;
+
+__host__ __device__ inline int bp_degree(double c, double s, double zeta) {
+  return (c != 0.0) + (s != 0.0) + (zeta > 0.0) - 1;
+}
+__host__ __device__ inline void bp_jrange(double W, double lam, int* J0, int* nJ) {
+  const double h = 0.5 * W / lam;
+  const int j0 = (int)floor(-h) + 1;
+  const int j1 = (int)ceil(h + 1.0) - 1;
+  *J0 = j0;
+  *nJ = j1 - j0 + 1;
+}
+
+__device__ inline void bp_dirs(double A, double B, double zeta, double lam, int d, BoxDirs* D, int* small) {
+  D->ng = 0;
+  if (A > 0.0) { D->a[D->ng] = A; D->m[D->ng] = 1; ++D->ng; }
+  if (B > 0.0) { D->a[D->ng] = B; D->m[D->ng] = 1; ++D->ng; }
+  if (zeta > 0.0) { D->a[D->ng] = zeta; D->m[D->ng] = 1; ++D->ng; }
+  D->a[D->ng] = lam; D->m[D->ng] = d + 1; ++D->ng;
+  for (int g = D->ng; g < 4; ++g) { D->a[g] = 0.0; D->m[g] = 0; }
+  *small = -1;
+  if (A > 0.0 && B > 0.0) {
+    if (B < BSCT_SHORT_DIR * A) *small = 1;
+    else if (A < BSCT_SHORT_DIR * B) *small = 0;
+  }
+}
+
+// one CTA (256 threads) per view
+template <typename T>
+__global__ void __launch_bounds__(256) k_bp_tables(const double* __restrict__ ang, int N, int M, double lam,
+                                                   double zeta, double merge_tol, T* __restrict__ tab,
+                                                   double* __restrict__ p00, double2* __restrict__ csl,
+                                                   int* __restrict__ status) {
+  const int a = blockIdx.x;
+  __shared__ double sig[64];
+  __shared__ int Qs;
+  double s_, c_;
+  sincospi(ang[a], &s_, &c_);
+  const double A = fabs(c_), B = fabs(s_);
+  const int d = bp_degree(c_, s_, zeta);
+  BoxDirs D;
+  int small;
+  bp_dirs(A, B, zeta, lam, d, &D, &small);
+  double W = 0.0;
+  for (int g = 0; g < D.ng; ++g) W += D.m[g] * D.a[g];
+  int J0, nJ;
+  bp_jrange(W, lam, &J0, &nJ);
+  if (threadIdx.x == 0) {
+    // kinks of K: -W/2 + sum_g k_g a_g ; their positions in f are frac(-kink / lam)
+    int n = 0;
+    sig[n++] = 0.0;
+    const int m0 = D.m[0], m1 = D.ng > 1 ? D.m[1] : 0, m2 = D.ng > 2 ? D.m[2] : 0, m3 = D.ng > 3 ? D.m[3] : 0;
+    for (int k0 = 0; k0 <= m0; ++k0)
+      for (int k1 = 0; k1 <= m1; ++k1)
+        for (int k2 = 0; k2 <= m2; ++k2)
+          for (int k3 = 0; k3 <= m3; ++k3) {
+            double kink = -0.5 * W + k0 * D.a[0] + k1 * D.a[1] + k2 * D.a[2] + k3 * D.a[3];
+            double fpos = -kink / lam;
+            fpos -= floor(fpos);
+            if (fpos >= 1.0) fpos = 0.0;
+            if (n < 63) sig[n++] = fpos;
+          }
+    for (int i = 1; i < n; ++i) {  // sort
+      double t = sig[i];
+      int j = i - 1;
+      while (j >= 0 && sig[j] > t) { sig[j + 1] = sig[j]; --j; }
+      sig[j + 1] = t;
+    }
+    int q = 1;  // merge kinks closer than merge_tol, drop those within merge_tol of 1
+    for (int i = 1; i < n; ++i)
+      if (sig[i] - sig[q - 1] > merge_tol && 1.0 - sig[i] > merge_tol) sig[q++] = sig[i];
+    sig[q] = 1.0;
+    Qs = q;
+    T* h = tab + (long)a * BP_STRIDE;
+    h[0] = T(c_ / lam);
+    h[1] = T(s_ / lam);
+    h[2] = T(q < BP_QMAX ? q : BP_QMAX);
+    h[3] = T(J0);
+    h[4] = T(nJ);
+    for (int i = 0; i <= BP_QMAX; ++i) h[BP_SIG + i] = i <= q ? T(sig[i]) : T(2.0);
+    if (q > BP_QMAX || nJ > BP_NJMAX) atomicExch(status, 1);
+    // detector coordinate of pixel (0, 0) in bin units, FP64
+    const double x0 = -0.5 * (N - 1);
+    p00[a] = (x0 * c_ + x0 * s_) / lam + 0.5 * (M - 1);
+    csl[a] = make_double2(c_ / lam, s_ / lam);
+  }
+  __syncthreads();
+  const int Q = Qs;
+  if (Q > BP_QMAX || nJ > BP_NJMAX) return;
+  T* h = tab + (long)a * BP_STRIDE;
+  for (int w = threadIdx.x; w < BP_QMAX * BP_NJMAX; w += blockDim.x) {
+    const int q = w / BP_NJMAX, j = w % BP_NJMAX;
+    T* cf = h + BP_COEF + (q * BP_NJMAX + j) * 8;
+    if (q >= Q || j >= nJ) {
+      for (int i = 0; i < 8; ++i) cf[i] = T(0);
+      if (j == 0 && q < BP_QMAX) { h[BP_MID + q] = T(0); h[BP_IHW + q] = T(0); }
+      continue;
+    }
+    const double lo = sig[q], hi = sig[q + 1];
+    const double mid = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
+    if (j == 0) { h[BP_MID + q] = T(mid); h[BP_IHW + q] = T(1.0 / hw); }
+    // Chebyshev interpolation at x_i = cos(pi (2i+1) / 12)
+    double fv[6];
+    for (int i = 0; i < 6; ++i) {
+      const double xi = cospi((2.0 * i + 1.0) / 12.0);
+      const double f = mid + hw * xi;
+      const double u = (J0 + j - f) * lam;
+      fv[i] = (fabs(u) < 0.5 * W) ? lam * box_eval(u, D, small) : 0.0;
+    }
+    double ch[6];
+    for (int k = 0; k < 6; ++k) {
+      double acc = 0.0;
+      for (int i = 0; i < 6; ++i) acc += fv[i] * cospi(k * (2.0 * i + 1.0) / 12.0);
+      ch[k] = acc * (k == 0 ? 1.0 / 6.0 : 2.0 / 6.0);
+    }
+    // Chebyshev -> monomial: T0=1, T1=v, T2=2v^2-1, T3=4v^3-3v, T4=8v^4-8v^2+1, T5=16v^5-20v^3+5v
+    const double m0 = ch[0] - ch[2] + ch[4];
+    const double m1 = ch[1] - 3.0 * ch[3] + 5.0 * ch[5];
+    const double m2 = 2.0 * ch[2] - 8.0 * ch[4];
+    const double m3 = 4.0 * ch[3] - 20.0 * ch[5];
+    const double m4 = 8.0 * ch[4];
+    const double m5 = 16.0 * ch[5];
+    cf[0] = T(m0); cf[1] = T(m1); cf[2] = T(m2); cf[3] = T(m3); cf[4] = T(m4); cf[5] = T(m5);
+    cf[6] = T(0); cf[7] = T(0);
+  }
+}
+
+template <typename T>
+__global__ void k_prefilter(const double* __restrict__ ang, const T* __restrict__ g, int na, int M, double zeta,
+                            T* __restrict__ ct) {
+  __shared__ double q[41];
+  if (threadIdx.x <= 40) {
+    const double z1 = 2.0 * 1.4142135623730951 - 3.0;
+    q[threadIdx.x] = 1.4142135623730951 * pow(z1, (double)threadIdx.x);
+  }
+  __syncthreads();
+  const int a = blockIdx.y;
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  double s_, c_;
+  sincospi(ang[a], &s_, &c_);
+  const T* gr = g + (long)a * M;
+  if (bp_degree(c_, s_, zeta) != 2) {
+    ct[(long)a * M + m] = gr[m];
+    return;
+  }
+  double acc = 0.0;
+  for (int j = -40; j <= 40; ++j) {
+    const int mm = m - j;
+    if (mm >= 0 && mm < M) acc += q[j < 0 ? -j : j] * (double)gr[mm];
+  }
+  ct[(long)a * M + m] = T(acc);
+}
+
+template <typename T> struct Acc { typedef float part; };
+template <> struct Acc<double> { typedef double part; };
+
+// Each warp owns an 8 x 4 pixel sub-tile; its detector coordinate is computed per view in
+// FP64 by the warp itself, so the FP32 part of p only spans |offset| <= 7|c| + 3|s| + 1.
+template <typename T>
+__global__ void __launch_bounds__(BP_TX* BP_TY) k_bp_gather(const T* __restrict__ tab, const double2* __restrict__ csl,
+                                                          const double* __restrict__ p00, const T* __restrict__ ct,
+                                                          int na, int N, int M, T* __restrict__ b) {
+  constexpr int WX = 8, WY = 4;
+  __shared__ int s_mb[8][BP_CHUNK];
+  __shared__ T s_fb[8][BP_CHUNK];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int X0 = blockIdx.x * BP_TX + (w & 3) * WX, Y0 = blockIdx.y * BP_TY + (w >> 2) * WY;
+  const int lx = lane & 7, ly = lane >> 3;
+  const int k1 = X0 + lx, k2 = Y0 + ly;
+  double total = 0.0;
+  for (int a0 = 0; a0 < na; a0 += BP_CHUNK) {
+    const int nc = min(BP_CHUNK, na - a0);
+    __syncwarp();
+    for (int i = lane; i < nc; i += 32) {
+      const double2 u = csl[a0 + i];
+      const double pt = p00[a0 + i] + (double)X0 * u.x + (double)Y0 * u.y;
+      const double mb = floor(pt);
+      s_mb[w][i] = (int)mb;
+      s_fb[w][i] = T(pt - mb);
+    }
+    __syncwarp();
+    typename Acc<T>::part part = 0;
+    for (int ai = 0; ai < nc; ++ai) {
+      const int a = a0 + ai;
+      const T* h = tab + (long)a * BP_STRIDE;
+      const T cl = h[0], sl = h[1];
+      const int Q = (int)h[2], J0 = (int)h[3], nJ = (int)h[4];
+      const T pl = s_fb[w][ai] + T(lx) * cl + T(ly) * sl;
+      const T fl = floor(pl);
+      const T f = pl - fl;
+      const int m0 = s_mb[w][ai] + (int)fl + J0;
+      int q = 0;
+#pragma unroll
+      for (int i = 1; i < BP_QMAX; ++i) q += (i < Q && h[BP_SIG + i] <= f) ? 1 : 0;
+      const T v = (f - h[BP_MID + q]) * h[BP_IHW + q];
+      const T* cf = h + BP_COEF + q * BP_NJMAX * 8;
+      const T* cr = ct + (long)a * M;
+      for (int j = 0; j < nJ; ++j) {
+        const int m = m0 + j;
+        if ((unsigned)m < (unsigned)M) {
+          const T* c = cf + j * 8;
+          T wv = c[5];
+          wv = fma(wv, v, c[4]);
+          wv = fma(wv, v, c[3]);
+          wv = fma(wv, v, c[2]);
+          wv = fma(wv, v, c[1]);
+          wv = fma(wv, v, c[0]);
+          part += wv * cr[m];
+        }
+      }
+      if ((ai & 31) == 31) { total += (double)part; part = 0; }
+    }
+    total += (double)part;
+  }
+  if (k1 < N && k2 < N) b[(long)k2 * N + k1] = T(total);
+}
+
+}  // namespace bsct
+
+using namespace bsct;
+
+int bsct_check_geom(const bsct_geom* g);
+
+static size_t bp_workspace(const bsct_geom* g, int precision) {
+  const size_t T = precision == BSCT_F32 ? 4 : 8;
+  size_t b = 0;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  b += al((size_t)g->n_angles * sizeof(double));             // angles
+  b += al((size_t)g->n_angles * sizeof(double));             // p00
+  b += al((size_t)g->n_angles * sizeof(double2));            // (c, s) / lambda
+  b += al((size_t)g->n_angles * BP_STRIDE * T);               // tables
+  b += al((size_t)g->n_angles * g->n_bins * T);               // prefiltered sinogram
+  b += al(sizeof(int));                                       // status
+  return b;
+}
+
+extern "C" int bsct_backproject_workspace(const bsct_geom* geom, int precision, size_t* bytes) {
+  int rc = bsct_check_geom(geom);
+  if (rc != BSCT_OK) return rc;
+  if (!bytes) { bsct_set_last_message("bytes is NULL"); return BSCT_ERR_INVALID_ARG; }
+  if (precision != BSCT_F32 && precision != BSCT_F64) { bsct_set_last_message("precision"); return BSCT_ERR_INVALID_ARG; }
+  *bytes = bp_workspace(geom, precision);
+  return BSCT_OK;
+}
+
+template <typename T>
+static int bp_run(const bsct_geom* g, const T* sino, T* b, char* work, cudaStream_t st) {
+  const int na = g->n_angles, M = g->n_bins, N = g->N;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  double* d_ang = (double*)work;
+  work += al((size_t)na * sizeof(double));
+  double* d_p00 = (double*)work;
+  work += al((size_t)na * sizeof(double));
+  double2* d_csl = (double2*)work;
+  work += al((size_t)na * sizeof(double2));
+  T* d_tab = (T*)work;
+  work += al((size_t)na * BP_STRIDE * sizeof(T));
+  T* d_ct = (T*)work;
+  work += al((size_t)na * M * sizeof(T));
+  int* d_status = (int*)work;
+  BSCT_CUDA_TRY(cudaMemcpyAsync(d_ang, g->angles_pi, na * sizeof(double), cudaMemcpyHostToDevice, st));
+  BSCT_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+  const double tol = sizeof(T) == 4 ? 1e-6 : 1e-12;
+  k_bp_tables<T><<<na, 256, 0, st>>>(d_ang, N, M, g->lambda_y, g->zeta_blur, tol, d_tab, d_p00, d_csl, d_status);
+  dim3 gp((M + 127) / 128, na);
+  k_prefilter<T><<<gp, 128, 0, st>>>(d_ang, sino, na, M, g->zeta_blur, d_ct);
+  dim3 gg((N + BP_TX - 1) / BP_TX, (N + BP_TY - 1) / BP_TY);
+  k_bp_gather<T><<<gg, BP_TX * BP_TY, 0, st>>>(d_tab, d_csl, d_p00, d_ct, na, N, M, b);
+  count_launch(3);
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+extern "C" int bsct_backproject(const bsct_geom* geom, const void* d_sino, void* d_b, int precision, void* d_work,
+                                size_t work_bytes, void* stream) {
+  int rc = bsct_check_geom(geom);
+  if (rc != BSCT_OK) return rc;
+  if (!d_sino || !d_b || !d_work) { bsct_set_last_message("NULL device pointer"); return BSCT_ERR_INVALID_ARG; }
+  if (geom->N < 1 || geom->N > 16384) { bsct_set_last_message("N out of range"); return BSCT_ERR_UNSUPPORTED_SIZE; }
+  if (precision != BSCT_F32 && precision != BSCT_F64) { bsct_set_last_message("precision"); return BSCT_ERR_INVALID_ARG; }
+  if (work_bytes < bp_workspace(geom, precision)) { bsct_set_last_message("workspace too small"); return BSCT_ERR_INVALID_ARG; }
+  // widest kernel: |c| + |s| <= sqrt(2), degree <= 2
+  const double W = 1.4142135623730951 + geom->zeta_blur + 3.0 * geom->lambda_y;
+  int J0, nJ;
+  bp_jrange(W, geom->lambda_y, &J0, &nJ);
+  if (nJ > BP_NJMAX) { bsct_set_last_message("lambda_y too small: too many samples per pixel"); return BSCT_ERR_UNSUPPORTED_SIZE; }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == BSCT_F32) return bp_run<float>(geom, (const float*)d_sino, (float*)d_b, (char*)d_work, st);
+  return bp_run<double>(geom, (const double*)d_sino, (double*)d_b, (char*)d_work, st);
+}

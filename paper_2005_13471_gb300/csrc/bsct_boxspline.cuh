@@ -1,0 +1,141 @@
+// FP64 evaluation of centred, unit-mass univariate box splines on the GPU (Sec. 3, Eq. 1-2).
+//
+// A direction list is given as up to 4 groups (value a_g > 0, multiplicity m_g).  Two
+// evaluators:
+//   box_tp     - the truncated-power expansion of the convolution of Eq. 1,
+//                M(x) = sum_k prod_g C(m_g, k_g) (-1)^k_g (x + sum m a / 2 - sum k a)_+^(n-1)
+//                       / ((n-1)! prod a_g^m_g),
+//                grouped by equal directions (27 terms for the 6-direction Gram kernel).
+//                Its terms are ~ (sum a)^(n-1) / prod a while the result is ~ 1 / sum a,
+//                so it loses about log10((sum a)^n / prod a) digits when one direction
+//                is short (views close to the axes).
+//   box_stable - for such lists: one short group S = (s, m_s), m_s in {1, 2}, is split
+//                off and M = M_L * M_S is integrated as  int M_L(x - v) M_S(v) dv  over
+//                |v| < m_s s / 2 by 3-point Gauss-Legendre on every piece between the
+//                kinks of both factors (exact: the integrand is piecewise polynomial of
+//                degree <= 5).  M_S is a box (m_s = 1) or a hat (m_s = 2) and M_L has no
+//                short direction, so no term cancels.
+#pragma once
+#include <math.h>
+
+namespace bsct {
+
+struct BoxDirs {
+  double a[4];
+  int m[4];
+  int ng;
+};
+
+__host__ __device__ __forceinline__ double ipow(double z, int p) {
+  double r = 1.0;
+  for (int i = 0; i < p; ++i) r *= z;
+  return r;
+}
+
+__device__ __forceinline__ int binom4(int m, int k) {
+  // C(m, k) for 0 <= k <= m <= 4
+  const int tab[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
+  return tab[m][k];
+}
+
+__device__ inline double box_tp(double x, const BoxDirs& D) {
+  int n = 0;
+  double tot = 0.0, prod = 1.0;
+  for (int g = 0; g < D.ng; ++g) {
+    n += D.m[g];
+    tot += D.m[g] * D.a[g];
+    prod *= ipow(D.a[g], D.m[g]);
+  }
+  if (n == 0) return 0.0;
+  double fact = 1.0;
+  for (int i = 2; i < n; ++i) fact *= i;
+  const double x0 = x + 0.5 * tot;
+  const int m0 = D.ng > 0 ? D.m[0] : 0, m1 = D.ng > 1 ? D.m[1] : 0;
+  const int m2 = D.ng > 2 ? D.m[2] : 0, m3 = D.ng > 3 ? D.m[3] : 0;
+  double acc = 0.0;
+  for (int k0 = 0; k0 <= m0; ++k0)
+    for (int k1 = 0; k1 <= m1; ++k1)
+      for (int k2 = 0; k2 <= m2; ++k2)
+        for (int k3 = 0; k3 <= m3; ++k3) {
+          double off = 0.0;
+          if (k0) off += k0 * D.a[0];
+          if (k1) off += k1 * D.a[1];
+          if (k2) off += k2 * D.a[2];
+          if (k3) off += k3 * D.a[3];
+          const double z = x0 - off;
+          if (z <= 0.0) continue;
+          const int w = binom4(m0, k0) * binom4(m1, k1) * binom4(m2, k2) * binom4(m3, k3);
+          const double term = (n == 1) ? 1.0 : ipow(z, n - 1);
+          acc += ((k0 + k1 + k2 + k3) & 1) ? -w * term : w * term;
+        }
+  return acc / (fact * prod);
+}
+
+// kinks (knots) of M_L: -sum/2 + sum_g k_g a_g; at most 3*3*1*5 combinations are used
+#define BSCT_MAXKNOTS 48
+
+__device__ inline double box_stable(double x, const BoxDirs& L, double s, int ms) {
+  const double half = 0.5 * ms * s;
+  // candidate cut points in v: window ends, centre of the hat, x - knot(M_L)
+  double cut[BSCT_MAXKNOTS + 3];
+  int nc = 0;
+  cut[nc++] = -half;
+  cut[nc++] = half;
+  if (ms == 2) cut[nc++] = 0.0;
+  double tot = 0.0;
+  for (int g = 0; g < L.ng; ++g) tot += L.m[g] * L.a[g];
+  const int m0 = L.ng > 0 ? L.m[0] : 0, m1 = L.ng > 1 ? L.m[1] : 0;
+  const int m2 = L.ng > 2 ? L.m[2] : 0, m3 = L.ng > 3 ? L.m[3] : 0;
+  for (int k0 = 0; k0 <= m0; ++k0)
+    for (int k1 = 0; k1 <= m1; ++k1)
+      for (int k2 = 0; k2 <= m2; ++k2)
+        for (int k3 = 0; k3 <= m3; ++k3) {
+          double knot = -0.5 * tot;
+          if (k0) knot += k0 * L.a[0];
+          if (k1) knot += k1 * L.a[1];
+          if (k2) knot += k2 * L.a[2];
+          if (k3) knot += k3 * L.a[3];
+          const double v = x - knot;
+          if (v > -half && v < half && nc < BSCT_MAXKNOTS + 3) cut[nc++] = v;
+        }
+  // insertion sort (nc is small)
+  for (int i = 1; i < nc; ++i) {
+    double t = cut[i];
+    int j = i - 1;
+    while (j >= 0 && cut[j] > t) { cut[j + 1] = cut[j]; --j; }
+    cut[j + 1] = t;
+  }
+  const double g0 = 0.11270166537925831148, g1 = 0.5, g2 = 0.88729833462074168852;  // (1 -+ sqrt(3/5))/2
+  const double w0 = 5.0 / 18.0, w1 = 8.0 / 18.0;
+  double acc = 0.0;
+  for (int i = 0; i + 1 < nc; ++i) {
+    const double lo = cut[i], w = cut[i + 1] - cut[i];
+    if (w <= 0.0) continue;
+    const double vs[3] = {lo + g0 * w, lo + g1 * w, lo + g2 * w};
+    const double ws[3] = {w0, w1, w0};
+    double piece = 0.0;
+    for (int q = 0; q < 3; ++q) {
+      const double v = vs[q];
+      const double ms_v = (ms == 1) ? 1.0 / s : (s - fabs(v)) / (s * s);
+      piece += ws[q] * ms_v * box_tp(x - v, L);
+    }
+    acc += piece * w;
+  }
+  return acc;
+}
+
+// Evaluate M_D(x) where group `small` (or -1) is short relative to the others.
+__device__ inline double box_eval(double x, const BoxDirs& D, int small) {
+  if (small < 0) return box_tp(x, D);
+  BoxDirs L;
+  L.ng = 0;
+  for (int g = 0; g < D.ng; ++g)
+    if (g != small) { L.a[L.ng] = D.a[g]; L.m[L.ng] = D.m[g]; ++L.ng; }
+  for (int g = L.ng; g < 4; ++g) { L.a[g] = 0.0; L.m[g] = 0; }
+  return box_stable(x, L, D.a[small], D.m[small]);
+}
+
+// Relative length below which the short direction goes through box_stable.
+#define BSCT_SHORT_DIR 0.2
+
+}  // namespace bsct

@@ -1,0 +1,219 @@
+// Block-level Stockham FFT for the Gram-filter convolution (sm_103a).
+//
+// One FFT of length L is computed by L/E threads, each holding E complex values in
+// registers.  A stage of radix R makes every thread run E/R radix-R butterflies on
+// its registers; between stages the values are exchanged once through shared
+// memory (padded index i + i/16 to spread the stride-R writes over the banks).
+// The first stage takes its inputs from registers that the caller filled from HBM
+// and the last stage leaves its outputs in registers for the caller to store, so a
+// 3-stage 4096-point FFT costs two shared-memory round trips.
+//
+// Register layout (Stockham autosort, natural order in and out):
+//   stage input : v[b*R + r] = x[j + r*L/R],            j = tid + b*(L/E)
+//   stage output: y[(j/Ns)*Ns*R + (j%Ns) + r*Ns]          (Ns = product of earlier radices)
+//   last output : v[b*R + r] = y[j + r*L/R]
+// so running the inverse with the radix order reversed starts from exactly the
+// registers the forward transform ended with (no exchange between them).
+#pragma once
+#include "bsct_common.cuh"
+
+namespace bsct {
+
+// ----------------------------------------------------------------------------------
+// Radix plans.  E values per thread must be a multiple of every radix used.
+// ----------------------------------------------------------------------------------
+template <int L> struct Plan;
+#define BSCT_PLAN(LEN, EPT, ...)                                                     \
+  template <> struct Plan<LEN> {                                                     \
+    static constexpr int E = EPT;                                                    \
+    static constexpr int R[] = {__VA_ARGS__};                                        \
+    static constexpr int NS = sizeof(R) / sizeof(int);                               \
+  };
+BSCT_PLAN(16, 16, 16)
+BSCT_PLAN(32, 16, 16, 2)
+BSCT_PLAN(64, 16, 16, 4)
+BSCT_PLAN(128, 16, 16, 8)
+BSCT_PLAN(256, 16, 16, 16)
+BSCT_PLAN(384, 24, 8, 4, 4, 3)
+BSCT_PLAN(512, 16, 16, 8, 4)
+BSCT_PLAN(768, 24, 8, 8, 4, 3)
+BSCT_PLAN(1024, 16, 16, 16, 4)
+BSCT_PLAN(1536, 24, 8, 8, 8, 3)
+BSCT_PLAN(2048, 16, 16, 16, 8)
+BSCT_PLAN(4096, 16, 16, 16, 16)
+#undef BSCT_PLAN
+
+// radix of stage s (REV = run the plan's radices in reverse order)
+template <int L, bool REV> __host__ __device__ constexpr int radix_of(int s) {
+  return REV ? Plan<L>::R[Plan<L>::NS - 1 - s] : Plan<L>::R[s];
+}
+template <int L, bool REV> __host__ __device__ constexpr int ns_of(int s) {
+  int p = 1;
+  for (int i = 0; i < s; ++i) p *= radix_of<L, REV>(i);
+  return p;
+}
+
+__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+template <int L> __host__ __device__ constexpr int smem_elems() { return L + L / 16; }
+
+// ----------------------------------------------------------------------------------
+// Small DFTs in registers: X[k] = sum_r v[r] w^(rk), w = exp(-+2 pi i / R)
+// ----------------------------------------------------------------------------------
+template <typename T, bool INV>
+__device__ __forceinline__ void dft2(cpx<T>& a, cpx<T>& b) {
+  cpx<T> t = a - b;
+  a = a + b;
+  b = t;
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft4(cpx<T>& v0, cpx<T>& v1, cpx<T>& v2, cpx<T>& v3) {
+  cpx<T> a0 = v0 + v2, a1 = v0 - v2, a2 = v1 + v3, a3 = mul_mi<T, INV>(v1 - v3);
+  v0 = a0 + a2;
+  v2 = a0 - a2;
+  v1 = a1 + a3;
+  v3 = a1 - a3;
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft3(cpx<T>& a, cpx<T>& b, cpx<T>& c) {
+  const T h3 = T(0.86602540378443864676);  // sqrt(3)/2
+  cpx<T> t1 = b + c;
+  cpx<T> t2 = mk(fma(T(-0.5), t1.x, a.x), fma(T(-0.5), t1.y, a.y));
+  cpx<T> t3 = mul_mi<T, INV>(scale(b - c, h3));
+  a = a + t1;
+  b = t2 + t3;
+  c = t2 - t3;
+}
+
+// exp(-+2 pi i k / 16) as constants
+template <typename T, bool INV> __device__ __forceinline__ cpx<T> w16(int k) {
+  const T C1 = T(0.92387953251128675613), S1 = T(0.38268343236508977173), H = T(0.70710678118654752440);
+  T c, s;
+  switch (k) {
+    case 1: c = C1; s = S1; break;
+    case 2: c = H; s = H; break;
+    case 3: c = S1; s = C1; break;
+    case 6: c = -H; s = H; break;
+    case 9: c = -C1; s = -S1; break;
+    default: c = T(1); s = T(0); break;
+  }
+  return mk(c, INV ? s : -s);
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft8(cpx<T>* v) {
+  dft4<T, INV>(v[0], v[2], v[4], v[6]);
+  dft4<T, INV>(v[1], v[3], v[5], v[7]);
+  const T H = T(0.70710678118654752440);
+  cpx<T> o0 = v[1];
+  cpx<T> o1 = cmul(v[3], mk(H, INV ? H : -H));
+  cpx<T> o2 = mul_mi<T, INV>(v[5]);
+  cpx<T> o3 = cmul(v[7], mk(-H, INV ? H : -H));
+  cpx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  v[0] = e0 + o0; v[4] = e0 - o0;
+  v[1] = e1 + o1; v[5] = e1 - o1;
+  v[2] = e2 + o2; v[6] = e2 - o2;
+  v[3] = e3 + o3; v[7] = e3 - o3;
+}
+
+// 16 = 4 x 4: r = r1 + 4 r2, k = k1 + 4 k2
+template <typename T, bool INV>
+__device__ __forceinline__ void dft16(cpx<T>* v) {
+#pragma unroll
+  for (int r1 = 0; r1 < 4; ++r1) dft4<T, INV>(v[r1], v[r1 + 4], v[r1 + 8], v[r1 + 12]);
+  // now v[r1 + 4 k1] = A[r1][k1]; twiddle by w16^(r1 k1)
+  v[5] = cmul(v[5], w16<T, INV>(1));
+  v[9] = cmul(v[9], w16<T, INV>(2));
+  v[13] = cmul(v[13], w16<T, INV>(3));
+  v[6] = cmul(v[6], w16<T, INV>(2));
+  v[10] = mul_mi<T, INV>(v[10]);
+  v[14] = cmul(v[14], w16<T, INV>(6));
+  v[7] = cmul(v[7], w16<T, INV>(3));
+  v[11] = cmul(v[11], w16<T, INV>(6));
+  v[15] = cmul(v[15], w16<T, INV>(9));
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<T, INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+  // v[4 k1 + k2] = X[k1 + 4 k2]: transpose into natural order
+  cpx<T> t[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = t[i];
+}
+
+template <int R, typename T, bool INV> __device__ __forceinline__ void dft(cpx<T>* v) {
+  if constexpr (R == 2) dft2<T, INV>(v[0], v[1]);
+  else if constexpr (R == 3) dft3<T, INV>(v[0], v[1], v[2]);
+  else if constexpr (R == 4) dft4<T, INV>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 8) dft8<T, INV>(v);
+  else if constexpr (R == 16) dft16<T, INV>(v);
+  else static_assert(R == 2, "unsupported radix");
+}
+
+// ----------------------------------------------------------------------------------
+// Stages
+// ----------------------------------------------------------------------------------
+// twiddle table tw[k] = exp(-2 pi i k / L), k < L (built in FP64, stored in T)
+template <typename T, int L, int R, int NSV, bool INV>
+__device__ __forceinline__ void stage_compute(cpx<T> (&v)[Plan<L>::E], int tid, const cpx<T>* __restrict__ tw) {
+  constexpr int E = Plan<L>::E;
+  constexpr int TT = L / E;
+#pragma unroll
+  for (int b = 0; b < E / R; ++b) {
+    if constexpr (NSV > 1) {
+      const int j = tid + b * TT;
+      const int step = (j % NSV) * (L / (NSV * R));
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const cpx<T> w = ld_cpx(tw + r * step);
+        v[b * R + r] = INV ? cmulc(v[b * R + r], w) : cmul(v[b * R + r], w);
+      }
+    }
+    dft<R, T, INV>(&v[b * R]);
+  }
+}
+
+template <typename T, int L, int R, int NSV, int R2>
+__device__ __forceinline__ void stage_exchange(cpx<T> (&v)[Plan<L>::E], cpx<T>* sm, int tid) {
+  constexpr int E = Plan<L>::E;
+  constexpr int TT = L / E;
+#pragma unroll
+  for (int b = 0; b < E / R; ++b) {
+    const int j = tid + b * TT;
+    const int base = (j / NSV) * NSV * R + (j % NSV);
+#pragma unroll
+    for (int r = 0; r < R; ++r) sm[spad(base + r * NSV)] = v[b * R + r];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < E / R2; ++b) {
+    const int j = tid + b * TT;
+#pragma unroll
+    for (int r = 0; r < R2; ++r) v[b * R2 + r] = sm[spad(j + r * (L / R2))];
+  }
+  __syncthreads();
+}
+
+template <typename T, int L, bool INV, bool REV, int S>
+__device__ __forceinline__ void fft_stages(cpx<T> (&v)[Plan<L>::E], cpx<T>* sm, int tid, const cpx<T>* __restrict__ tw) {
+  constexpr int R = radix_of<L, REV>(S);
+  constexpr int NSV = ns_of<L, REV>(S);
+  stage_compute<T, L, R, NSV, INV>(v, tid, tw);
+  if constexpr (S + 1 < Plan<L>::NS) {
+    stage_exchange<T, L, R, NSV, radix_of<L, REV>(S + 1)>(v, sm, tid);
+    fft_stages<T, L, INV, REV, S + 1>(v, sm, tid, tw);
+  }
+}
+
+// Full FFT of one length-L sequence by L/E threads.  On entry v holds the inputs in
+// the first-stage layout, on exit the outputs in the last-stage layout (see top).
+// sm: this FFT's shared buffer of smem_elems<L>() values.  Unnormalised both ways.
+template <typename T, int L, bool INV, bool REV>
+__device__ __forceinline__ void fft(cpx<T> (&v)[Plan<L>::E], cpx<T>* sm, int tid, const cpx<T>* __restrict__ tw) {
+  fft_stages<T, L, INV, REV, 0>(v, sm, tid, tw);
+}
+
+}  // namespace bsct

@@ -1,0 +1,49 @@
+// Internal (C++) interfaces between the libbsct translation units.
+#pragma once
+#include <atomic>
+#include <cuda_runtime.h>
+
+#include "bsct_common.cuh"
+
+namespace bsct {
+
+// Launch counter (exported through bsct_launch_count).
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch(int n = 1) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+// FFT convolution kernels for one image size N (row FFT length N, column length 2N).
+//   S:   N x N complex scratch (row-block interleaved half spectra)
+//   Gt:  spectrum, [N+1][2N] real, scaled by 1/(2N)^2 (row 0 = (G0+GN)/2, row N = (G0-GN)/2)
+//   twr: exp(-2 pi i k / N), k < N;  twc: exp(-2 pi i k / 2N), k < 2N
+template <typename T> struct FftOps {
+  int (*apply)(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* twr, const cpx<T>* twc,
+               cudaStream_t st);
+  // emb: 2N x 2N real circulant kernel; S2: 2N x N complex scratch; writes Gt (scaled)
+  int (*spectrum)(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* twr, const cpx<T>* twc,
+                  cudaStream_t st);
+};
+template <typename T, int N> FftOps<T> fft_ops();
+template <typename T> bool fft_ops_for(int N, FftOps<T>* out);
+
+// twiddle table exp(-2 pi i k / L), k < L
+template <typename T> int build_twiddles(cpx<T>* d_tw, int L, cudaStream_t st);
+
+}  // namespace bsct
+
+// Library-owned state of one geometry (see bsct_gram_build).
+struct bsct_gram {
+  int N = 0, precision = 0, n_angles = 0;
+  double zeta = 0.0, lambda = 1.0;
+  double* taps = nullptr;    // (2N-1)^2 FP64 taps
+  double* Gt64 = nullptr;    // scaled spectrum [N+1][2N], FP64
+  float* Gt32 = nullptr;     // same, FP32 (precision F32 only)
+  void* twr = nullptr;       // row twiddles (T)
+  void* twc = nullptr;       // column twiddles (T)
+  void* S = nullptr;         // apply scratch, N x N complex T
+  void* r = nullptr;         // CG vectors (T, N*N each)
+  void* p = nullptr;
+  void* q = nullptr;
+  double* scal = nullptr;    // CG scalars
+  double* partials = nullptr;
+  int n_partials = 0;
+};

@@ -1,0 +1,254 @@
+// Conjugate gradients on the normal equations G x = b (Sec. 2) with the Gram filter
+// applied by FFT convolution (Sec. 4).  Vectors in the handle's precision T; inner
+// products reduced in FP64 and the step scalars alpha, beta kept in FP64 in device
+// memory, so an iteration never waits for the host:
+//
+//   q = G p                              (gram apply, 3 kernels)
+//   pq = <p, q>;  alpha = rr / pq        (k_dot partials + k_finish)
+//   x += alpha p;  r -= alpha q;  <r, r> (k_xr_update partials + k_finish)
+//   beta = rr_new / rr;  rr = rr_new
+//   p = r + beta p                       (k_p_update)
+#include "bsct_internal.h"
+
+namespace bsct {
+
+enum { SC_RR = 0, SC_PQ = 1, SC_ALPHA = 2, SC_BETA = 3, SC_BB = 4, SC_TMP = 5 };
+enum { OP_STORE_RR = 0, OP_STORE_BB = 1, OP_ALPHA = 2, OP_BETA = 3, OP_STORE_TMP = 4 };
+
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double ws[RED_THREADS / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < RED_THREADS / 32 ? ws[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_dot(const T* __restrict__ a, const T* __restrict__ b, long n,
+                                                     double* __restrict__ part) {
+  double acc = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    acc += (double)a[i] * (double)b[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// ||a - b||^2
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_diff2(const T* __restrict__ a, const T* __restrict__ b, long n,
+                                                       double* __restrict__ part) {
+  double acc = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double d = (double)a[i] - (double)b[i];
+    acc += d * d;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_finish(const double* __restrict__ part, int np, double* __restrict__ sc,
+                                                        int op) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) acc += part[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) {
+    switch (op) {
+      case OP_STORE_RR: sc[SC_RR] = acc; break;
+      case OP_STORE_BB: sc[SC_BB] = acc; break;
+      case OP_ALPHA: sc[SC_PQ] = acc; sc[SC_ALPHA] = sc[SC_RR] / acc; break;
+      case OP_BETA: sc[SC_BETA] = acc / sc[SC_RR]; sc[SC_RR] = acc; break;
+      case OP_STORE_TMP: sc[SC_TMP] = acc; break;
+    }
+  }
+}
+
+// x += alpha p; r -= alpha q; partial <r, r>
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_xr_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                                           const T* __restrict__ q, const double* __restrict__ sc, long n,
+                                                           double* __restrict__ part) {
+  const T alpha = T(sc[SC_ALPHA]);
+  double acc = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const T ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    acc += (double)ri * (double)ri;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+template <typename T>
+__global__ void k_p_update(T* __restrict__ p, const T* __restrict__ r, const double* __restrict__ sc, long n) {
+  const T beta = T(sc[SC_BETA]);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], r[i]);
+}
+
+// r = b - q (q = G x0), p = r
+template <typename T>
+__global__ void k_init_r(const T* __restrict__ b, const T* __restrict__ q, T* __restrict__ r, T* __restrict__ p, long n,
+                         int has_x0) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const T v = has_x0 ? b[i] - q[i] : b[i];
+    r[i] = v;
+    p[i] = v;
+  }
+}
+
+template <typename T> __global__ void k_zero(T* __restrict__ x, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) x[i] = T(0);
+}
+
+}  // namespace bsct
+
+using namespace bsct;
+
+static int nblk(const bsct_gram* g, long n) {
+  long b = (n + RED_THREADS * 8 - 1) / (RED_THREADS * 8);
+  if (b < 1) b = 1;
+  if (b > g->n_partials) b = g->n_partials;
+  return (int)b;
+}
+
+static int apply_g(const bsct_gram* g, const void* x, void* y, cudaStream_t st) {
+  return bsct_gram_apply(g, x, y, g->precision == BSCT_F32 ? BSCT_APPLY_FFT32 : BSCT_APPLY_F64, st);
+}
+
+template <typename T>
+static int cg_begin_t(bsct_gram* g, const T* b, T* x, int x0_is_zero, cudaStream_t st) {
+  const long n = (long)g->N * g->N;
+  const int nb = nblk(g, n);
+  T* r = (T*)g->r;
+  T* p = (T*)g->p;
+  T* q = (T*)g->q;
+  if (x0_is_zero) {
+    k_zero<T><<<nb, RED_THREADS, 0, st>>>(x, n);
+    count_launch();
+  } else {
+    int rc = apply_g(g, x, q, st);
+    if (rc != BSCT_OK) return rc;
+  }
+  k_init_r<T><<<nb, RED_THREADS, 0, st>>>(b, q, r, p, n, x0_is_zero ? 0 : 1);
+  k_dot<T><<<nb, RED_THREADS, 0, st>>>(r, r, n, g->partials);
+  k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_STORE_RR);
+  k_dot<T><<<nb, RED_THREADS, 0, st>>>(b, b, n, g->partials);
+  k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_STORE_BB);
+  count_launch(5);
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+template <typename T>
+static int cg_iter_t(bsct_gram* g, T* x, int n_iter, cudaStream_t st) {
+  const long n = (long)g->N * g->N;
+  const int nb = nblk(g, n);
+  T* r = (T*)g->r;
+  T* p = (T*)g->p;
+  T* q = (T*)g->q;
+  for (int it = 0; it < n_iter; ++it) {
+    int rc = apply_g(g, p, q, st);
+    if (rc != BSCT_OK) return rc;
+    k_dot<T><<<nb, RED_THREADS, 0, st>>>(p, q, n, g->partials);
+    k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_ALPHA);
+    k_xr_update<T><<<nb, RED_THREADS, 0, st>>>(x, r, p, q, g->scal, n, g->partials);
+    k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_BETA);
+    k_p_update<T><<<nb, RED_THREADS, 0, st>>>(p, r, g->scal, n);
+    count_launch(5);
+  }
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+extern "C" int bsct_cg_begin(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero, void* stream) {
+  if (!g || !d_b || !d_x) { bsct_set_last_message("NULL argument"); return BSCT_ERR_INVALID_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (g->precision == BSCT_F32) return cg_begin_t<float>(g, (const float*)d_b, (float*)d_x, x0_is_zero, st);
+  return cg_begin_t<double>(g, (const double*)d_b, (double*)d_x, x0_is_zero, st);
+}
+
+extern "C" int bsct_cg_iterate(bsct_gram* g, void* d_x, int n_iter, void* stream) {
+  if (!g || !d_x || n_iter < 0) { bsct_set_last_message("invalid argument"); return BSCT_ERR_INVALID_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (g->precision == BSCT_F32) return cg_iter_t<float>(g, (float*)d_x, n_iter, st);
+  return cg_iter_t<double>(g, (double*)d_x, n_iter, st);
+}
+
+extern "C" int bsct_cg_residual(const bsct_gram* g, double* rr, double* bb, void* stream) {
+  if (!g) { bsct_set_last_message("NULL handle"); return BSCT_ERR_INVALID_ARG; }
+  double h[16];
+  cudaStream_t st = (cudaStream_t)stream;
+  BSCT_CUDA_TRY(cudaMemcpyAsync(h, g->scal, sizeof(h), cudaMemcpyDeviceToHost, st));
+  BSCT_CUDA_TRY(cudaStreamSynchronize(st));
+  if (rr) *rr = h[SC_RR];
+  if (bb) *bb = h[SC_BB];
+  return BSCT_OK;
+}
+
+template <typename T>
+static int true_residual_t(bsct_gram* g, const T* b, const T* x, double* out, cudaStream_t st) {
+  const long n = (long)g->N * g->N;
+  const int nb = nblk(g, n);
+  int rc = apply_g(g, x, g->q, st);
+  if (rc != BSCT_OK) return rc;
+  k_diff2<T><<<nb, RED_THREADS, 0, st>>>(b, (const T*)g->q, n, g->partials);
+  k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_STORE_TMP);
+  count_launch(2);
+  BSCT_CUDA_TRY(cudaGetLastError());
+  double h[16];
+  BSCT_CUDA_TRY(cudaMemcpyAsync(h, g->scal, sizeof(h), cudaMemcpyDeviceToHost, st));
+  BSCT_CUDA_TRY(cudaStreamSynchronize(st));
+  *out = (h[SC_BB] > 0.0) ? sqrt(h[SC_TMP] / h[SC_BB]) : 0.0;
+  return BSCT_OK;
+}
+
+extern "C" int bsct_cg_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero, int max_iter, double rel_tol,
+                             int check_every, bsct_cg_report* report, void* stream) {
+  if (!g || !d_b || !d_x || max_iter < 0) { bsct_set_last_message("invalid argument"); return BSCT_ERR_INVALID_ARG; }
+  if (check_every < 1) check_every = 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = bsct_cg_begin(g, d_b, d_x, x0_is_zero, stream);
+  if (rc != BSCT_OK) return rc;
+  double rr = 0.0, bb = 0.0;
+  int it = 0, converged = 0;
+  if (rel_tol > 0.0) {
+    rc = bsct_cg_residual(g, &rr, &bb, stream);
+    if (rc != BSCT_OK) return rc;
+    if (bb == 0.0 || sqrt(rr / bb) <= rel_tol) converged = 1;
+  }
+  while (!converged && it < max_iter) {
+    const int k = (rel_tol > 0.0) ? (check_every < max_iter - it ? check_every : max_iter - it) : max_iter - it;
+    rc = bsct_cg_iterate(g, d_x, k, stream);
+    if (rc != BSCT_OK) return rc;
+    it += k;
+    if (rel_tol > 0.0) {
+      rc = bsct_cg_residual(g, &rr, &bb, stream);
+      if (rc != BSCT_OK) return rc;
+      if (!isfinite(rr)) { bsct_set_last_message("CG residual is not finite"); return BSCT_ERR_NONFINITE; }
+      if (sqrt(rr / bb) <= rel_tol) converged = 1;
+    }
+  }
+  rc = bsct_cg_residual(g, &rr, &bb, stream);
+  if (rc != BSCT_OK) return rc;
+  double tr = -1.0;
+  if (rel_tol > 0.0) {
+    rc = (g->precision == BSCT_F32) ? true_residual_t<float>(g, (const float*)d_b, (const float*)d_x, &tr, st)
+                                    : true_residual_t<double>(g, (const double*)d_b, (const double*)d_x, &tr, st);
+    if (rc != BSCT_OK) return rc;
+  }
+  if (report) {
+    report->iterations = it;
+    report->converged = converged;
+    report->rel_residual = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    report->true_rel_residual = tr;
+  }
+  return (rel_tol > 0.0 && !converged) ? BSCT_WARN_NOT_CONVERGED : BSCT_OK;
+}

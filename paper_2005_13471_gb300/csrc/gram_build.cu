@@ -1,0 +1,393 @@
+// Gram filter build (Sec. 4) and the FFT-based Gram apply entry points.
+//
+//   k_geometry   : views reduced to half turns in [0, 1) (theta and theta + pi give the
+//                  same Gram kernel), cos/sin by cospi/sinpi (exact zeros on the axes),
+//                  sorted by angle with a rank count so every tap can find its views by
+//                  binary search.
+//   k_gram_taps  : one thread per tap d of the upper half plane:
+//                    G[d] = sum_theta M_[c, c, s, s, zeta, zeta](d . u_theta)
+//                  Only views with |d . u| < |c| + |s| + zeta contribute; for |d| larger
+//                  than the widest support those views form one arc of angles around the
+//                  normal of d, found by binary search.  FP64, mirrored to G[-d].
+//   k_embed      : taps -> 2N x 2N circulant kernel (tap d at d mod 2N).
+//   spectrum     : 2-D FFT of the circulant kernel in FP64 (same FFT kernels as the
+//                  apply), real part kept.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "bsct_boxspline.cuh"
+#include "bsct_internal.h"
+
+namespace bsct {
+
+std::atomic<unsigned long long> g_launches{0};
+
+// ------------------------------------------------------------------------------------
+// FFT dispatch over the supported sizes
+// ------------------------------------------------------------------------------------
+#define BSCT_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(384) X(512) X(768) X(1024) X(2048)
+
+template <typename T> bool fft_ops_for(int N, FftOps<T>* out) {
+  switch (N) {
+#define BSCT_CASE(N_) case N_: *out = fft_ops<T, N_>(); return true;
+    BSCT_SIZES(BSCT_CASE)
+#undef BSCT_CASE
+    default: return false;
+  }
+}
+template bool fft_ops_for<float>(int, FftOps<float>*);
+template bool fft_ops_for<double>(int, FftOps<double>*);
+
+// ------------------------------------------------------------------------------------
+// twiddles
+// ------------------------------------------------------------------------------------
+template <typename T> __global__ void k_twiddles(cpx<T>* tw, int L) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= L) return;
+  double s, c;
+  sincospi(-2.0 * (double)k / (double)L, &s, &c);
+  tw[k] = mk(T(c), T(s));
+}
+template <typename T> int build_twiddles(cpx<T>* d_tw, int L, cudaStream_t st) {
+  k_twiddles<T><<<(L + 255) / 256, 256, 0, st>>>(d_tw, L);
+  count_launch();
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+template int build_twiddles<float>(cpx<float>*, int, cudaStream_t);
+template int build_twiddles<double>(cpx<double>*, int, cudaStream_t);
+
+// ------------------------------------------------------------------------------------
+// geometry (views sorted by angle in half turns, [0, 1))
+// ------------------------------------------------------------------------------------
+__global__ void k_geometry(const double* __restrict__ ang, int na, double* __restrict__ th_sorted,
+                           double2* __restrict__ cs_sorted) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= na) return;
+  double a = ang[i];
+  a = a - floor(a);
+  if (a >= 1.0) a = 0.0;
+  int rank = 0;
+  for (int j = 0; j < na; ++j) {
+    double b = ang[j];
+    b = b - floor(b);
+    if (b >= 1.0) b = 0.0;
+    rank += (b < a) || (b == a && j < i);
+  }
+  double s, c;
+  sincospi(a, &s, &c);
+  th_sorted[rank] = a;
+  cs_sorted[rank] = make_double2(c, s);
+}
+
+// the per-view Gram kernel A(t) = M_[c,c,s,s,zeta,zeta](t)
+__device__ __forceinline__ double gram_kernel(double t, double a, double b, double zeta) {
+  BoxDirs D;
+  D.ng = 0;
+  if (a > 0.0) { D.a[D.ng] = a; D.m[D.ng] = 2; ++D.ng; }
+  if (b > 0.0) { D.a[D.ng] = b; D.m[D.ng] = 2; ++D.ng; }
+  if (zeta > 0.0) { D.a[D.ng] = zeta; D.m[D.ng] = 2; ++D.ng; }
+  for (int g = D.ng; g < 4; ++g) { D.a[g] = 0.0; D.m[g] = 0; }
+  int small = -1;
+  if (a > 0.0 && b > 0.0) {
+    if (b < BSCT_SHORT_DIR * a) small = 1;
+    else if (a < BSCT_SHORT_DIR * b) small = 0;
+  }
+  return box_eval(t, D, small);
+}
+
+__device__ __forceinline__ int lower_bound_d(const double* __restrict__ v, int n, double x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (v[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_gram_taps(int N, int na, const double* __restrict__ th, const double2* __restrict__ cs,
+                            double zeta, double* __restrict__ G) {
+  const long H = (long)(2 * N - 1) * (N - 1) + N;
+  const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= H) return;
+  int d1, d2;
+  if (h < N) { d2 = 0; d1 = (int)h; }
+  else {
+    const long q = h - N;
+    d2 = 1 + (int)(q / (2 * N - 1));
+    d1 = (int)(q % (2 * N - 1)) - (N - 1);
+  }
+  const double wmax = 1.4142135623730951 + zeta;  // >= |c| + |s| + zeta for every view
+  const double r = hypot((double)d1, (double)d2);
+  double acc = 0.0;
+  auto visit = [&](int j0, int j1) {
+    for (int j = j0; j < j1; ++j) {
+      const double2 u = cs[j];
+      const double t = d1 * u.x + d2 * u.y;
+      const double a = fabs(u.x), b = fabs(u.y);
+      if (fabs(t) < a + b + zeta) acc += gram_kernel(t, a, b, zeta);
+    }
+  };
+  const double hw = (r > wmax) ? asin(wmax / r) * 0.31830988618379067154 + 1e-12 : 1.0;
+  if (hw >= 0.5) {
+    visit(0, na);
+  } else {
+    const double phi = atan2((double)d2, (double)d1) * 0.31830988618379067154;  // / pi, in [0, 1]
+    double centre = phi + 0.5;
+    if (centre >= 1.0) centre -= 1.0;
+    const double lo = centre - hw, hi = centre + hw;
+    if (lo < 0.0) {
+      visit(lower_bound_d(th, na, lo + 1.0), na);
+      visit(0, lower_bound_d(th, na, hi));
+    } else if (hi > 1.0) {
+      visit(lower_bound_d(th, na, lo), na);
+      visit(0, lower_bound_d(th, na, hi - 1.0));
+    } else {
+      visit(lower_bound_d(th, na, lo), lower_bound_d(th, na, hi));
+    }
+  }
+  const int W = 2 * N - 1;
+  G[(long)(d2 + N - 1) * W + (d1 + N - 1)] = acc;
+  G[(long)(-d2 + N - 1) * W + (-d1 + N - 1)] = acc;
+}
+
+__global__ void k_embed(const double* __restrict__ G, int N, double* __restrict__ E) {
+  const int L = 2 * N;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)L * L) return;
+  const int a = (int)(i / L), b = (int)(i % L);
+  double v = 0.0;
+  if (a != N && b != N) {
+    const int d2 = a < N ? a : a - L;
+    const int d1 = b < N ? b : b - L;
+    v = G[(long)(d2 + N - 1) * (2 * N - 1) + (d1 + N - 1)];
+  }
+  E[i] = v;
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, long n) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// [N+1][2N] scaled packed spectrum -> [2N][N+1] plain spectrum
+__global__ void k_unpack_spectrum(const double* __restrict__ Gt, int N, double* __restrict__ out) {
+  const int L = 2 * N;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)L * (N + 1)) return;
+  const int u = (int)(i / (N + 1)), v = (int)(i % (N + 1));
+  const double sc = (double)L * (double)L;
+  double g;
+  if (v == 0) g = Gt[u] + Gt[(long)N * L + u];
+  else if (v == N) g = Gt[u] - Gt[(long)N * L + u];
+  else g = Gt[(long)v * L + u];
+  out[i] = g * sc;
+}
+
+}  // namespace bsct
+
+using namespace bsct;
+
+// ------------------------------------------------------------------------------------
+// error reporting
+// ------------------------------------------------------------------------------------
+static thread_local char g_msg[512] = "no error";
+void bsct_set_last_cuda_error(cudaError_t e) {
+  snprintf(g_msg, sizeof(g_msg), "CUDA error %d: %s", (int)e, cudaGetErrorString(e));
+}
+void bsct_set_last_message(const char* msg) { snprintf(g_msg, sizeof(g_msg), "%s", msg); }
+
+extern "C" const char* bsct_last_error_string(void) { return g_msg; }
+
+extern "C" const char* bsct_status_string(int s) {
+  switch (s) {
+    case BSCT_OK: return "ok";
+    case BSCT_ERR_INVALID_ARG: return "invalid argument";
+    case BSCT_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+    case BSCT_ERR_CUDA: return "CUDA error";
+    case BSCT_ERR_TIMEOUT: return "device wait timed out";
+    case BSCT_ERR_NONFINITE: return "non-finite value";
+    case BSCT_WARN_NOT_CONVERGED: return "not converged";
+    default: return "unknown status";
+  }
+}
+
+extern "C" uint64_t bsct_launch_count(void) { return (uint64_t)g_launches.load(); }
+
+extern "C" int bsct_supported_size(int32_t N) {
+  FftOps<float> o;
+  return fft_ops_for<float>(N, &o) ? 1 : 0;
+}
+
+static int fail(int code, const char* msg) {
+  bsct_set_last_message(msg);
+  return code;
+}
+
+int bsct_check_geom(const bsct_geom* g) {
+  if (!g) return fail(BSCT_ERR_INVALID_ARG, "geom is NULL");
+  if (!g->angles_pi) return fail(BSCT_ERR_INVALID_ARG, "angles_pi is NULL");
+  if (g->n_angles < 1) return fail(BSCT_ERR_INVALID_ARG, "n_angles < 1");
+  if (g->n_bins < 1) return fail(BSCT_ERR_INVALID_ARG, "n_bins < 1");
+  if (!(g->lambda_y > 0.0) || !isfinite(g->lambda_y)) return fail(BSCT_ERR_INVALID_ARG, "lambda_y must be > 0");
+  if (!(g->zeta_blur >= 0.0) || !isfinite(g->zeta_blur)) return fail(BSCT_ERR_INVALID_ARG, "zeta_blur must be >= 0");
+  if (g->zeta_blur > 0.0 && g->zeta_blur < BSCT_SHORT_DIR)
+    return fail(BSCT_ERR_INVALID_ARG, "0 < zeta_blur < 0.2 is not supported (short blur direction)");
+  for (int i = 0; i < g->n_angles; ++i)
+    if (!isfinite(g->angles_pi[i])) return fail(BSCT_ERR_INVALID_ARG, "angles_pi holds a non-finite value");
+  return BSCT_OK;
+}
+
+extern "C" void bsct_gram_free(bsct_gram* g) {
+  if (!g) return;
+  cudaDeviceSynchronize();
+  cudaFree(g->taps);
+  cudaFree(g->Gt64);
+  cudaFree(g->Gt32);
+  cudaFree(g->twr);
+  cudaFree(g->twc);
+  cudaFree(g->S);
+  cudaFree(g->r);
+  cudaFree(g->p);
+  cudaFree(g->q);
+  cudaFree(g->scal);
+  cudaFree(g->partials);
+  delete g;
+}
+
+#define TRY(expr)                                  \
+  do {                                             \
+    int _rc = (expr);                              \
+    if (_rc != BSCT_OK) { cleanup(); return _rc; } \
+  } while (0)
+#define CTRY(expr)                                                             \
+  do {                                                                         \
+    cudaError_t _e = (expr);                                                   \
+    if (_e != cudaSuccess) { bsct_set_last_cuda_error(_e); cleanup(); return BSCT_ERR_CUDA; } \
+  } while (0)
+
+extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram** out, void* stream) {
+  int rc = bsct_check_geom(geom);
+  if (rc != BSCT_OK) return rc;
+  if (!out) return fail(BSCT_ERR_INVALID_ARG, "out is NULL");
+  if (precision != BSCT_F32 && precision != BSCT_F64) return fail(BSCT_ERR_INVALID_ARG, "precision");
+  const int N = geom->N;
+  FftOps<double> o64;
+  FftOps<float> o32;
+  if (!fft_ops_for<double>(N, &o64) || !fft_ops_for<float>(N, &o32))
+    return fail(BSCT_ERR_UNSUPPORTED_SIZE, "unsupported N (see bsct_supported_size)");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int na = geom->n_angles;
+  const int L = 2 * N;
+  const long ntap = (long)(2 * N - 1) * (2 * N - 1);
+
+  bsct_gram* g = new bsct_gram();
+  g->N = N;
+  g->precision = precision;
+  g->n_angles = na;
+  g->zeta = geom->zeta_blur;
+  g->lambda = geom->lambda_y;
+  double *d_ang = nullptr, *d_th = nullptr, *d_emb = nullptr;
+  double2* d_cs = nullptr;
+  void* d_S2 = nullptr;
+  cpx<double>*twr64 = nullptr, *twc64 = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(d_ang); cudaFree(d_th); cudaFree(d_cs); cudaFree(d_emb); cudaFree(d_S2);
+    cudaFree(twr64); cudaFree(twc64);
+    if (g) { bsct_gram_free(g); g = nullptr; }
+  };
+  const size_t T = precision == BSCT_F32 ? sizeof(float) : sizeof(double);
+  CTRY(cudaMalloc(&d_ang, na * sizeof(double)));
+  CTRY(cudaMalloc(&d_th, na * sizeof(double)));
+  CTRY(cudaMalloc(&d_cs, na * sizeof(double2)));
+  CTRY(cudaMalloc(&g->taps, ntap * sizeof(double)));
+  CTRY(cudaMalloc(&d_emb, (size_t)L * L * sizeof(double)));
+  CTRY(cudaMalloc(&d_S2, (size_t)L * N * 2 * sizeof(double)));
+  CTRY(cudaMalloc(&g->Gt64, (size_t)(N + 1) * L * sizeof(double)));
+  CTRY(cudaMalloc(&twr64, (size_t)N * sizeof(cpx<double>)));
+  CTRY(cudaMalloc(&twc64, (size_t)L * sizeof(cpx<double>)));
+  CTRY(cudaMemcpyAsync(d_ang, geom->angles_pi, na * sizeof(double), cudaMemcpyHostToDevice, st));
+
+  k_geometry<<<(na + 127) / 128, 128, 0, st>>>(d_ang, na, d_th, d_cs);
+  const long H = (long)(2 * N - 1) * (N - 1) + N;
+  k_gram_taps<<<(unsigned)((H + 127) / 128), 128, 0, st>>>(N, na, d_th, d_cs, geom->zeta_blur, g->taps);
+  k_embed<<<(unsigned)(((long)L * L + 255) / 256), 256, 0, st>>>(g->taps, N, d_emb);
+  count_launch(3);
+  CTRY(cudaGetLastError());
+  TRY(build_twiddles<double>(twr64, N, st));
+  TRY(build_twiddles<double>(twc64, L, st));
+  TRY(o64.spectrum(d_emb, (cpx<double>*)d_S2, g->Gt64, twr64, twc64, st));
+
+  // per-precision apply state
+  CTRY(cudaMalloc(&g->S, (size_t)N * N * 2 * T));
+  CTRY(cudaMalloc(&g->r, (size_t)N * N * T));
+  CTRY(cudaMalloc(&g->p, (size_t)N * N * T));
+  CTRY(cudaMalloc(&g->q, (size_t)N * N * T));
+  g->n_partials = 1024;
+  CTRY(cudaMalloc(&g->partials, (size_t)g->n_partials * sizeof(double) * 2));
+  CTRY(cudaMalloc(&g->scal, 16 * sizeof(double)));
+  CTRY(cudaMemsetAsync(g->scal, 0, 16 * sizeof(double), st));
+  if (precision == BSCT_F32) {
+    const long ng = (long)(N + 1) * L;
+    CTRY(cudaMalloc(&g->Gt32, ng * sizeof(float)));
+    k_to_f32<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(g->Gt64, g->Gt32, ng);
+    count_launch();
+    CTRY(cudaMalloc(&g->twr, (size_t)N * sizeof(cpx<float>)));
+    CTRY(cudaMalloc(&g->twc, (size_t)L * sizeof(cpx<float>)));
+    TRY(build_twiddles<float>((cpx<float>*)g->twr, N, st));
+    TRY(build_twiddles<float>((cpx<float>*)g->twc, L, st));
+  } else {
+    g->twr = twr64;
+    g->twc = twc64;
+    twr64 = twc64 = nullptr;
+  }
+  CTRY(cudaGetLastError());
+  CTRY(cudaStreamSynchronize(st));
+  cudaFree(d_ang); cudaFree(d_th); cudaFree(d_cs); cudaFree(d_emb); cudaFree(d_S2);
+  cudaFree(twr64); cudaFree(twc64);
+  *out = g;
+  return BSCT_OK;
+}
+#undef TRY
+#undef CTRY
+
+extern "C" int bsct_gram_taps(const bsct_gram* g, double* d_out, void* stream) {
+  if (!g || !d_out) return fail(BSCT_ERR_INVALID_ARG, "NULL argument");
+  const long ntap = (long)(2 * g->N - 1) * (2 * g->N - 1);
+  BSCT_CUDA_TRY(cudaMemcpyAsync(d_out, g->taps, ntap * sizeof(double), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return BSCT_OK;
+}
+
+extern "C" int bsct_gram_spectrum(const bsct_gram* g, double* d_out, void* stream) {
+  if (!g || !d_out) return fail(BSCT_ERR_INVALID_ARG, "NULL argument");
+  const long n = (long)2 * g->N * (g->N + 1);
+  k_unpack_spectrum<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(g->Gt64, g->N, d_out);
+  count_launch();
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+extern "C" int bsct_gram_apply(const bsct_gram* g, const void* d_x, void* d_y, int mode, void* stream) {
+  if (!g || !d_x || !d_y) return fail(BSCT_ERR_INVALID_ARG, "NULL argument");
+  if (d_x == d_y) return fail(BSCT_ERR_INVALID_ARG, "x and y may not alias");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (mode == BSCT_APPLY_FFT32) {
+    if (g->precision != BSCT_F32) return fail(BSCT_ERR_INVALID_ARG, "FFT32 apply needs an F32 handle");
+    FftOps<float> o;
+    fft_ops_for<float>(g->N, &o);
+    return o.apply((const float*)d_x, (float*)d_y, (cpx<float>*)g->S, g->Gt32, (const cpx<float>*)g->twr,
+                   (const cpx<float>*)g->twc, st);
+  }
+  if (mode == BSCT_APPLY_F64) {
+    if (g->precision != BSCT_F64) return fail(BSCT_ERR_INVALID_ARG, "F64 apply needs an F64 handle");
+    FftOps<double> o;
+    fft_ops_for<double>(g->N, &o);
+    return o.apply((const double*)d_x, (double*)d_y, (cpx<double>*)g->S, g->Gt64, (const cpx<double>*)g->twr,
+                   (const cpx<double>*)g->twc, st);
+  }
+  return fail(BSCT_ERR_INVALID_ARG, "unknown apply mode");
+}

@@ -1,0 +1,362 @@
+// Gram apply as a zero-padded 2N x 2N FFT convolution (Sec. 4: G is Toeplitz-block-
+// Toeplitz, so G x is a linear convolution with the (2N-1)^2 filter, computed exactly by
+// a circular convolution on the doubled grid).  Compiled once per image size with
+// -DBSCT_FFT_N=<N>.
+//
+// Three HBM passes per apply:
+//   K5 rows_r2c   : each image row (N reals, zero-padded to 2N) -> N packed complex
+//                   half-spectrum values (Nyquist real part stored in the imaginary
+//                   slot of the DC bin), via one N-point complex FFT of the even/odd
+//                   interleaved row.
+//   K6 cols_conv  : each of the N packed columns: 2N-point FFT of the N non-zero rows,
+//                   times the real spectrum of G, inverse 2N-point FFT, keep N rows.
+//                   Column 0 carries the (DC, Nyquist) pair and is separated and
+//                   recombined with the two spectrum columns in the frequency domain.
+//   K7 rows_c2r   : inverse of K5, keeping the first N outputs of each row.
+// The half spectra live in a row-block interleaved layout, element (row, v) at
+// ((row/4) * N + v) * 4 + row%4, so K5/K7 stream whole 4-row blocks and K6 reads
+// 32-byte row segments per column.
+#include "bsct_fft.cuh"
+#include "bsct_internal.h"
+
+#ifndef BSCT_FFT_N
+#error "compile with -DBSCT_FFT_N=<N>"
+#endif
+
+namespace bsct {
+
+__host__ __device__ constexpr int threads_per_fft(int L, int E) { return L / E; }
+
+// rows handled per CTA: at least 4 (one row block) and at least ~128 threads
+template <int LR> __host__ __device__ constexpr int rows_per_cta() {
+  return (LR / Plan<LR>::E) >= 32 ? 4 : ((128 / (LR / Plan<LR>::E)) > LR ? LR : (128 / (LR / Plan<LR>::E)));
+}
+// columns per CTA
+template <typename T, int LC> __host__ __device__ constexpr int cols_per_cta() {
+  return (LC / Plan<LC>::E) >= 256 ? (sizeof(T) == 4 ? 2 : 1)
+                                   : ((256 / (LC / Plan<LC>::E)) > 8 ? 8 : (256 / (LC / Plan<LC>::E)));
+}
+
+__device__ __forceinline__ long blk_index(int row, int col, int ncols) {
+  return ((long)(row >> 2) * ncols + col) * 4 + (row & 3);
+}
+
+// ------------------------------------------------------------------------------------
+// K5: real rows -> packed half spectra.  PADDED: the row holds LR reals (zero-padded to
+// 2 LR); otherwise it holds 2 LR reals.  Row r of x starts at x + r * ld_x.
+// ------------------------------------------------------------------------------------
+template <typename T, int LR, bool PADDED, int RPC>
+__global__ void __launch_bounds__(RPC * (LR / Plan<LR>::E))
+k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
+           const cpx<T>* __restrict__ twr, const cpx<T>* __restrict__ twc) {
+  constexpr int E = Plan<LR>::E, TT = LR / E, R1 = Plan<LR>::R[0], RL = Plan<LR>::R[Plan<LR>::NS - 1];
+  constexpr int SME = smem_elems<LR>();
+  static_assert(R1 % 2 == 0, "zero-padding / crop split needs an even first radix");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* sm_all = reinterpret_cast<cpx<T>*>(smraw);
+  const int f = threadIdx.x / TT, tid = threadIdx.x % TT;
+  const int row0 = blockIdx.x * RPC;
+  cpx<T>* sm = sm_all + f * SME;
+  const cpx<T>* z = reinterpret_cast<const cpx<T>*>(x + (long)(row0 + f) * ld_x);
+
+  cpx<T> v[E];
+#pragma unroll
+  for (int b = 0; b < E / R1; ++b) {
+    const int j = tid + b * TT;
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      if (PADDED && r >= R1 / 2) v[b * R1 + r] = mk(T(0), T(0));  // z[n] = 0 for n >= LR/2
+      else v[b * R1 + r] = ld_cpx(z + j + r * (LR / R1));
+    }
+  }
+  fft<T, LR, false, false>(v, sm, tid, twr);
+#pragma unroll
+  for (int b = 0; b < E / RL; ++b) {
+    const int j = tid + b * TT;
+#pragma unroll
+    for (int r = 0; r < RL; ++r) sm[spad(j + r * (LR / RL))] = v[b * RL + r];
+  }
+  __syncthreads();
+  // untangle Z = FFT(x_even + i x_odd) into X[v] = E[v] + W^v O[v]; coalesced store
+  cpx<T>* out = S + (long)(row0 >> 2) * LR * 4;
+#pragma unroll 4
+  for (int it = 0; it < E; ++it) {
+    const int e = threadIdx.x + it * (RPC * TT);
+    const int rr = e & 3, vv = (e >> 2) % LR, fb = (e >> 2) / LR;
+    const cpx<T>* smf = sm_all + (fb * 4 + rr) * SME;
+    const cpx<T> Z = smf[spad(vv)];
+    cpx<T> X;
+    if (vv == 0) {
+      X = mk(Z.x + Z.y, Z.x - Z.y);  // (X[0], X[LR]) both real
+    } else {
+      const cpx<T> Zm = conj(smf[spad(LR - vv)]);
+      const cpx<T> Ev = scale(Z + Zm, T(0.5));
+      const cpx<T> Od = scale(mul_mi<T, false>(Z - Zm), T(0.5));
+      X = Ev + cmul(Od, ld_cpx(twc + vv));
+    }
+    st_cpx(out + e, X);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// K7: packed half spectra -> real rows, first LR outputs of 2 LR (crop)
+// ------------------------------------------------------------------------------------
+template <typename T, int LR, int RPC>
+__global__ void __launch_bounds__(RPC * (LR / Plan<LR>::E))
+k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
+           const cpx<T>* __restrict__ twr, const cpx<T>* __restrict__ twc) {
+  constexpr int E = Plan<LR>::E, TT = LR / E, R1 = Plan<LR>::R[0], RL = Plan<LR>::R[Plan<LR>::NS - 1];
+  constexpr int SME = smem_elems<LR>();
+  static_assert(R1 % 2 == 0, "zero-padding / crop split needs an even first radix");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* sm_all = reinterpret_cast<cpx<T>*>(smraw);
+  const int f = threadIdx.x / TT, tid = threadIdx.x % TT;
+  const int row0 = blockIdx.x * RPC;
+  cpx<T>* sm = sm_all + f * SME;
+
+  const cpx<T>* in = S + (long)(row0 >> 2) * LR * 4;
+#pragma unroll 4
+  for (int it = 0; it < E; ++it) {
+    const int e = threadIdx.x + it * (RPC * TT);
+    const int rr = e & 3, vv = (e >> 2) % LR, fb = (e >> 2) / LR;
+    sm_all[(fb * 4 + rr) * SME + spad(vv)] = ld_cpx(in + e);
+  }
+  __syncthreads();
+  // the inverse runs the plan reversed: its first radix is the plan's last (RF) and its
+  // last radix is the plan's first (R1, always even), so the crop m < LR/2 is r < R1/2
+  constexpr int RF = RL;
+  cpx<T> v[E];
+#pragma unroll
+  for (int b = 0; b < E / RF; ++b) {
+    const int j = tid + b * TT;
+#pragma unroll
+    for (int r = 0; r < RF; ++r) {
+      const int idx = j + r * (LR / RF);
+      const cpx<T> Y = sm[spad(idx)];
+      cpx<T> Zp;
+      if (idx == 0) {
+        Zp = mk(Y.x + Y.y, Y.x - Y.y);
+      } else {
+        const cpx<T> Ym = conj(sm[spad(LR - idx)]);
+        const cpx<T> Ev = Y + Ym;
+        const cpx<T> Od = cmulc(Y - Ym, ld_cpx(twc + idx));
+        Zp = Ev + mul_mi<T, true>(Od);  // E' + i O'
+      }
+      v[b * RF + r] = Zp;
+    }
+  }
+  __syncthreads();
+  fft<T, LR, true, true>(v, sm, tid, twr);
+  cpx<T>* yr = reinterpret_cast<cpx<T>*>(y + (long)(row0 + f) * ld_y);
+#pragma unroll
+  for (int b = 0; b < E / R1; ++b) {
+    const int j = tid + b * TT;
+#pragma unroll
+    for (int r = 0; r < R1 / 2; ++r) st_cpx(yr + j + r * (LR / R1), v[b * R1 + r]);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// K6: per packed column: forward 2N FFT (rows >= N are zero), multiply by the real
+// spectrum, inverse, keep rows < N.  In place on S.
+// ------------------------------------------------------------------------------------
+template <typename T, int LC, int CPC>
+__global__ void __launch_bounds__(CPC * (LC / Plan<LC>::E))
+k_cols_conv(cpx<T>* __restrict__ S, const T* __restrict__ Gt, const cpx<T>* __restrict__ twc) {
+  constexpr int E = Plan<LC>::E, TT = LC / E, R1 = Plan<LC>::R[0], RL = Plan<LC>::R[Plan<LC>::NS - 1];
+  constexpr int NC = LC / 2;
+  constexpr int SME = smem_elems<LC>();
+  static_assert(R1 % 2 == 0, "zero-padding / crop split needs an even first radix");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* sm_all = reinterpret_cast<cpx<T>*>(smraw);
+  const int f = threadIdx.x / TT, tid = threadIdx.x % TT;
+  const int col = blockIdx.x * CPC + f;
+  cpx<T>* sm = sm_all + f * SME;
+
+  cpx<T> v[E];
+#pragma unroll
+  for (int b = 0; b < E / R1; ++b) {
+    const int j = tid + b * TT;
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      if (r >= R1 / 2) v[b * R1 + r] = mk(T(0), T(0));  // zero-padded rows N..2N-1
+      else v[b * R1 + r] = ld_cpx(S + blk_index(j + r * (LC / R1), col, NC));
+    }
+  }
+  fft<T, LC, false, false>(v, sm, tid, twc);
+
+  const T* Gc = Gt + (long)col * LC;
+  if (blockIdx.x == 0) {
+    // column 0 holds a + i b (a = DC column, b = Nyquist column): needs Z[-u]
+#pragma unroll
+    for (int b = 0; b < E / RL; ++b) {
+      const int j = tid + b * TT;
+#pragma unroll
+      for (int r = 0; r < RL; ++r) sm[spad(j + r * (LC / RL))] = v[b * RL + r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < E / RL; ++b) {
+      const int j = tid + b * TT;
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int u = j + r * (LC / RL);
+        const cpx<T> Z = v[b * RL + r];
+        if (f == 0) {
+          const int um = (u == 0) ? 0 : LC - u;
+          const cpx<T> Zm = conj(sm[spad(um)]);
+          const T P = Gt[u], Q = Gt[(long)NC * LC + u];
+          v[b * RL + r] = mk(P * Z.x + Q * Zm.x, P * Z.y + Q * Zm.y);
+        } else {
+          const T g = Gc[u];
+          v[b * RL + r] = mk(g * Z.x, g * Z.y);
+        }
+      }
+    }
+    __syncthreads();
+  } else {
+#pragma unroll
+    for (int b = 0; b < E / RL; ++b) {
+      const int j = tid + b * TT;
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const T g = Gc[j + r * (LC / RL)];
+        v[b * RL + r] = mk(g * v[b * RL + r].x, g * v[b * RL + r].y);
+      }
+    }
+  }
+  fft<T, LC, true, true>(v, sm, tid, twc);
+  // reversed plan: last radix = forward first radix R1
+#pragma unroll
+  for (int b = 0; b < E / R1; ++b) {
+    const int j = tid + b * TT;
+#pragma unroll
+    for (int r = 0; r < R1 / 2; ++r) st_cpx(S + blk_index(j + r * (LC / R1), col, NC), v[b * R1 + r]);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Spectrum: per packed column, forward 2N FFT over all 2N rows, real part -> Gt (scaled)
+// ------------------------------------------------------------------------------------
+template <typename T, int LC, int CPC>
+__global__ void __launch_bounds__(CPC * (LC / Plan<LC>::E))
+k_cols_fwd_real(const cpx<T>* __restrict__ S2, T* __restrict__ Gt, const cpx<T>* __restrict__ twc, T sc) {
+  constexpr int E = Plan<LC>::E, TT = LC / E, R1 = Plan<LC>::R[0], RL = Plan<LC>::R[Plan<LC>::NS - 1];
+  constexpr int NC = LC / 2;
+  constexpr int SME = smem_elems<LC>();
+  static_assert(R1 % 2 == 0, "zero-padding / crop split needs an even first radix");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* sm_all = reinterpret_cast<cpx<T>*>(smraw);
+  const int f = threadIdx.x / TT, tid = threadIdx.x % TT;
+  const int col = blockIdx.x * CPC + f;
+  cpx<T>* sm = sm_all + f * SME;
+
+  cpx<T> v[E];
+#pragma unroll
+  for (int b = 0; b < E / R1; ++b) {
+    const int j = tid + b * TT;
+#pragma unroll
+    for (int r = 0; r < R1; ++r) v[b * R1 + r] = ld_cpx(S2 + blk_index(j + r * (LC / R1), col, NC));
+  }
+  fft<T, LC, false, false>(v, sm, tid, twc);
+  if (blockIdx.x == 0) {
+#pragma unroll
+    for (int b = 0; b < E / RL; ++b) {
+      const int j = tid + b * TT;
+#pragma unroll
+      for (int r = 0; r < RL; ++r) sm[spad(j + r * (LC / RL))] = v[b * RL + r];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int b = 0; b < E / RL; ++b) {
+    const int j = tid + b * TT;
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int u = j + r * (LC / RL);
+      const cpx<T> Z = v[b * RL + r];
+      if (blockIdx.x == 0 && f == 0) {
+        const int um = (u == 0) ? 0 : LC - u;
+        const cpx<T> Zn = sm[spad(um)];     // Z[-u]
+        const T g0 = T(0.5) * (Z.x + Zn.x);  // Re of DC-column spectrum
+        const T gN = T(0.5) * (Z.y + Zn.y);  // Re of Nyquist-column spectrum
+        Gt[u] = T(0.5) * (g0 + gN) * sc;
+        Gt[(long)NC * LC + u] = T(0.5) * (g0 - gN) * sc;
+      } else {
+        Gt[(long)col * LC + u] = Z.x * sc;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// host launchers
+// ------------------------------------------------------------------------------------
+template <typename K> static int set_smem(K kern, size_t bytes) {
+  if (bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) { bsct_set_last_cuda_error(e); return BSCT_ERR_CUDA; }
+  }
+  return BSCT_OK;
+}
+
+template <typename T, int N>
+static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* twr, const cpx<T>* twc,
+                      cudaStream_t st) {
+  constexpr int LR = N, LC = 2 * N;
+  constexpr int RPC = rows_per_cta<LR>();
+  constexpr int CPC = cols_per_cta<T, LC>();
+  static_assert(N % RPC == 0 && N % CPC == 0, "tile must divide N");
+  constexpr int TR = RPC * (LR / Plan<LR>::E), TC = CPC * (LC / Plan<LC>::E);
+  const size_t smr = (size_t)RPC * smem_elems<LR>() * sizeof(cpx<T>);
+  const size_t smc = (size_t)CPC * smem_elems<LC>() * sizeof(cpx<T>);
+  static bool attr_done = false;
+  if (!attr_done) {
+    int rc = set_smem(k_rows_r2c<T, LR, true, RPC>, smr);
+    if (rc == BSCT_OK) rc = set_smem(k_rows_c2r<T, LR, RPC>, smr);
+    if (rc == BSCT_OK) rc = set_smem(k_cols_conv<T, LC, CPC>, smc);
+    if (rc != BSCT_OK) return rc;
+    attr_done = true;
+  }
+  k_rows_r2c<T, LR, true, RPC><<<N / RPC, TR, smr, st>>>(x, N, S, twr, twc);
+  k_cols_conv<T, LC, CPC><<<N / CPC, TC, smc, st>>>(S, Gt, twc);
+  k_rows_c2r<T, LR, RPC><<<N / RPC, TR, smr, st>>>(S, y, N, twr, twc);
+  count_launch(3);
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+template <typename T, int N>
+static int spectrum_impl(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* twr, const cpx<T>* twc,
+                         cudaStream_t st) {
+  constexpr int LR = N, LC = 2 * N;
+  constexpr int RPC = rows_per_cta<LR>();
+  constexpr int CPC = cols_per_cta<T, LC>();
+  constexpr int TR = RPC * (LR / Plan<LR>::E), TC = CPC * (LC / Plan<LC>::E);
+  const size_t smr = (size_t)RPC * smem_elems<LR>() * sizeof(cpx<T>);
+  const size_t smc = (size_t)CPC * smem_elems<LC>() * sizeof(cpx<T>);
+  static bool attr_done = false;
+  if (!attr_done) {
+    int rc = set_smem(k_rows_r2c<T, LR, false, RPC>, smr);
+    if (rc == BSCT_OK) rc = set_smem(k_cols_fwd_real<T, LC, CPC>, smc);
+    if (rc != BSCT_OK) return rc;
+    attr_done = true;
+  }
+  k_rows_r2c<T, LR, false, RPC><<<LC / RPC, TR, smr, st>>>(emb, LC, S2, twr, twc);
+  k_cols_fwd_real<T, LC, CPC><<<N / CPC, TC, smc, st>>>(S2, Gt, twc, T(1.0 / ((double)LC * (double)LC)));
+  count_launch(2);
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+template <typename T, int N> FftOps<T> fft_ops() {
+  FftOps<T> o;
+  o.apply = &apply_impl<T, N>;
+  o.spectrum = &spectrum_impl<T, N>;
+  return o;
+}
+
+template FftOps<float> fft_ops<float, BSCT_FFT_N>();
+template FftOps<double> fft_ops<double, BSCT_FFT_N>();
+
+}  // namespace bsct

@@ -1,0 +1,74 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every declared entry
+point, and rejects bad arguments before touching the GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bsct.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2005_13471_gb300 import _build
+
+    _build.build()
+    import paper_2005_13471_gb300 as m
+
+    return m.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bsct_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("bsct_gram_build", "bsct_backproject", "bsct_gram_apply", "bsct_cg_solve"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_supported_sizes(lib):
+    import paper_2005_13471_gb300 as m
+
+    for n in (16, 32, 64, 128, 256, 384, 512, 768, 1024, 2048):
+        assert m.supported_size(n)
+    for n in (0, 100, 4096, 3000):
+        assert not m.supported_size(n)
+
+
+def test_status_strings(lib):
+    assert lib.bsct_status_string(0) == b"ok"
+    assert lib.bsct_status_string(-2) == b"unsupported size"
+
+
+def test_argument_validation_without_gpu(lib):
+    import paper_2005_13471_gb300 as m
+
+    h = ctypes.c_void_p()
+    # rejected on the host, before any CUDA call
+    bad = [
+        m.Geometry(100, np.arange(4) / 4, 150),                 # unsupported N
+        m.Geometry(64, np.arange(4) / 4, 90, lambda_y=0.0),      # lambda_y <= 0
+        m.Geometry(64, np.arange(4) / 4, 90, zeta_blur=-1.0),    # negative blur
+        m.Geometry(64, np.arange(4) / 4, 90, zeta_blur=0.1),     # short blur direction
+        m.Geometry(64, np.array([0.1, np.nan]), 90),             # non-finite angle
+    ]
+    codes = [lib.bsct_gram_build(g.cptr(), 0, ctypes.byref(h), None) for g in bad]
+    assert codes == [-2, -1, -1, -1, -1]
+    assert not h
+    nbytes = ctypes.c_size_t()
+    assert lib.bsct_backproject_workspace(m.Geometry(64, np.arange(10) / 10, 90).cptr(), 0, ctypes.byref(nbytes)) == 0
+    assert nbytes.value > 64 * 90 * 4
+    assert lib.bsct_backproject_workspace(m.Geometry(64, np.arange(10) / 10, 90).cptr(), 7, ctypes.byref(nbytes)) == -1
+    assert lib.bsct_gram_apply(None, None, None, 0, None) == -1

@@ -1,0 +1,304 @@
+"""GPU parity: every step of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative L2 unless stated): FP64 steps 1e-12, FP32 steps 1e-5.
+Inputs are seeded; expected values come only from ``oracle/``.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import backproject as obp  # noqa: E402
+from oracle import cg as ocg  # noqa: E402
+from oracle import gram as ogram  # noqa: E402
+from workloads import ellipse_params, ellipse_sinogram, get_config, make_problem  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bsct():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2005_13471_gb300 as m
+
+    m.lib()
+    return m
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+DEV = "cuda:0"
+
+
+# ---------------------------------------------------------------- gram_build (FP64)
+@pytest.mark.parametrize("N,na,zeta,kind", [
+    (16, 7, 0.0, "uniform"), (16, 7, 1.0, "random"), (32, 90, 0.0, "uniform"), (64, 90, 1.0, "uniform"),
+    (64, 33, 1.0, "random"), (128, 180, 0.5, "uniform"),
+])
+def test_gram_taps_fp64(bsct, N, na, zeta, kind):
+    rng = np.random.default_rng(N + na)
+    angles = np.arange(na) / na if kind == "uniform" else rng.uniform(-1.0, 2.0, na)
+    geom = bsct.Geometry(N, angles, 2 * N, 1.0, zeta)
+    g = bsct.gram_build(geom, bsct.F64)
+    taps = g.taps().cpu().numpy()
+    ref = ogram.gram_taps(N, angles, zeta)
+    assert rel(taps, ref) < 1e-12
+    spec = g.spectrum().cpu().numpy()
+    re, _ = ogram.gram_spectrum(ref)
+    assert rel(spec, re[:, :N + 1]) < 1e-12
+    g.close()
+
+
+def test_gram_taps_near_axis_views(bsct):
+    # views within a fraction of a degree of the axes (short direction path)
+    angles = np.array([1e-4, 2e-3, 0.0049, 0.4999, 0.501, 0.9993, 0.25])
+    geom = bsct.Geometry(16, angles, 32, 1.0, 1.0)
+    g = bsct.gram_build(geom, bsct.F64)
+    assert rel(g.taps().cpu().numpy(), ogram.gram_taps(16, angles, 1.0)) < 1e-12
+    g.close()
+
+
+def test_gram_taps_sampled_large(bsct):
+    # full-size geometry (N=2048, 1800 views, zeta=1): sampled taps against the oracle
+    cfg = get_config("fp32_n2048")
+    N, na = cfg["N"], cfg["n_angles"]
+    angles = np.arange(na) / na
+    geom = bsct.Geometry(N, angles, cfg["n_bins"], 1.0, cfg["zeta"])
+    g = bsct.gram_build(geom, bsct.F32)
+    taps = g.taps().cpu().numpy()
+    rng = np.random.default_rng(0)
+    offs = np.concatenate([rng.integers(-(N - 1), N, size=(40, 2)), rng.integers(-6, 7, size=(20, 2)),
+                           np.array([[0, 0], [N - 1, N - 1], [-(N - 1), 3], [1500, -2]])])
+    ref = ogram.gram_tap_values(offs, angles, cfg["zeta"])
+    got = taps[offs[:, 1] + N - 1, offs[:, 0] + N - 1]
+    assert rel(got, ref) < 1e-12
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+    g.close()
+
+
+# ---------------------------------------------------------------- gram_apply
+@pytest.mark.parametrize("N", [16, 32, 64, 128, 256, 384, 512, 768, 1024])
+def test_gram_apply_fp32(bsct, N):
+    na = 24
+    angles = np.arange(na) / na
+    geom = bsct.Geometry(N, angles, 2 * N, 1.0, 1.0)
+    g = bsct.gram_build(geom, bsct.F32)
+    G = ogram.gram_taps(N, angles, 1.0)
+    x = np.random.default_rng(N).standard_normal((N, N))
+    y = g.apply(torch.tensor(x, dtype=torch.float32, device=DEV)).cpu().numpy()
+    x32 = x.astype(np.float32).astype(np.float64)
+    assert rel(y, ogram.gram_apply_fft(G, x32)) < 1e-5
+    if N <= 32:
+        assert rel(y, ogram.gram_apply_direct(G, x32)) < 1e-5
+    g.close()
+
+
+@pytest.mark.parametrize("N", [16, 64, 384, 512])
+def test_gram_apply_fp64(bsct, N):
+    angles = np.arange(30) / 30
+    geom = bsct.Geometry(N, angles, 2 * N, 1.0, 0.0)
+    g = bsct.gram_build(geom, bsct.F64)
+    G = ogram.gram_taps(N, angles, 0.0)
+    x = np.random.default_rng(N).standard_normal((N, N))
+    y = g.apply(torch.tensor(x, dtype=torch.float64, device=DEV)).cpu().numpy()
+    assert rel(y, ogram.gram_apply_fft(G, x)) < 1e-12
+    if N <= 16:
+        assert rel(y, ogram.gram_apply_direct(G, x)) < 1e-13
+    g.close()
+
+
+def test_gram_apply_fp32_full_size_sampled(bsct):
+    # N = 2048 (4096^2 padded grids), launch configuration of the benchmark; outputs sampled
+    N = 2048
+    angles = np.arange(12) / 12
+    geom = bsct.Geometry(N, angles, 2900, 1.0, 1.0)
+    g = bsct.gram_build(geom, bsct.F32)
+    G = ogram.gram_taps(N, angles, 1.0)
+    x = np.random.default_rng(7).standard_normal((N, N)).astype(np.float32)
+    y = g.apply(torch.tensor(x, device=DEV)).cpu().numpy()
+    rng = np.random.default_rng(1)
+    pts = [tuple(p) for p in rng.integers(0, N, size=(12, 2))] + [(0, 0), (N - 1, N - 1), (0, N - 1)]
+    ref = ogram.gram_apply_sampled(G, x.astype(np.float64), pts)
+    got = np.array([y[p] for p in pts])
+    assert rel(got, ref) < 1e-5
+    # a point source returns the filter itself (column of G), checked on the full image
+    xd = torch.zeros((N, N), dtype=torch.float32, device=DEV)
+    xd[1000, 900] = 1.0
+    yd = g.apply(xd).cpu().numpy()
+    ref_d = G[N - 1 - 1000:2 * N - 1 - 1000, N - 1 - 900:2 * N - 1 - 900]
+    assert rel(yd, ref_d) < 1e-5
+    g.close()
+
+
+def test_gram_apply_linearity_and_symmetry(bsct):
+    # <G x, z> = <x, G z> and G(ax + z) = a Gx + Gz at the benchmark size
+    N = 2048
+    geom = bsct.Geometry.uniform(N, 1800, 2900, 1.0, 1.0)
+    g = bsct.gram_build(geom, bsct.F32)
+    gen = torch.Generator(device=DEV).manual_seed(0)
+    x = torch.randn((N, N), device=DEV, generator=gen)
+    z = torch.randn((N, N), device=DEV, generator=gen)
+    Gx, Gz = g.apply(x), g.apply(z)
+    lhs = float((Gx.double() * z.double()).sum())
+    rhs = float((x.double() * Gz.double()).sum())
+    assert abs(lhs - rhs) < 1e-5 * abs(lhs)
+    Gc = g.apply(2.5 * x + z)
+    assert float((Gc - (2.5 * Gx + Gz)).norm() / Gc.norm()) < 1e-5
+    assert float((x.double() * Gx.double()).sum()) > 0
+    g.close()
+
+
+# ---------------------------------------------------------------- backproject
+@pytest.mark.parametrize("N,na,M,lam,zeta", [
+    (32, 45, 48, 1.0, 0.0), (32, 45, 48, 1.0, 1.0), (50, 37, 77, 0.7, 1.0), (64, 90, 92, 1.0, 0.0),
+    (41, 16, 60, 1.6, 1.0), (16, 2, 20, 1.0, 1.0),
+])
+def test_backproject_fp32(bsct, N, na, M, lam, zeta):
+    angles = np.arange(na) / na
+    sino = np.random.default_rng(N + M).standard_normal((na, M))
+    geom = bsct.Geometry(N, angles, M, lam, zeta)
+    b = bsct.backproject(geom, torch.tensor(sino, dtype=torch.float32, device=DEV), bsct.F32).cpu().numpy()
+    ref = obp.backproject(sino.astype(np.float32).astype(np.float64), N, angles, lam, zeta)
+    assert rel(b, ref) < 1e-5
+
+
+@pytest.mark.parametrize("zeta", [0.0, 1.0])
+def test_backproject_fp64_config_small(bsct, zeta):
+    cfg = get_config("fp64_n64")
+    angles, sino, _ = make_problem(cfg)
+    geom = bsct.Geometry(cfg["N"], angles, cfg["n_bins"], cfg["lambda_y"], zeta)
+    b = bsct.backproject(geom, torch.tensor(sino, device=DEV), bsct.F64).cpu().numpy()
+    ref = obp.backproject(sino, cfg["N"], angles, cfg["lambda_y"], zeta)
+    assert rel(b, ref) < 1e-12
+
+
+def test_backproject_random_and_near_axis_angles(bsct):
+    rng = np.random.default_rng(3)
+    angles = np.concatenate([rng.uniform(-1, 2, 20), [1e-4, 0.4999, 0.5003, 0.75]])
+    sino = rng.standard_normal((angles.size, 70))
+    for zeta in (0.0, 1.0):
+        geom = bsct.Geometry(40, angles, 70, 0.9, zeta)
+        b = bsct.backproject(geom, torch.tensor(sino, device=DEV), bsct.F64).cpu().numpy()
+        assert rel(b, obp.backproject(sino, 40, angles, 0.9, zeta)) < 1e-12
+
+
+def test_backproject_exact_recovery(bsct):
+    # views {0, pi/2}, even N and M, lambda = 1: H^T S H c = G c (Sec. 5)
+    N, M = 32, 40
+    angles = np.array([0.0, 0.5])
+    c = np.random.default_rng(0).standard_normal((N, N))
+    for zeta in (0.0, 1.0):
+        sino = obp.forward_sample(c, angles, M, 1.0, zeta)
+        geom = bsct.Geometry(N, angles, M, 1.0, zeta)
+        b = bsct.backproject(geom, torch.tensor(sino, device=DEV), bsct.F64).cpu().numpy()
+        g = bsct.gram_build(geom, bsct.F64)
+        Gc = g.apply(torch.tensor(c, device=DEV)).cpu().numpy()
+        assert rel(b, Gc) < 1e-12
+        g.close()
+
+
+@pytest.mark.parametrize("name", ["fp32_n512", "fp32_n2048"])
+def test_backproject_full_size_sampled(bsct, name):
+    cfg = get_config(name)
+    N = cfg["N"]
+    angles, sino, _ = make_problem(cfg)
+    geom = bsct.Geometry(N, angles, cfg["n_bins"], cfg["lambda_y"], cfg["zeta"])
+    b = bsct.backproject(geom, torch.tensor(sino, dtype=torch.float32, device=DEV), bsct.F32).cpu().numpy()
+    rng = np.random.default_rng(5)
+    pts = [tuple(p) for p in rng.integers(0, N, size=(10, 2))] + [(0, 0), (N - 1, N - 1), (N // 2, N // 2)]
+    ref = obp.backproject_sampled(sino.astype(np.float32).astype(np.float64), N, angles, cfg["lambda_y"],
+                                  cfg["zeta"], pts)
+    got = np.array([b[p] for p in pts])
+    assert rel(got, ref) < 1e-5
+
+
+# ---------------------------------------------------------------- cg_solve
+# CG iterates are ill-conditioned functions of the data: in the oracle itself a relative
+# perturbation of b at the FP64 rounding level (1e-15) moves iterate 20 of the small FP64
+# workload by ~5e-9 and one of 1e-12 moves iterate 5 by ~8e-12.  Early iterates are gated
+# tightly, late ones with that measured amplification, and every result is finally
+# judged by the oracle's own FP64 true residual.  Both sides get the oracle's b.
+def test_cg_fp64_config_small(bsct):
+    cfg = get_config("fp64_n64")
+    angles, sino, _ = make_problem(cfg)
+    N = cfg["N"]
+    geom = bsct.Geometry(N, angles, cfg["n_bins"], cfg["lambda_y"], cfg["zeta"])
+    g = bsct.gram_build(geom, bsct.F64)
+    b_ref = obp.backproject(sino, N, angles, cfg["lambda_y"], cfg["zeta"])
+    b = torch.tensor(b_ref, device=DEV)
+    G = ogram.gram_taps(N, angles, cfg["zeta"])
+    apply = lambda v: ogram.gram_apply_fft(G, v)
+    x_ref, hist, iters = ocg.cg(apply, b_ref, iters=cfg["cg_iters"])
+    for k in (1, 2, 5):
+        xk, _ = g.cg_solve(b, max_iter=k)
+        assert rel(xk.cpu().numpy(), iters[k - 1]) < 1e-10
+    x, rep = g.cg_solve(b, max_iter=cfg["cg_iters"])
+    assert rep["iterations"] == cfg["cg_iters"]
+    assert rel(x.cpu().numpy(), x_ref) < 1e-6
+    assert abs(rep["rel_residual"] - hist[-1]) < 1e-6 * hist[-1]
+    r_gpu = ocg.true_relative_residual(apply, b_ref, x.cpu().numpy())
+    assert abs(r_gpu - ocg.true_relative_residual(apply, b_ref, x_ref)) < 1e-8 * r_gpu
+    g.close()
+
+
+def test_cg_fp32_iterates_and_converges(bsct):
+    # FP32 CG leaves the FP64 Krylov sequence after ~5 iterations (a CPU emulation of FP32
+    # CG with FP32 FFTs drifts by 1.2e-2 at iterate 20 on this problem); gate the early
+    # iterates, then judge convergence by the oracle's FP64 residual
+    N, na = 128, 180
+    angles = np.arange(na) / na
+    sino = ellipse_sinogram(ellipse_params(N, 20, seed=2), angles, 184, 1.0, 1.0)
+    geom = bsct.Geometry(N, angles, 184, 1.0, 1.0)
+    g = bsct.gram_build(geom, bsct.F32)
+    bd = obp.backproject(sino, N, angles, 1.0, 1.0).astype(np.float32).astype(np.float64)
+    b = torch.tensor(bd, dtype=torch.float32, device=DEV)
+    G = ogram.gram_taps(N, angles, 1.0)
+    apply = lambda v: ogram.gram_apply_fft(G, v)
+    _, hist, iters = ocg.cg(apply, bd, iters=20)
+    for k in (1, 3, 5):
+        xk, _ = g.cg_solve(b, max_iter=k)
+        assert rel(xk.cpu().numpy(), iters[k - 1]) < 1e-5
+    x20, rep20 = g.cg_solve(b, max_iter=20)
+    r20 = ocg.true_relative_residual(apply, bd, x20.cpu().double().numpy())
+    assert r20 < 1.5 * hist[-1]
+    x, rep = g.cg_solve(b, max_iter=500, rel_tol=1e-4, check_every=5)
+    assert rep["converged"] and rep["rel_residual"] <= 1e-4
+    r_final = ocg.true_relative_residual(apply, bd, x.cpu().double().numpy())
+    assert r_final < 2e-4
+    assert abs(rep["true_rel_residual"] - r_final) < 0.05 * r_final
+    g.close()
+
+
+def test_cg_warm_start(bsct):
+    N = 64
+    geom = bsct.Geometry.uniform(N, 60, 92, 1.0, 0.0)
+    g = bsct.gram_build(geom, bsct.F64)
+    b = torch.randn((N, N), dtype=torch.float64, device=DEV, generator=torch.Generator(device=DEV).manual_seed(1))
+    _, cold = g.cg_solve(b, max_iter=1000, rel_tol=1e-3, check_every=1)
+    assert cold["converged"]
+    x_part, _ = g.cg_solve(b, max_iter=(2 * cold["iterations"]) // 3)
+    _, warm = g.cg_solve(b, x0=x_part, max_iter=1000, rel_tol=1e-3, check_every=1)
+    assert warm["converged"] and warm["iterations"] < cold["iterations"]
+    assert warm["true_rel_residual"] < 1.01e-3
+    g.close()
+
+
+# ---------------------------------------------------------------- errors
+def test_error_codes(bsct):
+    with pytest.raises(RuntimeError, match="unsupported size"):
+        bsct.gram_build(bsct.Geometry.uniform(100, 10, 150), bsct.F32)
+    with pytest.raises(RuntimeError, match="invalid argument"):
+        bsct.gram_build(bsct.Geometry.uniform(64, 10, 90, zeta_blur=0.05), bsct.F32)
+    g = bsct.gram_build(bsct.Geometry.uniform(32, 10, 48), bsct.F32)
+    with pytest.raises(TypeError):
+        g.apply(torch.zeros((32, 32), dtype=torch.float64, device=DEV))
+    with pytest.raises(ValueError):
+        g.apply(torch.zeros((32, 31), dtype=torch.float32, device=DEV))
+    g.close()
