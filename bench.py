@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Benchmark of the pixel-basis Gram-filter reconstruction path on GB300.
+
+Workload: N = 2048 unit-pixel grid, 1800 views uniform in [0, pi), 2900 detector bins at
+lambda_y = 1, detector blur zeta = 1, seeded 40-ellipse phantom (4096 x 4096
+zero-padded FFT grids).  A step is one Gram apply y = G x on a resident 2048^2 image
+(the unit of the headline Gram-apply/s); L2 is flushed (256 MiB write) before every
+timed step, outside the timed events.  Alongside: CG iterations/s, one full pass of
+the hot path (Gram build + back projection + 100 CG iterations), plain-CG time to a
+1e-4 relative residual, the end-to-end rate through the C ABI with host buffers, the
+roofline of the dominant kernel and the FP64 CPU oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gram-apply/s and CG iters/s at N=2048; time-to-1e-4 residual, learned vs plain"
+UNIT = "Gram-apply/s"
+WORKLOAD = "fp32_n2048"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--cg-iters", type=int, default=100)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--quick", action="store_true", help="skip the hot-path pass and time-to-1e-4 extras")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("gram_fft.cu", "bsct_fft.cuh", "bsct_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2005_13471_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, n):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        e = rec[kernel]
+        if e.get("source_hash") != kernel_source_hash() or int(e.get("N", -1)) != n:
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bsct_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        import statistics
+
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_apply_rate(n_applies):
+    """The FP64 oracle's FFT Gram apply at N = 2048 on the host (as it stands)."""
+    import numpy as np
+
+    from oracle import gram as ogram
+
+    N = 2048
+    angles = np.arange(12) / 12  # the apply cost does not depend on the number of views
+    G = ogram.gram_taps(N, angles, 1.0)
+    x = np.random.default_rng(0).standard_normal((N, N))
+    t0 = time.perf_counter()
+    for _ in range(n_applies):
+        ogram.gram_apply_fft(G, x)
+    dt = time.perf_counter() - t0
+    return n_applies / dt, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_oracle_apply_rate(1)
+    rate, dt = cpu_oracle_apply_rate(args.steps)
+    cores = 1
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: N=2048 Gram apply (4096^2 zero-padded FFT convolution)",
+                   "N": 2048, "fft_grid": 4096},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} applies of the numpy FP64 oracle gram_apply_fft at N=2048 "
+                                   "(taps of a 12-view geometry; apply cost is independent of the view count)"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2005_13471_gb300 as bsct
+    from workloads import get_config, make_problem
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    bsct.lib()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        import torch.distributed as dist
+
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    cfg = get_config(WORKLOAD)
+    N = cfg["N"]
+    angles, sino_np, _ = make_problem(cfg, slice_id=rank)
+    geom = bsct.Geometry(N, angles, cfg["n_bins"], cfg["lambda_y"], cfg["zeta"])
+    sino = torch.tensor(sino_np, dtype=torch.float32, device=dev)
+    g = bsct.gram_build(geom, bsct.F32)
+    b = bsct.backproject(geom, sino, bsct.F32)
+    x = b.clone()
+    y = torch.empty_like(x)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # ---------------------------------------------------------------- timed steps
+    for _ in range(args.warmup):
+        flush.zero_()
+        g.apply(x, y)
+    bsct.set_kernel_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ktimes = np.zeros(3)
+    barrier()
+    launches0 = bsct.launch_count()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            g.apply(x, y)
+            ev[i][1].record(stream)
+            ktimes += np.array(bsct.kernel_times())
+        barrier()
+        wall = time.perf_counter() - wall0
+    launches = bsct.launch_count() - launches0
+    bsct.set_kernel_timing(False)
+    step_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
+    step_ms = max_over_ranks(step_ms)
+    value = world * args.steps / (step_ms * 1e-3)
+    kt = ktimes / args.steps  # ms per launch: row R2C, column conv, row C2R
+
+    # ---------------------------------------------------------------- roofline (dominant kernel)
+    hbm, peak_kind = measured_peaks()
+    kernel_bytes = {
+        "k_rows_r2c": 4 * N * N + 8 * N * N,
+        "k_cols_conv": 8 * N * N + 8 * N * (N + 1) + 8 * N * N,
+        "k_rows_c2r": 8 * N * N + 4 * N * N,
+    }
+    names = list(kernel_bytes)
+    dom = int(np.argmax(kt))
+    dname = names[dom]
+    achieved = kernel_bytes[dname] / (kt[dom] * 1e-3) / 1e9
+    apply_bytes = 8 * N * N + 40 * N * (N + 1)
+    roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": kernel_bytes[dname],
+                "traffic": profiled_traffic(dname, N),
+                "kernel_ms": {n: float(t) for n, t in zip(names, kt)},
+                "whole_apply": {"algorithmic_bytes": apply_bytes,
+                                "achieved_GBs": apply_bytes / (step_ms / args.steps * 1e-3) / 1e9 / world * world,
+                                "frac": apply_bytes / (step_ms / args.steps * 1e-3) / 1e9 / hbm}}
+
+    # ---------------------------------------------------------------- CG iterations/s
+    n_cg = args.cg_iters
+    g.cg_begin(b, x, x0_is_zero=True)
+    g.cg_iterate(x, 3)
+    flush.zero_()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.cg_iterate(x, n_cg)
+    e1.record(stream)
+    barrier()
+    cg_ms = max_over_ranks(e0.elapsed_time(e1))
+    cg_rate = world * n_cg / (cg_ms * 1e-3)
+    cg_bytes = apply_bytes + 36 * N * N
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    xh = torch.empty((N, N), dtype=torch.float32, pin_memory=True)
+    xh.copy_(x.cpu())
+    yh = torch.empty((N, N), dtype=torch.float32, pin_memory=True)
+    xd = torch.empty_like(x)
+    for _ in range(2):
+        xd.copy_(xh, non_blocking=True)
+        g.apply(xd, y)
+        yh.copy_(y, non_blocking=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        xd.copy_(xh, non_blocking=True)
+        g.apply(xd, y)
+        yh.copy_(y, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+    e2e = {"value": world * args.steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 4 * N * N,
+           "d2h_bytes_per_step": 4 * N * N}
+
+    # ---------------------------------------------------------------- whole hot path, time to 1e-4
+    extras = {}
+    if not args.quick:
+        barrier()
+        t = {}
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        g2 = bsct.gram_build(geom, bsct.F32)
+        e[1].record(stream)
+        b2 = bsct.backproject(geom, sino, bsct.F32)
+        e[2].record(stream)
+        x2, _ = g2.cg_solve(b2, max_iter=100)
+        e[3].record(stream)
+        barrier()
+        t = {"gram_build_ms": e[0].elapsed_time(e[1]), "backproject_ms": e[1].elapsed_time(e[2]),
+             "cg100_ms": e[2].elapsed_time(e[3])}
+        t["total_ms"] = sum(t.values())
+        t["backproject_Gpairs_per_s"] = N * N * cfg["n_angles"] / (t["backproject_ms"] * 1e-3) / 1e9
+        extras["hot_path_pass"] = t
+        g2.close()
+        # plain CG to a 1e-4 relative residual on the learned-evaluation geometry
+        c5 = get_config("learned_eval_n512")
+        a5, s5, _ = make_problem(c5, slice_id=100 + rank)
+        geom5 = bsct.Geometry(c5["N"], a5, c5["n_bins"], c5["lambda_y"], c5["zeta"])
+        g5 = bsct.gram_build(geom5, bsct.F32)
+        b5 = bsct.backproject(geom5, torch.tensor(s5, dtype=torch.float32, device=dev), bsct.F32)
+        g5.cg_solve(b5, max_iter=20)
+        barrier()
+        t0 = time.perf_counter()
+        _, rep5 = g5.cg_solve(b5, max_iter=2000, rel_tol=1e-4, check_every=5)
+        torch.cuda.synchronize()
+        extras["time_to_1e-4"] = {"workload": "N=512, 720 views, 726 bins, zeta=1, Poisson I0=1e5",
+                                  "plain_ms": 1e3 * (time.perf_counter() - t0), "plain_iters": rep5["iterations"],
+                                  "plain_true_rel_residual": rep5["true_rel_residual"],
+                                  "learned_ms": None, "learned_iters": None}
+        g5.close()
+
+    # ---------------------------------------------------------------- CPU baseline (rank 0, N=1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_cpu = 3
+        rate_cpu, dt_cpu = cpu_oracle_apply_rate(n_cpu)
+        cpu = {"value": rate_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n_cpu} applies of the numpy FP64 oracle gram_apply_fft at N=2048 "
+                         f"({dt_cpu:.1f} s; taps of a 12-view geometry, apply cost independent of the view count)"}
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: N=2048, 1800 views, 2900 bins, lambda_y=1, zeta=1, 40-ellipse phantom",
+                   "fft_grid": 4096, "l2": "flushed (256 MiB write) before every timed step, outside the events",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "cg_iters_per_s": cg_rate,
+        "cg": {"iters": n_cg, "ms_per_iter": cg_ms / n_cg, "algorithmic_bytes_per_iter": cg_bytes,
+               "frac_of_hbm": cg_bytes / (cg_ms / n_cg * 1e-3) / 1e9 / hbm,
+               "l2": "not flushed between iterations (135 MB working set)"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "wall_s_timed_loop": wall,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    line.update(extras)
+    if rank == 0:
+        print(json.dumps(line))
+    g.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
