@@ -145,6 +145,15 @@ int bsct_cg_residual(const bsct_gram* g, double* rr, double* bb, void* stream);
 const char* bsct_status_string(int status);
 const char* bsct_last_error_string(void);
 
+/* Kernel timing of bsct_gram_apply (measurement aid, not needed for computing).
+ * bsct_set_kernel_timing(1) makes every following gram_apply record CUDA events on its
+ * stream before and after each of its three kernels (row R2C, column convolution,
+ * row C2R); bsct_kernel_times waits for the events of the last timed apply and writes
+ * up to n kernel durations in milliseconds to the host array ms.  Returns the number
+ * written, or a negative error (no timed apply recorded yet).  Not thread-safe. */
+int bsct_set_kernel_timing(int on);
+int bsct_kernel_times(float* ms, int n);
+
 /* Number of kernel launches issued by this library since load (all threads). */
 uint64_t bsct_launch_count(void);
 

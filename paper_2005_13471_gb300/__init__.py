@@ -80,6 +80,10 @@ def _declare(L):
     L.bsct_status_string.restype = ctypes.c_char_p
     L.bsct_last_error_string.argtypes = []
     L.bsct_last_error_string.restype = ctypes.c_char_p
+    L.bsct_set_kernel_timing.argtypes = [ctypes.c_int]
+    L.bsct_set_kernel_timing.restype = ctypes.c_int
+    L.bsct_kernel_times.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+    L.bsct_kernel_times.restype = ctypes.c_int
     L.bsct_launch_count.argtypes = []
     L.bsct_launch_count.restype = ctypes.c_uint64
     for name in ("bsct_gram_build", "bsct_gram_taps", "bsct_gram_spectrum", "bsct_gram_apply",
@@ -115,6 +119,18 @@ def supported_size(N):
 
 def launch_count():
     return int(lib().bsct_launch_count())
+
+
+def set_kernel_timing(on):
+    """Record CUDA events between the three Gram-apply kernels (see bsct_kernel_times)."""
+    _check(lib().bsct_set_kernel_timing(1 if on else 0), "bsct_set_kernel_timing")
+
+
+def kernel_times():
+    """Durations (ms) of the row R2C, column convolution and row C2R kernels of the last timed apply."""
+    buf = (ctypes.c_float * 3)()
+    n = _check(lib().bsct_kernel_times(buf, 3), "bsct_kernel_times")
+    return [float(buf[i]) for i in range(n)]
 
 
 def _stream():

@@ -11,6 +11,25 @@ namespace bsct {
 extern std::atomic<unsigned long long> g_launches;
 inline void count_launch(int n = 1) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
+// Optional per-kernel timing of the Gram apply (CUDA events recorded on the launching
+// stream between its kernels; off unless bsct_set_kernel_timing(1)).
+struct KernelTimer {
+  bool on = false;
+  bool created = false;
+  cudaEvent_t ev[4];
+  int n_recorded = 0;
+};
+extern KernelTimer g_timer;
+inline void timer_mark(cudaStream_t st, int i) {
+  if (!g_timer.on) return;
+  if (!g_timer.created) {
+    for (int k = 0; k < 4; ++k) cudaEventCreate(&g_timer.ev[k]);
+    g_timer.created = true;
+  }
+  cudaEventRecord(g_timer.ev[i], st);
+  g_timer.n_recorded = i + 1;
+}
+
 // FFT convolution kernels for one image size N (row FFT length N, column length 2N).
 //   S:   N x N complex scratch (row-block interleaved half spectra)
 //   Gt:  spectrum, [N+1][2N] real, scaled by 1/(2N)^2 (row 0 = (G0+GN)/2, row N = (G0-GN)/2)

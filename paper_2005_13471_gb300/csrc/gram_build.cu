@@ -25,6 +25,7 @@
 namespace bsct {
 
 std::atomic<unsigned long long> g_launches{0};
+KernelTimer g_timer;
 
 // ------------------------------------------------------------------------------------
 // FFT dispatch over the supported sizes
@@ -226,6 +227,24 @@ extern "C" int bsct_supported_size(int32_t N) {
 static int fail(int code, const char* msg) {
   bsct_set_last_message(msg);
   return code;
+}
+static int fail_msg(int code, const char* msg) { return fail(code, msg); }
+
+extern "C" int bsct_set_kernel_timing(int on) {
+  g_timer.on = on != 0;
+  g_timer.n_recorded = 0;
+  return BSCT_OK;
+}
+
+extern "C" int bsct_kernel_times(float* ms, int n) {
+  if (!ms || n < 1) return fail_msg(BSCT_ERR_INVALID_ARG, "invalid argument");
+  if (!g_timer.created || g_timer.n_recorded < 2) return fail_msg(BSCT_ERR_INVALID_ARG, "no timed launch recorded");
+  const int k = g_timer.n_recorded - 1 < n ? g_timer.n_recorded - 1 : n;
+  for (int i = 0; i < k; ++i) {
+    BSCT_CUDA_TRY(cudaEventSynchronize(g_timer.ev[i + 1]));
+    BSCT_CUDA_TRY(cudaEventElapsedTime(&ms[i], g_timer.ev[i], g_timer.ev[i + 1]));
+  }
+  return k;
 }
 
 int bsct_check_geom(const bsct_geom* g) {

@@ -318,9 +318,13 @@ static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw
     if (rc != BSCT_OK) return rc;
     attr_done = true;
   }
+  timer_mark(st, 0);
   k_rows_r2c<T, LR, true, RPC><<<N / RPC, TR, smr, st>>>(x, N, S, twr, twc);
+  timer_mark(st, 1);
   k_cols_conv<T, LC, CPC><<<N / CPC, TC, smc, st>>>(S, Gt, twc);
+  timer_mark(st, 2);
   k_rows_c2r<T, LR, RPC><<<N / RPC, TR, smr, st>>>(S, y, N, twr, twc);
+  timer_mark(st, 3);
   count_launch(3);
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
