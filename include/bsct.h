@@ -106,6 +106,33 @@ int bsct_gram_spectrum(const bsct_gram* g, double* d_out, void* stream);
  * d_x and d_y: N*N elements, may not alias. */
 int bsct_gram_apply(const bsct_gram* g, const void* d_x, void* d_y, int mode, void* stream);
 
+/* Largest N accepted by bsct_gram_apply_noalloc. */
+#define BSCT_NOALLOC_MAX_N 512
+
+/* y = G x in FP32 without allocating any device memory.  The paper has no
+ * counterpart: this is a library service for callers that cannot allocate device
+ * memory - for example a plug-in inside a host application that owns the whole
+ * device memory pool, or code on a latency-critical path where cudaMalloc / cudaFree
+ * would synchronise the device or could fail under memory pressure.  Everything the
+ * three FFT passes need besides the caller's buffers (the N x N complex scratch, the
+ * packed spectrum, the twiddle tables) lives in fixed-size arrays inside the library
+ * that every GPU which loads it holds until the process exits (about 4 MiB).
+ *   N          : supported size <= BSCT_NOALLOC_MAX_N, else BSCT_ERR_UNSUPPORTED_SIZE
+ *                (nothing is launched);
+ *   d_spectrum : [2N][N+1] FP64 real spectrum of the Gram filter's circulant
+ *                embedding, the layout bsct_gram_spectrum writes (caller-owned,
+ *                device, read every call);
+ *   d_x, d_y   : [N][N] float on the device, may not alias.
+ * The first call on a device looks up the device addresses of those arrays (no
+ * allocation); make that first call before any stream capture.  All calls share the
+ * arrays and leave the last call's contents in them; every element a call reads is
+ * written by the same call first, so nothing has to be cleared.  Calls that overlap
+ * on the GPU (two streams, or two host threads) race on the shared arrays: serialise
+ * them.  Calls no cudaMalloc, cudaFree or allocating library routine.
+ * Returns BSCT_OK or a negative error. */
+int bsct_gram_apply_noalloc(int32_t N, const double* d_spectrum, const float* d_x, float* d_y,
+                            void* stream);
+
 /* Bytes of device workspace bsct_backproject needs for this geometry/precision. */
 int bsct_backproject_workspace(const bsct_geom* geom, int precision, size_t* bytes);
 
