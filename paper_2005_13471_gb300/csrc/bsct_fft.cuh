@@ -14,6 +14,11 @@
 //   last output : v[b*R + r] = y[j + r*L/R]
 // so running the inverse with the radix order reversed starts from exactly the
 // registers the forward transform ended with (no exchange between them).
+//
+// Twiddles: stage s (Ns = product of earlier radices, radix R) multiplies element r of
+// butterfly j by exp(-2 pi i r (j mod Ns) / (Ns R)).  They are read from a per-plan
+// table laid out [stage][r-1][j mod Ns] (Ns - 1 + (r-1) Ns + j mod Ns; the stages add
+// up to L - 1 entries), so consecutive threads read consecutive entries.
 #pragma once
 #include "bsct_common.cuh"
 
@@ -75,6 +80,16 @@ __device__ __forceinline__ void dft4(cpx<T>& v0, cpx<T>& v1, cpx<T>& v2, cpx<T>&
   v3 = a1 - a3;
 }
 
+// dft4 of (v0, v1, 0, 0): the upper half of the inputs is known to be zero
+template <typename T, bool INV>
+__device__ __forceinline__ void dft4h(cpx<T>& v0, cpx<T>& v1, cpx<T>& v2, cpx<T>& v3) {
+  const cpx<T> a = v0, b = v1, bi = mul_mi<T, INV>(v1);
+  v0 = a + b;
+  v2 = a - b;
+  v1 = a + bi;
+  v3 = a - bi;
+}
+
 template <typename T, bool INV>
 __device__ __forceinline__ void dft3(cpx<T>& a, cpx<T>& b, cpx<T>& c) {
   const T h3 = T(0.86602540378443864676);  // sqrt(3)/2
@@ -101,10 +116,15 @@ template <typename T, bool INV> __device__ __forceinline__ cpx<T> w16(int k) {
   return mk(c, INV ? s : -s);
 }
 
-template <typename T, bool INV>
+template <typename T, bool INV, bool HALF = false>
 __device__ __forceinline__ void dft8(cpx<T>* v) {
-  dft4<T, INV>(v[0], v[2], v[4], v[6]);
-  dft4<T, INV>(v[1], v[3], v[5], v[7]);
+  if constexpr (HALF) {
+    dft4h<T, INV>(v[0], v[2], v[4], v[6]);
+    dft4h<T, INV>(v[1], v[3], v[5], v[7]);
+  } else {
+    dft4<T, INV>(v[0], v[2], v[4], v[6]);
+    dft4<T, INV>(v[1], v[3], v[5], v[7]);
+  }
   const T H = T(0.70710678118654752440);
   cpx<T> o0 = v[1];
   cpx<T> o1 = cmul(v[3], mk(H, INV ? H : -H));
@@ -118,10 +138,13 @@ __device__ __forceinline__ void dft8(cpx<T>* v) {
 }
 
 // 16 = 4 x 4: r = r1 + 4 r2, k = k1 + 4 k2
-template <typename T, bool INV>
+template <typename T, bool INV, bool HALF = false>
 __device__ __forceinline__ void dft16(cpx<T>* v) {
 #pragma unroll
-  for (int r1 = 0; r1 < 4; ++r1) dft4<T, INV>(v[r1], v[r1 + 4], v[r1 + 8], v[r1 + 12]);
+  for (int r1 = 0; r1 < 4; ++r1) {
+    if constexpr (HALF) dft4h<T, INV>(v[r1], v[r1 + 4], v[r1 + 8], v[r1 + 12]);
+    else dft4<T, INV>(v[r1], v[r1 + 4], v[r1 + 8], v[r1 + 12]);
+  }
   // now v[r1 + 4 k1] = A[r1][k1]; twiddle by w16^(r1 k1)
   v[5] = cmul(v[5], w16<T, INV>(1));
   v[9] = cmul(v[9], w16<T, INV>(2));
@@ -144,35 +167,37 @@ __device__ __forceinline__ void dft16(cpx<T>* v) {
   for (int i = 0; i < 16; ++i) v[i] = t[i];
 }
 
-template <int R, typename T, bool INV> __device__ __forceinline__ void dft(cpx<T>* v) {
-  if constexpr (R == 2) dft2<T, INV>(v[0], v[1]);
+// HALF: inputs r >= R/2 are zero (zero-padded first stage); needs an even radix
+template <int R, typename T, bool INV, bool HALF = false> __device__ __forceinline__ void dft(cpx<T>* v) {
+  static_assert(!HALF || R % 2 == 0, "half-zero stage needs an even radix");
+  if constexpr (R == 2) { if constexpr (HALF) v[1] = v[0]; else dft2<T, INV>(v[0], v[1]); }
   else if constexpr (R == 3) dft3<T, INV>(v[0], v[1], v[2]);
-  else if constexpr (R == 4) dft4<T, INV>(v[0], v[1], v[2], v[3]);
-  else if constexpr (R == 8) dft8<T, INV>(v);
-  else if constexpr (R == 16) dft16<T, INV>(v);
+  else if constexpr (R == 4) { if constexpr (HALF) dft4h<T, INV>(v[0], v[1], v[2], v[3]); else dft4<T, INV>(v[0], v[1], v[2], v[3]); }
+  else if constexpr (R == 8) dft8<T, INV, HALF>(v);
+  else if constexpr (R == 16) dft16<T, INV, HALF>(v);
   else static_assert(R == 2, "unsupported radix");
 }
 
 // ----------------------------------------------------------------------------------
 // Stages
 // ----------------------------------------------------------------------------------
-// twiddle table tw[k] = exp(-2 pi i k / L), k < L (built in FP64, stored in T)
-template <typename T, int L, int R, int NSV, bool INV>
-__device__ __forceinline__ void stage_compute(cpx<T> (&v)[Plan<L>::E], int tid, const cpx<T>* __restrict__ tw) {
+// tws: stage twiddle table of this plan (and radix order), see the top of the file
+template <typename T, int L, int R, int NSV, bool INV, bool HALF>
+__device__ __forceinline__ void stage_compute(cpx<T> (&v)[Plan<L>::E], int tid, const cpx<T>* __restrict__ tws) {
   constexpr int E = Plan<L>::E;
   constexpr int TT = L / E;
 #pragma unroll
   for (int b = 0; b < E / R; ++b) {
     if constexpr (NSV > 1) {
       const int j = tid + b * TT;
-      const int step = (j % NSV) * (L / (NSV * R));
+      const cpx<T>* t = tws + (NSV - 1) + (j % NSV);
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const cpx<T> w = ld_cpx(tw + r * step);
+        const cpx<T> w = ld_cpx(t + (r - 1) * NSV);
         v[b * R + r] = INV ? cmulc(v[b * R + r], w) : cmul(v[b * R + r], w);
       }
     }
-    dft<R, T, INV>(&v[b * R]);
+    dft<R, T, INV, HALF>(&v[b * R]);
   }
 }
 
@@ -184,36 +209,75 @@ __device__ __forceinline__ void stage_exchange(cpx<T> (&v)[Plan<L>::E], cpx<T>* 
   for (int b = 0; b < E / R; ++b) {
     const int j = tid + b * TT;
     const int base = (j / NSV) * NSV * R + (j % NSV);
+    if constexpr (NSV % 16 == 0) {
+      // (base + r NSV) / 16 = base / 16 + r NSV / 16
+      const int pb = spad(base);
 #pragma unroll
-    for (int r = 0; r < R; ++r) sm[spad(base + r * NSV)] = v[b * R + r];
+      for (int r = 0; r < R; ++r) sm[pb + r * (NSV + NSV / 16)] = v[b * R + r];
+    } else if constexpr (NSV == 1 && 16 % R == 0) {
+      // base = j R and r < R <= 16 never crosses a 16-element boundary
+      const int pb = spad(base);
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[pb + r] = v[b * R + r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[spad(base + r * NSV)] = v[b * R + r];
+    }
   }
   __syncthreads();
 #pragma unroll
   for (int b = 0; b < E / R2; ++b) {
     const int j = tid + b * TT;
+    if constexpr ((L / R2) % 16 == 0) {
+      const int pj = spad(j);
 #pragma unroll
-    for (int r = 0; r < R2; ++r) v[b * R2 + r] = sm[spad(j + r * (L / R2))];
+      for (int r = 0; r < R2; ++r) v[b * R2 + r] = sm[pj + r * ((L / R2) + (L / R2) / 16)];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R2; ++r) v[b * R2 + r] = sm[spad(j + r * (L / R2))];
+    }
   }
   __syncthreads();
 }
 
-template <typename T, int L, bool INV, bool REV, int S>
-__device__ __forceinline__ void fft_stages(cpx<T> (&v)[Plan<L>::E], cpx<T>* sm, int tid, const cpx<T>* __restrict__ tw) {
+template <typename T, int L, bool INV, bool REV, bool HALF, int S>
+__device__ __forceinline__ void fft_stages(cpx<T> (&v)[Plan<L>::E], cpx<T>* sm, int tid, const cpx<T>* __restrict__ tws) {
   constexpr int R = radix_of<L, REV>(S);
   constexpr int NSV = ns_of<L, REV>(S);
-  stage_compute<T, L, R, NSV, INV>(v, tid, tw);
+  stage_compute<T, L, R, NSV, INV, HALF && S == 0>(v, tid, tws);
   if constexpr (S + 1 < Plan<L>::NS) {
     stage_exchange<T, L, R, NSV, radix_of<L, REV>(S + 1)>(v, sm, tid);
-    fft_stages<T, L, INV, REV, S + 1>(v, sm, tid, tw);
+    fft_stages<T, L, INV, REV, HALF, S + 1>(v, sm, tid, tws);
   }
 }
 
 // Full FFT of one length-L sequence by L/E threads.  On entry v holds the inputs in
 // the first-stage layout, on exit the outputs in the last-stage layout (see top).
-// sm: this FFT's shared buffer of smem_elems<L>() values.  Unnormalised both ways.
-template <typename T, int L, bool INV, bool REV>
-__device__ __forceinline__ void fft(cpx<T> (&v)[Plan<L>::E], cpx<T>* sm, int tid, const cpx<T>* __restrict__ tw) {
-  fft_stages<T, L, INV, REV, 0>(v, sm, tid, tw);
+// sm: this FFT's shared buffer of smem_elems<L>() values; tws: the stage twiddle table
+// of (L, REV).  HALF: the upper half of the input sequence is zero (its registers are
+// not read).  Unnormalised both ways.
+template <typename T, int L, bool INV, bool REV, bool HALF = false>
+__device__ __forceinline__ void fft(cpx<T> (&v)[Plan<L>::E], cpx<T>* sm, int tid, const cpx<T>* __restrict__ tws) {
+  fft_stages<T, L, INV, REV, HALF, 0>(v, sm, tid, tws);
+}
+
+// Host-side copy of a plan (for building the stage twiddle tables).
+struct PlanInfo {
+  int L, ns, R[8];
+};
+inline bool plan_info(int L, bool rev, PlanInfo* p) {
+  auto fill = [&](const int* R, int ns) {
+    p->L = L;
+    p->ns = ns;
+    for (int i = 0; i < ns; ++i) p->R[i] = rev ? R[ns - 1 - i] : R[i];
+  };
+  switch (L) {
+#define BSCT_PI(LEN) case LEN: fill(Plan<LEN>::R, Plan<LEN>::NS); return true;
+    BSCT_PI(16) BSCT_PI(32) BSCT_PI(64) BSCT_PI(128) BSCT_PI(256) BSCT_PI(384) BSCT_PI(512)
+    BSCT_PI(768) BSCT_PI(1024) BSCT_PI(1536) BSCT_PI(2048) BSCT_PI(4096)
+#undef BSCT_PI
+    default: return false;
+  }
 }
 
 }  // namespace bsct

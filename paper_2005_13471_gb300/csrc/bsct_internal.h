@@ -33,19 +33,20 @@ inline void timer_mark(cudaStream_t st, int i) {
 // FFT convolution kernels for one image size N (row FFT length N, column length 2N).
 //   S:   N x N complex scratch (row-block interleaved half spectra)
 //   Gt:  spectrum, [N+1][2N] real, scaled by 1/(2N)^2 (row 0 = (G0+GN)/2, row N = (G0-GN)/2)
-//   twr: exp(-2 pi i k / N), k < N;  twc: exp(-2 pi i k / 2N), k < 2N
+//   tw:  8N twiddles (fft_table_elems): [0, 2N) exp(-2 pi i k / 2N) for the real/complex
+//        untangling, then the stage tables of the row plan (forward order, reversed
+//        order; N each) and of the column plan (2N each)
 template <typename T> struct FftOps {
-  int (*apply)(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* twr, const cpx<T>* twc,
-               cudaStream_t st);
+  int (*apply)(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw, cudaStream_t st);
   // emb: 2N x 2N real circulant kernel; S2: 2N x N complex scratch; writes Gt (scaled)
-  int (*spectrum)(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* twr, const cpx<T>* twc,
-                  cudaStream_t st);
+  int (*spectrum)(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* tw, cudaStream_t st);
 };
 template <typename T, int N> FftOps<T> fft_ops();
 template <typename T> bool fft_ops_for(int N, FftOps<T>* out);
 
-// twiddle table exp(-2 pi i k / L), k < L
-template <typename T> int build_twiddles(cpx<T>* d_tw, int L, cudaStream_t st);
+inline long fft_table_elems(int N) { return 8L * N; }
+// fill the 8N-entry twiddle array of size N (see FftOps)
+template <typename T> int build_fft_tables(cpx<T>* d_tw, int N, cudaStream_t st);
 
 }  // namespace bsct
 
@@ -56,8 +57,7 @@ struct bsct_gram {
   double* taps = nullptr;    // (2N-1)^2 FP64 taps
   double* Gt64 = nullptr;    // scaled spectrum [N+1][2N], FP64
   float* Gt32 = nullptr;     // same, FP32 (precision F32 only)
-  void* twr = nullptr;       // row twiddles (T)
-  void* twc = nullptr;       // column twiddles (T)
+  void* tw = nullptr;        // FFT twiddle tables (T), fft_table_elems(N) entries
   void* S = nullptr;         // apply scratch, N x N complex T
   void* r = nullptr;         // CG vectors (T, N*N each)
   void* p = nullptr;

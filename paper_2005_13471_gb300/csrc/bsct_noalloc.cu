@@ -8,7 +8,7 @@
 // until the process exits):
 //   g_na_scratch   - the N x N complex half-spectrum scratch of the three FFT passes,
 //   g_na_spectrum  - the packed, scaled spectrum the column pass reads,
-//   g_na_tw_rows / g_na_tw_cols - FFT twiddle tables for the current N.
+//   g_na_tw        - FFT twiddle tables for the current N.
 // The size limit is BSCT_NOALLOC_MAX_N = 512 (2 MiB of scratch).  The kernels are the
 // ones bsct_gram_apply launches; only the buffers differ.
 #include "bsct_internal.h"
@@ -20,16 +20,14 @@ constexpr int NA_MAX_DEV = 64;
 
 static __device__ __align__(256) bsct::cpx<float> g_na_scratch[(size_t)NA_MAX_N * NA_MAX_N];
 static __device__ __align__(256) float g_na_spectrum[(size_t)(NA_MAX_N + 1) * 2 * NA_MAX_N];
-static __device__ __align__(256) bsct::cpx<float> g_na_tw_rows[NA_MAX_N];
-static __device__ __align__(256) bsct::cpx<float> g_na_tw_cols[2 * NA_MAX_N];
+static __device__ __align__(256) bsct::cpx<float> g_na_tw[8 * NA_MAX_N];
 
 struct NaDevice {
   bool ready = false;
   int tw_n = 0;  // N the twiddle tables currently hold
   bsct::cpx<float>* scratch = nullptr;
   float* spectrum = nullptr;
-  bsct::cpx<float>* tw_rows = nullptr;
-  bsct::cpx<float>* tw_cols = nullptr;
+  bsct::cpx<float>* tw = nullptr;
 };
 NaDevice g_na_dev[NA_MAX_DEV];
 
@@ -80,13 +78,11 @@ extern "C" int bsct_gram_apply_noalloc(int32_t N, const double* d_spectrum, cons
     // device addresses of this GPU's copies (the current device is `dev`)
     BSCT_CUDA_TRY(cudaGetSymbolAddress((void**)&d.scratch, g_na_scratch));
     BSCT_CUDA_TRY(cudaGetSymbolAddress((void**)&d.spectrum, g_na_spectrum));
-    BSCT_CUDA_TRY(cudaGetSymbolAddress((void**)&d.tw_rows, g_na_tw_rows));
-    BSCT_CUDA_TRY(cudaGetSymbolAddress((void**)&d.tw_cols, g_na_tw_cols));
+    BSCT_CUDA_TRY(cudaGetSymbolAddress((void**)&d.tw, g_na_tw));
     d.ready = true;
   }
   if (d.tw_n != N) {
-    int rc = build_twiddles<float>(d.tw_rows, N, st);
-    if (rc == BSCT_OK) rc = build_twiddles<float>(d.tw_cols, 2 * N, st);
+    const int rc = build_fft_tables<float>(d.tw, N, st);
     if (rc != BSCT_OK) return rc;
     d.tw_n = N;
   }
@@ -94,5 +90,5 @@ extern "C" int bsct_gram_apply_noalloc(int32_t N, const double* d_spectrum, cons
   k_na_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_spectrum, N, d.spectrum);
   count_launch();
   BSCT_CUDA_TRY(cudaGetLastError());
-  return ops.apply(d_x, d_y, d.scratch, d.spectrum, d.tw_rows, d.tw_cols, st);
+  return ops.apply(d_x, d_y, d.scratch, d.spectrum, d.tw, st);
 }

@@ -20,6 +20,7 @@
 #include <mutex>
 
 #include "bsct_boxspline.cuh"
+#include "bsct_fft.cuh"
 #include "bsct_internal.h"
 
 namespace bsct {
@@ -53,14 +54,54 @@ template <typename T> __global__ void k_twiddles(cpx<T>* tw, int L) {
   sincospi(-2.0 * (double)k / (double)L, &s, &c);
   tw[k] = mk(T(c), T(s));
 }
-template <typename T> int build_twiddles(cpx<T>* d_tw, int L, cudaStream_t st) {
-  k_twiddles<T><<<(L + 255) / 256, 256, 0, st>>>(d_tw, L);
+struct StageDesc {
+  int ns;
+  int R[8], NSV[8], off[8];
+};
+
+// entry (Ns - 1) + (r - 1) Ns + jm of a plan's stage table: exp(-2 pi i r jm / (Ns R))
+template <typename T> __global__ void k_stage_table(cpx<T>* out, StageDesc d, int n) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  int s = d.ns - 1;
+  while (s > 0 && idx < d.off[s]) --s;
+  const int local = idx - d.off[s];
+  const int r = local / d.NSV[s] + 1, jm = local % d.NSV[s];
+  double sn, cs;
+  sincospi(-2.0 * (double)r * (double)jm / ((double)d.NSV[s] * (double)d.R[s]), &sn, &cs);
+  out[idx] = mk(T(cs), T(sn));
+}
+
+template <typename T> static int stage_table(cpx<T>* out, int L, bool rev, cudaStream_t st) {
+  PlanInfo p;
+  if (!plan_info(L, rev, &p)) return BSCT_ERR_UNSUPPORTED_SIZE;
+  StageDesc d;
+  d.ns = p.ns;
+  int nsv = 1;
+  for (int i = 0; i < p.ns; ++i) {
+    d.R[i] = p.R[i];
+    d.NSV[i] = nsv;
+    d.off[i] = nsv - 1;
+    nsv *= p.R[i];
+  }
+  k_stage_table<T><<<(L + 255) / 256, 256, 0, st>>>(out, d, L - 1);
   count_launch();
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
 }
-template int build_twiddles<float>(cpx<float>*, int, cudaStream_t);
-template int build_twiddles<double>(cpx<double>*, int, cudaStream_t);
+
+template <typename T> int build_fft_tables(cpx<T>* tw, int N, cudaStream_t st) {
+  k_twiddles<T><<<(2 * N + 255) / 256, 256, 0, st>>>(tw, 2 * N);
+  count_launch();
+  BSCT_CUDA_TRY(cudaGetLastError());
+  int rc = stage_table<T>(tw + 2 * N, N, false, st);
+  if (rc == BSCT_OK) rc = stage_table<T>(tw + 3 * N, N, true, st);
+  if (rc == BSCT_OK) rc = stage_table<T>(tw + 4 * N, 2 * N, false, st);
+  if (rc == BSCT_OK) rc = stage_table<T>(tw + 6 * N, 2 * N, true, st);
+  return rc;
+}
+template int build_fft_tables<float>(cpx<float>*, int, cudaStream_t);
+template int build_fft_tables<double>(cpx<double>*, int, cudaStream_t);
 
 // ------------------------------------------------------------------------------------
 // geometry (views sorted by angle in half turns, [0, 1))
@@ -267,8 +308,7 @@ extern "C" void bsct_gram_free(bsct_gram* g) {
   cudaFree(g->taps);
   cudaFree(g->Gt64);
   cudaFree(g->Gt32);
-  cudaFree(g->twr);
-  cudaFree(g->twc);
+  cudaFree(g->tw);
   cudaFree(g->S);
   cudaFree(g->r);
   cudaFree(g->p);
@@ -313,10 +353,10 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
   double *d_ang = nullptr, *d_th = nullptr, *d_emb = nullptr;
   double2* d_cs = nullptr;
   void* d_S2 = nullptr;
-  cpx<double>*twr64 = nullptr, *twc64 = nullptr;
+  cpx<double>* tw64 = nullptr;
   auto cleanup = [&]() {
     cudaFree(d_ang); cudaFree(d_th); cudaFree(d_cs); cudaFree(d_emb); cudaFree(d_S2);
-    cudaFree(twr64); cudaFree(twc64);
+    cudaFree(tw64);
     if (g) { bsct_gram_free(g); g = nullptr; }
   };
   const size_t T = precision == BSCT_F32 ? sizeof(float) : sizeof(double);
@@ -327,8 +367,7 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
   CTRY(cudaMalloc(&d_emb, (size_t)L * L * sizeof(double)));
   CTRY(cudaMalloc(&d_S2, (size_t)L * N * 2 * sizeof(double)));
   CTRY(cudaMalloc(&g->Gt64, (size_t)(N + 1) * L * sizeof(double)));
-  CTRY(cudaMalloc(&twr64, (size_t)N * sizeof(cpx<double>)));
-  CTRY(cudaMalloc(&twc64, (size_t)L * sizeof(cpx<double>)));
+  CTRY(cudaMalloc(&tw64, (size_t)fft_table_elems(N) * sizeof(cpx<double>)));
   CTRY(cudaMemcpyAsync(d_ang, geom->angles_pi, na * sizeof(double), cudaMemcpyHostToDevice, st));
 
   k_geometry<<<(na + 127) / 128, 128, 0, st>>>(d_ang, na, d_th, d_cs);
@@ -337,9 +376,8 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
   k_embed<<<(unsigned)(((long)L * L + 255) / 256), 256, 0, st>>>(g->taps, N, d_emb);
   count_launch(3);
   CTRY(cudaGetLastError());
-  TRY(build_twiddles<double>(twr64, N, st));
-  TRY(build_twiddles<double>(twc64, L, st));
-  TRY(o64.spectrum(d_emb, (cpx<double>*)d_S2, g->Gt64, twr64, twc64, st));
+  TRY(build_fft_tables<double>(tw64, N, st));
+  TRY(o64.spectrum(d_emb, (cpx<double>*)d_S2, g->Gt64, tw64, st));
 
   // per-precision apply state
   CTRY(cudaMalloc(&g->S, (size_t)N * N * 2 * T));
@@ -355,19 +393,16 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
     CTRY(cudaMalloc(&g->Gt32, ng * sizeof(float)));
     k_to_f32<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(g->Gt64, g->Gt32, ng);
     count_launch();
-    CTRY(cudaMalloc(&g->twr, (size_t)N * sizeof(cpx<float>)));
-    CTRY(cudaMalloc(&g->twc, (size_t)L * sizeof(cpx<float>)));
-    TRY(build_twiddles<float>((cpx<float>*)g->twr, N, st));
-    TRY(build_twiddles<float>((cpx<float>*)g->twc, L, st));
+    CTRY(cudaMalloc(&g->tw, (size_t)fft_table_elems(N) * sizeof(cpx<float>)));
+    TRY(build_fft_tables<float>((cpx<float>*)g->tw, N, st));
   } else {
-    g->twr = twr64;
-    g->twc = twc64;
-    twr64 = twc64 = nullptr;
+    g->tw = tw64;
+    tw64 = nullptr;
   }
   CTRY(cudaGetLastError());
   CTRY(cudaStreamSynchronize(st));
   cudaFree(d_ang); cudaFree(d_th); cudaFree(d_cs); cudaFree(d_emb); cudaFree(d_S2);
-  cudaFree(twr64); cudaFree(twc64);
+  cudaFree(tw64);
   *out = g;
   return BSCT_OK;
 }
@@ -398,15 +433,13 @@ extern "C" int bsct_gram_apply(const bsct_gram* g, const void* d_x, void* d_y, i
     if (g->precision != BSCT_F32) return fail(BSCT_ERR_INVALID_ARG, "FFT32 apply needs an F32 handle");
     FftOps<float> o;
     fft_ops_for<float>(g->N, &o);
-    return o.apply((const float*)d_x, (float*)d_y, (cpx<float>*)g->S, g->Gt32, (const cpx<float>*)g->twr,
-                   (const cpx<float>*)g->twc, st);
+    return o.apply((const float*)d_x, (float*)d_y, (cpx<float>*)g->S, g->Gt32, (const cpx<float>*)g->tw, st);
   }
   if (mode == BSCT_APPLY_F64) {
     if (g->precision != BSCT_F64) return fail(BSCT_ERR_INVALID_ARG, "F64 apply needs an F64 handle");
     FftOps<double> o;
     fft_ops_for<double>(g->N, &o);
-    return o.apply((const double*)d_x, (double*)d_y, (cpx<double>*)g->S, g->Gt64, (const cpx<double>*)g->twr,
-                   (const cpx<double>*)g->twc, st);
+    return o.apply((const double*)d_x, (double*)d_y, (cpx<double>*)g->S, g->Gt64, (const cpx<double>*)g->tw, st);
   }
   return fail(BSCT_ERR_INVALID_ARG, "unknown apply mode");
 }

@@ -48,7 +48,7 @@ __device__ __forceinline__ long blk_index(int row, int col, int ncols) {
 template <typename T, int LR, bool PADDED, int RPC>
 __global__ void __launch_bounds__(RPC * (LR / Plan<LR>::E))
 k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
-           const cpx<T>* __restrict__ twr, const cpx<T>* __restrict__ twc) {
+           const cpx<T>* __restrict__ tsf, const cpx<T>* __restrict__ twc) {
   constexpr int E = Plan<LR>::E, TT = LR / E, R1 = Plan<LR>::R[0], RL = Plan<LR>::R[Plan<LR>::NS - 1];
   constexpr int SME = smem_elems<LR>();
   static_assert(R1 % 2 == 0, "zero-padding / crop split needs an even first radix");
@@ -65,11 +65,11 @@ k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
     const int j = tid + b * TT;
 #pragma unroll
     for (int r = 0; r < R1; ++r) {
-      if (PADDED && r >= R1 / 2) v[b * R1 + r] = mk(T(0), T(0));  // z[n] = 0 for n >= LR/2
+      if (PADDED && r >= R1 / 2) v[b * R1 + r] = mk(T(0), T(0));  // z[n] = 0 for n >= LR/2 (never read)
       else v[b * R1 + r] = ld_cpx(z + j + r * (LR / R1));
     }
   }
-  fft<T, LR, false, false>(v, sm, tid, twr);
+  fft<T, LR, false, false, PADDED>(v, sm, tid, tsf);
 #pragma unroll
   for (int b = 0; b < E / RL; ++b) {
     const int j = tid + b * TT;
@@ -104,7 +104,7 @@ k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
 template <typename T, int LR, int RPC>
 __global__ void __launch_bounds__(RPC * (LR / Plan<LR>::E))
 k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
-           const cpx<T>* __restrict__ twr, const cpx<T>* __restrict__ twc) {
+           const cpx<T>* __restrict__ tsr, const cpx<T>* __restrict__ twc) {
   constexpr int E = Plan<LR>::E, TT = LR / E, R1 = Plan<LR>::R[0], RL = Plan<LR>::R[Plan<LR>::NS - 1];
   constexpr int SME = smem_elems<LR>();
   static_assert(R1 % 2 == 0, "zero-padding / crop split needs an even first radix");
@@ -146,7 +146,7 @@ k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
     }
   }
   __syncthreads();
-  fft<T, LR, true, true>(v, sm, tid, twr);
+  fft<T, LR, true, true>(v, sm, tid, tsr);
   cpx<T>* yr = reinterpret_cast<cpx<T>*>(y + (long)(row0 + f) * ld_y);
 #pragma unroll
   for (int b = 0; b < E / R1; ++b) {
@@ -159,80 +159,133 @@ k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
 // ------------------------------------------------------------------------------------
 // K6: per packed column: forward 2N FFT (rows >= N are zero), multiply by the real
 // spectrum, inverse, keep rows < N.  In place on S.
+// Persistent CTAs walk over tiles of G columns; while a tile is transformed, the
+// column data (32-byte row-block chunks) and spectrum rows of the tiles STAGES-1 ahead
+// are already in flight into shared memory (cp.async), so HBM/L2 latency overlaps the
+// FFT arithmetic.
 // ------------------------------------------------------------------------------------
-template <typename T, int LC, int CPC>
-__global__ void __launch_bounds__(CPC * (LC / Plan<LC>::E))
-k_cols_conv(cpx<T>* __restrict__ S, const T* __restrict__ Gt, const cpx<T>* __restrict__ twc) {
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N_> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N_) : "memory");
+}
+
+template <typename T, int LC, int G> __host__ __device__ constexpr int cols_threads() { return G * (LC / Plan<LC>::E); }
+template <typename T, int LC, int G, int STAGES> __host__ __device__ constexpr size_t cols_smem() {
+  return (size_t)G * smem_elems<LC>() * sizeof(cpx<T>) + (size_t)STAGES * G * (LC / 2) * sizeof(cpx<T>) +
+         (size_t)STAGES * G * LC * sizeof(T);
+}
+
+template <typename T, int LC, int G, int STAGES, int MINB>
+__global__ void __launch_bounds__(G*(LC / Plan<LC>::E), MINB)
+k_cols_conv(cpx<T>* __restrict__ S, const T* __restrict__ Gt, const cpx<T>* __restrict__ tsf,
+            const cpx<T>* __restrict__ tsr, int ntiles) {
   constexpr int E = Plan<LC>::E, TT = LC / E, R1 = Plan<LC>::R[0], RL = Plan<LC>::R[Plan<LC>::NS - 1];
+  constexpr int NT = G * TT;
   constexpr int NC = LC / 2;
   constexpr int SME = smem_elems<LC>();
+  constexpr int IN_E = G * NC;  // complex per stage
+  constexpr int GT_E = G * LC;  // reals per stage
+  constexpr int PPC = 4 * (int)sizeof(cpx<T>) / 16;  // 16-byte pieces per 4-row chunk
+  constexpr int RPP = 16 / (int)sizeof(cpx<T>);      // rows per piece
   static_assert(R1 % 2 == 0, "zero-padding / crop split needs an even first radix");
   extern __shared__ __align__(16) unsigned char smraw[];
-  cpx<T>* sm_all = reinterpret_cast<cpx<T>*>(smraw);
-  const int f = threadIdx.x / TT, tid = threadIdx.x % TT;
-  const int col = blockIdx.x * CPC + f;
-  cpx<T>* sm = sm_all + f * SME;
+  cpx<T>* xsm = reinterpret_cast<cpx<T>*>(smraw);
+  cpx<T>* stin = xsm + G * SME;
+  T* stg = reinterpret_cast<T*>(stin + STAGES * IN_E);
+  const int g = threadIdx.x / TT, tid = threadIdx.x % TT;
+  cpx<T>* sm = xsm + g * SME;
 
-  cpx<T> v[E];
-#pragma unroll
-  for (int b = 0; b < E / R1; ++b) {
-    const int j = tid + b * TT;
-#pragma unroll
-    for (int r = 0; r < R1; ++r) {
-      if (r >= R1 / 2) v[b * R1 + r] = mk(T(0), T(0));  // zero-padded rows N..2N-1
-      else v[b * R1 + r] = ld_cpx(S + blk_index(j + r * (LC / R1), col, NC));
+  auto prefetch = [&](int tile, int stage) {
+    if (tile < ntiles) {
+      const int c0 = tile * G;
+      cpx<T>* din = stin + stage * IN_E;
+      for (int q = threadIdx.x; q < (NC / 4) * G * PPC; q += NT) {
+        const int p = q % PPC, gc = (q / PPC) % G, k = q / (PPC * G);
+        cp_async16(din + gc * NC + 4 * k + p * RPP, S + ((long)k * NC + c0 + gc) * 4 + p * RPP);
+      }
+      const T* src = Gt + (long)c0 * LC;
+      T* dg = stg + stage * GT_E;
+      constexpr int EPP = 16 / (int)sizeof(T);
+      for (int q = threadIdx.x; q < GT_E / EPP; q += NT) cp_async16(dg + q * EPP, src + q * EPP);
     }
-  }
-  fft<T, LC, false, false>(v, sm, tid, twc);
+    cp_async_commit();
+  };
 
-  const T* Gc = Gt + (long)col * LC;
-  if (blockIdx.x == 0) {
-    // column 0 holds a + i b (a = DC column, b = Nyquist column): needs Z[-u]
+  int tile = blockIdx.x;
 #pragma unroll
-    for (int b = 0; b < E / RL; ++b) {
-      const int j = tid + b * TT;
-#pragma unroll
-      for (int r = 0; r < RL; ++r) sm[spad(j + r * (LC / RL))] = v[b * RL + r];
-    }
+  for (int s = 0; s < STAGES; ++s) prefetch(tile + s * gridDim.x, s);
+
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    const int stage = it % STAGES;
+    cp_async_wait<STAGES - 1>();
     __syncthreads();
+    const int col = tile * G + g;
+    const cpx<T>* in = stin + stage * IN_E + g * NC;
+    const T* gs = stg + stage * GT_E + g * LC;
+    cpx<T> v[E];
 #pragma unroll
-    for (int b = 0; b < E / RL; ++b) {
+    for (int b = 0; b < E / R1; ++b) {
       const int j = tid + b * TT;
 #pragma unroll
-      for (int r = 0; r < RL; ++r) {
-        const int u = j + r * (LC / RL);
-        const cpx<T> Z = v[b * RL + r];
-        if (f == 0) {
-          const int um = (u == 0) ? 0 : LC - u;
-          const cpx<T> Zm = conj(sm[spad(um)]);
-          const T P = Gt[u], Q = Gt[(long)NC * LC + u];
-          v[b * RL + r] = mk(P * Z.x + Q * Zm.x, P * Z.y + Q * Zm.y);
-        } else {
-          const T g = Gc[u];
-          v[b * RL + r] = mk(g * Z.x, g * Z.y);
+      for (int r = 0; r < R1; ++r)
+        v[b * R1 + r] = (r < R1 / 2) ? in[j + r * (LC / R1)] : mk(T(0), T(0));  // rows >= N are zero
+    }
+    fft<T, LC, false, false, true>(v, sm, tid, tsf);
+    if (tile == 0) {
+      // column 0 holds a + i b (a = DC column, b = Nyquist column): needs Z[-u]
+#pragma unroll
+      for (int b = 0; b < E / RL; ++b) {
+        const int j = tid + b * TT;
+#pragma unroll
+        for (int r = 0; r < RL; ++r) sm[spad(j + r * (LC / RL))] = v[b * RL + r];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int b = 0; b < E / RL; ++b) {
+        const int j = tid + b * TT;
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const int u = j + r * (LC / RL);
+          const cpx<T> Z = v[b * RL + r];
+          if (col == 0) {
+            const int um = (u == 0) ? 0 : LC - u;
+            const cpx<T> Zm = conj(sm[spad(um)]);
+            const T P = gs[u], Q = Gt[(long)NC * LC + u];
+            v[b * RL + r] = mk(P * Z.x + Q * Zm.x, P * Z.y + Q * Zm.y);
+          } else {
+            const T gv = gs[u];
+            v[b * RL + r] = mk(gv * Z.x, gv * Z.y);
+          }
+        }
+      }
+      __syncthreads();
+    } else {
+#pragma unroll
+      for (int b = 0; b < E / RL; ++b) {
+        const int j = tid + b * TT;
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const T gv = gs[j + r * (LC / RL)];
+          v[b * RL + r] = mk(gv * v[b * RL + r].x, gv * v[b * RL + r].y);
         }
       }
     }
-    __syncthreads();
-  } else {
+    fft<T, LC, true, true>(v, sm, tid, tsr);
+    // reversed plan: last radix = forward first radix R1; keep rows < N
 #pragma unroll
-    for (int b = 0; b < E / RL; ++b) {
+    for (int b = 0; b < E / R1; ++b) {
       const int j = tid + b * TT;
 #pragma unroll
-      for (int r = 0; r < RL; ++r) {
-        const T g = Gc[j + r * (LC / RL)];
-        v[b * RL + r] = mk(g * v[b * RL + r].x, g * v[b * RL + r].y);
-      }
+      for (int r = 0; r < R1 / 2; ++r) st_cpx(S + blk_index(j + r * (LC / R1), col, NC), v[b * R1 + r]);
     }
+    __syncthreads();  // staging[stage] and the exchange buffer are free again
+    prefetch(tile + STAGES * gridDim.x, stage);
   }
-  fft<T, LC, true, true>(v, sm, tid, twc);
-  // reversed plan: last radix = forward first radix R1
-#pragma unroll
-  for (int b = 0; b < E / R1; ++b) {
-    const int j = tid + b * TT;
-#pragma unroll
-    for (int r = 0; r < R1 / 2; ++r) st_cpx(S + blk_index(j + r * (LC / R1), col, NC), v[b * R1 + r]);
-  }
+  cp_async_wait<0>();
 }
 
 // ------------------------------------------------------------------------------------
@@ -240,7 +293,7 @@ k_cols_conv(cpx<T>* __restrict__ S, const T* __restrict__ Gt, const cpx<T>* __re
 // ------------------------------------------------------------------------------------
 template <typename T, int LC, int CPC>
 __global__ void __launch_bounds__(CPC * (LC / Plan<LC>::E))
-k_cols_fwd_real(const cpx<T>* __restrict__ S2, T* __restrict__ Gt, const cpx<T>* __restrict__ twc, T sc) {
+k_cols_fwd_real(const cpx<T>* __restrict__ S2, T* __restrict__ Gt, const cpx<T>* __restrict__ tsf, T sc) {
   constexpr int E = Plan<LC>::E, TT = LC / E, R1 = Plan<LC>::R[0], RL = Plan<LC>::R[Plan<LC>::NS - 1];
   constexpr int NC = LC / 2;
   constexpr int SME = smem_elems<LC>();
@@ -258,7 +311,7 @@ k_cols_fwd_real(const cpx<T>* __restrict__ S2, T* __restrict__ Gt, const cpx<T>*
 #pragma unroll
     for (int r = 0; r < R1; ++r) v[b * R1 + r] = ld_cpx(S2 + blk_index(j + r * (LC / R1), col, NC));
   }
-  fft<T, LC, false, false>(v, sm, tid, twc);
+  fft<T, LC, false, false>(v, sm, tid, tsf);
   if (blockIdx.x == 0) {
 #pragma unroll
     for (int b = 0; b < E / RL; ++b) {
@@ -300,30 +353,67 @@ template <typename K> static int set_smem(K kern, size_t bytes) {
   return BSCT_OK;
 }
 
+// twiddle tables of one size N, packed in one array (see FftTables)
+template <typename T> struct TwPtrs {
+  const cpx<T>*untangle, *rows_f, *rows_r, *cols_f, *cols_r;
+};
+template <typename T> __host__ inline TwPtrs<T> tw_ptrs(const cpx<T>* tw, int N) {
+  TwPtrs<T> p;
+  p.untangle = tw;
+  p.rows_f = tw + 2 * N;
+  p.rows_r = tw + 3 * N;
+  p.cols_f = tw + 4 * N;
+  p.cols_r = tw + 6 * N;
+  return p;
+}
+
+template <typename T, int LC> struct ColsCfg {
+  static constexpr int TT = LC / Plan<LC>::E;
+  static constexpr int G = TT >= 256 ? 1 : (256 / TT > LC / 2 ? LC / 2 : 256 / TT);
+  static constexpr int STAGES = cols_smem<T, LC, G, 2>() <= 227 * 1024 ? 2 : 1;
+  static constexpr int MINB = (cols_smem<T, LC, G, STAGES>() * 2 <= 227 * 1024 && sizeof(T) == 4) ? 2 : 1;
+};
+
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
 template <typename T, int N>
-static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* twr, const cpx<T>* twc,
-                      cudaStream_t st) {
+static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw, cudaStream_t st) {
   constexpr int LR = N, LC = 2 * N;
   constexpr int RPC = rows_per_cta<LR>();
-  constexpr int CPC = cols_per_cta<T, LC>();
-  static_assert(N % RPC == 0 && N % CPC == 0, "tile must divide N");
-  constexpr int TR = RPC * (LR / Plan<LR>::E), TC = CPC * (LC / Plan<LC>::E);
+  typedef ColsCfg<T, LC> CC;
+  static_assert(N % RPC == 0 && N % CC::G == 0, "tile must divide N");
+  constexpr int TR = RPC * (LR / Plan<LR>::E), TC = cols_threads<T, LC, CC::G>();
   const size_t smr = (size_t)RPC * smem_elems<LR>() * sizeof(cpx<T>);
-  const size_t smc = (size_t)CPC * smem_elems<LC>() * sizeof(cpx<T>);
-  static bool attr_done = false;
-  if (!attr_done) {
+  constexpr size_t smc = cols_smem<T, LC, CC::G, CC::STAGES>();
+  auto kc = k_cols_conv<T, LC, CC::G, CC::STAGES, CC::MINB>;
+  static int grid_c = 0;
+  if (grid_c == 0) {
     int rc = set_smem(k_rows_r2c<T, LR, true, RPC>, smr);
     if (rc == BSCT_OK) rc = set_smem(k_rows_c2r<T, LR, RPC>, smr);
-    if (rc == BSCT_OK) rc = set_smem(k_cols_conv<T, LC, CPC>, smc);
+    if (rc == BSCT_OK) rc = set_smem(kc, smc);
     if (rc != BSCT_OK) return rc;
-    attr_done = true;
+    int per_sm = 0;
+    BSCT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc, TC, smc));
+    if (per_sm < 1) per_sm = 1;
+    const int tiles = N / CC::G;
+    grid_c = per_sm * sm_count() < tiles ? per_sm * sm_count() : tiles;
   }
+  const TwPtrs<T> t = tw_ptrs(tw, N);
   timer_mark(st, 0);
-  k_rows_r2c<T, LR, true, RPC><<<N / RPC, TR, smr, st>>>(x, N, S, twr, twc);
+  k_rows_r2c<T, LR, true, RPC><<<N / RPC, TR, smr, st>>>(x, N, S, t.rows_f, t.untangle);
   timer_mark(st, 1);
-  k_cols_conv<T, LC, CPC><<<N / CPC, TC, smc, st>>>(S, Gt, twc);
+  kc<<<grid_c, TC, smc, st>>>(S, Gt, t.cols_f, t.cols_r, N / CC::G);
   timer_mark(st, 2);
-  k_rows_c2r<T, LR, RPC><<<N / RPC, TR, smr, st>>>(S, y, N, twr, twc);
+  k_rows_c2r<T, LR, RPC><<<N / RPC, TR, smr, st>>>(S, y, N, t.rows_r, t.untangle);
   timer_mark(st, 3);
   count_launch(3);
   BSCT_CUDA_TRY(cudaGetLastError());
@@ -331,8 +421,7 @@ static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw
 }
 
 template <typename T, int N>
-static int spectrum_impl(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* twr, const cpx<T>* twc,
-                         cudaStream_t st) {
+static int spectrum_impl(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* tw, cudaStream_t st) {
   constexpr int LR = N, LC = 2 * N;
   constexpr int RPC = rows_per_cta<LR>();
   constexpr int CPC = cols_per_cta<T, LC>();
@@ -346,8 +435,9 @@ static int spectrum_impl(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* twr, con
     if (rc != BSCT_OK) return rc;
     attr_done = true;
   }
-  k_rows_r2c<T, LR, false, RPC><<<LC / RPC, TR, smr, st>>>(emb, LC, S2, twr, twc);
-  k_cols_fwd_real<T, LC, CPC><<<N / CPC, TC, smc, st>>>(S2, Gt, twc, T(1.0 / ((double)LC * (double)LC)));
+  const TwPtrs<T> t = tw_ptrs(tw, N);
+  k_rows_r2c<T, LR, false, RPC><<<LC / RPC, TR, smr, st>>>(emb, LC, S2, t.rows_f, t.untangle);
+  k_cols_fwd_real<T, LC, CPC><<<N / CPC, TC, smc, st>>>(S2, Gt, t.cols_f, T(1.0 / ((double)LC * (double)LC)));
   count_launch(2);
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
