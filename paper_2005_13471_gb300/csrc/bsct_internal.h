@@ -38,6 +38,11 @@ inline void timer_mark(cudaStream_t st, int i) {
 //        order; N each) and of the column plan (2N each)
 template <typename T> struct FftOps {
   int (*apply)(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw, cudaStream_t st);
+  // CG step q = G p with p = r + beta p done in the first pass (p overwritten) and the
+  // per-CTA partial sums of <p, q> written to part[0 .. cg_partials)
+  int (*apply_cg)(const T* r, T* p, T* q, const double* beta, double* part, cpx<T>* S, const T* Gt,
+                  const cpx<T>* tw, cudaStream_t st);
+  int cg_partials;
   // emb: 2N x 2N real circulant kernel; S2: 2N x N complex scratch; writes Gt (scaled)
   int (*spectrum)(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* tw, cudaStream_t st);
 };

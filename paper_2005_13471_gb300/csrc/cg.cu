@@ -3,11 +3,11 @@
 // products reduced in FP64 and the step scalars alpha, beta kept in FP64 in device
 // memory, so an iteration never waits for the host:
 //
-//   q = G p                              (gram apply, 3 kernels)
-//   pq = <p, q>;  alpha = rr / pq        (k_dot partials + k_finish)
+//   p = r + beta p; q = G p; <p, q>     (gram apply with the update fused into its
+//                                         first pass and the inner product into its
+//                                         last pass, 3 kernels) ; alpha = rr / pq
 //   x += alpha p;  r -= alpha q;  <r, r> (k_xr_update partials + k_finish)
-//   beta = rr_new / rr;  rr = rr_new
-//   p = r + beta p                       (k_p_update)
+//   beta = rr_new / rr;  rr = rr_new     (beta = 0 before the first iteration)
 #include "bsct_internal.h"
 
 namespace bsct {
@@ -69,14 +69,32 @@ __global__ void __launch_bounds__(RED_THREADS) k_finish(const double* __restrict
   }
 }
 
-// x += alpha p; r -= alpha q; partial <r, r>
+// x += alpha p; r -= alpha q; partial <r, r>  (4 elements per thread step)
+template <typename T> struct V4;
+template <> struct V4<float> { typedef float4 t; };
+template <> struct V4<double> { typedef double4 t; };
+
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_xr_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
                                                            const T* __restrict__ q, const double* __restrict__ sc, long n,
                                                            double* __restrict__ part) {
+  typedef typename V4<T>::t v4;
   const T alpha = T(sc[SC_ALPHA]);
   double acc = 0.0;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+  const long n4 = n / 4;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long)gridDim.x * blockDim.x) {
+    v4 xv = reinterpret_cast<v4*>(x)[i], rv = reinterpret_cast<v4*>(r)[i];
+    const v4 pv = reinterpret_cast<const v4*>(p)[i], qv = reinterpret_cast<const v4*>(q)[i];
+    xv.x = fma(alpha, pv.x, xv.x); xv.y = fma(alpha, pv.y, xv.y);
+    xv.z = fma(alpha, pv.z, xv.z); xv.w = fma(alpha, pv.w, xv.w);
+    rv.x = fma(-alpha, qv.x, rv.x); rv.y = fma(-alpha, qv.y, rv.y);
+    rv.z = fma(-alpha, qv.z, rv.z); rv.w = fma(-alpha, qv.w, rv.w);
+    reinterpret_cast<v4*>(x)[i] = xv;
+    reinterpret_cast<v4*>(r)[i] = rv;
+    const T s4 = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+    acc += (double)s4;
+  }
+  for (long i = n4 * 4 + (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     x[i] = fma(alpha, p[i], x[i]);
     const T ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
@@ -84,13 +102,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_xr_update(T* __restrict__ x, T*
   }
   acc = block_sum(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
-}
-
-template <typename T>
-__global__ void k_p_update(T* __restrict__ p, const T* __restrict__ r, const double* __restrict__ sc, long n) {
-  const T beta = T(sc[SC_BETA]);
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    p[i] = fma(beta, p[i], r[i]);
 }
 
 // r = b - q (q = G x0), p = r
@@ -138,6 +149,7 @@ static int cg_begin_t(bsct_gram* g, const T* b, T* x, int x0_is_zero, cudaStream
     if (rc != BSCT_OK) return rc;
   }
   k_init_r<T><<<nb, RED_THREADS, 0, st>>>(b, q, r, p, n, x0_is_zero ? 0 : 1);
+  BSCT_CUDA_TRY(cudaMemsetAsync(g->scal + SC_BETA, 0, sizeof(double), st));  // first direction p = r
   k_dot<T><<<nb, RED_THREADS, 0, st>>>(r, r, n, g->partials);
   k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_STORE_RR);
   k_dot<T><<<nb, RED_THREADS, 0, st>>>(b, b, n, g->partials);
@@ -154,15 +166,17 @@ static int cg_iter_t(bsct_gram* g, T* x, int n_iter, cudaStream_t st) {
   T* r = (T*)g->r;
   T* p = (T*)g->p;
   T* q = (T*)g->q;
+  FftOps<T> o;
+  if (!fft_ops_for<T>(g->N, &o)) return BSCT_ERR_UNSUPPORTED_SIZE;
+  const T* Gt = (g->precision == BSCT_F32) ? (const T*)(const void*)g->Gt32 : (const T*)(const void*)g->Gt64;
+  if (o.cg_partials > g->n_partials) return BSCT_ERR_UNSUPPORTED_SIZE;
   for (int it = 0; it < n_iter; ++it) {
-    int rc = apply_g(g, p, q, st);
+    int rc = o.apply_cg(r, p, q, g->scal + SC_BETA, g->partials, (cpx<T>*)g->S, Gt, (const cpx<T>*)g->tw, st);
     if (rc != BSCT_OK) return rc;
-    k_dot<T><<<nb, RED_THREADS, 0, st>>>(p, q, n, g->partials);
-    k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_ALPHA);
+    k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, o.cg_partials, g->scal, OP_ALPHA);
     k_xr_update<T><<<nb, RED_THREADS, 0, st>>>(x, r, p, q, g->scal, n, g->partials);
     k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_BETA);
-    k_p_update<T><<<nb, RED_THREADS, 0, st>>>(p, r, g->scal, n);
-    count_launch(5);
+    count_launch(3);
   }
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;

@@ -37,6 +37,13 @@ template <typename T, int LC> __host__ __device__ constexpr int cols_per_cta() {
                                    : ((256 / (LC / Plan<LC>::E)) > 8 ? 8 : (256 / (LC / Plan<LC>::E)));
 }
 
+// per-row shared region of the row kernels: the FFT buffer plus 8 words, so that the
+// four rows of a block start on different banks (the untangle phase reads the same
+// index of all four rows in one warp)
+template <typename T, int LR> __host__ __device__ constexpr int row_region() {
+  return smem_elems<LR>() + 8 / (int)(sizeof(cpx<T>) / 4);
+}
+
 __device__ __forceinline__ long blk_index(int row, int col, int ncols) {
   return ((long)(row >> 2) * ncols + col) * 4 + (row & 3);
 }
@@ -45,12 +52,15 @@ __device__ __forceinline__ long blk_index(int row, int col, int ncols) {
 // K5: real rows -> packed half spectra.  PADDED: the row holds LR reals (zero-padded to
 // 2 LR); otherwise it holds 2 LR reals.  Row r of x starts at x + r * ld_x.
 // ------------------------------------------------------------------------------------
-template <typename T, int LR, bool PADDED, int RPC>
+// CG: the row is p_new = x + beta * p_old (x = the CG residual r), written to p_new
+// and transformed (the CG direction update fused into the first FFT pass)
+template <typename T, int LR, bool PADDED, int RPC, bool CG = false>
 __global__ void __launch_bounds__(RPC * (LR / Plan<LR>::E))
 k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
-           const cpx<T>* __restrict__ tsf, const cpx<T>* __restrict__ twc) {
+           const cpx<T>* __restrict__ tsf, const cpx<T>* __restrict__ twc, const T* p_old = nullptr,
+           T* p_new = nullptr, const double* __restrict__ cg_beta = nullptr) {
   constexpr int E = Plan<LR>::E, TT = LR / E, R1 = Plan<LR>::R[0], RL = Plan<LR>::R[Plan<LR>::NS - 1];
-  constexpr int SME = smem_elems<LR>();
+  constexpr int SME = row_region<T, LR>();
   static_assert(R1 % 2 == 0, "zero-padding / crop split needs an even first radix");
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* sm_all = reinterpret_cast<cpx<T>*>(smraw);
@@ -58,6 +68,9 @@ k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
   const int row0 = blockIdx.x * RPC;
   cpx<T>* sm = sm_all + f * SME;
   const cpx<T>* z = reinterpret_cast<const cpx<T>*>(x + (long)(row0 + f) * ld_x);
+  const cpx<T>* zp = CG ? reinterpret_cast<const cpx<T>*>(p_old + (long)(row0 + f) * ld_x) : nullptr;
+  cpx<T>* zn = CG ? reinterpret_cast<cpx<T>*>(p_new + (long)(row0 + f) * ld_x) : nullptr;
+  const T beta = CG ? T(*cg_beta) : T(0);
 
   cpx<T> v[E];
 #pragma unroll
@@ -65,8 +78,17 @@ k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
     const int j = tid + b * TT;
 #pragma unroll
     for (int r = 0; r < R1; ++r) {
-      if (PADDED && r >= R1 / 2) v[b * R1 + r] = mk(T(0), T(0));  // z[n] = 0 for n >= LR/2 (never read)
-      else v[b * R1 + r] = ld_cpx(z + j + r * (LR / R1));
+      if (PADDED && r >= R1 / 2) {
+        v[b * R1 + r] = mk(T(0), T(0));  // z[n] = 0 for n >= LR/2 (never read)
+      } else if constexpr (CG) {
+        const int n = j + r * (LR / R1);
+        const cpx<T> a = ld_cpx(z + n), pp = ld_cpx(zp + n);
+        const cpx<T> pn = mk(fma(beta, pp.x, a.x), fma(beta, pp.y, a.y));
+        st_cpx(zn + n, pn);
+        v[b * R1 + r] = pn;
+      } else {
+        v[b * R1 + r] = ld_cpx(z + j + r * (LR / R1));
+      }
     }
   }
   fft<T, LR, false, false, PADDED>(v, sm, tid, tsf);
@@ -101,12 +123,14 @@ k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
 // ------------------------------------------------------------------------------------
 // K7: packed half spectra -> real rows, first LR outputs of 2 LR (crop)
 // ------------------------------------------------------------------------------------
-template <typename T, int LR, int RPC>
+// CG: also accumulate <p, y> over the block (p = the apply's input) into part[blockIdx.x]
+template <typename T, int LR, int RPC, bool CG = false>
 __global__ void __launch_bounds__(RPC * (LR / Plan<LR>::E))
 k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
-           const cpx<T>* __restrict__ tsr, const cpx<T>* __restrict__ twc) {
+           const cpx<T>* __restrict__ tsr, const cpx<T>* __restrict__ twc, const T* __restrict__ p = nullptr,
+           double* __restrict__ part = nullptr) {
   constexpr int E = Plan<LR>::E, TT = LR / E, R1 = Plan<LR>::R[0], RL = Plan<LR>::R[Plan<LR>::NS - 1];
-  constexpr int SME = smem_elems<LR>();
+  constexpr int SME = row_region<T, LR>();
   static_assert(R1 % 2 == 0, "zero-padding / crop split needs an even first radix");
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* sm_all = reinterpret_cast<cpx<T>*>(smraw);
@@ -148,11 +172,44 @@ k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
   __syncthreads();
   fft<T, LR, true, true>(v, sm, tid, tsr);
   cpx<T>* yr = reinterpret_cast<cpx<T>*>(y + (long)(row0 + f) * ld_y);
+  T dot = T(0);
 #pragma unroll
   for (int b = 0; b < E / R1; ++b) {
     const int j = tid + b * TT;
 #pragma unroll
-    for (int r = 0; r < R1 / 2; ++r) st_cpx(yr + j + r * (LR / R1), v[b * R1 + r]);
+    for (int r = 0; r < R1 / 2; ++r) {
+      st_cpx(yr + j + r * (LR / R1), v[b * R1 + r]);
+      if constexpr (CG) {
+        const cpx<T> pp = ld_cpx(reinterpret_cast<const cpx<T>*>(p + (long)(row0 + f) * ld_y) + j + r * (LR / R1));
+        dot = fma(pp.x, v[b * R1 + r].x, fma(pp.y, v[b * R1 + r].y, dot));
+      }
+    }
+  }
+  if constexpr (CG) {
+    // block sum in FP64 (the per-thread part is <= 16 products)
+    constexpr int NTH = RPC * TT;
+    double d = (double)dot;
+    __syncthreads();  // the exchange buffer is free: reuse it for the partial sums
+    double* ws = reinterpret_cast<double*>(sm_all);
+    if constexpr (NTH % 32 == 0) {
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+      if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = d;
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        constexpr int NW = NTH / 32;
+        double t = threadIdx.x < NW ? ws[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+      }
+    } else {
+      ws[threadIdx.x] = d;  // blocks of fewer than 32 threads (N = 16)
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < NTH; ++i) t += ws[i];
+        part[blockIdx.x] = t;
+      }
+    }
   }
 }
 
@@ -392,7 +449,7 @@ static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw
   typedef ColsCfg<T, LC> CC;
   static_assert(N % RPC == 0 && N % CC::G == 0, "tile must divide N");
   constexpr int TR = RPC * (LR / Plan<LR>::E), TC = cols_threads<T, LC, CC::G>();
-  const size_t smr = (size_t)RPC * smem_elems<LR>() * sizeof(cpx<T>);
+  const size_t smr = (size_t)RPC * row_region<T, LR>() * sizeof(cpx<T>);
   constexpr size_t smc = cols_smem<T, LC, CC::G, CC::STAGES>();
   auto kc = k_cols_conv<T, LC, CC::G, CC::STAGES, CC::MINB>;
   static int grid_c = 0;
@@ -420,13 +477,47 @@ static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw
   return BSCT_OK;
 }
 
+// q = G p for CG with the direction update and <p, q> fused into the row passes:
+//   K5: p = r + beta p (beta from the device), written back and transformed
+//   K7: q written, per-CTA partial sums of <p, q> into part[0 .. N/RPC)
+template <typename T, int N>
+static int apply_cg_impl(const T* r, T* p, T* q, const double* beta, double* part, cpx<T>* S, const T* Gt,
+                         const cpx<T>* tw, cudaStream_t st) {
+  constexpr int LR = N, LC = 2 * N;
+  constexpr int RPC = rows_per_cta<LR>();
+  typedef ColsCfg<T, LC> CC;
+  constexpr int TR = RPC * (LR / Plan<LR>::E), TC = cols_threads<T, LC, CC::G>();
+  const size_t smr = (size_t)RPC * row_region<T, LR>() * sizeof(cpx<T>);
+  constexpr size_t smc = cols_smem<T, LC, CC::G, CC::STAGES>();
+  auto kc = k_cols_conv<T, LC, CC::G, CC::STAGES, CC::MINB>;
+  static int grid_c = 0;
+  if (grid_c == 0) {
+    int rc = set_smem(k_rows_r2c<T, LR, true, RPC, true>, smr);
+    if (rc == BSCT_OK) rc = set_smem(k_rows_c2r<T, LR, RPC, true>, smr);
+    if (rc == BSCT_OK) rc = set_smem(kc, smc);
+    if (rc != BSCT_OK) return rc;
+    int per_sm = 0;
+    BSCT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc, TC, smc));
+    if (per_sm < 1) per_sm = 1;
+    const int tiles = N / CC::G;
+    grid_c = per_sm * sm_count() < tiles ? per_sm * sm_count() : tiles;
+  }
+  const TwPtrs<T> t = tw_ptrs(tw, N);
+  k_rows_r2c<T, LR, true, RPC, true><<<N / RPC, TR, smr, st>>>(r, N, S, t.rows_f, t.untangle, p, p, beta);
+  kc<<<grid_c, TC, smc, st>>>(S, Gt, t.cols_f, t.cols_r, N / CC::G);
+  k_rows_c2r<T, LR, RPC, true><<<N / RPC, TR, smr, st>>>(S, q, N, t.rows_r, t.untangle, p, part);
+  count_launch(3);
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
 template <typename T, int N>
 static int spectrum_impl(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* tw, cudaStream_t st) {
   constexpr int LR = N, LC = 2 * N;
   constexpr int RPC = rows_per_cta<LR>();
   constexpr int CPC = cols_per_cta<T, LC>();
   constexpr int TR = RPC * (LR / Plan<LR>::E), TC = CPC * (LC / Plan<LC>::E);
-  const size_t smr = (size_t)RPC * smem_elems<LR>() * sizeof(cpx<T>);
+  const size_t smr = (size_t)RPC * row_region<T, LR>() * sizeof(cpx<T>);
   const size_t smc = (size_t)CPC * smem_elems<LC>() * sizeof(cpx<T>);
   static bool attr_done = false;
   if (!attr_done) {
@@ -446,6 +537,8 @@ static int spectrum_impl(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* tw, cuda
 template <typename T, int N> FftOps<T> fft_ops() {
   FftOps<T> o;
   o.apply = &apply_impl<T, N>;
+  o.apply_cg = &apply_cg_impl<T, N>;
+  o.cg_partials = N / rows_per_cta<N>();
   o.spectrum = &spectrum_impl<T, N>;
   return o;
 }
