@@ -168,6 +168,27 @@ int bsct_cg_iterate(bsct_gram* g, void* d_x, int n_iter, void* stream);
 /* Copy the current recursive squared residual ||r||^2 and ||b||^2 to host (synchronous). */
 int bsct_cg_residual(const bsct_gram* g, double* rr, double* bb, void* stream);
 
+/* Batched reconstruction of many independent slices (FP32).  Each slice i has its own
+ * geometry geoms[i] (sizes, views, detector, blur may all differ; slices with an
+ * identical geometry share one Gram filter and one set of back-projection tables).
+ * bsct_batch_create builds the shared filters / tables and every slice's CG state
+ * (synchronous; library-owned memory, released by bsct_batch_free).
+ * bsct_batch_solve runs, for every slice, the back projection of its sinogram
+ * (Sec. 5) and cg_iters CG iterations on G x = b from x = 0 (Sec. 2, Sec. 4): the
+ * whole batch is recorded once into a CUDA graph whose per-slice branches run
+ * concurrently, and replayed with a single graph launch on the stream; it is
+ * re-recorded only when a pointer or cg_iters changes.  Asynchronous.
+ *   d_sino: HOST array of n_slices DEVICE pointers to float [n_angles_i][n_bins_i];
+ *   d_x:    HOST array of n_slices DEVICE pointers to float [N_i][N_i] (outputs).
+ * Buffers must stay valid while the batch may replay them.  Errors as elsewhere. */
+typedef struct bsct_batch bsct_batch;
+int bsct_batch_create(int32_t n_slices, const bsct_geom* geoms, bsct_batch** out, void* stream);
+int bsct_batch_solve(bsct_batch* b, const float* const* d_sino, float* const* d_x, int cg_iters, void* stream);
+/* Distinct geometries, nodes of the recorded graph, kernels per replay. */
+int bsct_batch_info(const bsct_batch* b, int* n_geometries, long long* graph_nodes,
+                    long long* kernels_per_launch);
+void bsct_batch_free(bsct_batch* b);
+
 /* Human-readable text of a status code, and of the last failure on this thread. */
 const char* bsct_status_string(int status);
 const char* bsct_last_error_string(void);

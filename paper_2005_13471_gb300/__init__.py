@@ -80,6 +80,15 @@ def _declare(L):
     L.bsct_status_string.restype = ctypes.c_char_p
     L.bsct_last_error_string.argtypes = []
     L.bsct_last_error_string.restype = ctypes.c_char_p
+    L.bsct_batch_create.argtypes = [i32, gp, ctypes.POINTER(vp), vp]
+    L.bsct_batch_create.restype = ctypes.c_int
+    L.bsct_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, vp]
+    L.bsct_batch_solve.restype = ctypes.c_int
+    L.bsct_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong),
+                                  ctypes.POINTER(ctypes.c_longlong)]
+    L.bsct_batch_info.restype = ctypes.c_int
+    L.bsct_batch_free.argtypes = [vp]
+    L.bsct_batch_free.restype = None
     L.bsct_set_kernel_timing.argtypes = [ctypes.c_int]
     L.bsct_set_kernel_timing.restype = ctypes.c_int
     L.bsct_kernel_times.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_int]
@@ -298,3 +307,44 @@ def backproject(geom, sino, precision=F32, out=None, work=None):
 
 def cg_solve(gram, b, x0=None, max_iter=100, rel_tol=0.0, check_every=10):
     return gram.cg_solve(b, x0, max_iter, rel_tol, check_every)
+
+
+class Batch:
+    """Many independent FP32 slices (own geometry each) solved by one CUDA-graph launch."""
+
+    def __init__(self, geoms):
+        self.geoms = list(geoms)
+        arr = (_Geom * len(self.geoms))(*[g._c for g in self.geoms])
+        self._arr = arr
+        self._h = ctypes.c_void_p()
+        _check(lib().bsct_batch_create(len(self.geoms), arr, ctypes.byref(self._h), _stream()), "bsct_batch_create")
+
+    def solve(self, sinos, xs=None, cg_iters=50):
+        """Back projection + cg_iters CG iterations for every slice; returns the list of x."""
+        import torch
+
+        if xs is None:
+            xs = [torch.empty((g.N, g.N), dtype=torch.float32, device=s.device) for g, s in zip(self.geoms, sinos)]
+        ps = (ctypes.c_void_p * len(sinos))(*[_dev(s, (g.n_angles, g.n_bins), torch.float32, "sino").value
+                                             for g, s in zip(self.geoms, sinos)])
+        px = (ctypes.c_void_p * len(xs))(*[_dev(x, (g.N, g.N), torch.float32, "x").value
+                                          for g, x in zip(self.geoms, xs)])
+        _check(lib().bsct_batch_solve(self._h, ps, px, int(cg_iters), _stream()), "bsct_batch_solve")
+        return xs
+
+    def info(self):
+        ng, nodes, kern = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(lib().bsct_batch_info(self._h, ctypes.byref(ng), ctypes.byref(nodes), ctypes.byref(kern)),
+               "bsct_batch_info")
+        return {"geometries": ng.value, "graph_nodes": nodes.value, "kernels_per_launch": kern.value}
+
+    def close(self):
+        if self._h:
+            lib().bsct_batch_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

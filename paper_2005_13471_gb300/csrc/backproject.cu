@@ -281,31 +281,66 @@ extern "C" int bsct_backproject_workspace(const bsct_geom* geom, int precision, 
   return BSCT_OK;
 }
 
+namespace bsct {
+// per-geometry part: view tables (device angles in p.ang must already be uploaded)
+template <typename T> int bp_make_tables(const BpPlan& p, cudaStream_t st) {
+  BSCT_CUDA_TRY(cudaMemsetAsync(p.status, 0, sizeof(int), st));
+  const double tol = sizeof(T) == 4 ? 1e-6 : 1e-12;
+  k_bp_tables<T><<<p.na, 256, 0, st>>>(p.ang, p.N, p.M, p.lambda, p.zeta, tol, (T*)p.tab, p.p00, p.csl, p.status);
+  count_launch();
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+// per-sinogram part: prefilter into ct ([na][M] scratch), then gather into b
+template <typename T> int bp_apply(const BpPlan& p, const T* sino, T* ct, T* b, cudaStream_t st) {
+  dim3 gp((p.M + 127) / 128, p.na);
+  k_prefilter<T><<<gp, 128, 0, st>>>(p.ang, sino, p.na, p.M, p.zeta, ct);
+  dim3 gg((p.N + BP_TX - 1) / BP_TX, (p.N + BP_TY - 1) / BP_TY);
+  k_bp_gather<T><<<gg, BP_TX * BP_TY, 0, st>>>((const T*)p.tab, p.csl, p.p00, ct, p.na, p.N, p.M, b);
+  count_launch(2);
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+template int bp_make_tables<float>(const BpPlan&, cudaStream_t);
+template int bp_make_tables<double>(const BpPlan&, cudaStream_t);
+template int bp_apply<float>(const BpPlan&, const float*, float*, float*, cudaStream_t);
+template int bp_apply<double>(const BpPlan&, const double*, double*, double*, cudaStream_t);
+
+size_t bp_table_bytes(int n_angles, int precision) {
+  return (size_t)n_angles * BP_STRIDE * (precision == BSCT_F32 ? 4 : 8);
+}
+}  // namespace bsct
+
 template <typename T>
 static int bp_run(const bsct_geom* g, const T* sino, T* b, char* work, cudaStream_t st) {
   const int na = g->n_angles, M = g->n_bins, N = g->N;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  double* d_ang = (double*)work;
+  BpPlan p;
+  p.N = N; p.na = na; p.M = M; p.lambda = g->lambda_y; p.zeta = g->zeta_blur;
+  p.ang = (double*)work;
   work += al((size_t)na * sizeof(double));
-  double* d_p00 = (double*)work;
+  p.p00 = (double*)work;
   work += al((size_t)na * sizeof(double));
-  double2* d_csl = (double2*)work;
+  p.csl = (double2*)work;
   work += al((size_t)na * sizeof(double2));
-  T* d_tab = (T*)work;
+  p.tab = work;
   work += al((size_t)na * BP_STRIDE * sizeof(T));
   T* d_ct = (T*)work;
   work += al((size_t)na * M * sizeof(T));
-  int* d_status = (int*)work;
-  BSCT_CUDA_TRY(cudaMemcpyAsync(d_ang, g->angles_pi, na * sizeof(double), cudaMemcpyHostToDevice, st));
-  BSCT_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), st));
-  const double tol = sizeof(T) == 4 ? 1e-6 : 1e-12;
-  k_bp_tables<T><<<na, 256, 0, st>>>(d_ang, N, M, g->lambda_y, g->zeta_blur, tol, d_tab, d_p00, d_csl, d_status);
-  dim3 gp((M + 127) / 128, na);
-  k_prefilter<T><<<gp, 128, 0, st>>>(d_ang, sino, na, M, g->zeta_blur, d_ct);
-  dim3 gg((N + BP_TX - 1) / BP_TX, (N + BP_TY - 1) / BP_TY);
-  k_bp_gather<T><<<gg, BP_TX * BP_TY, 0, st>>>(d_tab, d_csl, d_p00, d_ct, na, N, M, b);
-  count_launch(3);
-  BSCT_CUDA_TRY(cudaGetLastError());
+  p.status = (int*)work;
+  BSCT_CUDA_TRY(cudaMemcpyAsync(p.ang, g->angles_pi, na * sizeof(double), cudaMemcpyHostToDevice, st));
+  int rc = bp_make_tables<T>(p, st);
+  if (rc != BSCT_OK) return rc;
+  return bp_apply<T>(p, sino, d_ct, b, st);
+}
+
+int bsct_check_bp_geom(const bsct_geom* geom) {
+  if (geom->N < 1 || geom->N > 16384) { bsct_set_last_message("N out of range"); return BSCT_ERR_UNSUPPORTED_SIZE; }
+  // widest kernel: |c| + |s| <= sqrt(2), degree <= 2
+  const double W = 1.4142135623730951 + geom->zeta_blur + 3.0 * geom->lambda_y;
+  int J0, nJ;
+  bp_jrange(W, geom->lambda_y, &J0, &nJ);
+  if (nJ > BP_NJMAX) { bsct_set_last_message("lambda_y too small: too many samples per pixel"); return BSCT_ERR_UNSUPPORTED_SIZE; }
   return BSCT_OK;
 }
 
@@ -314,14 +349,10 @@ extern "C" int bsct_backproject(const bsct_geom* geom, const void* d_sino, void*
   int rc = bsct_check_geom(geom);
   if (rc != BSCT_OK) return rc;
   if (!d_sino || !d_b || !d_work) { bsct_set_last_message("NULL device pointer"); return BSCT_ERR_INVALID_ARG; }
-  if (geom->N < 1 || geom->N > 16384) { bsct_set_last_message("N out of range"); return BSCT_ERR_UNSUPPORTED_SIZE; }
   if (precision != BSCT_F32 && precision != BSCT_F64) { bsct_set_last_message("precision"); return BSCT_ERR_INVALID_ARG; }
+  rc = bsct_check_bp_geom(geom);
+  if (rc != BSCT_OK) return rc;
   if (work_bytes < bp_workspace(geom, precision)) { bsct_set_last_message("workspace too small"); return BSCT_ERR_INVALID_ARG; }
-  // widest kernel: |c| + |s| <= sqrt(2), degree <= 2
-  const double W = 1.4142135623730951 + geom->zeta_blur + 3.0 * geom->lambda_y;
-  int J0, nJ;
-  bp_jrange(W, geom->lambda_y, &J0, &nJ);
-  if (nJ > BP_NJMAX) { bsct_set_last_message("lambda_y too small: too many samples per pixel"); return BSCT_ERR_UNSUPPORTED_SIZE; }
   cudaStream_t st = (cudaStream_t)stream;
   if (precision == BSCT_F32) return bp_run<float>(geom, (const float*)d_sino, (float*)d_b, (char*)d_work, st);
   return bp_run<double>(geom, (const double*)d_sino, (double*)d_b, (char*)d_work, st);

@@ -53,7 +53,25 @@ inline long fft_table_elems(int N) { return 8L * N; }
 // fill the 8N-entry twiddle array of size N (see FftOps)
 template <typename T> int build_fft_tables(cpx<T>* d_tw, int N, cudaStream_t st);
 
+// Back projection split into its per-geometry and per-sinogram parts (device memory
+// owned by the caller of these functions).
+struct BpPlan {
+  int N = 0, na = 0, M = 0;
+  double lambda = 1.0, zeta = 0.0;
+  double* ang = nullptr;     // [na] half turns (device)
+  double* p00 = nullptr;     // [na]
+  double2* csl = nullptr;    // [na] (cos, sin) / lambda
+  void* tab = nullptr;       // bp_table_bytes(na, precision)
+  int* status = nullptr;
+};
+template <typename T> int bp_make_tables(const BpPlan& p, cudaStream_t st);
+template <typename T> int bp_apply(const BpPlan& p, const T* sino, T* ct, T* b, cudaStream_t st);
+size_t bp_table_bytes(int n_angles, int precision);
+
 }  // namespace bsct
+
+int bsct_check_geom(const bsct_geom* g);
+int bsct_check_bp_geom(const bsct_geom* g);
 
 // Library-owned state of one geometry (see bsct_gram_build).
 struct bsct_gram {
@@ -70,4 +88,5 @@ struct bsct_gram {
   double* scal = nullptr;    // CG scalars
   double* partials = nullptr;
   int n_partials = 0;
+  bool owns_filter = true;   // false for batch slices sharing another handle's taps/spectrum/twiddles
 };

@@ -305,10 +305,12 @@ int bsct_check_geom(const bsct_geom* g) {
 extern "C" void bsct_gram_free(bsct_gram* g) {
   if (!g) return;
   cudaDeviceSynchronize();
-  cudaFree(g->taps);
-  cudaFree(g->Gt64);
-  cudaFree(g->Gt32);
-  cudaFree(g->tw);
+  if (g->owns_filter) {
+    cudaFree(g->taps);
+    cudaFree(g->Gt64);
+    cudaFree(g->Gt32);
+    cudaFree(g->tw);
+  }
   cudaFree(g->S);
   cudaFree(g->r);
   cudaFree(g->p);

@@ -103,3 +103,33 @@ def make_problem(cfg, slice_id=0, noise=True):
     if noise and cfg.get("I0"):
         sino = poisson_log_sinogram(sino, cfg["I0"], cfg.get("seed", 0) + 1000 + slice_id)
     return angles, sino, params
+
+
+def ellipse_sinogram_torch(params, angles_pi, M, lambda_y, zeta=0.0, device="cuda", dtype=None):
+    """Same analytic sinogram as ``ellipse_sinogram`` evaluated with torch on a device
+    (used to synthesise many large batch inputs quickly)."""
+    import torch
+
+    dtype = dtype or torch.float64
+    c_np, s_np = _angles(angles_pi)
+    c = torch.tensor(c_np, dtype=torch.float64, device=device)
+    s = torch.tensor(s_np, dtype=torch.float64, device=device)
+    ym = (torch.arange(M, dtype=torch.float64, device=device) - (M - 1) / 2.0) * lambda_y
+    sino = torch.zeros((len(c_np), M), dtype=torch.float64, device=device)
+    for cx, cy, a, b, phi, rho in params:
+        cr = c * math.cos(phi) + s * math.sin(phi)
+        sr = s * math.cos(phi) - c * math.sin(phi)
+        r2 = (a * a * cr * cr + b * b * sr * sr)[:, None]
+        r = torch.sqrt(r2)
+        t = ym[None, :] - (cx * c + cy * s)[:, None]
+        scale = 2.0 * rho * a * b / r2
+        if zeta == 0.0:
+            sino += torch.where(t.abs() < r, scale * torch.sqrt(torch.clamp(r2 - t * t, min=0.0)),
+                                torch.zeros_like(t))
+        else:
+            def F(u):
+                u = torch.maximum(torch.minimum(u, r), -r)
+                return 0.5 * (u * torch.sqrt(torch.clamp(r2 - u * u, min=0.0))
+                              + r2 * torch.asin(torch.clamp(u / r, -1.0, 1.0)))
+            sino += scale * (F(t + 0.5 * zeta) - F(t - 0.5 * zeta)) / zeta
+    return sino.to(dtype)
