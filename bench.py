@@ -345,6 +345,29 @@ def run_ours(args):
                                   "learned_ms": None, "learned_iters": None}
         g5.close()
 
+    # ---------------------------------------------------------------- split-BF16 DFT-GEMM apply (tensor cores)
+    if not args.quick:
+        yd = torch.empty_like(y)
+        g.apply(x, yd, mode=bsct.APPLY_DFTGEMM_BF16)  # allocates the DFT-GEMM scratch
+        g.apply(x, y)
+        torch.cuda.synchronize()
+        nd = 5
+        e0.record(stream)
+        for _ in range(nd):
+            g.apply(x, yd, mode=bsct.APPLY_DFTGEMM_BF16)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dms = e0.elapsed_time(e1) / nd
+        L = 2 * N
+        P = 64 if L % 64 == 0 else 32
+        Q = L // P
+        gemm_flop = 4 * (2 * (2 * P) * (6 * P) * (Q * L) + 2 * (2 * Q) * (6 * Q) * (P * L))
+        extras["dftgemm_bf16"] = {
+            "ms_per_apply": dms, "applies_per_s": 1e3 / dms,
+            "rel_l2_diff_vs_fp32_fft": float((yd - y).double().norm() / y.double().norm()),
+            "gemm_flop_per_apply": gemm_flop, "gemm_tflops_effective": gemm_flop / (dms * 1e-3) / 1e12,
+            "note": "4 DFTs of 4096^2 as 8 split-BF16 GEMMs (mma.sync m16n8k16, FP32 accumulate) + split/twiddle kernels"}
+
     # ---------------------------------------------------------------- batched slices (one graph launch)
     if not args.quick and not args.no_batch:
         from workloads import configs as wcfg

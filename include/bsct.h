@@ -51,6 +51,7 @@ extern "C" {
 
 #define BSCT_APPLY_FFT32 0         /* FP32 zero-padded 2N x 2N FFT convolution */
 #define BSCT_APPLY_F64 1           /* FP64 zero-padded FFT convolution */
+#define BSCT_APPLY_DFTGEMM_BF16 2  /* DFTs as split-BF16 GEMMs on tensor cores, FP32 accumulate */
 
 /* Problem geometry (Sec. 2: coefficients c_k on an N x N grid, n_angles views, a
  * detector of n_bins samples with step lambda_y, blur width zeta_blur).
@@ -103,6 +104,10 @@ int bsct_gram_spectrum(const bsct_gram* g, double* d_out, void* stream);
 /* y = G x: y[i] = sum_j G[i - j] x[j] on the N x N grid (Sec. 4), computed as a
  * zero-padded 2N x 2N FFT convolution.  mode BSCT_APPLY_FFT32 needs a BSCT_F32
  * handle and float buffers, BSCT_APPLY_F64 a BSCT_F64 handle and double buffers.
+ * BSCT_APPLY_DFTGEMM_BF16 (F32 handle, float buffers) computes the same convolution
+ * with every length-2N DFT as two split-BF16 GEMMs on the tensor cores (operands split
+ * into BF16 high + low parts, FP32 accumulation; relative error ~1e-5 to 1e-4); its
+ * ~12 (2N)^2-float scratch is allocated in the handle on the first such call.
  * d_x and d_y: N*N elements, may not alias. */
 int bsct_gram_apply(const bsct_gram* g, const void* d_x, void* d_y, int mode, void* stream);
 
@@ -165,6 +170,14 @@ int bsct_cg_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero, int 
  * state (x, r, p and the scalars) lives in the handle: call bsct_cg_begin first. */
 int bsct_cg_begin(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero, void* stream);
 int bsct_cg_iterate(bsct_gram* g, void* d_x, int n_iter, void* stream);
+/* Mixed-precision CG: n_low iterations whose operator is the split-BF16 DFT-GEMM apply
+ * (BSCT_APPLY_DFTGEMM_BF16), then refinement by a residual CG step - the true residual
+ * b - G x is recomputed with the FP32 FFT apply and n_refine FP32 CG iterations continue
+ * from x.  F32 handle only; x starts at 0.  Synchronous; report->true_rel_residual is
+ * measured with the FP32 apply. */
+int bsct_cg_solve_mixed(bsct_gram* g, const void* d_b, void* d_x, int n_low, int n_refine,
+                        bsct_cg_report* report, void* stream);
+
 /* Copy the current recursive squared residual ||r||^2 and ||b||^2 to host (synchronous). */
 int bsct_cg_residual(const bsct_gram* g, double* rr, double* bb, void* stream);
 
@@ -188,6 +201,17 @@ int bsct_batch_solve(bsct_batch* b, const float* const* d_sino, float* const* d_
 int bsct_batch_info(const bsct_batch* b, int* n_geometries, long long* graph_nodes,
                     long long* kernels_per_launch);
 void bsct_batch_free(bsct_batch* b);
+
+/* C[b] = alpha op(A[b]) op(B[b]) + beta C[b] with BF16 A, B and FP32 C on the tensor
+ * cores (building block of the DFT-GEMM apply and the learned warm start; the paper has
+ * no counterpart).  op(A) is M x K: A row-major M x K (lda) or, with trans_a, K x M;
+ * op(B) is K x N: B row-major K x N (ldb) or, with trans_b, N x K.  C row-major (ldc).
+ * Batch b advances A, B, C by stride_a, stride_b, stride_c elements.  K, lda, ldb and
+ * the A/B strides must be multiples of 8, A and B 16-byte aligned; trans_a needs
+ * M % 8 == 0 and !trans_b needs N % 8 == 0.  All pointers device. */
+int bsct_gemm_bf16(int trans_a, int trans_b, int32_t M, int32_t N, int32_t K, float alpha, const void* d_A,
+                   int64_t lda, int64_t stride_a, const void* d_B, int64_t ldb, int64_t stride_b, float beta,
+                   float* d_C, int64_t ldc, int64_t stride_c, int32_t batch, void* stream);
 
 /* Human-readable text of a status code, and of the last failure on this thread. */
 const char* bsct_status_string(int status);

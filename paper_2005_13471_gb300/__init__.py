@@ -26,6 +26,7 @@ F32 = 0
 F64 = 1
 APPLY_FFT32 = 0
 APPLY_F64 = 1
+APPLY_DFTGEMM_BF16 = 2
 OK = 0
 WARN_NOT_CONVERGED = 1
 
@@ -80,6 +81,12 @@ def _declare(L):
     L.bsct_status_string.restype = ctypes.c_char_p
     L.bsct_last_error_string.argtypes = []
     L.bsct_last_error_string.restype = ctypes.c_char_p
+    L.bsct_cg_solve_mixed.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_CGReport), vp]
+    L.bsct_cg_solve_mixed.restype = ctypes.c_int
+    L.bsct_gemm_bf16.argtypes = [ctypes.c_int, ctypes.c_int, i32, i32, i32, ctypes.c_float, vp, ctypes.c_int64,
+                                 ctypes.c_int64, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_float, vp,
+                                 ctypes.c_int64, ctypes.c_int64, i32, vp]
+    L.bsct_gemm_bf16.restype = ctypes.c_int
     L.bsct_batch_create.argtypes = [i32, gp, ctypes.POINTER(vp), vp]
     L.bsct_batch_create.restype = ctypes.c_int
     L.bsct_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, vp]
@@ -232,7 +239,8 @@ class GramFilter:
         _check(lib().bsct_gram_spectrum(self._h, ctypes.c_void_p(out.data_ptr()), _stream()), "bsct_gram_spectrum")
         return out
 
-    def apply(self, x, out=None):
+    def apply(self, x, out=None, mode=None):
+        """y = G x; mode APPLY_DFTGEMM_BF16 selects the split-BF16 tensor-core DFT-GEMM path."""
         import torch
 
         n = self.N
@@ -240,9 +248,23 @@ class GramFilter:
         if out is None:
             out = torch.empty((n, n), dtype=self.dtype, device=x.device)
         py = _dev(out, (n, n), self.dtype, "out")
-        mode = APPLY_FFT32 if self.precision == F32 else APPLY_F64
-        _check(lib().bsct_gram_apply(self._h, px, py, mode, _stream()), "bsct_gram_apply")
+        if mode is None:
+            mode = APPLY_FFT32 if self.precision == F32 else APPLY_F64
+        _check(lib().bsct_gram_apply(self._h, px, py, int(mode), _stream()), "bsct_gram_apply")
         return out
+
+    def cg_solve_mixed(self, b, n_low, n_refine):
+        """CG with the split-BF16 DFT-GEMM operator, refined by FP32 residual CG steps."""
+        import torch
+
+        n = self.N
+        x = torch.empty((n, n), dtype=self.dtype, device=b.device)
+        rep = _CGReport()
+        _check(lib().bsct_cg_solve_mixed(self._h, _dev(b, (n, n), self.dtype, "b"), _dev(x, (n, n), self.dtype, "x"),
+                                         int(n_low), int(n_refine), ctypes.byref(rep), _stream()),
+               "bsct_cg_solve_mixed")
+        return x, dict(iterations=rep.iterations, rel_residual=rep.rel_residual,
+                       true_rel_residual=rep.true_rel_residual)
 
     def cg_solve(self, b, x0=None, max_iter=100, rel_tol=0.0, check_every=10):
         import torch
@@ -307,6 +329,35 @@ def backproject(geom, sino, precision=F32, out=None, work=None):
 
 def cg_solve(gram, b, x0=None, max_iter=100, rel_tol=0.0, check_every=10):
     return gram.cg_solve(b, x0, max_iter, rel_tol, check_every)
+
+
+def gemm_bf16(a, b, c=None, trans_a=False, trans_b=False, alpha=1.0, beta=0.0):
+    """c = alpha op(a) op(b) + beta c with BF16 a, b and FP32 c (2-D or batched 3-D tensors)."""
+    import torch
+
+    batched = a.dim() == 3
+    A = a if batched else a.unsqueeze(0)
+    B = b if batched else b.unsqueeze(0)
+    if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16 or not A.is_cuda or not B.is_cuda:
+        raise TypeError("a and b must be bfloat16 CUDA tensors")
+    if not A.is_contiguous() or not B.is_contiguous():
+        raise ValueError("a and b must be contiguous")
+    M = A.shape[2] if trans_a else A.shape[1]
+    K = A.shape[1] if trans_a else A.shape[2]
+    N = B.shape[1] if trans_b else B.shape[2]
+    if (B.shape[2] if trans_b else B.shape[1]) != K:
+        raise ValueError("inner dimensions differ")
+    nb = A.shape[0]
+    if c is None:
+        C = torch.zeros((nb, M, N), dtype=torch.float32, device=A.device)
+    else:
+        C = c if batched else c.unsqueeze(0)
+    _dev(C, (nb, M, N), torch.float32, "c")
+    _check(lib().bsct_gemm_bf16(int(trans_a), int(trans_b), M, N, K, float(alpha), ctypes.c_void_p(A.data_ptr()),
+                                A.shape[2], A.shape[1] * A.shape[2], ctypes.c_void_p(B.data_ptr()), B.shape[2],
+                                B.shape[1] * B.shape[2], float(beta), ctypes.c_void_p(C.data_ptr()), N, M * N, nb,
+                                _stream()), "bsct_gemm_bf16")
+    return C if batched else C[0]
 
 
 class Batch:

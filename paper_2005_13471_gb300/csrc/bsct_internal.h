@@ -68,6 +68,14 @@ template <typename T> int bp_make_tables(const BpPlan& p, cudaStream_t st);
 template <typename T> int bp_apply(const BpPlan& p, const T* sino, T* ct, T* b, cudaStream_t st);
 size_t bp_table_bytes(int n_angles, int precision);
 
+// split-BF16 DFT-GEMM Gram apply (dftgemm.cu)
+bool dftgemm_factor(int L, int* P, int* Q);
+size_t dftgemm_scratch_bytes(int N);
+int dftgemm_apply(int N, const float* x, float* y, const float* Gt, const float2* tw_untangle, void* work,
+                  cudaStream_t st);
+int gemm_bf16(bool ta, bool tb, int M, int N, int K, float alpha, const void* A, long lda, long sA, const void* B,
+              long ldb, long sB, float beta, float* C, long ldc, long sC, int batch, cudaStream_t st);
+
 }  // namespace bsct
 
 int bsct_check_geom(const bsct_geom* g);
@@ -89,4 +97,6 @@ struct bsct_gram {
   double* partials = nullptr;
   int n_partials = 0;
   bool owns_filter = true;   // false for batch slices sharing another handle's taps/spectrum/twiddles
+  void* dg_work = nullptr;   // DFT-GEMM scratch, allocated on first DFT-GEMM apply
+  size_t dg_bytes = 0;
 };

@@ -104,6 +104,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_xr_update(T* __restrict__ x, T*
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
+template <typename T>
+__global__ void k_p_update(T* __restrict__ p, const T* __restrict__ r, const double* __restrict__ sc, long n) {
+  const T beta = T(sc[SC_BETA]);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], r[i]);
+}
+
 // r = b - q (q = G x0), p = r
 template <typename T>
 __global__ void k_init_r(const T* __restrict__ b, const T* __restrict__ q, T* __restrict__ r, T* __restrict__ p, long n,
@@ -265,4 +272,50 @@ extern "C" int bsct_cg_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is
     report->true_rel_residual = tr;
   }
   return (rel_tol > 0.0 && !converged) ? BSCT_WARN_NOT_CONVERGED : BSCT_OK;
+}
+
+// CG whose operator is the split-BF16 DFT-GEMM apply (unfused: p update, apply, <p, q>),
+// followed by iterative refinement: the FP32 FFT apply recomputes the true residual
+// b - G x and n_refine FP32 CG iterations continue from x.
+extern "C" int bsct_cg_solve_mixed(bsct_gram* g, const void* d_b, void* d_x, int n_low, int n_refine,
+                                   bsct_cg_report* report, void* stream) {
+  if (!g || !d_b || !d_x || n_low < 0 || n_refine < 0) { bsct_set_last_message("invalid argument"); return BSCT_ERR_INVALID_ARG; }
+  if (g->precision != BSCT_F32) { bsct_set_last_message("mixed CG needs an F32 handle"); return BSCT_ERR_INVALID_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const long n = (long)g->N * g->N;
+  const int nb = nblk(g, n);
+  float* x = (float*)d_x;
+  float* r = (float*)g->r;
+  float* p = (float*)g->p;
+  float* q = (float*)g->q;
+  int rc = bsct_cg_begin(g, d_b, d_x, 1, stream);
+  if (rc != BSCT_OK) return rc;
+  for (int it = 0; it < n_low; ++it) {
+    k_p_update<float><<<nb, RED_THREADS, 0, st>>>(p, r, g->scal, n);
+    count_launch();
+    rc = bsct_gram_apply(g, p, q, BSCT_APPLY_DFTGEMM_BF16, stream);
+    if (rc != BSCT_OK) return rc;
+    k_dot<float><<<nb, RED_THREADS, 0, st>>>(p, q, n, g->partials);
+    k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_ALPHA);
+    k_xr_update<float><<<nb, RED_THREADS, 0, st>>>(x, r, p, q, g->scal, n, g->partials);
+    k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_BETA);
+    count_launch(4);
+  }
+  BSCT_CUDA_TRY(cudaGetLastError());
+  if (n_refine > 0) {
+    rc = bsct_cg_begin(g, d_b, d_x, 0, stream);  // r = b - G x with the FP32 apply
+    if (rc == BSCT_OK) rc = bsct_cg_iterate(g, d_x, n_refine, stream);
+    if (rc != BSCT_OK) return rc;
+  }
+  double rr = 0.0, bb = 0.0, tr = -1.0;
+  rc = bsct_cg_residual(g, &rr, &bb, stream);
+  if (rc == BSCT_OK) rc = true_residual_t<float>(g, (const float*)d_b, (const float*)d_x, &tr, st);
+  if (rc != BSCT_OK) return rc;
+  if (report) {
+    report->iterations = n_low + n_refine;
+    report->converged = 0;
+    report->rel_residual = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    report->true_rel_residual = tr;
+  }
+  return BSCT_OK;
 }

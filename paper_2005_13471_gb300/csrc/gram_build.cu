@@ -312,6 +312,7 @@ extern "C" void bsct_gram_free(bsct_gram* g) {
     cudaFree(g->tw);
   }
   cudaFree(g->S);
+  cudaFree(g->dg_work);
   cudaFree(g->r);
   cudaFree(g->p);
   cudaFree(g->q);
@@ -442,6 +443,18 @@ extern "C" int bsct_gram_apply(const bsct_gram* g, const void* d_x, void* d_y, i
     FftOps<double> o;
     fft_ops_for<double>(g->N, &o);
     return o.apply((const double*)d_x, (double*)d_y, (cpx<double>*)g->S, g->Gt64, (const cpx<double>*)g->tw, st);
+  }
+  if (mode == BSCT_APPLY_DFTGEMM_BF16) {
+    if (g->precision != BSCT_F32) return fail(BSCT_ERR_INVALID_ARG, "DFT-GEMM apply needs an F32 handle");
+    int P, Q;
+    if (!dftgemm_factor(2 * g->N, &P, &Q)) return fail(BSCT_ERR_UNSUPPORTED_SIZE, "no DFT-GEMM factorisation for 2N");
+    bsct_gram* gm = const_cast<bsct_gram*>(g);
+    if (!gm->dg_work) {
+      const size_t bytes = dftgemm_scratch_bytes(g->N);
+      BSCT_CUDA_TRY(cudaMalloc(&gm->dg_work, bytes));
+      gm->dg_bytes = bytes;
+    }
+    return dftgemm_apply(g->N, (const float*)d_x, (float*)d_y, g->Gt32, (const float2*)g->tw, gm->dg_work, st);
   }
   return fail(BSCT_ERR_INVALID_ARG, "unknown apply mode");
 }
