@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--quick", action="store_true", help="skip the hot-path pass, batch and time-to-1e-4 extras")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--batch-slices", type=int, default=256)
+    p.add_argument("--learned-pairs", type=int, default=512, help="training pairs for the learned warm start (0 = skip)")
+    p.add_argument("--learned-epochs", type=int, default=2)
     return p.parse_args()
 
 
@@ -339,10 +341,32 @@ def run_ours(args):
         t0 = time.perf_counter()
         _, rep5 = g5.cg_solve(b5, max_iter=2000, rel_tol=1e-4, check_every=5)
         torch.cuda.synchronize()
-        extras["time_to_1e-4"] = {"workload": "N=512, 720 views, 726 bins, zeta=1, Poisson I0=1e5",
-                                  "plain_ms": 1e3 * (time.perf_counter() - t0), "plain_iters": rep5["iterations"],
-                                  "plain_true_rel_residual": rep5["true_rel_residual"],
-                                  "learned_ms": None, "learned_iters": None}
+        plain_ms = 1e3 * (time.perf_counter() - t0)
+        tt = {"workload": "N=512, 720 views, 726 bins, zeta=1, Poisson I0=1e5",
+              "plain_ms": plain_ms, "plain_iters": rep5["iterations"],
+              "plain_true_rel_residual": rep5["true_rel_residual"], "learned_ms": None, "learned_iters": None}
+        if args.learned_pairs > 0:
+            from paper_2005_13471_gb300 import learned
+
+            t_tr = time.perf_counter()
+            Xl, Yl = learned.generate_pairs(args.learned_pairs, N=256, n_angles=360, n_bins=364, zeta=1.0, I0=1e5,
+                                            cg_iters=200, chunk=256, seed=rank)
+            t_gen = time.perf_counter() - t_tr
+            net = bsct.UNet(32, seed=rank)
+            losses = learned.train(net, Xl, Yl, epochs=args.learned_epochs, batch_size=8, lr=1e-3, lr_final=5e-5,
+                                   log_every=25)
+            t_train = time.perf_counter() - t_tr - t_gen
+            del Xl, Yl
+            r5, _, xl = learned.compare_solvers(net, g5, b5, c5["n_angles"])
+            tt.update({"learned_ms": r5["learned_ms"], "learned_iters": r5["learned_iters"],
+                       "learned_true_rel_residual": r5["learned_true"], "plain_ms_same_run": r5["plain_ms"],
+                       "plain_iters_same_run": r5["plain_iters"], "warm_start_alpha": r5["alpha"],
+                       "training": {"pairs": args.learned_pairs, "geometry": "N=256, 360 views, 364 bins, zeta=1",
+                                    "target": "200-iteration CG", "epochs": args.learned_epochs,
+                                    "generate_s": t_gen, "train_s": t_train,
+                                    "loss_first_last": [losses[0], losses[-1]] if losses else None}})
+            net.close()
+        extras["time_to_1e-4"] = tt
         g5.close()
 
     # ---------------------------------------------------------------- split-BF16 DFT-GEMM apply (tensor cores)

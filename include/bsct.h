@@ -213,6 +213,44 @@ int bsct_gemm_bf16(int trans_a, int trans_b, int32_t M, int32_t N, int32_t K, fl
                    int64_t lda, int64_t stride_a, const void* d_B, int64_t ldb, int64_t stride_b, float beta,
                    float* d_C, int64_t ldc, int64_t stride_c, int32_t batch, void* stream);
 
+/* Learned warm start (no counterpart in the paper): a 4-level encoder-decoder CNN
+ * (U-Net, base_channels / 2x / 4x / 8x channels, two 3x3 conv + ReLU per level, 2x2
+ * max-pool, 2x2 transposed convolutions, skip connections, 1x1 head; 1.92M parameters
+ * at base 32) whose 3x3 and transposed convolutions run as BF16 tensor-core GEMMs with
+ * FP32 accumulation.  Parameters are FP32 masters with a BF16 copy for the GEMMs,
+ * trained with Adam by the library's own backward kernels.
+ *   create: He-normal initialisation from a counter-based generator seeded by seed;
+ *   params: device pointers to the flat FP32 parameters / gradients (library-owned;
+ *           after writing parameters call bsct_unet_sync_weights);
+ *   forward: d_in, d_out device float [n][H][W], H and W multiples of 64; keeps the
+ *           activations for one following backward;
+ *   backward: d_gout = dLoss/d_out of the last forward; adds into the gradients;
+ *   adam_step: Adam update (bias-corrected with step >= 1), then zeroes the gradients. */
+typedef struct bsct_unet bsct_unet;
+int bsct_unet_create(int32_t base_channels, uint64_t seed, bsct_unet** out, void* stream);
+int bsct_unet_params(bsct_unet* net, float** d_params, float** d_grads, int64_t* n_params);
+int bsct_unet_sync_weights(bsct_unet* net, void* stream);
+/* Copy the n_params FP32 parameters (which = 0) or gradients (which = 1) between the
+ * net and the caller's device buffer d_buf (to_net = 1: into the net; parameters are
+ * then re-rounded into the BF16 copy). */
+int bsct_unet_copy(bsct_unet* net, int which, int to_net, float* d_buf, void* stream);
+int bsct_unet_forward(bsct_unet* net, const float* d_in, float* d_out, int32_t n, int32_t H, int32_t W, void* stream);
+int bsct_unet_backward(bsct_unet* net, const float* d_gout, void* stream);
+int bsct_unet_adam_step(bsct_unet* net, float lr, float beta1, float beta2, float eps, int32_t step, void* stream);
+void bsct_unet_free(bsct_unet* net);
+/* Mean-squared-error loss for training: d_grad = 2 (pred - target) / n and
+ * *d_loss += mean (pred - target)^2 (device double, not cleared). */
+int bsct_mse_loss_grad(const float* d_pred, const float* d_target, int64_t n, float* d_grad, double* d_loss,
+                       void* stream);
+
+/* CG with a learned warm start: x_hat = net(in_scale * b); x0 = alpha x_hat with
+ * alpha = <x_hat, b> / <x_hat, G x_hat> (the G-norm-optimal scaling); if alpha is not
+ * positive and finite, x0 = 0 (plain CG).  Then bsct_cg_solve from x0 with the given
+ * tolerance - plain CG is the judge of the warm start's error.  *alpha_out (may be
+ * NULL) receives alpha.  F32 handle; N a multiple of 64.  Synchronous. */
+int bsct_cg_solve_learned(bsct_gram* g, bsct_unet* net, const void* d_b, void* d_x, float in_scale, int max_iter,
+                          double rel_tol, int check_every, bsct_cg_report* report, double* alpha_out, void* stream);
+
 /* Human-readable text of a status code, and of the last failure on this thread. */
 const char* bsct_status_string(int status);
 const char* bsct_last_error_string(void);

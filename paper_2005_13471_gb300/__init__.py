@@ -87,6 +87,22 @@ def _declare(L):
                                  ctypes.c_int64, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_float, vp,
                                  ctypes.c_int64, ctypes.c_int64, i32, vp]
     L.bsct_gemm_bf16.restype = ctypes.c_int
+    L.bsct_unet_create.argtypes = [i32, ctypes.c_uint64, ctypes.POINTER(vp), vp]
+    L.bsct_unet_params.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64)]
+    L.bsct_unet_sync_weights.argtypes = [vp, vp]
+    L.bsct_unet_copy.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp]
+    L.bsct_unet_copy.restype = ctypes.c_int
+    L.bsct_unet_forward.argtypes = [vp, vp, vp, i32, i32, i32, vp]
+    L.bsct_unet_backward.argtypes = [vp, vp, vp]
+    L.bsct_unet_adam_step.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, i32, vp]
+    L.bsct_unet_free.argtypes = [vp]
+    L.bsct_unet_free.restype = None
+    L.bsct_mse_loss_grad.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp]
+    L.bsct_cg_solve_learned.argtypes = [vp, vp, vp, vp, ctypes.c_float, ctypes.c_int, dbl, ctypes.c_int,
+                                        ctypes.POINTER(_CGReport), ctypes.POINTER(dbl), vp]
+    for name in ("bsct_unet_create", "bsct_unet_params", "bsct_unet_sync_weights", "bsct_unet_forward",
+                 "bsct_unet_backward", "bsct_unet_adam_step", "bsct_mse_loss_grad", "bsct_cg_solve_learned"):
+        getattr(L, name).restype = ctypes.c_int
     L.bsct_batch_create.argtypes = [i32, gp, ctypes.POINTER(vp), vp]
     L.bsct_batch_create.restype = ctypes.c_int
     L.bsct_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, vp]
@@ -253,6 +269,21 @@ class GramFilter:
         _check(lib().bsct_gram_apply(self._h, px, py, int(mode), _stream()), "bsct_gram_apply")
         return out
 
+    def cg_solve_learned(self, net, b, in_scale, max_iter=1000, rel_tol=1e-4, check_every=5):
+        """CG from the learned warm start alpha * net(in_scale * b) (plain CG if alpha <= 0)."""
+        import torch
+
+        n = self.N
+        x = torch.empty((n, n), dtype=self.dtype, device=b.device)
+        rep = _CGReport()
+        alpha = ctypes.c_double()
+        rc = _check(lib().bsct_cg_solve_learned(self._h, net._h, _dev(b, (n, n), self.dtype, "b"),
+                                                _dev(x, (n, n), self.dtype, "x"), float(in_scale), int(max_iter),
+                                                float(rel_tol), int(check_every), ctypes.byref(rep),
+                                                ctypes.byref(alpha), _stream()), "bsct_cg_solve_learned")
+        return x, dict(iterations=rep.iterations, converged=bool(rep.converged), rel_residual=rep.rel_residual,
+                       true_rel_residual=rep.true_rel_residual, alpha=alpha.value, status=rc)
+
     def cg_solve_mixed(self, b, n_low, n_refine):
         """CG with the split-BF16 DFT-GEMM operator, refined by FP32 residual CG steps."""
         import torch
@@ -358,6 +389,97 @@ def gemm_bf16(a, b, c=None, trans_a=False, trans_b=False, alpha=1.0, beta=0.0):
                                 B.shape[1] * B.shape[2], float(beta), ctypes.c_void_p(C.data_ptr()), N, M * N, nb,
                                 _stream()), "bsct_gemm_bf16")
     return C if batched else C[0]
+
+
+class UNet:
+    """Encoder-decoder CNN of the learned warm start (library kernels; see include/bsct.h)."""
+
+    def __init__(self, base_channels=32, seed=0):
+        self._h = ctypes.c_void_p()
+        _check(lib().bsct_unet_create(int(base_channels), int(seed), ctypes.byref(self._h), _stream()),
+               "bsct_unet_create")
+        self.base = int(base_channels)
+
+    def _raw(self):
+        w, g, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
+        _check(lib().bsct_unet_params(self._h, ctypes.byref(w), ctypes.byref(g), ctypes.byref(n)), "bsct_unet_params")
+        return w.value, g.value, n.value
+
+    @property
+    def n_params(self):
+        return self._raw()[2]
+
+    def _copy(self, which, to_net, t):
+        _check(lib().bsct_unet_copy(self._h, which, to_net, ctypes.c_void_p(t.data_ptr()), _stream()),
+               "bsct_unet_copy")
+
+    def get_params(self):
+        """Copy of the flat FP32 parameter vector (device tensor)."""
+        import torch
+
+        out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        self._copy(0, 0, out)
+        return out
+
+    def get_grads(self):
+        import torch
+
+        out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        self._copy(1, 0, out)
+        return out
+
+    def set_params(self, t):
+        import torch
+
+        t = t.to(device="cuda", dtype=torch.float32).contiguous()
+        if t.numel() != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        self._copy(0, 1, t)
+
+    def forward(self, x, out=None):
+        """x: [n, H, W] float32 CUDA tensor (H, W multiples of 64); returns [n, H, W]."""
+        import torch
+
+        if x.dim() == 2:
+            x = x.unsqueeze(0)
+        nb, H, W = x.shape
+        if out is None:
+            out = torch.empty_like(x)
+        _check(lib().bsct_unet_forward(self._h, _dev(x, (nb, H, W), torch.float32, "x"),
+                                       _dev(out, (nb, H, W), torch.float32, "out"), nb, H, W, _stream()),
+               "bsct_unet_forward")
+        return out
+
+    def backward(self, gout):
+        import torch
+
+        _check(lib().bsct_unet_backward(self._h, _dev(gout, tuple(gout.shape), torch.float32, "gout"), _stream()),
+               "bsct_unet_backward")
+
+    def adam_step(self, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(lib().bsct_unet_adam_step(self._h, float(lr), float(beta1), float(beta2), float(eps), int(step),
+                                         _stream()), "bsct_unet_adam_step")
+
+    def close(self):
+        if self._h:
+            lib().bsct_unet_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mse_loss_grad(pred, target, grad, loss_acc):
+    """grad = 2 (pred - target) / n ; loss_acc (1-element float64 CUDA tensor) += mean squared error."""
+    import torch
+
+    n = pred.numel()
+    _check(lib().bsct_mse_loss_grad(ctypes.c_void_p(pred.data_ptr()), ctypes.c_void_p(target.data_ptr()), n,
+                                    ctypes.c_void_p(grad.data_ptr()), _dev(loss_acc, (1,), torch.float64, "loss"),
+                                    _stream()), "bsct_mse_loss_grad")
 
 
 class Batch:

@@ -1,0 +1,713 @@
+// Learned warm start for CG: a 4-level encoder-decoder CNN (U-Net) with BF16 tensor-core
+// convolutions and FP32 accumulation, trained on (back projection, converged
+// reconstruction) pairs that the method itself produces.  Not part of the paper.
+//
+// Architecture (channels-first, activations stored [C][n][H][W] in FP32):
+//   level 0: conv3x3(1->32)+ReLU, conv3x3(32->32)+ReLU -> e0 ; maxpool 2x2
+//   level 1: 32->64, 64->64 -> e1 ; pool      level 2: 64->128, 128->128 -> e2 ; pool
+//   level 3: 128->256, 256->256
+//   up 3: convT2x2(256->128) ++ e2 -> conv(256->128), conv(128->128)
+//   up 2: convT2x2(128->64)  ++ e1 -> conv(128->64),  conv(64->64)
+//   up 1: convT2x2(64->32)   ++ e0 -> conv(64->32),   conv(32->32) ; head conv1x1(32->1)
+// 3x3 convolutions run as im2col (BF16) x weights (BF16) GEMMs on the tensor cores;
+// backward: weight gradient = dpre x col^T, data gradient = W^T x dpre then a col2im
+// gather; the transposed convolutions are GEMMs followed by a 2x2 scatter (gather in
+// the backward pass).  Master weights, gradients and Adam moments are FP32; a BF16 copy
+// of the weights feeds the GEMMs.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <vector>
+
+#include "bsct_internal.h"
+
+namespace {
+
+using bsct::count_launch;
+typedef __nv_bfloat16 bf16;
+
+constexpr int TPB = 256;
+inline unsigned nblk(long n) { return (unsigned)((n + TPB - 1) / TPB); }
+
+// ---------------------------------------------------------------------------- kernels
+__device__ __forceinline__ unsigned long long splitmix(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+// He-normal weights by Box-Muller on a counter-based generator; valid < cols of each row
+__global__ void k_init_weights(float* w, long n, int cols, int valid, float stdv, unsigned long long seed) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if ((int)(i % cols) >= valid) { w[i] = 0.f; return; }
+  const unsigned long long a = splitmix(seed * 0x100000001B3ull + 2 * (unsigned long long)i);
+  const unsigned long long b = splitmix(seed * 0x100000001B3ull + 2 * (unsigned long long)i + 1);
+  const double u1 = ((a >> 11) + 1.0) * (1.0 / 9007199254740993.0), u2 = (b >> 11) * (1.0 / 9007199254740992.0);
+  w[i] = (float)(stdv * sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));
+}
+
+__global__ void k_to_bf16(const float* __restrict__ a, bf16* __restrict__ b, long n) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16_rn(a[i]);
+}
+
+// col[(ci*9 + ky*3 + kx)][(n, y, x)] = in[ci][n][y+ky-1][x+kx-1] (zero outside), rows >= 9*C zero
+__global__ void k_im2col3(const float* __restrict__ in, int C, int NB, int H, int W, int Kpad, bf16* __restrict__ col) {
+  const long P = (long)NB * H * W;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)Kpad * P) return;
+  const int k = (int)(i / P);
+  const long p = i % P;
+  float v = 0.f;
+  if (k < 9 * C) {
+    const int ci = k / 9, ky = (k % 9) / 3, kx = k % 3;
+    const int x = (int)(p % W), y = (int)((p / W) % H);
+    const long nb = p / ((long)H * W);
+    const int yy = y + ky - 1, xx = x + kx - 1;
+    if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = in[((long)ci * NB + nb) * H * W + (long)yy * W + xx];
+  }
+  col[i] = __float2bfloat16_rn(v);
+}
+
+// gin[ci][n][y][x] = sum_{ky,kx} dcol[(ci,ky,kx)][n][y-ky+1][x-kx+1]
+__global__ void k_col2im3(const float* __restrict__ dcol, int C, int NB, int H, int W, float* __restrict__ gin) {
+  const long P = (long)NB * H * W;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)C * P) return;
+  const int ci = (int)(i / P);
+  const long p = i % P;
+  const int x = (int)(p % W), y = (int)((p / W) % H);
+  const long base = p - (long)y * W - x;  // (n, 0, 0)
+  float acc = 0.f;
+  for (int ky = 0; ky < 3; ++ky) {
+    const int yy = y - ky + 1;
+    if (yy < 0 || yy >= H) continue;
+    for (int kx = 0; kx < 3; ++kx) {
+      const int xx = x - kx + 1;
+      if (xx < 0 || xx >= W) continue;
+      acc += dcol[(long)(ci * 9 + ky * 3 + kx) * P + base + (long)yy * W + xx];
+    }
+  }
+  gin[i] = acc;
+}
+
+__global__ void k_bias_relu(float* __restrict__ a, const float* __restrict__ b, int C, long P, int relu) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)C * P) return;
+  float v = a[i] + b[i / P];
+  a[i] = relu ? fmaxf(v, 0.f) : v;
+}
+
+// dpre = g * (out > 0) (BF16 for the GEMMs); db[c] += sum over the channel
+// (grid: x = chunks of the channel, y = channel; one atomic add per block)
+__device__ __forceinline__ float block_reduce(float v) {
+  __shared__ float red[TPB / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < TPB / 32 ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+constexpr int CHUNK = 8192;
+__global__ void k_relu_bwd(const float* __restrict__ g, const float* __restrict__ out, long P, bf16* __restrict__ dpre,
+                           float* __restrict__ db) {
+  const int c = blockIdx.y;
+  const long p0 = (long)blockIdx.x * CHUNK, p1 = p0 + CHUNK < P ? p0 + CHUNK : P;
+  float acc = 0.f;
+  for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    const long i = (long)c * P + p;
+    const float d = out[i] > 0.f ? g[i] : 0.f;
+    dpre[i] = __float2bfloat16_rn(d);
+    acc += d;
+  }
+  acc = block_reduce(acc);
+  if (threadIdx.x == 0) atomicAdd(db + c, acc);
+}
+
+// db[c] += sum_p g[c][p]
+__global__ void k_chan_sum(const float* __restrict__ g, long P, float* __restrict__ db) {
+  const int c = blockIdx.y;
+  const long p0 = (long)blockIdx.x * CHUNK, p1 = p0 + CHUNK < P ? p0 + CHUNK : P;
+  float acc = 0.f;
+  for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) acc += g[(long)c * P + p];
+  acc = block_reduce(acc);
+  if (threadIdx.x == 0) atomicAdd(db + c, acc);
+}
+inline dim3 chan_grid(long P, int C) { return dim3((unsigned)((P + CHUNK - 1) / CHUNK), (unsigned)C); }
+
+__global__ void k_maxpool2(const float* __restrict__ in, int C, int NB, int H, int W, float* __restrict__ out) {
+  const int Ho = H / 2, Wo = W / 2;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)C * NB * Ho * Wo) return;
+  const int x = (int)(i % Wo), y = (int)((i / Wo) % Ho);
+  const long cn = i / ((long)Ho * Wo);
+  const float* s = in + cn * H * W + (long)(2 * y) * W + 2 * x;
+  out[i] = fmaxf(fmaxf(s[0], s[1]), fmaxf(s[W], s[W + 1]));
+}
+// routes g_out to the first maximum of each 2x2 window, adding into gin
+__global__ void k_maxpool2_bwd(const float* __restrict__ in, const float* __restrict__ gout, int C, int NB, int H, int W,
+                               float* __restrict__ gin) {
+  const int Ho = H / 2, Wo = W / 2;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)C * NB * Ho * Wo) return;
+  const int x = (int)(i % Wo), y = (int)((i / Wo) % Ho);
+  const long cn = i / ((long)Ho * Wo);
+  const long o = cn * H * W + (long)(2 * y) * W + 2 * x;
+  const float v[4] = {in[o], in[o + 1], in[o + W], in[o + W + 1]};
+  int a = 0;
+  for (int k = 1; k < 4; ++k)
+    if (v[k] > v[a]) a = k;
+  const long t = o + (a >> 1) * W + (a & 1);
+  gin[t] += gout[i];
+}
+
+// tmp[(co,dy,dx)][(n,y,x)] (+ b[co]) -> out[co][n][2y+dy][2x+dx]
+__global__ void k_tconv_scatter(const float* __restrict__ tmp, const float* __restrict__ b, int Co, int NB, int H,
+                                int W, float* __restrict__ out) {
+  const long P = (long)NB * H * W;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;  // over out
+  const long Pout = P * 4;
+  if (i >= (long)Co * Pout) return;
+  const int co = (int)(i / Pout);
+  const long q = i % Pout;
+  const int X = (int)(q % (2 * W)), Y = (int)((q / (2 * W)) % (2 * H));
+  const long nb = q / ((long)4 * H * W);
+  const int dy = Y & 1, dx = X & 1, y = Y >> 1, x = X >> 1;
+  out[i] = tmp[(long)(co * 4 + dy * 2 + dx) * P + nb * H * W + (long)y * W + x] + b[co];
+}
+// gathered[(co,dy,dx)][(n,y,x)] = bf16(gout[co][n][2y+dy][2x+dx])
+__global__ void k_tconv_gather(const float* __restrict__ gout, int Co, int NB, int H, int W, bf16* __restrict__ g) {
+  const long P = (long)NB * H * W;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)Co * 4 * P) return;
+  const int r = (int)(i / P);
+  const long p = i % P;
+  const int co = r / 4, dy = (r % 4) / 2, dx = r % 2;
+  const int x = (int)(p % W), y = (int)((p / W) % H);
+  const long nb = p / ((long)H * W);
+  g[i] = __float2bfloat16_rn(gout[(long)co * 4 * P + nb * 4 * H * W + (long)(2 * y + dy) * (2 * W) + 2 * x + dx]);
+}
+
+// head: out[p] = sum_c w[c] a[c][p] + b
+__global__ void k_head_fwd(const float* __restrict__ a, const float* __restrict__ w, const float* __restrict__ b, int C,
+                           long P, float* __restrict__ out) {
+  const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float acc = b[0];
+  for (int c = 0; c < C; ++c) acc = fmaf(w[c], a[(long)c * P + p], acc);
+  out[p] = acc;
+}
+__global__ void k_head_bwd_data(const float* __restrict__ gout, const float* __restrict__ w, int C, long P,
+                                float* __restrict__ ga) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)C * P) return;
+  ga[i] = w[i / P] * gout[i % P];
+}
+// dw[c] += sum_p a[c][p] g[p] (grid y = channel; y == C accumulates db)
+__global__ void k_head_bwd_w(const float* __restrict__ a, const float* __restrict__ g, int C, long P,
+                             float* __restrict__ dw, float* __restrict__ db) {
+  const int c = blockIdx.y;
+  const long p0 = (long)blockIdx.x * CHUNK, p1 = p0 + CHUNK < P ? p0 + CHUNK : P;
+  float acc = 0.f;
+  for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) acc += (c < C ? a[(long)c * P + p] : 1.f) * g[p];
+  acc = block_reduce(acc);
+  if (threadIdx.x == 0) atomicAdd(c < C ? dw + c : db, acc);
+}
+
+__global__ void k_adam(float* __restrict__ w, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       bf16* __restrict__ wb, long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  w[i] = wi;
+  wb[i] = __float2bfloat16_rn(wi);
+  g[i] = 0.f;
+}
+
+// ---------------------------------------------------------------------------- network
+struct Conv3 {
+  int cin, cout, kpad;
+  long w, b;  // offsets into the parameter arrays (w: cout x kpad)
+};
+struct TConv {
+  int cin, cout;
+  long w, b;  // w: (cout*4) x cin
+};
+
+}  // namespace
+
+struct bsct_unet {
+  int base = 32;
+  long n_params = 0;
+  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  bf16* wb = nullptr;
+  Conv3 c0a, c0b, c1a, c1b, c2a, c2b, c3a, c3b, d2a, d2b, d1a, d1b, d0a, d0b;
+  TConv t3, t2, t1;
+  long hw, hb;  // head
+  // activations for the cached shape
+  int NB = 0, H = 0, W = 0;
+  std::vector<void*> bufs;
+  float *x = nullptr, *a00, *cat0, *p0, *a10, *cat1, *p1, *a20, *cat2, *p2, *a30, *a31, *u2a, *u2b, *u1a, *u1b, *u0a, *u0b;
+  float *tmp, *dcol;
+  float *g00, *gcat0, *gp0, *g10, *gcat1, *gp1, *g20, *gcat2, *gp2, *g30, *g31, *gu2a, *gu2b, *gu1a, *gu1b, *gu0a,
+      *gu0b;
+  bf16 *col, *dpre;
+  float* out = nullptr;
+};
+
+namespace {
+
+long add_conv(bsct_unet* u, Conv3& c, int cin, int cout, long off) {
+  c.cin = cin;
+  c.cout = cout;
+  c.kpad = ((9 * cin + 7) / 8) * 8;
+  c.w = off;
+  off += (long)cout * c.kpad;
+  c.b = off;
+  off += cout;
+  return off;
+}
+long add_tconv(TConv& t, int cin, int cout, long off) {
+  t.cin = cin;
+  t.cout = cout;
+  t.w = off;
+  off += (long)cout * 4 * cin;
+  t.b = off;
+  off += cout;
+  return off;
+}
+
+void free_acts(bsct_unet* u) {
+  for (void* p : u->bufs) cudaFree(p);
+  u->bufs.clear();
+  u->NB = u->H = u->W = 0;
+}
+
+int alloc_acts(bsct_unet* u, int NB, int H, int W) {
+  if (u->NB == NB && u->H == H && u->W == W) return BSCT_OK;
+  free_acts(u);
+  const int B = u->base;
+  const long P0 = (long)NB * H * W, P1 = P0 / 4, P2 = P0 / 16, P3 = P0 / 64;
+  auto mk = [&](long n, size_t es = 4) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, (size_t)n * es) != cudaSuccess) return nullptr;
+    u->bufs.push_back(p);
+    return p;
+  };
+  bool ok = true;
+  auto f = [&](long n) {
+    float* p = (float*)mk(n);
+    ok = ok && p;
+    return p;
+  };
+  u->x = f(P0);
+  u->a00 = f(B * P0); u->cat0 = f(2 * B * P0); u->p0 = f(B * P1);
+  u->a10 = f(2 * B * P1); u->cat1 = f(4 * B * P1); u->p1 = f(2 * B * P2);
+  u->a20 = f(4 * B * P2); u->cat2 = f(8 * B * P2); u->p2 = f(4 * B * P3);
+  u->a30 = f(8 * B * P3); u->a31 = f(8 * B * P3);
+  u->u2a = f(4 * B * P2); u->u2b = f(4 * B * P2);
+  u->u1a = f(2 * B * P1); u->u1b = f(2 * B * P1);
+  u->u0a = f(B * P0); u->u0b = f(B * P0);
+  u->out = f(P0);
+  u->g00 = f(B * P0); u->gcat0 = f(2 * B * P0); u->gp0 = f(B * P1);
+  u->g10 = f(2 * B * P1); u->gcat1 = f(4 * B * P1); u->gp1 = f(2 * B * P2);
+  u->g20 = f(4 * B * P2); u->gcat2 = f(8 * B * P2); u->gp2 = f(4 * B * P3);
+  u->g30 = f(8 * B * P3); u->g31 = f(8 * B * P3);
+  u->gu2a = f(4 * B * P2); u->gu2b = f(4 * B * P2);
+  u->gu1a = f(2 * B * P1); u->gu1b = f(2 * B * P1);
+  u->gu0a = f(B * P0); u->gu0b = f(B * P0);
+  // scratch: the largest im2col (K x P) over all layers, transposed-conv products
+  long colmax = 0;
+  const Conv3* cs[] = {&u->c0a, &u->c0b, &u->c1a, &u->c1b, &u->c2a, &u->c2b, &u->c3a,
+                       &u->c3b, &u->d2a, &u->d2b, &u->d1a, &u->d1b, &u->d0a, &u->d0b};
+  const long Ps[] = {P0, P0, P1, P1, P2, P2, P3, P3, P2, P2, P1, P1, P0, P0};
+  for (int i = 0; i < 14; ++i) colmax = colmax > cs[i]->kpad * Ps[i] ? colmax : cs[i]->kpad * Ps[i];
+  long tmpmax = 4L * B * 4 * P1;  // (cout*4) x P_in of the largest transposed conv
+  if (8L * B * P3 * 4 > tmpmax) tmpmax = 8L * B * P3 * 4;
+  if (2L * B * P2 * 4 > tmpmax) tmpmax = 2L * B * P2 * 4;
+  u->col = (bf16*)mk(colmax, 2);
+  u->dcol = f(colmax);
+  u->tmp = f(tmpmax > 8L * B * P0 ? tmpmax : 8L * B * P0);
+  u->dpre = (bf16*)mk(tmpmax > 8L * B * P0 ? tmpmax : 8L * B * P0, 2);
+  ok = ok && u->col && u->dpre;
+  if (!ok) {
+    free_acts(u);
+    bsct_set_last_message("out of device memory for U-Net activations");
+    return BSCT_ERR_CUDA;
+  }
+  u->NB = NB;
+  u->H = H;
+  u->W = W;
+  return BSCT_OK;
+}
+
+#define UTRY(expr)                            \
+  do {                                        \
+    int _rc = (expr);                         \
+    if (_rc != BSCT_OK) return _rc;           \
+  } while (0)
+
+int conv_fwd(bsct_unet* u, const Conv3& c, const float* in, int NB, int H, int W, float* out, cudaStream_t st) {
+  const long P = (long)NB * H * W;
+  k_im2col3<<<nblk((long)c.kpad * P), TPB, 0, st>>>(in, c.cin, NB, H, W, c.kpad, u->col);
+  count_launch();
+  UTRY(bsct::gemm_bf16(false, false, c.cout, (int)P, c.kpad, 1.f, u->wb + c.w, c.kpad, 0, u->col, P, 0, 0.f, out, P,
+                       0, 1, st));
+  k_bias_relu<<<nblk((long)c.cout * P), TPB, 0, st>>>(out, u->w + c.b, c.cout, P, 1);
+  count_launch();
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+// gout: gradient of the post-ReLU output; gin (optional): gradient of the input (overwritten)
+int conv_bwd(bsct_unet* u, const Conv3& c, const float* in, const float* out, const float* gout, int NB, int H, int W,
+             float* gin, cudaStream_t st) {
+  const long P = (long)NB * H * W;
+  k_relu_bwd<<<chan_grid(P, c.cout), TPB, 0, st>>>(gout, out, P, u->dpre, u->g + c.b);
+  k_im2col3<<<nblk((long)c.kpad * P), TPB, 0, st>>>(in, c.cin, NB, H, W, c.kpad, u->col);
+  count_launch(2);
+  // dW[cout][kpad] += dpre[cout][P] col[kpad][P]^T
+  UTRY(bsct::gemm_bf16(false, true, c.cout, c.kpad, (int)P, 1.f, u->dpre, P, 0, u->col, P, 0, 1.f, u->g + c.w, c.kpad,
+                       0, 1, st));
+  if (gin) {
+    // dcol[kpad][P] = W^T dpre
+    UTRY(bsct::gemm_bf16(true, false, c.kpad, (int)P, c.cout, 1.f, u->wb + c.w, c.kpad, 0, u->dpre, P, 0, 0.f, u->dcol,
+                         P, 0, 1, st));
+    k_col2im3<<<nblk((long)c.cin * P), TPB, 0, st>>>(u->dcol, c.cin, NB, H, W, gin);
+    count_launch();
+  }
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+// transposed 2x2 stride-2 convolution from [cin][n][H][W] to [cout][n][2H][2W]
+int tconv_fwd(bsct_unet* u, const TConv& t, const float* in, int NB, int H, int W, float* out, cudaStream_t st) {
+  const long P = (long)NB * H * W;
+  k_to_bf16<<<nblk((long)t.cin * P), TPB, 0, st>>>(in, u->dpre, (long)t.cin * P);
+  count_launch();
+  UTRY(bsct::gemm_bf16(false, false, t.cout * 4, (int)P, t.cin, 1.f, u->wb + t.w, t.cin, 0, u->dpre, P, 0, 0.f, u->tmp,
+                       P, 0, 1, st));
+  k_tconv_scatter<<<nblk((long)t.cout * 4 * P), TPB, 0, st>>>(u->tmp, u->w + t.b, t.cout, NB, H, W, out);
+  count_launch();
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+int tconv_bwd(bsct_unet* u, const TConv& t, const float* in, const float* gout, int NB, int H, int W, float* gin,
+              cudaStream_t st) {
+  const long P = (long)NB * H * W;
+  bf16* gg = u->dpre;                          // gathered gradient [(cout*4)][P]
+  bf16* inb = u->col;                          // BF16 copy of the input [cin][P]
+  k_tconv_gather<<<nblk((long)t.cout * 4 * P), TPB, 0, st>>>(gout, t.cout, NB, H, W, gg);
+  k_to_bf16<<<nblk((long)t.cin * P), TPB, 0, st>>>(in, inb, (long)t.cin * P);
+  k_chan_sum<<<chan_grid(4 * P, t.cout), TPB, 0, st>>>(gout, 4 * P, u->g + t.b);
+  count_launch(3);
+  // dW[(cout*4)][cin] += gg[(cout*4)][P] in[cin][P]^T
+  UTRY(bsct::gemm_bf16(false, true, t.cout * 4, t.cin, (int)P, 1.f, gg, P, 0, inb, P, 0, 1.f, u->g + t.w, t.cin, 0, 1,
+                       st));
+  // gin[cin][P] = W^T gg
+  UTRY(bsct::gemm_bf16(true, false, t.cin, (int)P, t.cout * 4, 1.f, u->wb + t.w, t.cin, 0, gg, P, 0, 0.f, gin, P, 0, 1,
+                       st));
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+}  // namespace
+
+extern "C" int bsct_unet_create(int32_t base_channels, uint64_t seed, bsct_unet** out, void* stream) {
+  if (!out || base_channels < 8 || base_channels % 8) {
+    bsct_set_last_message("base_channels must be a positive multiple of 8");
+    return BSCT_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  bsct_unet* u = new bsct_unet();
+  const int B = base_channels;
+  u->base = B;
+  long o = 0;
+  o = add_conv(u, u->c0a, 1, B, o);
+  o = add_conv(u, u->c0b, B, B, o);
+  o = add_conv(u, u->c1a, B, 2 * B, o);
+  o = add_conv(u, u->c1b, 2 * B, 2 * B, o);
+  o = add_conv(u, u->c2a, 2 * B, 4 * B, o);
+  o = add_conv(u, u->c2b, 4 * B, 4 * B, o);
+  o = add_conv(u, u->c3a, 4 * B, 8 * B, o);
+  o = add_conv(u, u->c3b, 8 * B, 8 * B, o);
+  o = add_tconv(u->t3, 8 * B, 4 * B, o);
+  o = add_conv(u, u->d2a, 8 * B, 4 * B, o);
+  o = add_conv(u, u->d2b, 4 * B, 4 * B, o);
+  o = add_tconv(u->t2, 4 * B, 2 * B, o);
+  o = add_conv(u, u->d1a, 4 * B, 2 * B, o);
+  o = add_conv(u, u->d1b, 2 * B, 2 * B, o);
+  o = add_tconv(u->t1, 2 * B, B, o);
+  o = add_conv(u, u->d0a, 2 * B, B, o);
+  o = add_conv(u, u->d0b, B, B, o);
+  u->hw = o;
+  o += B;
+  u->hb = o;
+  o += 1;
+  o = ((o + 7) / 8) * 8;
+  u->n_params = o;
+  auto fail = [&](cudaError_t e) {
+    bsct_set_last_cuda_error(e);
+    cudaFree(u->w); cudaFree(u->g); cudaFree(u->m); cudaFree(u->v); cudaFree(u->wb);
+    delete u;
+    return BSCT_ERR_CUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&u->w, o * 4)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&u->g, o * 4)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&u->m, o * 4)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&u->v, o * 4)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&u->wb, o * 2)) != cudaSuccess) return fail(e);
+  cudaMemsetAsync(u->w, 0, o * 4, st);
+  cudaMemsetAsync(u->g, 0, o * 4, st);
+  cudaMemsetAsync(u->m, 0, o * 4, st);
+  cudaMemsetAsync(u->v, 0, o * 4, st);
+  unsigned long long s = seed;
+  auto init_conv = [&](const Conv3& c) {
+    const long n = (long)c.cout * c.kpad;
+    k_init_weights<<<nblk(n), TPB, 0, st>>>(u->w + c.w, n, c.kpad, 9 * c.cin, sqrtf(2.f / (9.f * c.cin)), ++s);
+  };
+  auto init_t = [&](const TConv& t) {
+    const long n = (long)t.cout * 4 * t.cin;
+    k_init_weights<<<nblk(n), TPB, 0, st>>>(u->w + t.w, n, t.cin, t.cin, sqrtf(1.f / t.cin), ++s);
+  };
+  for (const Conv3* c : {&u->c0a, &u->c0b, &u->c1a, &u->c1b, &u->c2a, &u->c2b, &u->c3a, &u->c3b, &u->d2a, &u->d2b,
+                         &u->d1a, &u->d1b, &u->d0a, &u->d0b})
+    init_conv(*c);
+  init_t(u->t3);
+  init_t(u->t2);
+  init_t(u->t1);
+  k_init_weights<<<1, TPB, 0, st>>>(u->w + u->hw, B, B, B, sqrtf(1.f / B), ++s);
+  k_to_bf16<<<nblk(o), TPB, 0, st>>>(u->w, u->wb, o);
+  count_launch(20);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+  *out = u;
+  return BSCT_OK;
+}
+
+extern "C" void bsct_unet_free(bsct_unet* u) {
+  if (!u) return;
+  cudaDeviceSynchronize();
+  free_acts(u);
+  cudaFree(u->w); cudaFree(u->g); cudaFree(u->m); cudaFree(u->v); cudaFree(u->wb);
+  delete u;
+}
+
+extern "C" int bsct_unet_params(bsct_unet* u, float** d_params, float** d_grads, int64_t* n_params) {
+  if (!u) { bsct_set_last_message("NULL net"); return BSCT_ERR_INVALID_ARG; }
+  if (d_params) *d_params = u->w;
+  if (d_grads) *d_grads = u->g;
+  if (n_params) *n_params = u->n_params;
+  return BSCT_OK;
+}
+
+extern "C" int bsct_unet_sync_weights(bsct_unet* u, void* stream) {
+  if (!u) { bsct_set_last_message("NULL net"); return BSCT_ERR_INVALID_ARG; }
+  k_to_bf16<<<nblk(u->n_params), TPB, 0, (cudaStream_t)stream>>>(u->w, u->wb, u->n_params);
+  count_launch();
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+extern "C" int bsct_unet_forward(bsct_unet* u, const float* d_in, float* d_out, int32_t NB, int32_t H, int32_t W,
+                                 void* stream) {
+  if (!u || !d_in || !d_out || NB < 1 || H < 64 || W < 64 || H % 64 || W % 64) {
+    bsct_set_last_message("U-Net input must be n x H x W with H, W multiples of 64");
+    return BSCT_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  UTRY(alloc_acts(u, NB, H, W));
+  const int B = u->base;
+  const long P0 = (long)NB * H * W, P1 = P0 / 4, P2 = P0 / 16;
+  BSCT_CUDA_TRY(cudaMemcpyAsync(u->x, d_in, P0 * 4, cudaMemcpyDeviceToDevice, st));
+  // encoder (skip tensors written straight into the upper halves of the concat buffers)
+  UTRY(conv_fwd(u, u->c0a, u->x, NB, H, W, u->a00, st));
+  UTRY(conv_fwd(u, u->c0b, u->a00, NB, H, W, u->cat0 + B * P0, st));
+  k_maxpool2<<<nblk(B * P1), TPB, 0, st>>>(u->cat0 + B * P0, B, NB, H, W, u->p0);
+  UTRY(conv_fwd(u, u->c1a, u->p0, NB, H / 2, W / 2, u->a10, st));
+  UTRY(conv_fwd(u, u->c1b, u->a10, NB, H / 2, W / 2, u->cat1 + 2 * B * P1, st));
+  k_maxpool2<<<nblk(2 * B * P2), TPB, 0, st>>>(u->cat1 + 2 * B * P1, 2 * B, NB, H / 2, W / 2, u->p1);
+  UTRY(conv_fwd(u, u->c2a, u->p1, NB, H / 4, W / 4, u->a20, st));
+  UTRY(conv_fwd(u, u->c2b, u->a20, NB, H / 4, W / 4, u->cat2 + 4 * B * P2, st));
+  k_maxpool2<<<nblk(4 * B * P2 / 4), TPB, 0, st>>>(u->cat2 + 4 * B * P2, 4 * B, NB, H / 4, W / 4, u->p2);
+  count_launch(3);
+  UTRY(conv_fwd(u, u->c3a, u->p2, NB, H / 8, W / 8, u->a30, st));
+  UTRY(conv_fwd(u, u->c3b, u->a30, NB, H / 8, W / 8, u->a31, st));
+  // decoder
+  UTRY(tconv_fwd(u, u->t3, u->a31, NB, H / 8, W / 8, u->cat2, st));
+  UTRY(conv_fwd(u, u->d2a, u->cat2, NB, H / 4, W / 4, u->u2a, st));
+  UTRY(conv_fwd(u, u->d2b, u->u2a, NB, H / 4, W / 4, u->u2b, st));
+  UTRY(tconv_fwd(u, u->t2, u->u2b, NB, H / 4, W / 4, u->cat1, st));
+  UTRY(conv_fwd(u, u->d1a, u->cat1, NB, H / 2, W / 2, u->u1a, st));
+  UTRY(conv_fwd(u, u->d1b, u->u1a, NB, H / 2, W / 2, u->u1b, st));
+  UTRY(tconv_fwd(u, u->t1, u->u1b, NB, H / 2, W / 2, u->cat0, st));
+  UTRY(conv_fwd(u, u->d0a, u->cat0, NB, H, W, u->u0a, st));
+  UTRY(conv_fwd(u, u->d0b, u->u0a, NB, H, W, u->u0b, st));
+  k_head_fwd<<<nblk(P0), TPB, 0, st>>>(u->u0b, u->w + u->hw, u->w + u->hb, B, P0, u->out);
+  count_launch();
+  BSCT_CUDA_TRY(cudaMemcpyAsync(d_out, u->out, P0 * 4, cudaMemcpyDeviceToDevice, st));
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+// gradient of the loss w.r.t. the last forward's output; accumulates parameter gradients
+extern "C" int bsct_unet_backward(bsct_unet* u, const float* d_gout, void* stream) {
+  if (!u || !d_gout || !u->NB) {
+    bsct_set_last_message("backward needs a preceding forward");
+    return BSCT_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int B = u->base, NB = u->NB, H = u->H, W = u->W;
+  const long P0 = (long)NB * H * W, P1 = P0 / 4, P2 = P0 / 16;
+  k_head_bwd_w<<<chan_grid(P0, B + 1), TPB, 0, st>>>(u->u0b, d_gout, B, P0, u->g + u->hw, u->g + u->hb);
+  k_head_bwd_data<<<nblk(B * P0), TPB, 0, st>>>(d_gout, u->w + u->hw, B, P0, u->gu0b);
+  count_launch(2);
+  UTRY(conv_bwd(u, u->d0b, u->u0a, u->u0b, u->gu0b, NB, H, W, u->gu0a, st));
+  UTRY(conv_bwd(u, u->d0a, u->cat0, u->u0a, u->gu0a, NB, H, W, u->gcat0, st));
+  UTRY(tconv_bwd(u, u->t1, u->u1b, u->gcat0, NB, H / 2, W / 2, u->gu1b, st));
+  UTRY(conv_bwd(u, u->d1b, u->u1a, u->u1b, u->gu1b, NB, H / 2, W / 2, u->gu1a, st));
+  UTRY(conv_bwd(u, u->d1a, u->cat1, u->u1a, u->gu1a, NB, H / 2, W / 2, u->gcat1, st));
+  UTRY(tconv_bwd(u, u->t2, u->u2b, u->gcat1, NB, H / 4, W / 4, u->gu2b, st));
+  UTRY(conv_bwd(u, u->d2b, u->u2a, u->u2b, u->gu2b, NB, H / 4, W / 4, u->gu2a, st));
+  UTRY(conv_bwd(u, u->d2a, u->cat2, u->u2a, u->gu2a, NB, H / 4, W / 4, u->gcat2, st));
+  UTRY(tconv_bwd(u, u->t3, u->a31, u->gcat2, NB, H / 8, W / 8, u->g31, st));
+  UTRY(conv_bwd(u, u->c3b, u->a30, u->a31, u->g31, NB, H / 8, W / 8, u->g30, st));
+  UTRY(conv_bwd(u, u->c3a, u->p2, u->a30, u->g30, NB, H / 8, W / 8, u->gp2, st));
+  // e2 receives the skip gradient (upper half of gcat2) plus the pooled path
+  k_maxpool2_bwd<<<nblk(4 * B * P2 / 4), TPB, 0, st>>>(u->cat2 + 4 * B * P2, u->gp2, 4 * B, NB, H / 4, W / 4,
+                                                     u->gcat2 + 4 * B * P2);
+  count_launch();
+  UTRY(conv_bwd(u, u->c2b, u->a20, u->cat2 + 4 * B * P2, u->gcat2 + 4 * B * P2, NB, H / 4, W / 4, u->g20, st));
+  UTRY(conv_bwd(u, u->c2a, u->p1, u->a20, u->g20, NB, H / 4, W / 4, u->gp1, st));
+  k_maxpool2_bwd<<<nblk(2 * B * P2), TPB, 0, st>>>(u->cat1 + 2 * B * P1, u->gp1, 2 * B, NB, H / 2, W / 2,
+                                                  u->gcat1 + 2 * B * P1);
+  count_launch();
+  UTRY(conv_bwd(u, u->c1b, u->a10, u->cat1 + 2 * B * P1, u->gcat1 + 2 * B * P1, NB, H / 2, W / 2, u->g10, st));
+  UTRY(conv_bwd(u, u->c1a, u->p0, u->a10, u->g10, NB, H / 2, W / 2, u->gp0, st));
+  k_maxpool2_bwd<<<nblk(B * P1), TPB, 0, st>>>(u->cat0 + B * P0, u->gp0, B, NB, H, W, u->gcat0 + B * P0);
+  count_launch();
+  UTRY(conv_bwd(u, u->c0b, u->a00, u->cat0 + B * P0, u->gcat0 + B * P0, NB, H, W, u->g00, st));
+  UTRY(conv_bwd(u, u->c0a, u->x, u->a00, u->g00, NB, H, W, nullptr, st));
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+extern "C" int bsct_unet_adam_step(bsct_unet* u, float lr, float beta1, float beta2, float eps, int32_t step,
+                                   void* stream) {
+  if (!u || step < 1) { bsct_set_last_message("invalid argument"); return BSCT_ERR_INVALID_ARG; }
+  const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+  k_adam<<<nblk(u->n_params), TPB, 0, (cudaStream_t)stream>>>(u->w, u->g, u->m, u->v, u->wb, u->n_params, lr, beta1,
+                                                              beta2, eps, c1, c2);
+  count_launch();
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+// ---------------------------------------------------------------------------- warm start
+namespace {
+__global__ void k_scale_copy(const float* __restrict__ a, float s, float* __restrict__ b, long n) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = s * a[i];
+}
+__global__ void k_dot2(const float* __restrict__ a, const float* __restrict__ b, const float* __restrict__ c, long n,
+                       double* __restrict__ out) {
+  // out[0] += <a, b>, out[1] += <a, c>
+  double s0 = 0.0, s1 = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    s0 += (double)a[i] * b[i];
+    s1 += (double)a[i] * c[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(out, s0);
+    atomicAdd(out + 1, s1);
+  }
+}
+}  // namespace
+
+extern "C" int bsct_cg_solve_learned(bsct_gram* g, bsct_unet* net, const void* d_b, void* d_x, float in_scale,
+                                     int max_iter, double rel_tol, int check_every, bsct_cg_report* report,
+                                     double* alpha_out, void* stream) {
+  if (!g || !net || !d_b || !d_x) { bsct_set_last_message("invalid argument"); return BSCT_ERR_INVALID_ARG; }
+  if (g->precision != BSCT_F32) { bsct_set_last_message("learned warm start needs an F32 handle"); return BSCT_ERR_INVALID_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = g->N;
+  const long n = (long)N * N;
+  float* xin = (float*)g->q;   // CG scratch is free before the solve
+  float* xhat = (float*)d_x;
+  k_scale_copy<<<nblk(n), TPB, 0, st>>>((const float*)d_b, in_scale, xin, n);
+  count_launch();
+  UTRY(bsct_unet_forward(net, xin, xhat, 1, N, N, stream));
+  float* Gx = (float*)g->r;
+  UTRY(bsct_gram_apply(g, xhat, Gx, BSCT_APPLY_FFT32, stream));
+  double* acc = g->partials;  // two doubles
+  BSCT_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
+  k_dot2<<<1024, TPB, 0, st>>>(xhat, (const float*)d_b, Gx, n, acc);
+  count_launch();
+  double h[2];
+  BSCT_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+  BSCT_CUDA_TRY(cudaStreamSynchronize(st));
+  // x0 = alpha xhat minimises the G-norm error along xhat; plain CG (x0 = 0) if it is unusable
+  const double alpha = (h[1] > 0.0 && isfinite(h[0]) && isfinite(h[1])) ? h[0] / h[1] : 0.0;
+  if (alpha_out) *alpha_out = alpha;
+  int x0_zero = 1;
+  if (alpha > 0.0 && isfinite(alpha)) {
+    k_scale_copy<<<nblk(n), TPB, 0, st>>>(xhat, (float)alpha, xhat, n);
+    count_launch();
+    x0_zero = 0;
+  }
+  return bsct_cg_solve(g, d_b, d_x, x0_zero, max_iter, rel_tol, check_every, report, stream);
+}
+
+namespace {
+// grad = 2 (pred - target) / n; loss[0] += sum (pred - target)^2 / n
+__global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ target, long n, float* __restrict__ grad,
+                      double* __restrict__ loss) {
+  double acc = 0.0;
+  const float inv = 1.f / (float)n;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const float d = pred[i] - target[i];
+    grad[i] = 2.f * d * inv;
+    acc += (double)d * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc / (double)n);
+}
+}  // namespace
+
+extern "C" int bsct_mse_loss_grad(const float* d_pred, const float* d_target, int64_t n, float* d_grad, double* d_loss,
+                                  void* stream) {
+  if (!d_pred || !d_target || !d_grad || !d_loss || n < 1) { bsct_set_last_message("invalid argument"); return BSCT_ERR_INVALID_ARG; }
+  k_mse<<<1024, TPB, 0, (cudaStream_t)stream>>>(d_pred, d_target, n, d_grad, d_loss);
+  count_launch();
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+// copy the FP32 parameters (which = 0) or gradients (which = 1) to / from caller memory
+extern "C" int bsct_unet_copy(bsct_unet* u, int which, int to_net, float* d_buf, void* stream) {
+  if (!u || !d_buf || which < 0 || which > 1) { bsct_set_last_message("invalid argument"); return BSCT_ERR_INVALID_ARG; }
+  float* net = which == 0 ? u->w : u->g;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (to_net) {
+    BSCT_CUDA_TRY(cudaMemcpyAsync(net, d_buf, u->n_params * 4, cudaMemcpyDeviceToDevice, st));
+    if (which == 0) return bsct_unet_sync_weights(u, stream);
+  } else {
+    BSCT_CUDA_TRY(cudaMemcpyAsync(d_buf, net, u->n_params * 4, cudaMemcpyDeviceToDevice, st));
+  }
+  return BSCT_OK;
+}

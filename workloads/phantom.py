@@ -133,3 +133,14 @@ def ellipse_sinogram_torch(params, angles_pi, M, lambda_y, zeta=0.0, device="cud
                               + r2 * torch.asin(torch.clamp(u / r, -1.0, 1.0)))
             sino += scale * (F(t + 0.5 * zeta) - F(t - 0.5 * zeta)) / zeta
     return sino.to(dtype)
+
+
+def poisson_log_sinogram_torch(sino, I0, generator):
+    """Torch version of ``poisson_log_sinogram`` (same scaling reading), for device tensors."""
+    import torch
+
+    pmax = float(sino.abs().max())
+    alpha = 4.0 / pmax if pmax > 0 else 1.0
+    counts = torch.poisson(I0 * torch.exp(-alpha * sino.double()), generator=generator)
+    counts = torch.clamp(counts, min=1.0)
+    return (-torch.log(counts / I0) / alpha).to(sino.dtype)
