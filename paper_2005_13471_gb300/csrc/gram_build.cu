@@ -4,8 +4,10 @@
 //                  same Gram kernel), cos/sin by cospi/sinpi (exact zeros on the axes),
 //                  sorted by angle with a rank count so every tap can find its views by
 //                  binary search.
+//   k_gram_tables: per view, the Gram kernel A(t) = M_[c, c, s, s, zeta, zeta](t) as an
+//                  exact piecewise polynomial between its kinks (FP64).
 //   k_gram_taps  : one thread per tap d of the upper half plane:
-//                    G[d] = sum_theta M_[c, c, s, s, zeta, zeta](d . u_theta)
+//                    G[d] = sum_theta A_theta(d . u_theta)
 //                  Only views with |d . u| < |c| + |s| + zeta contribute; for |d| larger
 //                  than the widest support those views form one arc of angles around the
 //                  normal of d, found by binary search.  FP64, mirrored to G[-d].
@@ -151,8 +153,96 @@ __device__ __forceinline__ int lower_bound_d(const double* __restrict__ v, int n
   return lo;
 }
 
+// Per-view table of the Gram kernel A(t) = M_[c,c,s,s,zeta,zeta](t) on t >= 0 (A is
+// even): its kinks -S + i|c| + j|s| + k zeta (i, j, k in 0..2, S = |c|+|s|+zeta) cut
+// [0, S] into <= 13 pieces on which A is a polynomial of degree <= 5; each piece is
+// stored as monomials in v = (t - mid) / halfwidth in [-1, 1], obtained by Chebyshev
+// interpolation at 6 nodes of exact FP64 values (gram_kernel, with the short-direction
+// split near the axes).  Taps then cost a 4-step search and a 6-term Horner per view.
+constexpr int GT_KMAX = 16;
+constexpr int GT_S = 0, GT_NK = 1, GT_KN = 2, GT_MID = GT_KN + GT_KMAX, GT_IHW = GT_MID + GT_KMAX,
+              GT_COEF = GT_IHW + GT_KMAX, GT_STRIDE = GT_COEF + 6 * GT_KMAX;
+
+__global__ void __launch_bounds__(32) k_gram_tables(const double2* __restrict__ cs, double zeta, double merge_tol,
+                                                    double* __restrict__ tab) {
+  const int j = blockIdx.x;
+  const double a = fabs(cs[j].x), b = fabs(cs[j].y);
+  const double S = a + b + zeta;
+  __shared__ double kn[32];
+  __shared__ int nk_s;
+  double* T = tab + (long)j * GT_STRIDE;
+  if (threadIdx.x == 0) {
+    int n = 0;
+    kn[n++] = 0.0;
+    for (int i = 0; i <= 2; ++i)
+      for (int jj = 0; jj <= 2; ++jj)
+        for (int k = 0; k <= (zeta > 0.0 ? 2 : 0); ++k) {
+          const double x = -S + i * a + jj * b + k * zeta;
+          if (x > 0.0 && x < S) kn[n++] = x;
+        }
+    kn[n++] = S;
+    for (int i = 1; i < n; ++i) {  // sort
+      const double t = kn[i];
+      int q = i - 1;
+      while (q >= 0 && kn[q] > t) { kn[q + 1] = kn[q]; --q; }
+      kn[q + 1] = t;
+    }
+    int m = 1;  // merge kinks closer than merge_tol (keep S as the last one)
+    for (int i = 1; i < n; ++i)
+      if (kn[i] - kn[m - 1] > merge_tol) kn[m++] = kn[i];
+      else if (i == n - 1) kn[m - 1] = kn[i];
+    nk_s = m;
+    T[GT_S] = S;
+    T[GT_NK] = m;
+    for (int i = 0; i < GT_KMAX; ++i) T[GT_KN + i] = i < m ? kn[i] : 1e300;
+  }
+  __syncthreads();
+  const int nk = nk_s;
+  const int q = threadIdx.x;
+  if (q >= GT_KMAX) return;
+  if (q >= nk - 1) {
+    T[GT_MID + q] = 0.0;
+    T[GT_IHW + q] = 0.0;
+    for (int i = 0; i < 6; ++i) T[GT_COEF + 6 * q + i] = 0.0;
+    return;
+  }
+  const double lo = kn[q], hi = kn[q + 1];
+  const double mid = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
+  double fv[6], ch[6];
+  for (int i = 0; i < 6; ++i) fv[i] = gram_kernel(mid + hw * cospi((2.0 * i + 1.0) / 12.0), a, b, zeta);
+  for (int k = 0; k < 6; ++k) {
+    double acc = 0.0;
+    for (int i = 0; i < 6; ++i) acc += fv[i] * cospi(k * (2.0 * i + 1.0) / 12.0);
+    ch[k] = acc * (k == 0 ? 1.0 / 6.0 : 2.0 / 6.0);
+  }
+  double* c = T + GT_COEF + 6 * q;
+  c[0] = ch[0] - ch[2] + ch[4];
+  c[1] = ch[1] - 3.0 * ch[3] + 5.0 * ch[5];
+  c[2] = 2.0 * ch[2] - 8.0 * ch[4];
+  c[3] = 4.0 * ch[3] - 20.0 * ch[5];
+  c[4] = 8.0 * ch[4];
+  c[5] = 16.0 * ch[5];
+  T[GT_MID + q] = mid;
+  T[GT_IHW + q] = 1.0 / hw;
+}
+
+__device__ __forceinline__ double gram_table_eval(const double* __restrict__ T, double t) {
+  int q = 0;
+#pragma unroll
+  for (int step = 8; step > 0; step >>= 1)
+    if (T[GT_KN + q + step] <= t) q += step;
+  const double v = (t - T[GT_MID + q]) * T[GT_IHW + q];
+  const double* c = T + GT_COEF + 6 * q;
+  double r = c[5];
+  r = fma(r, v, c[4]);
+  r = fma(r, v, c[3]);
+  r = fma(r, v, c[2]);
+  r = fma(r, v, c[1]);
+  return fma(r, v, c[0]);
+}
+
 __global__ void k_gram_taps(int N, int na, const double* __restrict__ th, const double2* __restrict__ cs,
-                            double zeta, double* __restrict__ G) {
+                            const double* __restrict__ tab, double zeta, double* __restrict__ G) {
   const long H = (long)(2 * N - 1) * (N - 1) + N;
   const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= H) return;
@@ -169,9 +259,9 @@ __global__ void k_gram_taps(int N, int na, const double* __restrict__ th, const 
   auto visit = [&](int j0, int j1) {
     for (int j = j0; j < j1; ++j) {
       const double2 u = cs[j];
-      const double t = d1 * u.x + d2 * u.y;
-      const double a = fabs(u.x), b = fabs(u.y);
-      if (fabs(t) < a + b + zeta) acc += gram_kernel(t, a, b, zeta);
+      const double t = fabs(d1 * u.x + d2 * u.y);
+      const double* T = tab + (long)j * GT_STRIDE;
+      if (t < T[GT_S]) acc += gram_table_eval(T, t);
     }
   };
   const double hw = (r > wmax) ? asin(wmax / r) * 0.31830988618379067154 + 1e-12 : 1.0;
@@ -353,19 +443,20 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
   g->n_angles = na;
   g->zeta = geom->zeta_blur;
   g->lambda = geom->lambda_y;
-  double *d_ang = nullptr, *d_th = nullptr, *d_emb = nullptr;
+  double *d_ang = nullptr, *d_th = nullptr, *d_emb = nullptr, *d_gtab = nullptr;
   double2* d_cs = nullptr;
   void* d_S2 = nullptr;
   cpx<double>* tw64 = nullptr;
   auto cleanup = [&]() {
     cudaFree(d_ang); cudaFree(d_th); cudaFree(d_cs); cudaFree(d_emb); cudaFree(d_S2);
-    cudaFree(tw64);
+    cudaFree(tw64); cudaFree(d_gtab);
     if (g) { bsct_gram_free(g); g = nullptr; }
   };
   const size_t T = precision == BSCT_F32 ? sizeof(float) : sizeof(double);
   CTRY(cudaMalloc(&d_ang, na * sizeof(double)));
   CTRY(cudaMalloc(&d_th, na * sizeof(double)));
   CTRY(cudaMalloc(&d_cs, na * sizeof(double2)));
+  CTRY(cudaMalloc(&d_gtab, (size_t)na * GT_STRIDE * sizeof(double)));
   CTRY(cudaMalloc(&g->taps, ntap * sizeof(double)));
   CTRY(cudaMalloc(&d_emb, (size_t)L * L * sizeof(double)));
   CTRY(cudaMalloc(&d_S2, (size_t)L * N * 2 * sizeof(double)));
@@ -375,9 +466,10 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
 
   k_geometry<<<(na + 127) / 128, 128, 0, st>>>(d_ang, na, d_th, d_cs);
   const long H = (long)(2 * N - 1) * (N - 1) + N;
-  k_gram_taps<<<(unsigned)((H + 127) / 128), 128, 0, st>>>(N, na, d_th, d_cs, geom->zeta_blur, g->taps);
+  k_gram_tables<<<na, 32, 0, st>>>(d_cs, geom->zeta_blur, 1e-13, d_gtab);
+  k_gram_taps<<<(unsigned)((H + 127) / 128), 128, 0, st>>>(N, na, d_th, d_cs, d_gtab, geom->zeta_blur, g->taps);
   k_embed<<<(unsigned)(((long)L * L + 255) / 256), 256, 0, st>>>(g->taps, N, d_emb);
-  count_launch(3);
+  count_launch(4);
   CTRY(cudaGetLastError());
   TRY(build_fft_tables<double>(tw64, N, st));
   TRY(o64.spectrum(d_emb, (cpx<double>*)d_S2, g->Gt64, tw64, st));
@@ -405,7 +497,7 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
   CTRY(cudaGetLastError());
   CTRY(cudaStreamSynchronize(st));
   cudaFree(d_ang); cudaFree(d_th); cudaFree(d_cs); cudaFree(d_emb); cudaFree(d_S2);
-  cudaFree(tw64);
+  cudaFree(tw64); cudaFree(d_gtab);
   *out = g;
   return BSCT_OK;
 }
