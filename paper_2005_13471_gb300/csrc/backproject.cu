@@ -30,11 +30,12 @@ namespace bsct {
 constexpr int BP_QMAX = 12;   // pieces per view (<= 9 occur)
 constexpr int BP_NJMAX = 16;  // samples touching one pixel (lambda_y >= ~0.2)
 constexpr int BP_HDR = 8;
-constexpr int BP_SIG = BP_HDR;                      // sigma[QMAX+1]
-constexpr int BP_MID = BP_SIG + BP_QMAX + 1;        // mid[QMAX]
+constexpr int BP_SIG = BP_HDR;                      // sigma[16] (padded with 2, for a 4-step search)
+constexpr int BP_MID = BP_SIG + 16;                 // mid[QMAX]
 constexpr int BP_IHW = BP_MID + BP_QMAX;            // 1/halfwidth[QMAX]
 constexpr int BP_COEF = 48;                         // coef[QMAX][NJMAX][8], aligned
-constexpr int BP_STRIDE = BP_COEF + BP_QMAX * BP_NJMAX * 8;
+constexpr int BP_QSTRIDE = BP_NJMAX * 8 + 4;        // piece stride: +4 words moves each piece to other banks
+constexpr int BP_STRIDE = BP_COEF + BP_QMAX * BP_QSTRIDE;
 constexpr int BP_TX = 32, BP_TY = 8, BP_CHUNK = 64;
 
 __host__ __device__ inline int bp_degree(double c, double s, double zeta) {
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(256) k_bp_tables(const double* __restrict__ an
     h[2] = T(q < BP_QMAX ? q : BP_QMAX);
     h[3] = T(J0);
     h[4] = T(nJ);
-    for (int i = 0; i <= BP_QMAX; ++i) h[BP_SIG + i] = i <= q ? T(sig[i]) : T(2.0);
+    for (int i = 0; i < 16; ++i) h[BP_SIG + i] = i <= q ? T(sig[i]) : T(2.0);
     if (q > BP_QMAX || nJ > BP_NJMAX) atomicExch(status, 1);
     // detector coordinate of pixel (0, 0) in bin units, FP64
     const double x0 = -0.5 * (N - 1);
@@ -125,9 +126,10 @@ __global__ void __launch_bounds__(256) k_bp_tables(const double* __restrict__ an
   const int Q = Qs;
   if (Q > BP_QMAX || nJ > BP_NJMAX) return;
   T* h = tab + (long)a * BP_STRIDE;
+  for (int i = threadIdx.x; i < BP_QMAX * 4; i += blockDim.x) h[BP_COEF + (i / 4) * BP_QSTRIDE + BP_NJMAX * 8 + i % 4] = T(0);
   for (int w = threadIdx.x; w < BP_QMAX * BP_NJMAX; w += blockDim.x) {
     const int q = w / BP_NJMAX, j = w % BP_NJMAX;
-    T* cf = h + BP_COEF + (q * BP_NJMAX + j) * 8;
+    T* cf = h + BP_COEF + q * BP_QSTRIDE + j * 8;
     if (q >= Q || j >= nJ) {
       for (int i = 0; i < 8; ++i) cf[i] = T(0);
       if (j == 0 && q < BP_QMAX) { h[BP_MID + q] = T(0); h[BP_IHW + q] = T(0); }
@@ -194,62 +196,116 @@ template <> struct Acc<double> { typedef double part; };
 
 // Each warp owns an 8 x 4 pixel sub-tile; its detector coordinate is computed per view in
 // FP64 by the warp itself, so the FP32 part of p only spans |offset| <= 7|c| + 3|s| + 1.
+// The tables of BP_CH views at a time are staged in shared memory (one float4 copy per
+// chunk), so the per-pair piece search and coefficient reads hit shared memory.
+constexpr int BP_CH = 8;
+// Detector samples one view needs for a 32 x 8 tile.  Over the tile the detector
+// coordinate spans at most (31|c| + 7|s|) / lambda <= 31.7805 / lambda bins; a pixel's
+// first sample index is floor(p) + J0 with floor(p) in [floor(p_min) - 1, p_max + 1]
+// (the -1 / +1 absorb FP32 rounding of p), and it reads nJ <= BP_NJMAX samples from
+// there, so the window [floor(p_min) - 1 + J0, ...) needs 31.7805 / lambda + BP_NJMAX + 3
+// entries; bp_window() adds one more and rounds up to a multiple of 4.
+inline int bp_window(double lambda) {
+  const int w = (int)ceil(31.7806 / lambda) + BP_NJMAX + 4;
+  return (w + 3) & ~3;
+}
+template <typename T> size_t bp_gather_smem(int win) { return (size_t)BP_CH * (BP_STRIDE + win) * sizeof(T); }
+
+// eight consecutive table entries (16-byte aligned) from shared memory
+__device__ inline void bp_load8(const float* p, float c[8]) {
+  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+  c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w; c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+}
+__device__ inline void bp_load8(const double* p, double c[8]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double2 a = *reinterpret_cast<const double2*>(p + 2 * i);
+    c[2 * i] = a.x; c[2 * i + 1] = a.y;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(BP_TX* BP_TY) k_bp_gather(const T* __restrict__ tab, const double2* __restrict__ csl,
                                                           const double* __restrict__ p00, const T* __restrict__ ct,
-                                                          int na, int N, int M, T* __restrict__ b) {
+                                                          int na, int N, int M, int win, T* __restrict__ b) {
   constexpr int WX = 8, WY = 4;
-  __shared__ int s_mb[8][BP_CHUNK];
-  __shared__ T s_fb[8][BP_CHUNK];
+  extern __shared__ __align__(16) unsigned char bp_smraw[];
+  T* stab = reinterpret_cast<T*>(bp_smraw);  // [BP_CH][BP_STRIDE] view tables
+  T* s_ct = stab + BP_CH * BP_STRIDE;        // [BP_CH][win] detector samples of this tile
+  __shared__ int s_mlo[BP_CH];
+  __shared__ int s_mb[8][BP_CH];
+  __shared__ T s_fb[8][BP_CH];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int X0 = blockIdx.x * BP_TX + (w & 3) * WX, Y0 = blockIdx.y * BP_TY + (w >> 2) * WY;
+  const int TX0 = blockIdx.x * BP_TX, TY0 = blockIdx.y * BP_TY;
+  const int X0 = TX0 + (w & 3) * WX, Y0 = TY0 + (w >> 2) * WY;
   const int lx = lane & 7, ly = lane >> 3;
   const int k1 = X0 + lx, k2 = Y0 + ly;
   double total = 0.0;
-  for (int a0 = 0; a0 < na; a0 += BP_CHUNK) {
-    const int nc = min(BP_CHUNK, na - a0);
-    __syncwarp();
-    for (int i = lane; i < nc; i += 32) {
-      const double2 u = csl[a0 + i];
-      const double pt = p00[a0 + i] + (double)X0 * u.x + (double)Y0 * u.y;
-      const double mb = floor(pt);
-      s_mb[w][i] = (int)mb;
-      s_fb[w][i] = T(pt - mb);
+  typename Acc<T>::part part = 0;
+  for (int a0 = 0; a0 < na; a0 += BP_CH) {
+    const int nc = min(BP_CH, na - a0);
+    __syncthreads();  // previous chunk's tables are no longer read
+    {
+      constexpr int V = 16 / sizeof(T);  // elements per 16-byte vector
+      const int nv = nc * BP_STRIDE / V;
+      const float4* src = reinterpret_cast<const float4*>(tab + (long)a0 * BP_STRIDE);
+      float4* dst = reinterpret_cast<float4*>(stab);
+      for (int i = threadIdx.x; i < nv; i += blockDim.x) dst[i] = src[i];
     }
-    __syncwarp();
-    typename Acc<T>::part part = 0;
+    if (threadIdx.x < nc) {
+      // lowest sample any pixel of the tile touches for this view (tile corners, FP64)
+      const int a = a0 + threadIdx.x;
+      const double2 u = csl[a];
+      const double pa = p00[a] + (double)TX0 * u.x + (double)TY0 * u.y;
+      const double ex = (double)(BP_TX - 1) * u.x, ey = (double)(BP_TY - 1) * u.y;
+      const double pmin = pa + (ex < 0 ? ex : 0.0) + (ey < 0 ? ey : 0.0);
+      const int J0 = (int)tab[(long)a * BP_STRIDE + 3];
+      s_mlo[threadIdx.x] = (int)floor(pmin) - 1 + J0;
+    }
+    if (lane < nc) {
+      const double2 u = csl[a0 + lane];
+      const double pt = p00[a0 + lane] + (double)X0 * u.x + (double)Y0 * u.y;
+      const double mb = floor(pt);
+      s_mb[w][lane] = (int)mb;
+      s_fb[w][lane] = T(pt - mb);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc * win; i += blockDim.x) {
+      const int ai = i / win, k = i - ai * win;
+      const int m = s_mlo[ai] + k;
+      s_ct[i] = ((unsigned)m < (unsigned)M) ? ct[(long)(a0 + ai) * M + m] : T(0);
+    }
+    __syncthreads();
     for (int ai = 0; ai < nc; ++ai) {
-      const int a = a0 + ai;
-      const T* h = tab + (long)a * BP_STRIDE;
+      const T* h = stab + ai * BP_STRIDE;
       const T cl = h[0], sl = h[1];
-      const int Q = (int)h[2], J0 = (int)h[3], nJ = (int)h[4];
+      const int J0 = (int)h[3], nJ = (int)h[4];
       const T pl = s_fb[w][ai] + T(lx) * cl + T(ly) * sl;
       const T fl = floor(pl);
       const T f = pl - fl;
-      const int m0 = s_mb[w][ai] + (int)fl + J0;
+      const int moff = s_mb[w][ai] + (int)fl + J0 - s_mlo[ai];  // window index of offset j = 0
       int q = 0;
 #pragma unroll
-      for (int i = 1; i < BP_QMAX; ++i) q += (i < Q && h[BP_SIG + i] <= f) ? 1 : 0;
+      for (int step = 8; step > 0; step >>= 1)
+        if (h[BP_SIG + q + step] <= f) q += step;
       const T v = (f - h[BP_MID + q]) * h[BP_IHW + q];
-      const T* cf = h + BP_COEF + q * BP_NJMAX * 8;
-      const T* cr = ct + (long)a * M;
+      const T* cf = h + BP_COEF + q * BP_QSTRIDE;
+      const T* cw = s_ct + ai * win + moff;
       for (int j = 0; j < nJ; ++j) {
-        const int m = m0 + j;
-        if ((unsigned)m < (unsigned)M) {
-          const T* c = cf + j * 8;
-          T wv = c[5];
-          wv = fma(wv, v, c[4]);
-          wv = fma(wv, v, c[3]);
-          wv = fma(wv, v, c[2]);
-          wv = fma(wv, v, c[1]);
-          wv = fma(wv, v, c[0]);
-          part += wv * cr[m];
-        }
+        T c[8];
+        bp_load8(cf + j * 8, c);
+        T wv = c[5];
+        wv = fma(wv, v, c[4]);
+        wv = fma(wv, v, c[3]);
+        wv = fma(wv, v, c[2]);
+        wv = fma(wv, v, c[1]);
+        wv = fma(wv, v, c[0]);
+        part += wv * cw[j];
       }
-      if ((ai & 31) == 31) { total += (double)part; part = 0; }
     }
-    total += (double)part;
+    if (((a0 / BP_CH) & 3) == 3) { total += (double)part; part = 0; }
   }
+  total += (double)part;
   if (k1 < N && k2 < N) b[(long)k2 * N + k1] = T(total);
 }
 
@@ -296,7 +352,10 @@ template <typename T> int bp_apply(const BpPlan& p, const T* sino, T* ct, T* b, 
   dim3 gp((p.M + 127) / 128, p.na);
   k_prefilter<T><<<gp, 128, 0, st>>>(p.ang, sino, p.na, p.M, p.zeta, ct);
   dim3 gg((p.N + BP_TX - 1) / BP_TX, (p.N + BP_TY - 1) / BP_TY);
-  k_bp_gather<T><<<gg, BP_TX * BP_TY, 0, st>>>((const T*)p.tab, p.csl, p.p00, ct, p.na, p.N, p.M, b);
+  const int win = bp_window(p.lambda);
+  const size_t smem = bp_gather_smem<T>(win);
+  BSCT_CUDA_TRY(cudaFuncSetAttribute(k_bp_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_bp_gather<T><<<gg, BP_TX * BP_TY, smem, st>>>((const T*)p.tab, p.csl, p.p00, ct, p.na, p.N, p.M, win, b);
   count_launch(2);
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
@@ -341,6 +400,10 @@ int bsct_check_bp_geom(const bsct_geom* geom) {
   int J0, nJ;
   bp_jrange(W, geom->lambda_y, &J0, &nJ);
   if (nJ > BP_NJMAX) { bsct_set_last_message("lambda_y too small: too many samples per pixel"); return BSCT_ERR_UNSUPPORTED_SIZE; }
+  if (bp_gather_smem<double>(bp_window(geom->lambda_y)) > 227 * 1024) {
+    bsct_set_last_message("lambda_y too small: detector window does not fit in shared memory");
+    return BSCT_ERR_UNSUPPORTED_SIZE;
+  }
   return BSCT_OK;
 }
 
