@@ -264,6 +264,15 @@ const char* bsct_last_error_string(void);
 int bsct_set_kernel_timing(int on);
 int bsct_kernel_times(float* ms, int n);
 
+/* Launch overlap of the Gram-apply kernels (a scheduling choice, not part of the method).
+ * When on (the default), each of the three kernels of an FFT-mode apply (and of the CG
+ * applies) is launched as a programmatic dependent launch: its CTAs may be scheduled
+ * while the previous kernel on the stream is finishing, and each kernel waits for its
+ * predecessor's completion before its first global-memory access, so results and stream
+ * order are the same either way.  bsct_set_launch_overlap(0) launches them plainly.
+ * Process-wide; returns BSCT_OK.  Not thread-safe with concurrent applies. */
+int bsct_set_launch_overlap(int on);
+
 /* Number of kernel launches issued by this library since load (all threads). */
 uint64_t bsct_launch_count(void);
 

@@ -116,6 +116,8 @@ def _declare(L):
     L.bsct_set_kernel_timing.restype = ctypes.c_int
     L.bsct_kernel_times.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_int]
     L.bsct_kernel_times.restype = ctypes.c_int
+    L.bsct_set_launch_overlap.argtypes = [ctypes.c_int]
+    L.bsct_set_launch_overlap.restype = ctypes.c_int
     L.bsct_launch_count.argtypes = []
     L.bsct_launch_count.restype = ctypes.c_uint64
     for name in ("bsct_gram_build", "bsct_gram_taps", "bsct_gram_spectrum", "bsct_gram_apply",
@@ -156,6 +158,11 @@ def launch_count():
 def set_kernel_timing(on):
     """Record CUDA events between the three Gram-apply kernels (see bsct_kernel_times)."""
     _check(lib().bsct_set_kernel_timing(1 if on else 0), "bsct_set_kernel_timing")
+
+
+def set_launch_overlap(on):
+    """Programmatic dependent launch of the Gram-apply kernels (on by default; see bsct_set_launch_overlap)."""
+    _check(lib().bsct_set_launch_overlap(1 if on else 0), "bsct_set_launch_overlap")
 
 
 def kernel_times():

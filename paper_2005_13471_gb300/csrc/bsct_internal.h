@@ -30,6 +30,31 @@ inline void timer_mark(cudaStream_t st, int i) {
   g_timer.n_recorded = i + 1;
 }
 
+// Programmatic dependent launch of the Gram-apply kernels: a kernel launched by
+// launch_overlap() may be scheduled while the previous kernel of the stream is still
+// running its last CTAs.  Each such kernel calls pdl_trigger() first (its own successor
+// may then be scheduled once all of its CTAs have started) and pdl_wait() before its
+// first global-memory access; pdl_wait returns once the previous grid has completed and
+// its writes are visible, so the stream order of all memory effects is unchanged.
+// On by default; bsct_set_launch_overlap(0) launches them plainly.
+extern bool g_overlap;
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KP, typename... A>
+inline cudaError_t launch_overlap(void (*k)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = g_overlap ? 1 : 0;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KP>(args)...);
+}
+
 // FFT convolution kernels for one image size N (row FFT length N, column length 2N).
 //   S:   N x N complex scratch (row-block interleaved half spectra)
 //   Gt:  spectrum, [N+1][2N] real, scaled by 1/(2N)^2 (row 0 = (G0+GN)/2, row N = (G0-GN)/2)

@@ -29,6 +29,7 @@ namespace bsct {
 
 std::atomic<unsigned long long> g_launches{0};
 KernelTimer g_timer;
+bool g_overlap = true;
 
 // ------------------------------------------------------------------------------------
 // FFT dispatch over the supported sizes
@@ -364,6 +365,11 @@ static int fail_msg(int code, const char* msg) { return fail(code, msg); }
 extern "C" int bsct_set_kernel_timing(int on) {
   g_timer.on = on != 0;
   g_timer.n_recorded = 0;
+  return BSCT_OK;
+}
+
+extern "C" int bsct_set_launch_overlap(int on) {
+  g_overlap = on != 0;
   return BSCT_OK;
 }
 

@@ -70,6 +70,8 @@ k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
   const cpx<T>* z = reinterpret_cast<const cpx<T>*>(x + (long)(row0 + f) * ld_x);
   const cpx<T>* zp = CG ? reinterpret_cast<const cpx<T>*>(p_old + (long)(row0 + f) * ld_x) : nullptr;
   cpx<T>* zn = CG ? reinterpret_cast<cpx<T>*>(p_new + (long)(row0 + f) * ld_x) : nullptr;
+  pdl_trigger();
+  pdl_wait();
   const T beta = CG ? T(*cg_beta) : T(0);
 
   cpx<T> v[E];
@@ -99,24 +101,30 @@ k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
     for (int r = 0; r < RL; ++r) sm[spad(j + r * (LR / RL))] = v[b * RL + r];
   }
   __syncthreads();
-  // untangle Z = FFT(x_even + i x_odd) into X[v] = E[v] + W^v O[v]; coalesced store
+  // untangle Z = FFT(x_even + i x_odd) into X[v] = E[v] + W^v O[v], two bins per item:
+  // E and O are spectra of real sequences, and W^(LR - v) = -conj(W^v), so
+  // X[LR - v] = conj(E[v] - W^v O[v]); item v = 0 gives the packed (X[0], X[LR]) and
+  // X[LR/2] = conj(Z[LR/2]).  Stores of both bins are coalesced (ascending / descending).
+  constexpr int HL = LR / 2;
   cpx<T>* out = S + (long)(row0 >> 2) * LR * 4;
 #pragma unroll 4
-  for (int it = 0; it < E; ++it) {
+  for (int it = 0; it < E / 2; ++it) {
     const int e = threadIdx.x + it * (RPC * TT);
-    const int rr = e & 3, vv = (e >> 2) % LR, fb = (e >> 2) / LR;
+    const int rr = e & 3, vv = (e >> 2) % HL, fb = (e >> 2) / HL;
     const cpx<T>* smf = sm_all + (fb * 4 + rr) * SME;
+    cpx<T>* o = out + (long)fb * LR * 4 + rr;
     const cpx<T> Z = smf[spad(vv)];
-    cpx<T> X;
     if (vv == 0) {
-      X = mk(Z.x + Z.y, Z.x - Z.y);  // (X[0], X[LR]) both real
+      const cpx<T> Zh = smf[spad(HL)];
+      st_cpx(o, mk(Z.x + Z.y, Z.x - Z.y));  // (X[0], X[LR]) both real
+      st_cpx(o + HL * 4, conj(Zh));
     } else {
       const cpx<T> Zm = conj(smf[spad(LR - vv)]);
       const cpx<T> Ev = scale(Z + Zm, T(0.5));
-      const cpx<T> Od = scale(mul_mi<T, false>(Z - Zm), T(0.5));
-      X = Ev + cmul(Od, ld_cpx(twc + vv));
+      const cpx<T> WO = cmul(scale(mul_mi<T, false>(Z - Zm), T(0.5)), ld_cpx(twc + vv));
+      st_cpx(o + vv * 4, Ev + WO);
+      st_cpx(o + (LR - vv) * 4, conj(Ev - WO));
     }
-    st_cpx(out + e, X);
   }
 }
 
@@ -138,12 +146,32 @@ k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
   const int row0 = blockIdx.x * RPC;
   cpx<T>* sm = sm_all + f * SME;
 
+  // inverse untangle straight from the half spectra, two bins per item: with
+  // Ev = Y[v] + conj(Y[LR-v]) and Od = (Y[v] - conj(Y[LR-v])) conj(W^v), the row FFT input
+  // is Zp[v] = Ev + i Od and Zp[LR - v] = conj(Ev - i Od); item v = 0 also gives
+  // Zp[LR/2] = 2 conj(Y[LR/2]).  All loads of a thread are issued together.
+  constexpr int HL = LR / 2;
   const cpx<T>* in = S + (long)(row0 >> 2) * LR * 4;
-#pragma unroll 4
-  for (int it = 0; it < E; ++it) {
+  pdl_trigger();
+  pdl_wait();
+#pragma unroll
+  for (int it = 0; it < E / 2; ++it) {
     const int e = threadIdx.x + it * (RPC * TT);
-    const int rr = e & 3, vv = (e >> 2) % LR, fb = (e >> 2) / LR;
-    sm_all[(fb * 4 + rr) * SME + spad(vv)] = ld_cpx(in + e);
+    const int rr = e & 3, vv = (e >> 2) % HL, fb = (e >> 2) / HL;
+    const cpx<T>* ir = in + (long)fb * LR * 4 + rr;
+    cpx<T>* smf = sm_all + (fb * 4 + rr) * SME;
+    const cpx<T> Y = ld_cpx(ir + vv * 4);
+    const cpx<T> Yo = ld_cpx(ir + (vv == 0 ? HL : LR - vv) * 4);
+    if (vv == 0) {
+      smf[spad(0)] = mk(Y.x + Y.y, Y.x - Y.y);
+      smf[spad(HL)] = mk(Yo.x + Yo.x, -(Yo.y + Yo.y));
+    } else {
+      const cpx<T> Ym = conj(Yo);
+      const cpx<T> Ev = Y + Ym;
+      const cpx<T> iOd = mul_mi<T, true>(cmulc(Y - Ym, ld_cpx(twc + vv)));
+      smf[spad(vv)] = Ev + iOd;
+      smf[spad(LR - vv)] = conj(Ev - iOd);
+    }
   }
   __syncthreads();
   // the inverse runs the plan reversed: its first radix is the plan's last (RF) and its
@@ -154,20 +182,7 @@ k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
   for (int b = 0; b < E / RF; ++b) {
     const int j = tid + b * TT;
 #pragma unroll
-    for (int r = 0; r < RF; ++r) {
-      const int idx = j + r * (LR / RF);
-      const cpx<T> Y = sm[spad(idx)];
-      cpx<T> Zp;
-      if (idx == 0) {
-        Zp = mk(Y.x + Y.y, Y.x - Y.y);
-      } else {
-        const cpx<T> Ym = conj(sm[spad(LR - idx)]);
-        const cpx<T> Ev = Y + Ym;
-        const cpx<T> Od = cmulc(Y - Ym, ld_cpx(twc + idx));
-        Zp = Ev + mul_mi<T, true>(Od);  // E' + i O'
-      }
-      v[b * RF + r] = Zp;
-    }
+    for (int r = 0; r < RF; ++r) v[b * RF + r] = sm[spad(j + r * (LR / RF))];
   }
   __syncthreads();
   fft<T, LR, true, true>(v, sm, tid, tsr);
@@ -273,6 +288,8 @@ k_cols_conv(cpx<T>* __restrict__ S, const T* __restrict__ Gt, const cpx<T>* __re
   };
 
   int tile = blockIdx.x;
+  pdl_trigger();
+  pdl_wait();
 #pragma unroll
   for (int s = 0; s < STAGES; ++s) prefetch(tile + s * gridDim.x, s);
 
@@ -466,11 +483,13 @@ static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw
   }
   const TwPtrs<T> t = tw_ptrs(tw, N);
   timer_mark(st, 0);
-  k_rows_r2c<T, LR, true, RPC><<<N / RPC, TR, smr, st>>>(x, N, S, t.rows_f, t.untangle);
+  BSCT_CUDA_TRY(launch_overlap(k_rows_r2c<T, LR, true, RPC>, dim3(N / RPC), dim3(TR), smr, st, x, (long)N, S,
+                               t.rows_f, t.untangle, (const T*)nullptr, (T*)nullptr, (const double*)nullptr));
   timer_mark(st, 1);
-  kc<<<grid_c, TC, smc, st>>>(S, Gt, t.cols_f, t.cols_r, N / CC::G);
+  BSCT_CUDA_TRY(launch_overlap(kc, dim3(grid_c), dim3(TC), smc, st, S, Gt, t.cols_f, t.cols_r, N / CC::G));
   timer_mark(st, 2);
-  k_rows_c2r<T, LR, RPC><<<N / RPC, TR, smr, st>>>(S, y, N, t.rows_r, t.untangle);
+  BSCT_CUDA_TRY(launch_overlap(k_rows_c2r<T, LR, RPC>, dim3(N / RPC), dim3(TR), smr, st, (const cpx<T>*)S, y,
+                               (long)N, t.rows_r, t.untangle, (const T*)nullptr, (double*)nullptr));
   timer_mark(st, 3);
   count_launch(3);
   BSCT_CUDA_TRY(cudaGetLastError());
@@ -503,9 +522,11 @@ static int apply_cg_impl(const T* r, T* p, T* q, const double* beta, double* par
     grid_c = per_sm * sm_count() < tiles ? per_sm * sm_count() : tiles;
   }
   const TwPtrs<T> t = tw_ptrs(tw, N);
-  k_rows_r2c<T, LR, true, RPC, true><<<N / RPC, TR, smr, st>>>(r, N, S, t.rows_f, t.untangle, p, p, beta);
-  kc<<<grid_c, TC, smc, st>>>(S, Gt, t.cols_f, t.cols_r, N / CC::G);
-  k_rows_c2r<T, LR, RPC, true><<<N / RPC, TR, smr, st>>>(S, q, N, t.rows_r, t.untangle, p, part);
+  BSCT_CUDA_TRY(launch_overlap(k_rows_r2c<T, LR, true, RPC, true>, dim3(N / RPC), dim3(TR), smr, st, r, (long)N, S,
+                               t.rows_f, t.untangle, (const T*)p, p, beta));
+  BSCT_CUDA_TRY(launch_overlap(kc, dim3(grid_c), dim3(TC), smc, st, S, Gt, t.cols_f, t.cols_r, N / CC::G));
+  BSCT_CUDA_TRY(launch_overlap(k_rows_c2r<T, LR, RPC, true>, dim3(N / RPC), dim3(TR), smr, st, (const cpx<T>*)S, q,
+                               (long)N, t.rows_r, t.untangle, (const T*)p, part));
   count_launch(3);
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
