@@ -225,9 +225,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         flush.zero_()
         g.apply(x, y)
-    bsct.set_kernel_timing(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    ktimes = np.zeros(3)
     barrier()
     with ClockSampler(local) as clk:
         # keep the GPU busy for ~1.5 s first so that the clock samples see it under load
@@ -236,7 +234,6 @@ def run_ours(args):
             for _ in range(50):
                 g.apply(x, y)
             torch.cuda.synchronize()
-        bsct.kernel_times()  # discard the events of the load phase
         launches0 = bsct.launch_count()
         wall0 = time.perf_counter()
         for i in range(args.steps):
@@ -244,11 +241,19 @@ def run_ours(args):
             ev[i][0].record(stream)
             g.apply(x, y)
             ev[i][1].record(stream)
-            ktimes += np.array(bsct.kernel_times())
         barrier()
         wall = time.perf_counter() - wall0
-    launches = bsct.launch_count() - launches0
-    bsct.set_kernel_timing(False)
+        launches = bsct.launch_count() - launches0
+        # per-kernel durations: the same K steps again with CUDA events recorded on the
+        # launching stream between the three kernels.  The events serialise the kernels
+        # (no launch overlap), so this pass is kept out of the headline loop above.
+        bsct.set_kernel_timing(True)
+        ktimes = np.zeros(3)
+        for i in range(args.steps):
+            flush.zero_()
+            g.apply(x, y)
+            ktimes += np.array(bsct.kernel_times())
+        bsct.set_kernel_timing(False)
     step_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
     step_ms = max_over_ranks(step_ms)
     value = world * args.steps / (step_ms * 1e-3)
@@ -271,6 +276,8 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": kernel_bytes[dname],
                 "traffic": profiled_traffic(dname, N),
                 "kernel_ms": {n: float(t) for n, t in zip(names, kt)},
+                "kernel_timing": "CUDA events between the kernels in a second pass of the K steps, after the "
+                                 "headline loop (the events serialise the kernels)",
                 "whole_apply": {"algorithmic_bytes": apply_bytes,
                                 "achieved_GBs": apply_bytes / (step_ms / args.steps * 1e-3) / 1e9 / world * world,
                                 "frac": apply_bytes / (step_ms / args.steps * 1e-3) / 1e9 / hbm}}

@@ -40,13 +40,22 @@ BSCT_PLAN(64, 16, 16, 4)
 BSCT_PLAN(128, 16, 16, 8)
 BSCT_PLAN(256, 16, 16, 16)
 BSCT_PLAN(384, 24, 8, 4, 4, 3)
-BSCT_PLAN(512, 16, 16, 8, 4)
+BSCT_PLAN(512, 16, 16, 2, 16)
 BSCT_PLAN(768, 24, 8, 8, 4, 3)
-BSCT_PLAN(1024, 16, 16, 16, 4)
+BSCT_PLAN(1024, 16, 16, 4, 16)
 BSCT_PLAN(1536, 24, 8, 8, 8, 3)
-BSCT_PLAN(2048, 16, 16, 16, 8)
+BSCT_PLAN(2048, 16, 16, 8, 16)
 BSCT_PLAN(4096, 16, 16, 16, 16)
 #undef BSCT_PLAN
+
+// Plans of 512, 1024, 2048 and 4096 points read the same forwards and backwards, so the
+// inverse transforms (run with the plan reversed) share the forward stage twiddle table:
+// one table per length stays resident in L1 next to the large shared-memory buffers.
+template <int L> __host__ __device__ constexpr bool plan_palindrome() {
+  for (int i = 0; i < Plan<L>::NS; ++i)
+    if (Plan<L>::R[i] != Plan<L>::R[Plan<L>::NS - 1 - i]) return false;
+  return true;
+}
 
 // radix of stage s (REV = run the plan's radices in reverse order)
 template <int L, bool REV> __host__ __device__ constexpr int radix_of(int s) {

@@ -27,21 +27,31 @@ namespace bsct {
 
 __host__ __device__ constexpr int threads_per_fft(int L, int E) { return L / E; }
 
-// rows handled per CTA: at least 4 (one row block) and at least ~128 threads
+// rows handled per CTA of the forward row kernel: at least 4 (one row block, so its
+// stores fill whole 32-byte sectors of the interleaved spectra) and at least ~128 threads
 template <int LR> __host__ __device__ constexpr int rows_per_cta() {
   return (LR / Plan<LR>::E) >= 32 ? 4 : ((128 / (LR / Plan<LR>::E)) > LR ? LR : (128 / (LR / Plan<LR>::E)));
 }
+// rows per CTA of the inverse row kernel: long rows go two per CTA (half of a row block;
+// its reads hit spectra the column kernel has just left in L2), so the rows spread
+// evenly over the SMs instead of leaving a partial second wave of 4-row CTAs
+template <int LR> __host__ __device__ constexpr int rows_per_cta_inv() {
+  return (LR / Plan<LR>::E) >= 64 ? 2 : rows_per_cta<LR>();
+}
+// rows of one 4-row block that a CTA of RPC rows touches (2 or 4)
+template <int RPC> __host__ __device__ constexpr int rows_per_group() { return RPC < 4 ? 2 : 4; }
+
 // columns per CTA
 template <typename T, int LC> __host__ __device__ constexpr int cols_per_cta() {
   return (LC / Plan<LC>::E) >= 256 ? (sizeof(T) == 4 ? 2 : 1)
                                    : ((256 / (LC / Plan<LC>::E)) > 8 ? 8 : (256 / (LC / Plan<LC>::E)));
 }
 
-// per-row shared region of the row kernels: the FFT buffer plus 8 words, so that the
-// four rows of a block start on different banks (the untangle phase reads the same
-// index of all four rows in one warp)
-template <typename T, int LR> __host__ __device__ constexpr int row_region() {
-  return smem_elems<LR>() + 8 / (int)(sizeof(cpx<T>) / 4);
+// per-row shared region of the row kernels: the FFT buffer plus 32/RB words (RB = rows of
+// a 4-row block in the CTA), so that those rows start on different banks (the untangle
+// phase touches the same index of all of them in one warp)
+template <typename T, int LR, int RPC> __host__ __device__ constexpr int row_region() {
+  return smem_elems<LR>() + (32 / rows_per_group<RPC>()) / (int)(sizeof(cpx<T>) / 4);
 }
 
 __device__ __forceinline__ long blk_index(int row, int col, int ncols) {
@@ -60,7 +70,7 @@ k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
            const cpx<T>* __restrict__ tsf, const cpx<T>* __restrict__ twc, const T* p_old = nullptr,
            T* p_new = nullptr, const double* __restrict__ cg_beta = nullptr) {
   constexpr int E = Plan<LR>::E, TT = LR / E, R1 = Plan<LR>::R[0], RL = Plan<LR>::R[Plan<LR>::NS - 1];
-  constexpr int SME = row_region<T, LR>();
+  constexpr int SME = row_region<T, LR, RPC>();
   static_assert(R1 % 2 == 0, "zero-padding / crop split needs an even first radix");
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* sm_all = reinterpret_cast<cpx<T>*>(smraw);
@@ -105,14 +115,13 @@ k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
   // E and O are spectra of real sequences, and W^(LR - v) = -conj(W^v), so
   // X[LR - v] = conj(E[v] - W^v O[v]); item v = 0 gives the packed (X[0], X[LR]) and
   // X[LR/2] = conj(Z[LR/2]).  Stores of both bins are coalesced (ascending / descending).
-  constexpr int HL = LR / 2;
-  cpx<T>* out = S + (long)(row0 >> 2) * LR * 4;
+  constexpr int HL = LR / 2, RB = rows_per_group<RPC>();
 #pragma unroll 4
   for (int it = 0; it < E / 2; ++it) {
     const int e = threadIdx.x + it * (RPC * TT);
-    const int rr = e & 3, vv = (e >> 2) % HL, fb = (e >> 2) / HL;
-    const cpx<T>* smf = sm_all + (fb * 4 + rr) * SME;
-    cpx<T>* o = out + (long)fb * LR * 4 + rr;
+    const int rr = e % RB, vv = (e / RB) % HL, lr = (e / RB) / HL * RB + rr, row = row0 + lr;
+    const cpx<T>* smf = sm_all + lr * SME;
+    cpx<T>* o = S + (long)(row >> 2) * LR * 4 + (row & 3);
     const cpx<T> Z = smf[spad(vv)];
     if (vv == 0) {
       const cpx<T> Zh = smf[spad(HL)];
@@ -138,7 +147,7 @@ k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
            const cpx<T>* __restrict__ tsr, const cpx<T>* __restrict__ twc, const T* __restrict__ p = nullptr,
            double* __restrict__ part = nullptr) {
   constexpr int E = Plan<LR>::E, TT = LR / E, R1 = Plan<LR>::R[0], RL = Plan<LR>::R[Plan<LR>::NS - 1];
-  constexpr int SME = row_region<T, LR>();
+  constexpr int SME = row_region<T, LR, RPC>();
   static_assert(R1 % 2 == 0, "zero-padding / crop split needs an even first radix");
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* sm_all = reinterpret_cast<cpx<T>*>(smraw);
@@ -150,16 +159,15 @@ k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
   // Ev = Y[v] + conj(Y[LR-v]) and Od = (Y[v] - conj(Y[LR-v])) conj(W^v), the row FFT input
   // is Zp[v] = Ev + i Od and Zp[LR - v] = conj(Ev - i Od); item v = 0 also gives
   // Zp[LR/2] = 2 conj(Y[LR/2]).  All loads of a thread are issued together.
-  constexpr int HL = LR / 2;
-  const cpx<T>* in = S + (long)(row0 >> 2) * LR * 4;
+  constexpr int HL = LR / 2, RB = rows_per_group<RPC>();
   pdl_trigger();
   pdl_wait();
 #pragma unroll
   for (int it = 0; it < E / 2; ++it) {
     const int e = threadIdx.x + it * (RPC * TT);
-    const int rr = e & 3, vv = (e >> 2) % HL, fb = (e >> 2) / HL;
-    const cpx<T>* ir = in + (long)fb * LR * 4 + rr;
-    cpx<T>* smf = sm_all + (fb * 4 + rr) * SME;
+    const int rr = e % RB, vv = (e / RB) % HL, lr = (e / RB) / HL * RB + rr, row = row0 + lr;
+    const cpx<T>* ir = S + (long)(row >> 2) * LR * 4 + (row & 3);
+    cpx<T>* smf = sm_all + lr * SME;
     const cpx<T> Y = ld_cpx(ir + vv * 4);
     const cpx<T> Yo = ld_cpx(ir + (vv == 0 ? HL : LR - vv) * 4);
     if (vv == 0) {
@@ -431,13 +439,13 @@ template <typename K> static int set_smem(K kern, size_t bytes) {
 template <typename T> struct TwPtrs {
   const cpx<T>*untangle, *rows_f, *rows_r, *cols_f, *cols_r;
 };
-template <typename T> __host__ inline TwPtrs<T> tw_ptrs(const cpx<T>* tw, int N) {
+template <typename T, int N> __host__ inline TwPtrs<T> tw_ptrs(const cpx<T>* tw) {
   TwPtrs<T> p;
   p.untangle = tw;
   p.rows_f = tw + 2 * N;
-  p.rows_r = tw + 3 * N;
+  p.rows_r = plan_palindrome<N>() ? p.rows_f : tw + 3 * N;  // identical tables
   p.cols_f = tw + 4 * N;
-  p.cols_r = tw + 6 * N;
+  p.cols_r = plan_palindrome<2 * N>() ? p.cols_f : tw + 6 * N;
   return p;
 }
 
@@ -462,17 +470,18 @@ static int sm_count() {
 template <typename T, int N>
 static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw, cudaStream_t st) {
   constexpr int LR = N, LC = 2 * N;
-  constexpr int RPC = rows_per_cta<LR>();
+  constexpr int RPC = rows_per_cta<LR>(), RPI = rows_per_cta_inv<LR>();
   typedef ColsCfg<T, LC> CC;
-  static_assert(N % RPC == 0 && N % CC::G == 0, "tile must divide N");
-  constexpr int TR = RPC * (LR / Plan<LR>::E), TC = cols_threads<T, LC, CC::G>();
-  const size_t smr = (size_t)RPC * row_region<T, LR>() * sizeof(cpx<T>);
+  static_assert(N % RPC == 0 && N % RPI == 0 && N % CC::G == 0, "tile must divide N");
+  constexpr int TR = RPC * (LR / Plan<LR>::E), TI = RPI * (LR / Plan<LR>::E), TC = cols_threads<T, LC, CC::G>();
+  const size_t smr = (size_t)RPC * row_region<T, LR, RPC>() * sizeof(cpx<T>);
+  const size_t smi = (size_t)RPI * row_region<T, LR, RPI>() * sizeof(cpx<T>);
   constexpr size_t smc = cols_smem<T, LC, CC::G, CC::STAGES>();
   auto kc = k_cols_conv<T, LC, CC::G, CC::STAGES, CC::MINB>;
   static int grid_c = 0;
   if (grid_c == 0) {
     int rc = set_smem(k_rows_r2c<T, LR, true, RPC>, smr);
-    if (rc == BSCT_OK) rc = set_smem(k_rows_c2r<T, LR, RPC>, smr);
+    if (rc == BSCT_OK) rc = set_smem(k_rows_c2r<T, LR, RPI>, smi);
     if (rc == BSCT_OK) rc = set_smem(kc, smc);
     if (rc != BSCT_OK) return rc;
     int per_sm = 0;
@@ -481,14 +490,14 @@ static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw
     const int tiles = N / CC::G;
     grid_c = per_sm * sm_count() < tiles ? per_sm * sm_count() : tiles;
   }
-  const TwPtrs<T> t = tw_ptrs(tw, N);
+  const TwPtrs<T> t = tw_ptrs<T, N>(tw);
   timer_mark(st, 0);
   BSCT_CUDA_TRY(launch_overlap(k_rows_r2c<T, LR, true, RPC>, dim3(N / RPC), dim3(TR), smr, st, x, (long)N, S,
                                t.rows_f, t.untangle, (const T*)nullptr, (T*)nullptr, (const double*)nullptr));
   timer_mark(st, 1);
   BSCT_CUDA_TRY(launch_overlap(kc, dim3(grid_c), dim3(TC), smc, st, S, Gt, t.cols_f, t.cols_r, N / CC::G));
   timer_mark(st, 2);
-  BSCT_CUDA_TRY(launch_overlap(k_rows_c2r<T, LR, RPC>, dim3(N / RPC), dim3(TR), smr, st, (const cpx<T>*)S, y,
+  BSCT_CUDA_TRY(launch_overlap(k_rows_c2r<T, LR, RPI>, dim3(N / RPI), dim3(TI), smi, st, (const cpx<T>*)S, y,
                                (long)N, t.rows_r, t.untangle, (const T*)nullptr, (double*)nullptr));
   timer_mark(st, 3);
   count_launch(3);
@@ -503,16 +512,18 @@ template <typename T, int N>
 static int apply_cg_impl(const T* r, T* p, T* q, const double* beta, double* part, cpx<T>* S, const T* Gt,
                          const cpx<T>* tw, cudaStream_t st) {
   constexpr int LR = N, LC = 2 * N;
-  constexpr int RPC = rows_per_cta<LR>();
+  constexpr int RPC = rows_per_cta<LR>(), RPI = rows_per_cta_inv<LR>();
   typedef ColsCfg<T, LC> CC;
-  constexpr int TR = RPC * (LR / Plan<LR>::E), TC = cols_threads<T, LC, CC::G>();
-  const size_t smr = (size_t)RPC * row_region<T, LR>() * sizeof(cpx<T>);
+  static_assert(N % RPC == 0 && N % RPI == 0 && N % CC::G == 0, "tile must divide N");
+  constexpr int TR = RPC * (LR / Plan<LR>::E), TI = RPI * (LR / Plan<LR>::E), TC = cols_threads<T, LC, CC::G>();
+  const size_t smr = (size_t)RPC * row_region<T, LR, RPC>() * sizeof(cpx<T>);
+  const size_t smi = (size_t)RPI * row_region<T, LR, RPI>() * sizeof(cpx<T>);
   constexpr size_t smc = cols_smem<T, LC, CC::G, CC::STAGES>();
   auto kc = k_cols_conv<T, LC, CC::G, CC::STAGES, CC::MINB>;
   static int grid_c = 0;
   if (grid_c == 0) {
     int rc = set_smem(k_rows_r2c<T, LR, true, RPC, true>, smr);
-    if (rc == BSCT_OK) rc = set_smem(k_rows_c2r<T, LR, RPC, true>, smr);
+    if (rc == BSCT_OK) rc = set_smem(k_rows_c2r<T, LR, RPI, true>, smi);
     if (rc == BSCT_OK) rc = set_smem(kc, smc);
     if (rc != BSCT_OK) return rc;
     int per_sm = 0;
@@ -521,11 +532,11 @@ static int apply_cg_impl(const T* r, T* p, T* q, const double* beta, double* par
     const int tiles = N / CC::G;
     grid_c = per_sm * sm_count() < tiles ? per_sm * sm_count() : tiles;
   }
-  const TwPtrs<T> t = tw_ptrs(tw, N);
+  const TwPtrs<T> t = tw_ptrs<T, N>(tw);
   BSCT_CUDA_TRY(launch_overlap(k_rows_r2c<T, LR, true, RPC, true>, dim3(N / RPC), dim3(TR), smr, st, r, (long)N, S,
                                t.rows_f, t.untangle, (const T*)p, p, beta));
   BSCT_CUDA_TRY(launch_overlap(kc, dim3(grid_c), dim3(TC), smc, st, S, Gt, t.cols_f, t.cols_r, N / CC::G));
-  BSCT_CUDA_TRY(launch_overlap(k_rows_c2r<T, LR, RPC, true>, dim3(N / RPC), dim3(TR), smr, st, (const cpx<T>*)S, q,
+  BSCT_CUDA_TRY(launch_overlap(k_rows_c2r<T, LR, RPI, true>, dim3(N / RPI), dim3(TI), smi, st, (const cpx<T>*)S, q,
                                (long)N, t.rows_r, t.untangle, (const T*)p, part));
   count_launch(3);
   BSCT_CUDA_TRY(cudaGetLastError());
@@ -538,7 +549,7 @@ static int spectrum_impl(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* tw, cuda
   constexpr int RPC = rows_per_cta<LR>();
   constexpr int CPC = cols_per_cta<T, LC>();
   constexpr int TR = RPC * (LR / Plan<LR>::E), TC = CPC * (LC / Plan<LC>::E);
-  const size_t smr = (size_t)RPC * row_region<T, LR>() * sizeof(cpx<T>);
+  const size_t smr = (size_t)RPC * row_region<T, LR, RPC>() * sizeof(cpx<T>);
   const size_t smc = (size_t)CPC * smem_elems<LC>() * sizeof(cpx<T>);
   static bool attr_done = false;
   if (!attr_done) {
@@ -547,7 +558,7 @@ static int spectrum_impl(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* tw, cuda
     if (rc != BSCT_OK) return rc;
     attr_done = true;
   }
-  const TwPtrs<T> t = tw_ptrs(tw, N);
+  const TwPtrs<T> t = tw_ptrs<T, N>(tw);
   k_rows_r2c<T, LR, false, RPC><<<LC / RPC, TR, smr, st>>>(emb, LC, S2, t.rows_f, t.untangle);
   k_cols_fwd_real<T, LC, CPC><<<N / CPC, TC, smc, st>>>(S2, Gt, t.cols_f, T(1.0 / ((double)LC * (double)LC)));
   count_launch(2);
@@ -559,7 +570,7 @@ template <typename T, int N> FftOps<T> fft_ops() {
   FftOps<T> o;
   o.apply = &apply_impl<T, N>;
   o.apply_cg = &apply_cg_impl<T, N>;
-  o.cg_partials = N / rows_per_cta<N>();
+  o.cg_partials = N / rows_per_cta_inv<N>();
   o.spectrum = &spectrum_impl<T, N>;
   return o;
 }
