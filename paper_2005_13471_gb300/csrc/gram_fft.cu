@@ -240,9 +240,8 @@ k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
 // K6: per packed column: forward 2N FFT (rows >= N are zero), multiply by the real
 // spectrum, inverse, keep rows < N.  In place on S.
 // Persistent CTAs walk over tiles of G columns; while a tile is transformed, the
-// column data (32-byte row-block chunks) and spectrum rows of the tiles STAGES-1 ahead
-// are already in flight into shared memory (cp.async), so HBM/L2 latency overlaps the
-// FFT arithmetic.
+// column data (32-byte row-block chunks) and spectrum rows of the next tile are already
+// in flight into shared memory (cp.async), so HBM/L2 latency overlaps the FFT arithmetic.
 // ------------------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -254,12 +253,17 @@ template <int N_> __device__ __forceinline__ void cp_async_wait() {
 }
 
 template <typename T, int LC, int G> __host__ __device__ constexpr int cols_threads() { return G * (LC / Plan<LC>::E); }
-template <typename T, int LC, int G, int STAGES> __host__ __device__ constexpr size_t cols_smem() {
-  return (size_t)G * smem_elems<LC>() * sizeof(cpx<T>) + (size_t)STAGES * G * (LC / 2) * sizeof(cpx<T>) +
-         (size_t)STAGES * G * LC * sizeof(T);
+template <typename T, int LC, int G> __host__ __device__ constexpr size_t cols_smem() {
+  return (size_t)G * smem_elems<LC>() * sizeof(cpx<T>) + (size_t)G * (LC / 2) * sizeof(cpx<T>) +
+         (size_t)G * LC * sizeof(T);
 }
 
-template <typename T, int LC, int G, int STAGES, int MINB>
+// Shared memory: the FFT exchange buffers, one staging buffer for the next tile's column
+// data and one for its spectrum columns.  The column data is consumed at the start of a
+// tile and the spectrum after the forward FFT, so each buffer is refilled (one cp.async
+// group each) right after it is consumed and has a whole tile of compute to arrive.
+// Keeping to one staging set leaves L1 room for the stage twiddle table.
+template <typename T, int LC, int G, int MINB>
 __global__ void __launch_bounds__(G*(LC / Plan<LC>::E), MINB)
 k_cols_conv(cpx<T>* __restrict__ S, const T* __restrict__ Gt, const cpx<T>* __restrict__ tsf,
             const cpx<T>* __restrict__ tsr, int ntiles) {
@@ -267,30 +271,33 @@ k_cols_conv(cpx<T>* __restrict__ S, const T* __restrict__ Gt, const cpx<T>* __re
   constexpr int NT = G * TT;
   constexpr int NC = LC / 2;
   constexpr int SME = smem_elems<LC>();
-  constexpr int IN_E = G * NC;  // complex per stage
-  constexpr int GT_E = G * LC;  // reals per stage
+  constexpr int IN_E = G * NC;  // complex per tile
+  constexpr int GT_E = G * LC;  // reals per tile
   constexpr int PPC = 4 * (int)sizeof(cpx<T>) / 16;  // 16-byte pieces per 4-row chunk
   constexpr int RPP = 16 / (int)sizeof(cpx<T>);      // rows per piece
   static_assert(R1 % 2 == 0, "zero-padding / crop split needs an even first radix");
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* xsm = reinterpret_cast<cpx<T>*>(smraw);
   cpx<T>* stin = xsm + G * SME;
-  T* stg = reinterpret_cast<T*>(stin + STAGES * IN_E);
+  T* stg = reinterpret_cast<T*>(stin + IN_E);
   const int g = threadIdx.x / TT, tid = threadIdx.x % TT;
   cpx<T>* sm = xsm + g * SME;
 
-  auto prefetch = [&](int tile, int stage) {
+  auto prefetch_in = [&](int tile) {
     if (tile < ntiles) {
       const int c0 = tile * G;
-      cpx<T>* din = stin + stage * IN_E;
       for (int q = threadIdx.x; q < (NC / 4) * G * PPC; q += NT) {
         const int p = q % PPC, gc = (q / PPC) % G, k = q / (PPC * G);
-        cp_async16(din + gc * NC + 4 * k + p * RPP, S + ((long)k * NC + c0 + gc) * 4 + p * RPP);
+        cp_async16(stin + gc * NC + 4 * k + p * RPP, S + ((long)k * NC + c0 + gc) * 4 + p * RPP);
       }
-      const T* src = Gt + (long)c0 * LC;
-      T* dg = stg + stage * GT_E;
+    }
+    cp_async_commit();
+  };
+  auto prefetch_spec = [&](int tile) {
+    if (tile < ntiles) {
+      const T* src = Gt + (long)tile * G * LC;
       constexpr int EPP = 16 / (int)sizeof(T);
-      for (int q = threadIdx.x; q < GT_E / EPP; q += NT) cp_async16(dg + q * EPP, src + q * EPP);
+      for (int q = threadIdx.x; q < GT_E / EPP; q += NT) cp_async16(stg + q * EPP, src + q * EPP);
     }
     cp_async_commit();
   };
@@ -298,16 +305,15 @@ k_cols_conv(cpx<T>* __restrict__ S, const T* __restrict__ Gt, const cpx<T>* __re
   int tile = blockIdx.x;
   pdl_trigger();
   pdl_wait();
-#pragma unroll
-  for (int s = 0; s < STAGES; ++s) prefetch(tile + s * gridDim.x, s);
-
-  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-    const int stage = it % STAGES;
-    cp_async_wait<STAGES - 1>();
+  prefetch_in(tile);
+  prefetch_spec(tile);
+  // cp.async groups in commit order: in(t0), spec(t0), in(t1), spec(t1), ...; each wait
+  // below leaves only the most recent group in flight
+  for (; tile < ntiles; tile += gridDim.x) {
+    cp_async_wait<1>();  // column data of this tile
     __syncthreads();
     const int col = tile * G + g;
-    const cpx<T>* in = stin + stage * IN_E + g * NC;
-    const T* gs = stg + stage * GT_E + g * LC;
+    const cpx<T>* in = stin + g * NC;
     cpx<T> v[E];
 #pragma unroll
     for (int b = 0; b < E / R1; ++b) {
@@ -316,7 +322,12 @@ k_cols_conv(cpx<T>* __restrict__ S, const T* __restrict__ Gt, const cpx<T>* __re
       for (int r = 0; r < R1; ++r)
         v[b * R1 + r] = (r < R1 / 2) ? in[j + r * (LC / R1)] : mk(T(0), T(0));  // rows >= N are zero
     }
+    __syncthreads();  // column staging consumed
+    prefetch_in(tile + gridDim.x);
     fft<T, LC, false, false, true>(v, sm, tid, tsf);
+    cp_async_wait<1>();  // spectrum of this tile
+    __syncthreads();
+    const T* gs = stg + g * LC;
     if (tile == 0) {
       // column 0 holds a + i b (a = DC column, b = Nyquist column): needs Z[-u]
 #pragma unroll
@@ -344,7 +355,6 @@ k_cols_conv(cpx<T>* __restrict__ S, const T* __restrict__ Gt, const cpx<T>* __re
           }
         }
       }
-      __syncthreads();
     } else {
 #pragma unroll
       for (int b = 0; b < E / RL; ++b) {
@@ -356,6 +366,8 @@ k_cols_conv(cpx<T>* __restrict__ S, const T* __restrict__ Gt, const cpx<T>* __re
         }
       }
     }
+    __syncthreads();  // spectrum staging (and, for tile 0, the exchange buffer) consumed
+    prefetch_spec(tile + gridDim.x);
     fft<T, LC, true, true>(v, sm, tid, tsr);
     // reversed plan: last radix = forward first radix R1; keep rows < N
 #pragma unroll
@@ -364,8 +376,6 @@ k_cols_conv(cpx<T>* __restrict__ S, const T* __restrict__ Gt, const cpx<T>* __re
 #pragma unroll
       for (int r = 0; r < R1 / 2; ++r) st_cpx(S + blk_index(j + r * (LC / R1), col, NC), v[b * R1 + r]);
     }
-    __syncthreads();  // staging[stage] and the exchange buffer are free again
-    prefetch(tile + STAGES * gridDim.x, stage);
   }
   cp_async_wait<0>();
 }
@@ -434,7 +444,6 @@ template <typename K> static int set_smem(K kern, size_t bytes) {
   }
   return BSCT_OK;
 }
-
 // twiddle tables of one size N, packed in one array (see FftTables)
 template <typename T> struct TwPtrs {
   const cpx<T>*untangle, *rows_f, *rows_r, *cols_f, *cols_r;
@@ -452,8 +461,7 @@ template <typename T, int N> __host__ inline TwPtrs<T> tw_ptrs(const cpx<T>* tw)
 template <typename T, int LC> struct ColsCfg {
   static constexpr int TT = LC / Plan<LC>::E;
   static constexpr int G = TT >= 256 ? 1 : (256 / TT > LC / 2 ? LC / 2 : 256 / TT);
-  static constexpr int STAGES = cols_smem<T, LC, G, 2>() <= 227 * 1024 ? 2 : 1;
-  static constexpr int MINB = (cols_smem<T, LC, G, STAGES>() * 2 <= 227 * 1024 && sizeof(T) == 4) ? 2 : 1;
+  static constexpr int MINB = (cols_smem<T, LC, G>() * 2 <= 227 * 1024 && sizeof(T) == 4) ? 2 : 1;
 };
 
 static int sm_count() {
@@ -474,10 +482,10 @@ static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw
   typedef ColsCfg<T, LC> CC;
   static_assert(N % RPC == 0 && N % RPI == 0 && N % CC::G == 0, "tile must divide N");
   constexpr int TR = RPC * (LR / Plan<LR>::E), TI = RPI * (LR / Plan<LR>::E), TC = cols_threads<T, LC, CC::G>();
-  const size_t smr = (size_t)RPC * row_region<T, LR, RPC>() * sizeof(cpx<T>);
-  const size_t smi = (size_t)RPI * row_region<T, LR, RPI>() * sizeof(cpx<T>);
-  constexpr size_t smc = cols_smem<T, LC, CC::G, CC::STAGES>();
-  auto kc = k_cols_conv<T, LC, CC::G, CC::STAGES, CC::MINB>;
+  constexpr size_t smr = (size_t)RPC * row_region<T, LR, RPC>() * sizeof(cpx<T>);
+  constexpr size_t smi = (size_t)RPI * row_region<T, LR, RPI>() * sizeof(cpx<T>);
+  constexpr size_t smc = cols_smem<T, LC, CC::G>();
+  auto kc = k_cols_conv<T, LC, CC::G, CC::MINB>;
   static int grid_c = 0;
   if (grid_c == 0) {
     int rc = set_smem(k_rows_r2c<T, LR, true, RPC>, smr);
@@ -516,10 +524,10 @@ static int apply_cg_impl(const T* r, T* p, T* q, const double* beta, double* par
   typedef ColsCfg<T, LC> CC;
   static_assert(N % RPC == 0 && N % RPI == 0 && N % CC::G == 0, "tile must divide N");
   constexpr int TR = RPC * (LR / Plan<LR>::E), TI = RPI * (LR / Plan<LR>::E), TC = cols_threads<T, LC, CC::G>();
-  const size_t smr = (size_t)RPC * row_region<T, LR, RPC>() * sizeof(cpx<T>);
-  const size_t smi = (size_t)RPI * row_region<T, LR, RPI>() * sizeof(cpx<T>);
-  constexpr size_t smc = cols_smem<T, LC, CC::G, CC::STAGES>();
-  auto kc = k_cols_conv<T, LC, CC::G, CC::STAGES, CC::MINB>;
+  constexpr size_t smr = (size_t)RPC * row_region<T, LR, RPC>() * sizeof(cpx<T>);
+  constexpr size_t smi = (size_t)RPI * row_region<T, LR, RPI>() * sizeof(cpx<T>);
+  constexpr size_t smc = cols_smem<T, LC, CC::G>();
+  auto kc = k_cols_conv<T, LC, CC::G, CC::MINB>;
   static int grid_c = 0;
   if (grid_c == 0) {
     int rc = set_smem(k_rows_r2c<T, LR, true, RPC, true>, smr);
