@@ -16,9 +16,10 @@
 // registers the forward transform ended with (no exchange between them).
 //
 // Twiddles: stage s (Ns = product of earlier radices, radix R) multiplies element r of
-// butterfly j by exp(-2 pi i r (j mod Ns) / (Ns R)).  They are read from a per-plan
-// table laid out [stage][r-1][j mod Ns] (Ns - 1 + (r-1) Ns + j mod Ns; the stages add
-// up to L - 1 entries), so consecutive threads read consecutive entries.
+// butterfly j by exp(-2 pi i r (j mod Ns) / (Ns R)).  They come from a per-plan table
+// laid out [stage][r-1][j mod Ns] (Ns - 1 + (r-1) Ns + j mod Ns; the stages add up to
+// L - 1 entries), so consecutive threads read consecutive entries; FP32 radix-8/16
+// stages read the powers 1, 2, 4, 8 and multiply out the rest (see stage_compute).
 #pragma once
 #include "bsct_common.cuh"
 
@@ -191,13 +192,36 @@ template <int R, typename T, bool INV, bool HALF = false> __device__ __forceinli
 // Stages
 // ----------------------------------------------------------------------------------
 // tws: stage twiddle table of this plan (and radix order), see the top of the file
+// FP32 radix-8 and radix-16 stages load only w^1, w^2, w^4 (and w^8) of their butterfly
+// from the table and form the other powers by at most three complex products (a few
+// ulps): the table loads compete with the exchanges for the L1 / shared-memory pipe, and
+// measured, fewer loads and more FMAs win.  FP64 (the reference-precision path) loads
+// every twiddle.
 template <typename T, int L, int R, int NSV, bool INV, bool HALF>
 __device__ __forceinline__ void stage_compute(cpx<T> (&v)[Plan<L>::E], int tid, const cpx<T>* __restrict__ tws) {
   constexpr int E = Plan<L>::E;
   constexpr int TT = L / E;
 #pragma unroll
   for (int b = 0; b < E / R; ++b) {
-    if constexpr (NSV > 1) {
+    if constexpr (NSV > 1 && (R == 8 || R == 16) && sizeof(T) == 4) {
+      const int j = tid + b * TT;
+      const cpx<T>* t = tws + (NSV - 1) + (j % NSV);
+      cpx<T> w[R];
+      w[1] = ld_cpx(t);
+      w[2] = ld_cpx(t + NSV);
+      w[4] = ld_cpx(t + 3 * NSV);
+      if constexpr (R == 16) w[8] = ld_cpx(t + 7 * NSV);
+      w[3] = cmul(w[2], w[1]);
+      w[5] = cmul(w[4], w[1]);
+      w[6] = cmul(w[4], w[2]);
+      w[7] = cmul(w[4], w[3]);
+      if constexpr (R == 16) {
+#pragma unroll
+        for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+      }
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[b * R + r] = INV ? cmulc(v[b * R + r], w[r]) : cmul(v[b * R + r], w[r]);
+    } else if constexpr (NSV > 1) {
       const int j = tid + b * TT;
       const cpx<T>* t = tws + (NSV - 1) + (j % NSV);
 #pragma unroll
