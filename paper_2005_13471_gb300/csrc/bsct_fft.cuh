@@ -192,25 +192,60 @@ template <int R, typename T, bool INV, bool HALF = false> __device__ __forceinli
 // Stages
 // ----------------------------------------------------------------------------------
 // tws: stage twiddle table of this plan (and radix order), see the top of the file
+// Per-thread cache of the base twiddle powers (w^1, w^2, w^4, w^8) of every radix-8/16
+// stage of a plan, for persistent kernels that run many FFTs of one length with one
+// thread layout: loaded once into registers, their latency leaves the stages.
+template <typename T, int L> struct TwCache {
+  static constexpr int NB = Plan<L>::E / 8;  // butterflies per thread of a radix-8 stage
+  cpx<T> w[Plan<L>::NS][NB][4];
+};
+template <typename T, int L, bool REV, int S>
+__device__ __forceinline__ void tw_cache_stages(TwCache<T, L>& c, int tid, const cpx<T>* __restrict__ tws) {
+  constexpr int R = radix_of<L, REV>(S), NSV = ns_of<L, REV>(S), E = Plan<L>::E, TT = L / E;
+  if constexpr (NSV > 1 && (R == 8 || R == 16)) {
+#pragma unroll
+    for (int b = 0; b < E / R; ++b) {
+      const cpx<T>* t = tws + (NSV - 1) + ((tid + b * TT) % NSV);
+      c.w[S][b][0] = ld_cpx(t);
+      c.w[S][b][1] = ld_cpx(t + NSV);
+      c.w[S][b][2] = ld_cpx(t + 3 * NSV);
+      if constexpr (R == 16) c.w[S][b][3] = ld_cpx(t + 7 * NSV);
+    }
+  }
+  if constexpr (S + 1 < Plan<L>::NS) tw_cache_stages<T, L, REV, S + 1>(c, tid, tws);
+}
+template <typename T, int L, bool REV>
+__device__ __forceinline__ void tw_cache_load(TwCache<T, L>& c, int tid, const cpx<T>* __restrict__ tws) {
+  tw_cache_stages<T, L, REV, 0>(c, tid, tws);
+}
+
 // FP32 radix-8 and radix-16 stages load only w^1, w^2, w^4 (and w^8) of their butterfly
 // from the table and form the other powers by at most three complex products (a few
 // ulps): the table loads compete with the exchanges for the L1 / shared-memory pipe, and
 // measured, fewer loads and more FMAs win.  FP64 (the reference-precision path) loads
 // every twiddle.
-template <typename T, int L, int R, int NSV, bool INV, bool HALF>
-__device__ __forceinline__ void stage_compute(cpx<T> (&v)[Plan<L>::E], int tid, const cpx<T>* __restrict__ tws) {
+template <typename T, int L, int R, int NSV, bool INV, bool HALF, int S = 0, bool CACHED = false>
+__device__ __forceinline__ void stage_compute(cpx<T> (&v)[Plan<L>::E], int tid, const cpx<T>* __restrict__ tws,
+                                              const TwCache<T, L>* cache = nullptr) {
   constexpr int E = Plan<L>::E;
   constexpr int TT = L / E;
 #pragma unroll
   for (int b = 0; b < E / R; ++b) {
     if constexpr (NSV > 1 && (R == 8 || R == 16) && sizeof(T) == 4) {
       const int j = tid + b * TT;
-      const cpx<T>* t = tws + (NSV - 1) + (j % NSV);
       cpx<T> w[R];
-      w[1] = ld_cpx(t);
-      w[2] = ld_cpx(t + NSV);
-      w[4] = ld_cpx(t + 3 * NSV);
-      if constexpr (R == 16) w[8] = ld_cpx(t + 7 * NSV);
+      if constexpr (CACHED) {
+        w[1] = cache->w[S][b][0];
+        w[2] = cache->w[S][b][1];
+        w[4] = cache->w[S][b][2];
+        if constexpr (R == 16) w[8] = cache->w[S][b][3];
+      } else {
+        const cpx<T>* t = tws + (NSV - 1) + (j % NSV);
+        w[1] = ld_cpx(t);
+        w[2] = ld_cpx(t + NSV);
+        w[4] = ld_cpx(t + 3 * NSV);
+        if constexpr (R == 16) w[8] = ld_cpx(t + 7 * NSV);
+      }
       w[3] = cmul(w[2], w[1]);
       w[5] = cmul(w[4], w[1]);
       w[6] = cmul(w[4], w[2]);
@@ -273,14 +308,15 @@ __device__ __forceinline__ void stage_exchange(cpx<T> (&v)[Plan<L>::E], cpx<T>* 
   __syncthreads();
 }
 
-template <typename T, int L, bool INV, bool REV, bool HALF, int S>
-__device__ __forceinline__ void fft_stages(cpx<T> (&v)[Plan<L>::E], cpx<T>* sm, int tid, const cpx<T>* __restrict__ tws) {
+template <typename T, int L, bool INV, bool REV, bool HALF, int S, bool CACHED>
+__device__ __forceinline__ void fft_stages(cpx<T> (&v)[Plan<L>::E], cpx<T>* sm, int tid, const cpx<T>* __restrict__ tws,
+                                           const TwCache<T, L>* cache) {
   constexpr int R = radix_of<L, REV>(S);
   constexpr int NSV = ns_of<L, REV>(S);
-  stage_compute<T, L, R, NSV, INV, HALF && S == 0>(v, tid, tws);
+  stage_compute<T, L, R, NSV, INV, HALF && S == 0, S, CACHED>(v, tid, tws, cache);
   if constexpr (S + 1 < Plan<L>::NS) {
     stage_exchange<T, L, R, NSV, radix_of<L, REV>(S + 1)>(v, sm, tid);
-    fft_stages<T, L, INV, REV, HALF, S + 1>(v, sm, tid, tws);
+    fft_stages<T, L, INV, REV, HALF, S + 1, CACHED>(v, sm, tid, tws, cache);
   }
 }
 
@@ -291,7 +327,15 @@ __device__ __forceinline__ void fft_stages(cpx<T> (&v)[Plan<L>::E], cpx<T>* sm, 
 // not read).  Unnormalised both ways.
 template <typename T, int L, bool INV, bool REV, bool HALF = false>
 __device__ __forceinline__ void fft(cpx<T> (&v)[Plan<L>::E], cpx<T>* sm, int tid, const cpx<T>* __restrict__ tws) {
-  fft_stages<T, L, INV, REV, HALF, 0>(v, sm, tid, tws);
+  fft_stages<T, L, INV, REV, HALF, 0, false>(v, sm, tid, tws, nullptr);
+}
+// Same with the radix-8/16 stage twiddles taken from a register cache filled by
+// tw_cache_load for the same plan order (for a palindromic plan the forward cache serves
+// the reversed order); stages of other radices still read tws.
+template <typename T, int L, bool INV, bool REV, bool HALF = false>
+__device__ __forceinline__ void fft_cached(cpx<T> (&v)[Plan<L>::E], cpx<T>* sm, int tid, const cpx<T>* __restrict__ tws,
+                                           const TwCache<T, L>& cache) {
+  fft_stages<T, L, INV, REV, HALF, 0, true>(v, sm, tid, tws, &cache);
 }
 
 // Host-side copy of a plan (for building the stage twiddle tables).

@@ -304,6 +304,11 @@ k_cols_conv(cpx<T>* __restrict__ S, const T* __restrict__ Gt, const cpx<T>* __re
 
   int tile = blockIdx.x;
   pdl_trigger();
+  // FP32 palindromic plans: the stage twiddles of this thread, the same for every tile and
+  // (conjugated) for the inverse, go to registers once; constant data, so before the wait
+  constexpr bool TWREG = sizeof(T) == 4 && plan_palindrome<LC>();
+  TwCache<T, LC> twr;
+  if constexpr (TWREG) tw_cache_load<T, LC, false>(twr, tid, tsf);
   pdl_wait();
   prefetch_in(tile);
   prefetch_spec(tile);
@@ -324,7 +329,8 @@ k_cols_conv(cpx<T>* __restrict__ S, const T* __restrict__ Gt, const cpx<T>* __re
     }
     __syncthreads();  // column staging consumed
     prefetch_in(tile + gridDim.x);
-    fft<T, LC, false, false, true>(v, sm, tid, tsf);
+    if constexpr (TWREG) fft_cached<T, LC, false, false, true>(v, sm, tid, tsf, twr);
+    else fft<T, LC, false, false, true>(v, sm, tid, tsf);
     cp_async_wait<1>();  // spectrum of this tile
     __syncthreads();
     const T* gs = stg + g * LC;
@@ -368,7 +374,8 @@ k_cols_conv(cpx<T>* __restrict__ S, const T* __restrict__ Gt, const cpx<T>* __re
     }
     __syncthreads();  // spectrum staging (and, for tile 0, the exchange buffer) consumed
     prefetch_spec(tile + gridDim.x);
-    fft<T, LC, true, true>(v, sm, tid, tsr);
+    if constexpr (TWREG) fft_cached<T, LC, true, true>(v, sm, tid, tsr, twr);
+    else fft<T, LC, true, true>(v, sm, tid, tsr);
     // reversed plan: last radix = forward first radix R1; keep rows < N
 #pragma unroll
     for (int b = 0; b < E / R1; ++b) {
