@@ -33,9 +33,14 @@ constexpr int BP_HDR = 8;
 constexpr int BP_SIG = BP_HDR;                      // sigma[16] (padded with 2, for a 4-step search)
 constexpr int BP_MID = BP_SIG + 16;                 // mid[QMAX]
 constexpr int BP_IHW = BP_MID + BP_QMAX;            // 1/halfwidth[QMAX]
-constexpr int BP_COEF = 48;                         // coef[QMAX][NJMAX][8], aligned
-constexpr int BP_QSTRIDE = BP_NJMAX * 8 + 4;        // piece stride: +4 words moves each piece to other banks
-constexpr int BP_STRIDE = BP_COEF + BP_QMAX * BP_QSTRIDE;
+// coefficients of piece q, offset j: (c0..c3) at BP_CA + q BP_QA + 4 j, (c4, c5) at
+// BP_CB + q BP_QB + 2 j; the +4 / +2 pads put the pieces one warp touches on different
+// banks for the 16-byte and 8-byte reads
+constexpr int BP_CA = 48;
+constexpr int BP_QA = BP_NJMAX * 4 + 4;
+constexpr int BP_CB = BP_CA + BP_QMAX * BP_QA;
+constexpr int BP_QB = BP_NJMAX * 2 + 2;
+constexpr int BP_STRIDE = BP_CB + BP_QMAX * BP_QB;
 constexpr int BP_TX = 32, BP_TY = 8, BP_CHUNK = 64;
 
 __host__ __device__ inline int bp_degree(double c, double s, double zeta) {
@@ -126,12 +131,18 @@ __global__ void __launch_bounds__(256) k_bp_tables(const double* __restrict__ an
   const int Q = Qs;
   if (Q > BP_QMAX || nJ > BP_NJMAX) return;
   T* h = tab + (long)a * BP_STRIDE;
-  for (int i = threadIdx.x; i < BP_QMAX * 4; i += blockDim.x) h[BP_COEF + (i / 4) * BP_QSTRIDE + BP_NJMAX * 8 + i % 4] = T(0);
+  for (int i = threadIdx.x; i < BP_QMAX * 6; i += blockDim.x) {  // pads
+    if (i < BP_QMAX * 4) h[BP_CA + (i / 4) * BP_QA + BP_NJMAX * 4 + i % 4] = T(0);
+    else h[BP_CB + ((i - BP_QMAX * 4) / 2) * BP_QB + BP_NJMAX * 2 + i % 2] = T(0);
+  }
   for (int w = threadIdx.x; w < BP_QMAX * BP_NJMAX; w += blockDim.x) {
     const int q = w / BP_NJMAX, j = w % BP_NJMAX;
-    T* cf = h + BP_COEF + q * BP_QSTRIDE + j * 8;
+    T* ca = h + BP_CA + q * BP_QA + j * 4;
+    T* cb = h + BP_CB + q * BP_QB + j * 2;
     if (q >= Q || j >= nJ) {
-      for (int i = 0; i < 8; ++i) cf[i] = T(0);
+      for (int i = 0; i < 4; ++i) ca[i] = T(0);
+      cb[0] = T(0);
+      cb[1] = T(0);
       if (j == 0 && q < BP_QMAX) { h[BP_MID + q] = T(0); h[BP_IHW + q] = T(0); }
       continue;
     }
@@ -159,8 +170,8 @@ __global__ void __launch_bounds__(256) k_bp_tables(const double* __restrict__ an
     const double m3 = 4.0 * ch[3] - 20.0 * ch[5];
     const double m4 = 8.0 * ch[4];
     const double m5 = 16.0 * ch[5];
-    cf[0] = T(m0); cf[1] = T(m1); cf[2] = T(m2); cf[3] = T(m3); cf[4] = T(m4); cf[5] = T(m5);
-    cf[6] = T(0); cf[7] = T(0);
+    ca[0] = T(m0); ca[1] = T(m1); ca[2] = T(m2); ca[3] = T(m3);
+    cb[0] = T(m4); cb[1] = T(m5);
   }
 }
 
@@ -211,17 +222,17 @@ inline int bp_window(double lambda) {
 }
 template <typename T> size_t bp_gather_smem(int win) { return (size_t)BP_CH * (BP_STRIDE + win) * sizeof(T); }
 
-// eight consecutive table entries (16-byte aligned) from shared memory
-__device__ inline void bp_load8(const float* p, float c[8]) {
-  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
-  c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w; c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+// the six coefficients of one (piece, offset) from shared memory: one 16-byte and one
+// 8-byte read in FP32 (three 16-byte reads in FP64)
+__device__ inline void bp_load6(const float* a, const float* b, float c[6]) {
+  const float4 x = *reinterpret_cast<const float4*>(a);
+  const float2 y = *reinterpret_cast<const float2*>(b);
+  c[0] = x.x; c[1] = x.y; c[2] = x.z; c[3] = x.w; c[4] = y.x; c[5] = y.y;
 }
-__device__ inline void bp_load8(const double* p, double c[8]) {
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const double2 a = *reinterpret_cast<const double2*>(p + 2 * i);
-    c[2 * i] = a.x; c[2 * i + 1] = a.y;
-  }
+__device__ inline void bp_load6(const double* a, const double* b, double c[6]) {
+  const double2 x0 = *reinterpret_cast<const double2*>(a), x1 = *reinterpret_cast<const double2*>(a + 2);
+  const double2 y = *reinterpret_cast<const double2*>(b);
+  c[0] = x0.x; c[1] = x0.y; c[2] = x1.x; c[3] = x1.y; c[4] = y.x; c[5] = y.y;
 }
 
 template <typename T>
@@ -289,11 +300,12 @@ __global__ void __launch_bounds__(BP_TX* BP_TY) k_bp_gather(const T* __restrict_
       for (int step = 8; step > 0; step >>= 1)
         if (h[BP_SIG + q + step] <= f) q += step;
       const T v = (f - h[BP_MID + q]) * h[BP_IHW + q];
-      const T* cf = h + BP_COEF + q * BP_QSTRIDE;
+      const T* ca = h + BP_CA + q * BP_QA;
+      const T* cb = h + BP_CB + q * BP_QB;
       const T* cw = s_ct + ai * win + moff;
       for (int j = 0; j < nJ; ++j) {
-        T c[8];
-        bp_load8(cf + j * 8, c);
+        T c[6];
+        bp_load6(ca + j * 4, cb + j * 2, c);
         T wv = c[5];
         wv = fma(wv, v, c[4]);
         wv = fma(wv, v, c[3]);
