@@ -29,19 +29,23 @@ namespace bsct {
 
 constexpr int BP_QMAX = 12;   // pieces per view (<= 9 occur)
 constexpr int BP_NJMAX = 16;  // samples touching one pixel (lambda_y >= ~0.2)
-constexpr int BP_HDR = 8;
+// header: c/lambda, s/lambda, Q, J0, nJ, then the FP32 split of the detector coordinate
+// p = p00 + X c/lambda + Y s/lambda (pixel X, Y): floor(p00), p00 - floor(p00), and
+// c/lambda = c_hi + c_lo, s/lambda = s_hi + s_lo with hi parts short enough that
+// X c_hi and Y s_hi are exact in FP32 for every pixel index of the image
+constexpr int BP_HDR = 12;
 constexpr int BP_SIG = BP_HDR;                      // sigma[16] (padded with 2, for a 4-step search)
 constexpr int BP_MID = BP_SIG + 16;                 // mid[QMAX]
 constexpr int BP_IHW = BP_MID + BP_QMAX;            // 1/halfwidth[QMAX]
 // coefficients of piece q, offset j: (c0..c3) at BP_CA + q BP_QA + 4 j, (c4, c5) at
 // BP_CB + q BP_QB + 2 j; the +4 / +2 pads put the pieces one warp touches on different
 // banks for the 16-byte and 8-byte reads
-constexpr int BP_CA = 48;
+constexpr int BP_CA = BP_IHW + BP_QMAX;  // 52: 16-byte aligned
 constexpr int BP_QA = BP_NJMAX * 4 + 4;
 constexpr int BP_CB = BP_CA + BP_QMAX * BP_QA;
 constexpr int BP_QB = BP_NJMAX * 2 + 2;
 constexpr int BP_STRIDE = BP_CB + BP_QMAX * BP_QB;
-constexpr int BP_TX = 32, BP_TY = 8, BP_CHUNK = 64;
+constexpr int BP_TX = 32, BP_TY = 8;
 
 __host__ __device__ inline int bp_degree(double c, double s, double zeta) {
   return (c != 0.0) + (s != 0.0) + (zeta > 0.0) - 1;
@@ -124,8 +128,25 @@ __global__ void __launch_bounds__(256) k_bp_tables(const double* __restrict__ an
     if (q > BP_QMAX || nJ > BP_NJMAX) atomicExch(status, 1);
     // detector coordinate of pixel (0, 0) in bin units, FP64
     const double x0 = -0.5 * (N - 1);
-    p00[a] = (x0 * c_ + x0 * s_) / lam + 0.5 * (M - 1);
+    const double pz = (x0 * c_ + x0 * s_) / lam + 0.5 * (M - 1);
+    p00[a] = pz;
     csl[a] = make_double2(c_ / lam, s_ / lam);
+    // FP32 split (pixel indices < 2^nb need hi parts of 24 - nb significant bits; the
+    // indices reach the end of the last 64-pixel tile)
+    int nb = 1;
+    while ((1 << nb) < (N + 63) / 64 * 64) ++nb;
+    const double nz = floor(pz);
+    h[5] = T(nz);
+    h[6] = T(pz - nz);
+    const double cs[2] = {c_ / lam, s_ / lam};
+    for (int k = 0; k < 2; ++k) {
+      int e;
+      const double m = frexp(cs[k], &e);                        // cs = m 2^e, 0.5 <= |m| < 1
+      const double hi = ldexp(trunc(ldexp(m, 24 - nb)), e - (24 - nb));
+      h[7 + 2 * k] = T(hi);
+      h[8 + 2 * k] = T(cs[k] - hi);
+    }
+    h[11] = T(0);
   }
   __syncthreads();
   const int Q = Qs;
@@ -201,6 +222,13 @@ __global__ void k_prefilter(const double* __restrict__ ang, const T* __restrict_
   }
   ct[(long)a * M + m] = T(acc);
 }
+
+__device__ __forceinline__ void cp_async16_bp(void* smem, const void* gmem) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_bp() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_bp() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <typename T> struct Acc { typedef float part; };
 template <> struct Acc<double> { typedef double part; };
@@ -299,6 +327,8 @@ __global__ void __launch_bounds__(BP_TX* BP_TY) k_bp_gather(const T* __restrict_
 #pragma unroll
       for (int step = 8; step > 0; step >>= 1)
         if (h[BP_SIG + q + step] <= f) q += step;
+      const int Qm1 = (int)h[2] - 1;
+      q = q < Qm1 ? q : Qm1;  // f rounded up to 1.0: the last piece's right end
       const T v = (f - h[BP_MID + q]) * h[BP_IHW + q];
       const T* ca = h + BP_CA + q * BP_QA;
       const T* cb = h + BP_CB + q * BP_QB;
@@ -319,6 +349,173 @@ __global__ void __launch_bounds__(BP_TX* BP_TY) k_bp_gather(const T* __restrict_
   }
   total += (double)part;
   if (k1 < N && k2 < N) b[(long)k2 * N + k1] = T(total);
+}
+
+// ------------------------------------------------------------------------------------
+// Spline-window gather (FP32, lambda_y >= BS_LAMBDA_MIN).  For one view the pixel sum
+//     b_k += sum_j c~[m0 + J0 + j] phi_j(f),  p_k = m0 + f,
+// is a function F(p_k) of the detector coordinate alone, and on piece q of bin m0 it is
+// one degree-5 polynomial in v = (f - mid_q) / halfwidth_q whose coefficients are
+// sum_j c~[m0 + J0 + j] coef_{q,j}.  A CTA owns a 64 x 64 tile; per view it first forms
+// those coefficients for every bin slot the tile touches (<= 153 slots, ~0.2 extra FMA
+// per pixel-view pair), then every pixel costs one piece search and one Horner step.
+// The next view's piece table (cp.async) and detector-sample window are fetched while
+// the current view is processed.  Each lane owns a 4 x 4 pixel block whose detector
+// coordinate is computed in FP64 per view, so FP32 offsets stay below 4.3 bins; FP32
+// partial sums go into FP64 totals every 32 views.
+// ------------------------------------------------------------------------------------
+constexpr int BS_TS = 64;                          // tile edge (pixels)
+constexpr int BS_NT = 256;                         // 8 warps x 32 lanes x (4 x 4 pixels)
+constexpr double BS_LAMBDA_MIN = 0.6;              // window <= 63 sqrt(2) / lambda + 4 <= 153
+constexpr int BS_WMAX = 160;                       // bin slots of the coefficient window
+constexpr int BS_WS = BS_WMAX + 1;                 // piece stride (odd: spreads the banks)
+constexpr int BS_CW = BS_WMAX + BP_NJMAX + 4;      // detector-sample window
+struct BsHeader {
+  double p00, c, s;   // detector coordinate of pixel (0, 0) and its steps, in bins
+  int m0lo, W, J0, nJ, Q;
+};
+constexpr size_t bs_smem() {
+  return (size_t)BP_QMAX * BS_WS * (16 + 8) + 2 * (size_t)BP_STRIDE * 4 + 2 * (size_t)BS_CW * 4;
+}
+
+__global__ void __launch_bounds__(BS_NT, 3) k_bp_spline(const float* __restrict__ tab, const double2* __restrict__ csl,
+                                                     const double* __restrict__ p00, const float* __restrict__ ct,
+                                                     int na, int N, int M, float* __restrict__ b) {
+  extern __shared__ __align__(16) unsigned char bs_raw[];
+  float4* FcA = reinterpret_cast<float4*>(bs_raw);                 // [QMAX][BS_WS]
+  float2* FcB = reinterpret_cast<float2*>(FcA + BP_QMAX * BS_WS);  // [QMAX][BS_WS]
+  float* tb = reinterpret_cast<float*>(FcB + BP_QMAX * BS_WS);     // [2][BP_STRIDE]
+  float* ctw = tb + 2 * BP_STRIDE;                                  // [2][BS_CW]
+  __shared__ BsHeader hdr[2];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int TX0 = blockIdx.x * BS_TS, TY0 = blockIdx.y * BS_TS;
+  const int Xb = TX0 + 4 * (lane & 15), Yb = TY0 + 8 * w + 4 * (lane >> 4);
+
+  auto header = [&](int a, BsHeader& h) {
+    const double2 u = csl[a];
+    h.p00 = p00[a];
+    h.c = u.x;
+    h.s = u.y;
+    const double pa = h.p00 + (double)TX0 * u.x + (double)TY0 * u.y;
+    const double ex = (double)(BS_TS - 1) * u.x, ey = (double)(BS_TS - 1) * u.y;
+    const double pmin = pa + (ex < 0 ? ex : 0.0) + (ey < 0 ? ey : 0.0);
+    const double pmax = pa + (ex > 0 ? ex : 0.0) + (ey > 0 ? ey : 0.0);
+    h.m0lo = (int)floor(pmin) - 1;
+    const int W = (int)floor(pmax) + 1 - h.m0lo + 1;
+    h.W = W < BS_WMAX ? W : BS_WMAX;  // W <= 153 for lambda >= BS_LAMBDA_MIN
+    const float* t = tab + (long)a * BP_STRIDE;
+    h.Q = (int)t[2];
+    h.J0 = (int)t[3];
+    h.nJ = (int)t[4];
+  };
+  auto stage_table = [&](int a, int buf) {
+    const char* src = reinterpret_cast<const char*>(tab + (long)a * BP_STRIDE);
+    char* dst = reinterpret_cast<char*>(tb + buf * BP_STRIDE);
+    for (int q = threadIdx.x; q < BP_STRIDE * 4 / 16; q += BS_NT) cp_async16_bp(dst + q * 16, src + q * 16);
+    cp_async_commit_bp();
+  };
+  auto sample = [&](int a, const BsHeader& h, int t) -> float {
+    const int m = h.m0lo + h.J0 + t;
+    return (t < h.W + h.nJ - 1 && (unsigned)m < (unsigned)M) ? ct[(long)a * M + m] : 0.f;
+  };
+
+  // prologue: view 0
+  if (threadIdx.x == 0) header(0, hdr[0]);
+  stage_table(0, 0);
+  __syncthreads();
+  if (threadIdx.x < BS_CW) ctw[threadIdx.x] = sample(0, hdr[0], threadIdx.x);
+  cp_async_wait_bp();
+
+  float acc[16];
+  double tot[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) { acc[i] = 0.f; tot[i] = 0.0; }
+
+  for (int a = 0; a < na; ++a) {
+    const int buf = a & 1;
+    __syncthreads();  // view a staged; the previous view's pixel phase is done
+    if (a + 1 < na) {
+      if (threadIdx.x == 0) header(a + 1, hdr[buf ^ 1]);
+      stage_table(a + 1, buf ^ 1);
+    }
+    // coefficient window: F on (slot s, piece q) = sum_j c~[m0lo + s + J0 + j] coef_{q,j}
+    {
+      const BsHeader& h = hdr[buf];
+      const float* t = tb + buf * BP_STRIDE;
+      const float* cw = ctw + buf * BS_CW;
+      const int W = h.W, nJ = h.nJ, items = h.Q * W;
+      for (int it = threadIdx.x; it < items; it += BS_NT) {
+        const int q = it / W, sl = it - q * W;
+        const float* ca = t + BP_CA + q * BP_QA;
+        const float* cb = t + BP_CB + q * BP_QB;
+        float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f, r4 = 0.f, r5 = 0.f;
+        for (int j = 0; j < nJ; ++j) {
+          const float cv = cw[sl + j];
+          const float4 x = *reinterpret_cast<const float4*>(ca + 4 * j);
+          const float2 y = *reinterpret_cast<const float2*>(cb + 2 * j);
+          r0 = fmaf(cv, x.x, r0); r1 = fmaf(cv, x.y, r1); r2 = fmaf(cv, x.z, r2); r3 = fmaf(cv, x.w, r3);
+          r4 = fmaf(cv, y.x, r4); r5 = fmaf(cv, y.y, r5);
+        }
+        FcA[q * BS_WS + sl] = make_float4(r0, r1, r2, r3);
+        FcB[q * BS_WS + sl] = make_float2(r4, r5);
+      }
+    }
+    __syncthreads();  // window ready; next header visible
+    float cnext = 0.f;
+    if (a + 1 < na && threadIdx.x < BS_CW) cnext = sample(a + 1, hdr[buf ^ 1], threadIdx.x);
+    // pixels
+    {
+      const BsHeader& h = hdr[buf];
+      const float* t = tb + buf * BP_STRIDE;
+      // p = floor(p00) + frac(p00) + X c_hi + Y s_hi + (X c_lo + Y s_lo): the two hi
+      // products are exact, so their integer and fractional parts separate exactly
+      const float X = (float)Xb, Y = (float)Yb;
+      const float a1 = X * t[7], a2 = Y * t[9];
+      const float n1 = floorf(a1), n2 = floorf(a2);
+      const float fr = (t[6] + (a1 - n1)) + ((a2 - n2) + fmaf(Y, t[10], X * t[8]));
+      const float n3 = floorf(fr);
+      const int mb = (int)t[5] + (int)n1 + (int)n2 + (int)n3 - h.m0lo;
+      const float fb = fr - n3, cl = t[0], sl = t[1];
+      const int Qm1 = h.Q - 1;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float pl = fb + (float)i * cl + (float)k * sl;
+          const float fl = floorf(pl);
+          const float f = pl - fl;
+          const int slot = mb + (int)fl;
+          int q = 0;
+#pragma unroll
+          for (int step = 8; step > 0; step >>= 1)
+            if (t[BP_SIG + q + step] <= f) q += step;
+          q = q < Qm1 ? q : Qm1;  // f rounded up to 1.0: the last piece's right end
+          const float v = (f - t[BP_MID + q]) * t[BP_IHW + q];
+          const float4 x = FcA[q * BS_WS + slot];
+          const float2 y = FcB[q * BS_WS + slot];
+          float r = fmaf(y.y, v, y.x);
+          r = fmaf(r, v, x.w);
+          r = fmaf(r, v, x.z);
+          r = fmaf(r, v, x.y);
+          r = fmaf(r, v, x.x);
+          acc[4 * k + i] += r;
+        }
+      }
+    }
+    if (a + 1 < na && threadIdx.x < BS_CW) ctw[(buf ^ 1) * BS_CW + threadIdx.x] = cnext;
+    if ((a & 31) == 31) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) { tot[i] += (double)acc[i]; acc[i] = 0.f; }
+    }
+    cp_async_wait_bp();
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int X = Xb + i, Y = Yb + k;
+      if (X < N && Y < N) b[(long)Y * N + X] = (float)(tot[4 * k + i] + (double)acc[4 * k + i]);
+    }
 }
 
 }  // namespace bsct
@@ -363,6 +560,17 @@ template <typename T> int bp_make_tables(const BpPlan& p, cudaStream_t st) {
 template <typename T> int bp_apply(const BpPlan& p, const T* sino, T* ct, T* b, cudaStream_t st) {
   dim3 gp((p.M + 127) / 128, p.na);
   k_prefilter<T><<<gp, 128, 0, st>>>(p.ang, sino, p.na, p.M, p.zeta, ct);
+  if constexpr (sizeof(T) == 4) {
+    if (p.lambda >= BS_LAMBDA_MIN) {
+      dim3 gs((p.N + BS_TS - 1) / BS_TS, (p.N + BS_TS - 1) / BS_TS);
+      BSCT_CUDA_TRY(cudaFuncSetAttribute(k_bp_spline, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs_smem()));
+      k_bp_spline<<<gs, BS_NT, bs_smem(), st>>>((const float*)p.tab, p.csl, p.p00, (const float*)ct, p.na, p.N, p.M,
+                                               (float*)b);
+      count_launch(2);
+      BSCT_CUDA_TRY(cudaGetLastError());
+      return BSCT_OK;
+    }
+  }
   dim3 gg((p.N + BP_TX - 1) / BP_TX, (p.N + BP_TY - 1) / BP_TY);
   const int win = bp_window(p.lambda);
   const size_t smem = bp_gather_smem<T>(win);

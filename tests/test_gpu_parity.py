@@ -159,6 +159,8 @@ def test_gram_apply_linearity_and_symmetry(bsct):
 @pytest.mark.parametrize("N,na,M,lam,zeta", [
     (32, 45, 48, 1.0, 0.0), (32, 45, 48, 1.0, 1.0), (50, 37, 77, 0.7, 1.0), (64, 90, 92, 1.0, 0.0),
     (41, 16, 60, 1.6, 1.0), (16, 2, 20, 1.0, 1.0),
+    (40, 30, 160, 0.45, 1.0),  # fine detector sampling: the per-offset gather (window too long for the tile)
+    (130, 24, 200, 0.95, 0.0),  # several 64 x 64 tiles with a ragged edge
 ])
 def test_backproject_fp32(bsct, N, na, M, lam, zeta):
     angles = np.arange(na) / na
