@@ -196,31 +196,43 @@ __global__ void __launch_bounds__(256) k_bp_tables(const double* __restrict__ an
   }
 }
 
+// One CTA per 256 outputs of one view: the sinogram segment with a 40-sample halo on
+// each side (zero outside the detector) is staged in shared memory and the symmetric
+// 81-tap filter is summed from the outermost taps inwards in T.
+constexpr int PF_T = 256, PF_H = 40;
 template <typename T>
-__global__ void k_prefilter(const double* __restrict__ ang, const T* __restrict__ g, int na, int M, double zeta,
-                            T* __restrict__ ct) {
-  __shared__ double q[41];
-  if (threadIdx.x <= 40) {
+__global__ void __launch_bounds__(PF_T) k_prefilter(const double* __restrict__ ang, const T* __restrict__ g, int na,
+                                                    int M, double zeta, T* __restrict__ ct) {
+  __shared__ T qs[PF_H + 1];
+  __shared__ T seg[PF_T + 2 * PF_H];
+  __shared__ int deg2;
+  const int a = blockIdx.y, m0 = blockIdx.x * PF_T;
+  const T* gr = g + (long)a * M;
+  if (threadIdx.x == 0) {
+    double s_, c_;
+    sincospi(ang[a], &s_, &c_);
+    deg2 = bp_degree(c_, s_, zeta) == 2;
+  }
+  if (threadIdx.x <= PF_H) {
     const double z1 = 2.0 * 1.4142135623730951 - 3.0;
-    q[threadIdx.x] = 1.4142135623730951 * pow(z1, (double)threadIdx.x);
+    qs[threadIdx.x] = T(1.4142135623730951 * pow(z1, (double)threadIdx.x));
+  }
+  for (int i = threadIdx.x; i < PF_T + 2 * PF_H; i += PF_T) {
+    const int mm = m0 - PF_H + i;
+    seg[i] = (mm >= 0 && mm < M) ? gr[mm] : T(0);
   }
   __syncthreads();
-  const int a = blockIdx.y;
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = m0 + threadIdx.x;
   if (m >= M) return;
-  double s_, c_;
-  sincospi(ang[a], &s_, &c_);
-  const T* gr = g + (long)a * M;
-  if (bp_degree(c_, s_, zeta) != 2) {
-    ct[(long)a * M + m] = gr[m];
+  const T* c = seg + PF_H + threadIdx.x;
+  if (!deg2) {
+    ct[(long)a * M + m] = c[0];
     return;
   }
-  double acc = 0.0;
-  for (int j = -40; j <= 40; ++j) {
-    const int mm = m - j;
-    if (mm >= 0 && mm < M) acc += q[j < 0 ? -j : j] * (double)gr[mm];
-  }
-  ct[(long)a * M + m] = T(acc);
+  T acc = T(0);
+#pragma unroll 8
+  for (int j = PF_H; j >= 1; --j) acc = fma(qs[j], c[-j] + c[j], acc);
+  ct[(long)a * M + m] = fma(qs[0], c[0], acc);
 }
 
 __device__ __forceinline__ void cp_async16_bp(void* smem, const void* gmem) {
@@ -558,8 +570,8 @@ template <typename T> int bp_make_tables(const BpPlan& p, cudaStream_t st) {
 }
 // per-sinogram part: prefilter into ct ([na][M] scratch), then gather into b
 template <typename T> int bp_apply(const BpPlan& p, const T* sino, T* ct, T* b, cudaStream_t st) {
-  dim3 gp((p.M + 127) / 128, p.na);
-  k_prefilter<T><<<gp, 128, 0, st>>>(p.ang, sino, p.na, p.M, p.zeta, ct);
+  dim3 gp((p.M + PF_T - 1) / PF_T, p.na);
+  k_prefilter<T><<<gp, PF_T, 0, st>>>(p.ang, sino, p.na, p.M, p.zeta, ct);
   if constexpr (sizeof(T) == 4) {
     if (p.lambda >= BS_LAMBDA_MIN) {
       dim3 gs((p.N + BS_TS - 1) / BS_TS, (p.N + BS_TS - 1) / BS_TS);
