@@ -380,7 +380,10 @@ constexpr int BS_TS = 64;                          // tile edge (pixels)
 constexpr int BS_NT = 256;                         // 8 warps x 32 lanes x (4 x 4 pixels)
 constexpr double BS_LAMBDA_MIN = 0.6;              // window <= 63 sqrt(2) / lambda + 4 <= 153
 constexpr int BS_WMAX = 160;                       // bin slots of the coefficient window
-constexpr int BS_WS = BS_WMAX + 1;                 // piece stride (odd: spreads the banks)
+// bin slot s of piece q lives at q BS_WS + s + s/4: lanes whose slots differ by a
+// multiple of 4 (near-axis views) then fall on different banks
+constexpr int BS_WS = BS_WMAX + BS_WMAX / 4 + 1;
+__device__ __forceinline__ int bs_slot(int s) { return s + (s >> 2); }
 constexpr int BS_CW = BS_WMAX + BP_NJMAX + 4;      // detector-sample window
 struct BsHeader {
   double p00, c, s;   // detector coordinate of pixel (0, 0) and its steps, in bins
@@ -390,9 +393,11 @@ constexpr size_t bs_smem() {
   return (size_t)BP_QMAX * BS_WS * (16 + 8) + 2 * (size_t)BP_STRIDE * 4 + 2 * (size_t)BS_CW * 4;
 }
 
+// blockIdx.z takes views [z vc, min(na, (z + 1) vc)); with more than one z the sums go to
+// the partial image out + z N^2 (summed in order by k_bp_reduce), else to out.
 __global__ void __launch_bounds__(BS_NT, 3) k_bp_spline(const float* __restrict__ tab, const double2* __restrict__ csl,
-                                                     const double* __restrict__ p00, const float* __restrict__ ct,
-                                                     int na, int N, int M, float* __restrict__ b) {
+                                                        const double* __restrict__ p00, const float* __restrict__ ct,
+                                                        int na, int vc, int N, int M, float* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char bs_raw[];
   float4* FcA = reinterpret_cast<float4*>(bs_raw);                 // [QMAX][BS_WS]
   float2* FcB = reinterpret_cast<float2*>(FcA + BP_QMAX * BS_WS);  // [QMAX][BS_WS]
@@ -431,11 +436,13 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bp_spline(const float* __restrict_
     return (t < h.W + h.nJ - 1 && (unsigned)m < (unsigned)M) ? ct[(long)a * M + m] : 0.f;
   };
 
-  // prologue: view 0
-  if (threadIdx.x == 0) header(0, hdr[0]);
-  stage_table(0, 0);
+  const int a_begin = blockIdx.z * vc, a_end = min(na, a_begin + vc);
+  float* b = out + (long)blockIdx.z * N * N;
+  // prologue: first view
+  if (threadIdx.x == 0) header(a_begin, hdr[0]);
+  stage_table(a_begin, 0);
   __syncthreads();
-  if (threadIdx.x < BS_CW) ctw[threadIdx.x] = sample(0, hdr[0], threadIdx.x);
+  if (threadIdx.x < BS_CW) ctw[threadIdx.x] = sample(a_begin, hdr[0], threadIdx.x);
   cp_async_wait_bp();
 
   float acc[16];
@@ -443,10 +450,10 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bp_spline(const float* __restrict_
 #pragma unroll
   for (int i = 0; i < 16; ++i) { acc[i] = 0.f; tot[i] = 0.0; }
 
-  for (int a = 0; a < na; ++a) {
-    const int buf = a & 1;
+  for (int a = a_begin; a < a_end; ++a) {
+    const int buf = (a - a_begin) & 1;
     __syncthreads();  // view a staged; the previous view's pixel phase is done
-    if (a + 1 < na) {
+    if (a + 1 < a_end) {
       if (threadIdx.x == 0) header(a + 1, hdr[buf ^ 1]);
       stage_table(a + 1, buf ^ 1);
     }
@@ -468,13 +475,13 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bp_spline(const float* __restrict_
           r0 = fmaf(cv, x.x, r0); r1 = fmaf(cv, x.y, r1); r2 = fmaf(cv, x.z, r2); r3 = fmaf(cv, x.w, r3);
           r4 = fmaf(cv, y.x, r4); r5 = fmaf(cv, y.y, r5);
         }
-        FcA[q * BS_WS + sl] = make_float4(r0, r1, r2, r3);
-        FcB[q * BS_WS + sl] = make_float2(r4, r5);
+        FcA[q * BS_WS + bs_slot(sl)] = make_float4(r0, r1, r2, r3);
+        FcB[q * BS_WS + bs_slot(sl)] = make_float2(r4, r5);
       }
     }
     __syncthreads();  // window ready; next header visible
     float cnext = 0.f;
-    if (a + 1 < na && threadIdx.x < BS_CW) cnext = sample(a + 1, hdr[buf ^ 1], threadIdx.x);
+    if (a + 1 < a_end && threadIdx.x < BS_CW) cnext = sample(a + 1, hdr[buf ^ 1], threadIdx.x);
     // pixels
     {
       const BsHeader& h = hdr[buf];
@@ -503,8 +510,8 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bp_spline(const float* __restrict_
             if (t[BP_SIG + q + step] <= f) q += step;
           q = q < Qm1 ? q : Qm1;  // f rounded up to 1.0: the last piece's right end
           const float v = (f - t[BP_MID + q]) * t[BP_IHW + q];
-          const float4 x = FcA[q * BS_WS + slot];
-          const float2 y = FcB[q * BS_WS + slot];
+          const float4 x = FcA[q * BS_WS + bs_slot(slot)];
+          const float2 y = FcB[q * BS_WS + bs_slot(slot)];
           float r = fmaf(y.y, v, y.x);
           r = fmaf(r, v, x.w);
           r = fmaf(r, v, x.z);
@@ -514,8 +521,8 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bp_spline(const float* __restrict_
         }
       }
     }
-    if (a + 1 < na && threadIdx.x < BS_CW) ctw[(buf ^ 1) * BS_CW + threadIdx.x] = cnext;
-    if ((a & 31) == 31) {
+    if (a + 1 < a_end && threadIdx.x < BS_CW) ctw[(buf ^ 1) * BS_CW + threadIdx.x] = cnext;
+    if (((a - a_begin) & 31) == 31) {
 #pragma unroll
       for (int i = 0; i < 16; ++i) { tot[i] += (double)acc[i]; acc[i] = 0.f; }
     }
@@ -528,6 +535,29 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bp_spline(const float* __restrict_
       const int X = Xb + i, Y = Yb + k;
       if (X < N && Y < N) b[(long)Y * N + X] = (float)(tot[4 * k + i] + (double)acc[4 * k + i]);
     }
+}
+
+// b = sum over z of part[z] (fixed order)
+__global__ void k_bp_reduce(const float* __restrict__ part, int S, long n, float* __restrict__ b) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int z = 0; z < S; ++z) acc += (double)part[(long)z * n + i];
+  b[i] = (float)acc;
+}
+
+// views per spline-gather CTA: enough view splits that a small image still fills about
+// 1024 CTAs, at least 16 views each (the split is fixed by N and the view count only)
+int bp_view_split(int N, int na, double lambda, int precision) {
+  if (precision != BSCT_F32 || lambda < BS_LAMBDA_MIN) return 1;
+  const int t = (N + BS_TS - 1) / BS_TS;
+  int S = (1024 + t * t - 1) / (t * t);
+  const int smax = na / 16 > 1 ? na / 16 : 1;
+  return S < smax ? S : smax;
+}
+size_t bp_partial_bytes(int N, int na, double lambda, int precision) {
+  const int S = bp_view_split(N, na, lambda, precision);
+  return S > 1 ? (size_t)S * N * N * sizeof(float) : 0;
 }
 
 }  // namespace bsct
@@ -546,6 +576,7 @@ static size_t bp_workspace(const bsct_geom* g, int precision) {
   b += al((size_t)g->n_angles * BP_STRIDE * T);               // tables
   b += al((size_t)g->n_angles * g->n_bins * T);               // prefiltered sinogram
   b += al(sizeof(int));                                       // status
+  b += al(bp_partial_bytes(g->N, g->n_angles, g->lambda_y, precision));  // partial images
   return b;
 }
 
@@ -574,11 +605,19 @@ template <typename T> int bp_apply(const BpPlan& p, const T* sino, T* ct, T* b, 
   k_prefilter<T><<<gp, PF_T, 0, st>>>(p.ang, sino, p.na, p.M, p.zeta, ct);
   if constexpr (sizeof(T) == 4) {
     if (p.lambda >= BS_LAMBDA_MIN) {
-      dim3 gs((p.N + BS_TS - 1) / BS_TS, (p.N + BS_TS - 1) / BS_TS);
+      const int S = bp_view_split(p.N, p.na, p.lambda, BSCT_F32);
+      if (S > 1 && !p.part) { bsct_set_last_message("back projection: no partial-image scratch"); return BSCT_ERR_INVALID_ARG; }
+      const int vc = (p.na + S - 1) / S;
+      dim3 gs((p.N + BS_TS - 1) / BS_TS, (p.N + BS_TS - 1) / BS_TS, (p.na + vc - 1) / vc);
       BSCT_CUDA_TRY(cudaFuncSetAttribute(k_bp_spline, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs_smem()));
-      k_bp_spline<<<gs, BS_NT, bs_smem(), st>>>((const float*)p.tab, p.csl, p.p00, (const float*)ct, p.na, p.N, p.M,
-                                               (float*)b);
+      k_bp_spline<<<gs, BS_NT, bs_smem(), st>>>((const float*)p.tab, p.csl, p.p00, (const float*)ct, p.na, vc, p.N,
+                                               p.M, gs.z > 1 ? p.part : (float*)b);
       count_launch(2);
+      if (gs.z > 1) {
+        const long n = (long)p.N * p.N;
+        k_bp_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p.part, (int)gs.z, n, (float*)b);
+        count_launch();
+      }
       BSCT_CUDA_TRY(cudaGetLastError());
       return BSCT_OK;
     }
@@ -619,6 +658,8 @@ static int bp_run(const bsct_geom* g, const T* sino, T* b, char* work, cudaStrea
   T* d_ct = (T*)work;
   work += al((size_t)na * M * sizeof(T));
   p.status = (int*)work;
+  work += al(sizeof(int));
+  p.part = bp_partial_bytes(N, na, g->lambda_y, sizeof(T) == 4 ? BSCT_F32 : BSCT_F64) ? (float*)work : nullptr;
   BSCT_CUDA_TRY(cudaMemcpyAsync(p.ang, g->angles_pi, na * sizeof(double), cudaMemcpyHostToDevice, st));
   int rc = bp_make_tables<T>(p, st);
   if (rc != BSCT_OK) return rc;

@@ -43,6 +43,7 @@ struct bsct_batch {
   std::vector<BatchGeom> geoms;
   std::vector<BatchSlice> slices;
   std::vector<cudaStream_t> pool;
+  std::vector<float*> pool_part;  // per pool stream: back-projection partial images of its slices
   std::vector<cudaEvent_t> joins;
   cudaEvent_t fork = nullptr;
   cudaStream_t cap = nullptr;  // non-blocking stream the graph is recorded on
@@ -74,6 +75,7 @@ static void batch_release(bsct_batch* b) {
     cudaFree(g.bp.status);
   }
   for (auto s : b->pool) cudaStreamDestroy(s);
+  for (auto q : b->pool_part) cudaFree(q);
   for (auto e : b->joins) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -174,6 +176,16 @@ extern "C" int bsct_batch_create(int n_slices, const bsct_geom* geoms, bsct_batc
   const int npool = n_slices < 32 ? n_slices : 32;
   bt->pool.resize(npool);
   bt->joins.resize(npool);
+  bt->pool_part.assign(npool, nullptr);
+  for (int k = 0; k < npool; ++k) {  // slices i with i % npool == k run in order on stream k
+    size_t need = 0;
+    for (size_t i = k; i < bt->slices.size(); i += npool) {
+      const bsct_geom& g = bt->geoms[bt->slices[i].geom].g;
+      const size_t nb = bp_partial_bytes(g.N, g.n_angles, g.lambda_y, BSCT_F32);
+      need = nb > need ? nb : need;
+    }
+    if (need) BCTRY(cudaMalloc(&bt->pool_part[k], need));
+  }
   for (int k = 0; k < npool; ++k) {
     BCTRY(cudaStreamCreateWithFlags(&bt->pool[k], cudaStreamNonBlocking));
     BCTRY(cudaEventCreateWithFlags(&bt->joins[k], cudaEventDisableTiming));
@@ -202,7 +214,9 @@ static int batch_record(bsct_batch* bt, const float* const* sino, float* const* 
   for (size_t i = 0; e == cudaSuccess && rc == BSCT_OK && i < bt->slices.size(); ++i) {
     BatchSlice& S = bt->slices[i];
     cudaStream_t s = bt->pool[i % bt->pool.size()];
-    rc = bp_apply<float>(bt->geoms[S.geom].bp, sino[i], S.ct, S.b, s);
+    BpPlan bp = bt->geoms[S.geom].bp;
+    bp.part = bt->pool_part[i % bt->pool.size()];
+    rc = bp_apply<float>(bp, sino[i], S.ct, S.b, s);
     if (rc == BSCT_OK) rc = bsct_cg_begin(S.st, S.b, x[i], 1, s);
     if (rc == BSCT_OK && iters > 0) rc = bsct_cg_iterate(S.st, x[i], iters, s);
   }

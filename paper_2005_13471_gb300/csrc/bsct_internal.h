@@ -88,10 +88,13 @@ struct BpPlan {
   double2* csl = nullptr;    // [na] (cos, sin) / lambda
   void* tab = nullptr;       // bp_table_bytes(na, precision)
   int* status = nullptr;
+  float* part = nullptr;     // bp_partial_bytes(N, na, lambda, precision) of scratch (may be 0 bytes)
 };
 template <typename T> int bp_make_tables(const BpPlan& p, cudaStream_t st);
 template <typename T> int bp_apply(const BpPlan& p, const T* sino, T* ct, T* b, cudaStream_t st);
 size_t bp_table_bytes(int n_angles, int precision);
+int bp_view_split(int N, int na, double lambda, int precision);
+size_t bp_partial_bytes(int N, int na, double lambda, int precision);
 
 // split-BF16 DFT-GEMM Gram apply (dftgemm.cu)
 bool dftgemm_factor(int L, int* P, int* Q);
