@@ -84,6 +84,29 @@ def test_gram_taps_sampled_large(bsct):
 
 
 # ---------------------------------------------------------------- gram_apply
+@pytest.mark.parametrize("N", [256, 2048])
+def test_launch_overlap_same_results(bsct, N):
+    # programmatic dependent launch of the apply kernels changes scheduling only: applies
+    # and CG iterates are bit-identical with it on and off
+    na = 36
+    angles = np.arange(na) / na
+    geom = bsct.Geometry(N, angles, int(1.42 * N) + 2, 1.0, 1.0)
+    g = bsct.gram_build(geom, bsct.F32)
+    x = torch.tensor(np.random.default_rng(7).standard_normal((N, N)), dtype=torch.float32, device=DEV)
+    out = {}
+    try:
+        for ov in (0, 1):
+            bsct.set_launch_overlap(ov)
+            y = g.apply(x)
+            xs, _ = g.cg_solve(y, max_iter=4)
+            out[ov] = (y.cpu().numpy(), xs.cpu().numpy())
+    finally:
+        bsct.set_launch_overlap(1)
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    g.close()
+
+
 @pytest.mark.parametrize("N", [16, 32, 64, 128, 256, 384, 512, 768, 1024])
 def test_gram_apply_fp32(bsct, N):
     na = 24
