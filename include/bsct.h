@@ -251,6 +251,24 @@ int bsct_mse_loss_grad(const float* d_pred, const float* d_target, int64_t n, fl
 int bsct_cg_solve_learned(bsct_gram* g, bsct_unet* net, const void* d_b, void* d_x, float in_scale, int max_iter,
                           double rel_tol, int check_every, bsct_cg_report* report, double* alpha_out, void* stream);
 
+/* Flexible CG with the network as preconditioner (a learned extension; the paper solves
+ * with steepest descent, Sec. 6).  Truncated flexible CG, FCG(1), on G x = b from x0 = 0:
+ *   alpha = <p, r> / <p, G p>,  x += alpha p,  r -= alpha G p,
+ *   z = M(r),  beta = -<z, G p> / <p, G p>,  p = z + beta p,
+ * with M(r) = net(in_scale * s r) / s, s = ||b|| / ||r|| (the network maps right-hand
+ * sides scaled by in_scale to solutions, so it approximates G^-1 on residuals brought
+ * to the scale of b).  The network is applied every precond_every iterations
+ * (1 = every iteration) and M = identity in between; whenever <r, M(r)> <= 0 the
+ * identity is used instead (fallback).  Stops when ||r|| / ||b|| <= rel_tol (r the
+ * recursive residual) or after max_iter iterations; report as for bsct_cg_solve with the
+ * true residual ||b - G x|| / ||b|| recomputed at exit.  *n_precond / *n_fallback (may
+ * be NULL) receive the network applications and the fallbacks.  F32 handle, N a multiple
+ * of 64; d_b, d_x device FP32 N x N.  Uses the handle's CG scratch (not with a CG in
+ * flight on it) and allocates 2 N^2 floats for the call.  Synchronous. */
+int bsct_fcg_solve_learned(bsct_gram* g, bsct_unet* net, const void* d_b, void* d_x, float in_scale, int max_iter,
+                           double rel_tol, int precond_every, bsct_cg_report* report, int32_t* n_precond,
+                           int32_t* n_fallback, void* stream);
+
 /* Human-readable text of a status code, and of the last failure on this thread. */
 const char* bsct_status_string(int status);
 const char* bsct_last_error_string(void);

@@ -100,8 +100,11 @@ def _declare(L):
     L.bsct_mse_loss_grad.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp]
     L.bsct_cg_solve_learned.argtypes = [vp, vp, vp, vp, ctypes.c_float, ctypes.c_int, dbl, ctypes.c_int,
                                         ctypes.POINTER(_CGReport), ctypes.POINTER(dbl), vp]
+    L.bsct_fcg_solve_learned.argtypes = [vp, vp, vp, vp, ctypes.c_float, ctypes.c_int, dbl, ctypes.c_int,
+                                         ctypes.POINTER(_CGReport), ctypes.POINTER(i32), ctypes.POINTER(i32), vp]
     for name in ("bsct_unet_create", "bsct_unet_params", "bsct_unet_sync_weights", "bsct_unet_forward",
-                 "bsct_unet_backward", "bsct_unet_adam_step", "bsct_mse_loss_grad", "bsct_cg_solve_learned"):
+                 "bsct_unet_backward", "bsct_unet_adam_step", "bsct_mse_loss_grad", "bsct_cg_solve_learned",
+                 "bsct_fcg_solve_learned"):
         getattr(L, name).restype = ctypes.c_int
     L.bsct_batch_create.argtypes = [i32, gp, ctypes.POINTER(vp), vp]
     L.bsct_batch_create.restype = ctypes.c_int
@@ -290,6 +293,22 @@ class GramFilter:
                                                 ctypes.byref(alpha), _stream()), "bsct_cg_solve_learned")
         return x, dict(iterations=rep.iterations, converged=bool(rep.converged), rel_residual=rep.rel_residual,
                        true_rel_residual=rep.true_rel_residual, alpha=alpha.value, status=rc)
+
+    def fcg_solve_learned(self, net, b, in_scale, max_iter=1000, rel_tol=1e-4, precond_every=1):
+        """Flexible CG with the network as preconditioner (identity fallback when <r, z> <= 0)."""
+        import torch
+
+        n = self.N
+        x = torch.empty((n, n), dtype=self.dtype, device=b.device)
+        rep = _CGReport()
+        npre, nfb = ctypes.c_int32(), ctypes.c_int32()
+        rc = _check(lib().bsct_fcg_solve_learned(self._h, net._h, _dev(b, (n, n), self.dtype, "b"),
+                                                 _dev(x, (n, n), self.dtype, "x"), float(in_scale), int(max_iter),
+                                                 float(rel_tol), int(precond_every), ctypes.byref(rep),
+                                                 ctypes.byref(npre), ctypes.byref(nfb), _stream()),
+                    "bsct_fcg_solve_learned")
+        return x, dict(iterations=rep.iterations, converged=bool(rep.converged), rel_residual=rep.rel_residual,
+                       true_rel_residual=rep.true_rel_residual, n_precond=npre.value, n_fallback=nfb.value, status=rc)
 
     def cg_solve_mixed(self, b, n_low, n_refine):
         """CG with the split-BF16 DFT-GEMM operator, refined by FP32 residual CG steps."""

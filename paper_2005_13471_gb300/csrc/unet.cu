@@ -674,6 +674,168 @@ extern "C" int bsct_cg_solve_learned(bsct_gram* g, bsct_unet* net, const void* d
 }
 
 namespace {
+// out[k] += <a_k, b_k> for k < 3 (null a_k skipped)
+__global__ void k_dots3(const float* __restrict__ a0, const float* __restrict__ b0, const float* __restrict__ a1,
+                        const float* __restrict__ b1, const float* __restrict__ a2, const float* __restrict__ b2, long n,
+                        double* __restrict__ out) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    if (a0) s0 += (double)a0[i] * b0[i];
+    if (a1) s1 += (double)a1[i] * b1[i];
+    if (a2) s2 += (double)a2[i] * b2[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+    s2 += __shfl_down_sync(0xffffffffu, s2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (a0) atomicAdd(out, s0);
+    if (a1) atomicAdd(out + 1, s1);
+    if (a2) atomicAdd(out + 2, s2);
+  }
+}
+// x += alpha p; r -= alpha q
+__global__ void k_fcg_update(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ p,
+                             const float* __restrict__ q, float alpha, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    x[i] = fmaf(alpha, p[i], x[i]);
+    r[i] = fmaf(-alpha, q[i], r[i]);
+  }
+}
+// p = z + beta p
+__global__ void k_fcg_dir(float* __restrict__ p, const float* __restrict__ z, float beta, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    p[i] = fmaf(beta, p[i], z[i]);
+}
+// out[0] += sum (b - y)^2
+__global__ void k_resid2(const float* __restrict__ b, const float* __restrict__ y, long n, double* __restrict__ out) {
+  double s = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double d = (double)b[i] - y[i];
+    s += d * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+}  // namespace
+
+// Flexible CG with the network as preconditioner (see bsct.h).  Host-driven: every dot
+// product is read back, so the loop can branch on the fallback and the tolerance.
+extern "C" int bsct_fcg_solve_learned(bsct_gram* g, bsct_unet* net, const void* d_b, void* d_x, float in_scale,
+                                      int max_iter, double rel_tol, int precond_every, bsct_cg_report* report,
+                                      int32_t* n_precond, int32_t* n_fallback, void* stream) {
+  if (!g || !net || !d_b || !d_x || max_iter < 0 || precond_every < 1) {
+    bsct_set_last_message("invalid argument");
+    return BSCT_ERR_INVALID_ARG;
+  }
+  if (g->precision != BSCT_F32) { bsct_set_last_message("learned preconditioner needs an F32 handle"); return BSCT_ERR_INVALID_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = g->N;
+  const long n = (long)N * N;
+  const unsigned nb = 1024;
+  const float* b = (const float*)d_b;
+  float* x = (float*)d_x;
+  float* r = (float*)g->r;
+  float* p = (float*)g->p;
+  float* q = (float*)g->q;
+  float *z = nullptr, *xin = nullptr;
+  double* acc = g->partials;  // >= 3 doubles
+  int rc = BSCT_OK, npre = 0, nfb = 0, it = 0, conv = 0;
+  double h[3], bb = 0.0, rr = 0.0;
+  auto dots = [&](const float* a0, const float* b0, const float* a1, const float* b1, const float* a2,
+                  const float* b2) -> int {
+    BSCT_CUDA_TRY(cudaMemsetAsync(acc, 0, 3 * sizeof(double), st));
+    k_dots3<<<nb, TPB, 0, st>>>(a0, b0, a1, b1, a2, b2, n, acc);
+    count_launch();
+    BSCT_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+    BSCT_CUDA_TRY(cudaStreamSynchronize(st));
+    return BSCT_OK;
+  };
+  // z = M(r) (network every precond_every iterations, else identity), with the fallback
+  // z = r when <r, z> <= 0; returns <r, z> in *rz
+  auto precondition = [&](int k, double* rz) -> int {
+    if (k % precond_every == 0 && rr > 0.0) {
+      const double s = sqrt(bb / rr);
+      k_scale_copy<<<nblk(n), TPB, 0, st>>>(r, (float)(in_scale * s), xin, n);
+      count_launch();
+      int e = bsct_unet_forward(net, xin, z, 1, N, N, stream);
+      if (e != BSCT_OK) return e;
+      k_scale_copy<<<nblk(n), TPB, 0, st>>>(z, (float)(1.0 / s), z, n);
+      count_launch();
+      ++npre;
+      e = dots(r, z, nullptr, nullptr, nullptr, nullptr);
+      if (e != BSCT_OK) return e;
+      if (h[0] > 0.0 && isfinite(h[0])) { *rz = h[0]; return BSCT_OK; }
+      ++nfb;
+    }
+    BSCT_CUDA_TRY(cudaMemcpyAsync(z, r, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    *rz = rr;
+    return BSCT_OK;
+  };
+  do {
+    if (cudaMalloc(&z, n * sizeof(float)) != cudaSuccess || cudaMalloc(&xin, n * sizeof(float)) != cudaSuccess) {
+      bsct_set_last_message("out of device memory");
+      rc = BSCT_ERR_CUDA;
+      break;
+    }
+    if ((rc = dots(b, b, nullptr, nullptr, nullptr, nullptr)) != BSCT_OK) break;
+    bb = h[0];
+    rr = bb;
+    if (cudaMemsetAsync(x, 0, n * sizeof(float), st) != cudaSuccess ||
+        cudaMemcpyAsync(r, b, n * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+      rc = BSCT_ERR_CUDA;
+      break;
+    }
+    if (bb == 0.0) { conv = 1; break; }
+    double rz = 0.0;
+    if ((rc = precondition(0, &rz)) != BSCT_OK) break;
+    if (cudaMemcpyAsync(p, z, n * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess) { rc = BSCT_ERR_CUDA; break; }
+    while (it < max_iter) {
+      if ((rc = bsct_gram_apply(g, p, q, BSCT_APPLY_FFT32, stream)) != BSCT_OK) break;
+      if ((rc = dots(p, q, p, r, nullptr, nullptr)) != BSCT_OK) break;
+      const double pq = h[0], pr = h[1];
+      if (!(pq > 0.0) || !isfinite(pq)) break;  // breakdown: p is (numerically) in G's null space
+      const double alpha = pr / pq;
+      k_fcg_update<<<nb, TPB, 0, st>>>(x, r, p, q, (float)alpha, n);
+      count_launch();
+      ++it;
+      if ((rc = dots(r, r, nullptr, nullptr, nullptr, nullptr)) != BSCT_OK) break;
+      rr = h[0];
+      if (sqrt(rr / bb) <= rel_tol) { conv = 1; break; }
+      if (it >= max_iter) break;
+      if ((rc = precondition(it, &rz)) != BSCT_OK) break;
+      if ((rc = dots(z, q, nullptr, nullptr, nullptr, nullptr)) != BSCT_OK) break;
+      const double beta = -h[0] / pq;
+      k_fcg_dir<<<nb, TPB, 0, st>>>(p, z, (float)beta, n);
+      count_launch();
+    }
+  } while (0);
+  if (rc == BSCT_OK && report) {
+    report->iterations = it;
+    report->converged = conv;
+    report->rel_residual = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    report->true_rel_residual = -1.0;
+    // true residual ||b - G x|| / ||b||
+    if ((rc = bsct_gram_apply(g, x, q, BSCT_APPLY_FFT32, stream)) == BSCT_OK) {
+      if (cudaMemsetAsync(acc, 0, sizeof(double), st) == cudaSuccess) {
+        k_resid2<<<nb, TPB, 0, st>>>(b, q, n, acc);
+        count_launch();
+        if (cudaMemcpyAsync(h, acc, sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess)
+          report->true_rel_residual = bb > 0.0 ? sqrt(h[0] / bb) : 0.0;
+      }
+    }
+  }
+  if (n_precond) *n_precond = npre;
+  if (n_fallback) *n_fallback = nfb;
+  cudaStreamSynchronize(st);
+  if (z) cudaFree(z);
+  if (xin) cudaFree(xin);
+  return rc;
+}
+
+namespace {
 // grad = 2 (pred - target) / n; loss[0] += sum (pred - target)^2 / n
 __global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ target, long n, float* __restrict__ grad,
                       double* __restrict__ loss) {

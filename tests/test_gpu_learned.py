@@ -107,6 +107,17 @@ def test_learned_warm_start_gain(bsct):
         rows.append((r0, r["plain_iters"], r["learned_iters"], r["plain_ms"], r["learned_ms"]))
     print("warm-start residual, iterations plain/learned, ms plain/learned:", rows)
     assert np.mean([row[0] for row in rows]) < 0.5  # the warm start beats x0 = 0 by this measure
+    # the same network as flexible-CG preconditioner: reaches the tolerance (by the FP32
+    # true residual) with the network applied every iteration and every 4th
+    b = (Xe[1] * na).contiguous()
+    _, rp = g.cg_solve(b, max_iter=2000, rel_tol=1e-4, check_every=1)
+    fc = []
+    for every in (1, 4):
+        _, rf = g.fcg_solve_learned(net, b, 1.0 / na, max_iter=2000, rel_tol=1e-4, precond_every=every)
+        assert rf["converged"] and rf["true_rel_residual"] <= 1.2e-4
+        assert rf["n_precond"] == (rf["iterations"] - 1) // every + 1
+        fc.append((every, rf["iterations"], rf["n_precond"], rf["n_fallback"]))
+    print("flexible CG (every, iterations, network applications, fallbacks) vs plain", rp["iterations"], fc)
     # fallback: a network whose output is useless (alpha <= 0) leaves plain CG unchanged
     bad = bsct.UNet(base_channels=8, seed=5)
     bad.set_params(torch.zeros(bad.n_params, device=DEV))
@@ -114,6 +125,12 @@ def test_learned_warm_start_gain(bsct):
     _, rp = g.cg_solve(b, max_iter=2000, rel_tol=1e-4, check_every=5)
     _, rl = g.cg_solve_learned(bad, b, 1.0 / na, max_iter=2000, rel_tol=1e-4, check_every=5)
     assert rl["alpha"] == 0.0 and rl["iterations"] == rp["iterations"]
+    # ... and as a preconditioner (<r, z> = 0) falls back to the identity every time, which
+    # makes flexible CG the same method as CG
+    _, rp1 = g.cg_solve(b, max_iter=2000, rel_tol=1e-4, check_every=1)
+    _, rf = g.fcg_solve_learned(bad, b, 1.0 / na, max_iter=2000, rel_tol=1e-4, precond_every=1)
+    assert rf["converged"] and rf["n_fallback"] == rf["n_precond"] == rf["iterations"]
+    assert abs(rf["iterations"] - rp1["iterations"]) <= 2
     g.close()
     net.close()
     bad.close()
