@@ -294,6 +294,12 @@ int bsct_set_launch_overlap(int on);
 /* Number of kernel launches issued by this library since load (all threads). */
 uint64_t bsct_launch_count(void);
 
+/* FMA throughput of the current device (measurement aid, not part of the method): the
+ * best of three timed runs of a kernel in which every thread runs 8 independent FMA
+ * chains, in FP32 (precision BSCT_F32) or FP64 (BSCT_F64); *flops_per_s receives
+ * 2 x FMAs / s.  Allocates and frees a small device buffer.  Synchronous. */
+int bsct_fma_peak(int precision, double* flops_per_s, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -119,6 +119,8 @@ def _declare(L):
     L.bsct_set_kernel_timing.restype = ctypes.c_int
     L.bsct_kernel_times.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_int]
     L.bsct_kernel_times.restype = ctypes.c_int
+    L.bsct_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    L.bsct_fma_peak.restype = ctypes.c_int
     L.bsct_set_launch_overlap.argtypes = [ctypes.c_int]
     L.bsct_set_launch_overlap.restype = ctypes.c_int
     L.bsct_launch_count.argtypes = []
@@ -161,6 +163,13 @@ def launch_count():
 def set_kernel_timing(on):
     """Record CUDA events between the three Gram-apply kernels (see bsct_kernel_times)."""
     _check(lib().bsct_set_kernel_timing(1 if on else 0), "bsct_set_kernel_timing")
+
+
+def fma_peak(precision):
+    """Measured FMA throughput of the device in flop/s (FP32 for F32, FP64 for F64)."""
+    v = ctypes.c_double()
+    _check(lib().bsct_fma_peak(int(precision), ctypes.byref(v), _stream()), "bsct_fma_peak")
+    return v.value
 
 
 def set_launch_overlap(on):

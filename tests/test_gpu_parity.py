@@ -327,3 +327,13 @@ def test_error_codes(bsct):
     with pytest.raises(ValueError):
         g.apply(torch.zeros((32, 31), dtype=torch.float32, device=DEV))
     g.close()
+
+
+def test_fma_peak_sane(bsct):
+    # the FMA probe behind the ALU-bound fractions: FP32 well above FP64, both finite and
+    # within an order of magnitude of a GB300's nominal rates (74 / 1.25 TFLOP/s)
+    f32 = bsct.fma_peak(bsct.F32)
+    f64 = bsct.fma_peak(bsct.F64)
+    assert 7e12 < f32 < 2e14
+    assert 1e11 < f64 < 1.5e13
+    assert f32 > 4 * f64
