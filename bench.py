@@ -162,6 +162,23 @@ def cpu_oracle_apply_rate(n_applies):
     return n_applies / dt, dt
 
 
+def reduce_max(v, device):
+    """Maximum of v over the ranks of the default process group (v itself without one)."""
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, step_ms):
+    """Units of all ranks per second: each rank ran `steps` units; step_ms is the max over ranks."""
+    return world * steps / (step_ms * 1e-3)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -209,13 +226,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        import torch.distributed as dist
-
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, dev)
 
     cfg = get_config(args.workload)
     N = cfg["N"]
@@ -264,7 +275,7 @@ def run_ours(args):
         bsct.set_kernel_timing(False)
     step_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
     step_ms = max_over_ranks(step_ms)
-    value = world * args.steps / (step_ms * 1e-3)
+    value = whole_job_rate(world, args.steps, step_ms)
     kt = ktimes / args.steps  # ms per launch: row R2C, column conv, row C2R
 
     # ---------------------------------------------------------------- roofline (dominant kernel)
