@@ -471,15 +471,24 @@ template <typename T, int LC> struct ColsCfg {
   static constexpr int MINB = (cols_smem<T, LC, G>() * 2 <= 227 * 1024 && sizeof(T) == 4) ? 2 : 1;
 };
 
+// One-time launch setup (shared-memory attributes, persistent grid sizes) is cached per
+// device, so one process may drive several GPUs.
+constexpr int MAX_DEVICES = 64;
+static int device_slot() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return dev < 0 ? 0 : (dev < MAX_DEVICES ? dev : MAX_DEVICES - 1);
+}
 static int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
+  static int n[MAX_DEVICES] = {};
+  const int d = device_slot();
+  if (n[d] == 0) {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    n[d] = v > 0 ? v : 1;
   }
-  return n;
+  return n[d];
 }
 
 template <typename T, int N>
@@ -493,7 +502,8 @@ static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw
   constexpr size_t smi = (size_t)RPI * row_region<T, LR, RPI>() * sizeof(cpx<T>);
   constexpr size_t smc = cols_smem<T, LC, CC::G>();
   auto kc = k_cols_conv<T, LC, CC::G, CC::MINB>;
-  static int grid_c = 0;
+  static int grid_cs[MAX_DEVICES] = {};
+  int& grid_c = grid_cs[device_slot()];
   if (grid_c == 0) {
     int rc = set_smem(k_rows_r2c<T, LR, true, RPC>, smr);
     if (rc == BSCT_OK) rc = set_smem(k_rows_c2r<T, LR, RPI>, smi);
@@ -535,7 +545,8 @@ static int apply_cg_impl(const T* r, T* p, T* q, const double* beta, double* par
   constexpr size_t smi = (size_t)RPI * row_region<T, LR, RPI>() * sizeof(cpx<T>);
   constexpr size_t smc = cols_smem<T, LC, CC::G>();
   auto kc = k_cols_conv<T, LC, CC::G, CC::MINB>;
-  static int grid_c = 0;
+  static int grid_cs[MAX_DEVICES] = {};
+  int& grid_c = grid_cs[device_slot()];
   if (grid_c == 0) {
     int rc = set_smem(k_rows_r2c<T, LR, true, RPC, true>, smr);
     if (rc == BSCT_OK) rc = set_smem(k_rows_c2r<T, LR, RPI, true>, smi);
@@ -566,7 +577,8 @@ static int spectrum_impl(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* tw, cuda
   constexpr int TR = RPC * (LR / Plan<LR>::E), TC = CPC * (LC / Plan<LC>::E);
   const size_t smr = (size_t)RPC * row_region<T, LR, RPC>() * sizeof(cpx<T>);
   const size_t smc = (size_t)CPC * smem_elems<LC>() * sizeof(cpx<T>);
-  static bool attr_done = false;
+  static bool attr_dones[MAX_DEVICES] = {};
+  bool& attr_done = attr_dones[device_slot()];
   if (!attr_done) {
     int rc = set_smem(k_rows_r2c<T, LR, false, RPC>, smr);
     if (rc == BSCT_OK) rc = set_smem(k_cols_fwd_real<T, LC, CPC>, smc);
