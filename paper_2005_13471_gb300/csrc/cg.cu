@@ -62,8 +62,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_finish(const double* __restrict
     switch (op) {
       case OP_STORE_RR: sc[SC_RR] = acc; break;
       case OP_STORE_BB: sc[SC_BB] = acc; break;
-      case OP_ALPHA: sc[SC_PQ] = acc; sc[SC_ALPHA] = sc[SC_RR] / acc; break;
-      case OP_BETA: sc[SC_BETA] = acc / sc[SC_RR]; sc[SC_RR] = acc; break;
+      // an exactly zero residual (or <p, Gp> <= 0) stops the update instead of 0 / 0
+      case OP_ALPHA: sc[SC_PQ] = acc; sc[SC_ALPHA] = acc > 0.0 ? sc[SC_RR] / acc : 0.0; break;
+      case OP_BETA: sc[SC_BETA] = sc[SC_RR] > 0.0 ? acc / sc[SC_RR] : 0.0; sc[SC_RR] = acc; break;
       case OP_STORE_TMP: sc[SC_TMP] = acc; break;
     }
   }

@@ -329,6 +329,29 @@ def test_error_codes(bsct):
     g.close()
 
 
+def test_degenerate_inputs(bsct):
+    # a single view; zero image, zero right-hand side and zero sinogram give exact zeros
+    # (CG without a tolerance keeps x = 0 instead of dividing 0 by 0)
+    N, M = 64, 92
+    angles = np.array([0.3])
+    for prec, dt, tol in ((bsct.F64, torch.float64, 1e-12), (bsct.F32, torch.float32, 1e-5)):
+        geom = bsct.Geometry(N, angles, M, 1.0, 1.0)
+        g = bsct.gram_build(geom, prec)
+        x = np.random.default_rng(1).standard_normal((N, N))
+        y = g.apply(torch.tensor(x, dtype=dt, device=DEV)).cpu().numpy()
+        x_in = x.astype(np.float32).astype(np.float64) if dt == torch.float32 else x
+        assert rel(y, ogram.gram_apply_fft(ogram.gram_taps(N, angles, 1.0), x_in)) < tol
+        z = torch.zeros((N, N), dtype=dt, device=DEV)
+        assert torch.count_nonzero(g.apply(z)) == 0
+        xs, rep = g.cg_solve(z, max_iter=7)
+        assert torch.count_nonzero(xs) == 0 and rep["iterations"] == 7
+        xs, rep = g.cg_solve(z, max_iter=50, rel_tol=1e-4)
+        assert torch.count_nonzero(xs) == 0 and rep["converged"] and rep["iterations"] == 0
+        b = bsct.backproject(geom, torch.zeros((1, M), dtype=dt, device=DEV), prec)
+        assert torch.count_nonzero(b) == 0
+        g.close()
+
+
 def test_fma_peak_sane(bsct):
     # the FMA probe behind the ALU-bound fractions: FP32 well above FP64, both finite and
     # within an order of magnitude of a GB300's nominal rates (74 / 1.25 TFLOP/s)
