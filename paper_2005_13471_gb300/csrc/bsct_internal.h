@@ -55,6 +55,54 @@ inline cudaError_t launch_overlap(void (*k)(KP...), dim3 grid, dim3 block, size_
   return cudaLaunchKernelEx(&cfg, k, static_cast<KP>(args)...);
 }
 
+// CG scalars in device memory (FP64), 16 slots per CG state; the last two hold the
+// arrival counters of the last-block reductions below (zero between launches).
+enum { SC_RR = 0, SC_PQ = 1, SC_ALPHA = 2, SC_BETA = 3, SC_BB = 4, SC_TMP = 5, SC_CNT_PQ = 14, SC_CNT_RR = 15 };
+__device__ __forceinline__ unsigned long long* sc_counter(double* sc, int slot) {
+  return reinterpret_cast<unsigned long long*>(sc + slot);
+}
+
+// Last-block reduction: thread 0 of every CTA has written its partial to part[blockIdx.x];
+// the CTA that arrives last sums part[0 .. gridDim.x) in index order (so the result does
+// not depend on which CTA that is), calls fin(sum) in thread 0 and resets the counter.
+// ws: shared scratch of blockDim.x doubles.  Called by all threads of every CTA.
+template <typename F>
+__device__ __forceinline__ void last_block_sum(const double* part, unsigned long long* cnt, double* ws, F fin) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(cnt, 1ull) == (unsigned long long)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(part + i);
+  if (blockDim.x % 32 == 0) {  // shuffle tree (FP64 adds are slow: keep the chain short)
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double t = threadIdx.x < (int)(blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (threadIdx.x == 0) {
+        fin(t);
+        *cnt = 0ull;
+      }
+    }
+  } else {  // blocks of fewer than 32 threads
+    ws[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < (int)blockDim.x; ++i) t += ws[i];
+      fin(t);
+      *cnt = 0ull;
+    }
+  }
+}
+
 // FFT convolution kernels for one image size N (row FFT length N, column length 2N).
 //   S:   N x N complex scratch (row-block interleaved half spectra)
 //   Gt:  spectrum, [N+1][2N] real, scaled by 1/(2N)^2 (row 0 = (G0+GN)/2, row N = (G0-GN)/2)
@@ -63,10 +111,12 @@ inline cudaError_t launch_overlap(void (*k)(KP...), dim3 grid, dim3 block, size_
 //        order; N each) and of the column plan (2N each)
 template <typename T> struct FftOps {
   int (*apply)(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw, cudaStream_t st);
-  // CG step q = G p with p = r + beta p done in the first pass (p overwritten) and the
-  // per-CTA partial sums of <p, q> written to part[0 .. cg_partials)
-  int (*apply_cg)(const T* r, T* p, T* q, const double* beta, double* part, cpx<T>* S, const T* Gt,
-                  const cpx<T>* tw, cudaStream_t st);
+  // CG step q = G p with p = r + beta p done in the first pass (p overwritten,
+  // beta = sc[SC_BETA]); the last pass writes per-CTA partial sums of <p, q> to
+  // part[0 .. cg_partials) and its last CTA turns them into sc[SC_PQ] and
+  // sc[SC_ALPHA] = sc[SC_RR] / <p, q>
+  int (*apply_cg)(const T* r, T* p, T* q, double* sc, double* part, cpx<T>* S, const T* Gt, const cpx<T>* tw,
+                  cudaStream_t st);
   int cg_partials;
   // emb: 2N x 2N real circulant kernel; S2: 2N x N complex scratch; writes Gt (scaled)
   int (*spectrum)(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* tw, cudaStream_t st);

@@ -5,15 +5,16 @@
 //
 //   p = r + beta p; q = G p; <p, q>     (gram apply with the update fused into its
 //                                         first pass and the inner product into its
-//                                         last pass, 3 kernels) ; alpha = rr / pq
-//   x += alpha p;  r -= alpha q;  <r, r> (k_xr_update partials + k_finish)
-//   beta = rr_new / rr;  rr = rr_new     (beta = 0 before the first iteration)
+//                                         last pass, whose last CTA forms
+//                                         alpha = rr / pq)
+//   x += alpha p;  r -= alpha q;  <r, r> (k_xr_update; its last CTA forms
+//   beta = rr_new / rr;  rr = rr_new      beta and rr; beta = 0 before the first iteration)
+// so one iteration is four kernels and the scalar reductions need no launches of their own.
 #include "bsct_internal.h"
 
 namespace bsct {
 
-enum { SC_RR = 0, SC_PQ = 1, SC_ALPHA = 2, SC_BETA = 3, SC_BB = 4, SC_TMP = 5 };
-enum { OP_STORE_RR = 0, OP_STORE_BB = 1, OP_ALPHA = 2, OP_BETA = 3, OP_STORE_TMP = 4 };
+enum { OP_STORE_RR = 0, OP_STORE_BB = 1, OP_ALPHA = 2, OP_STORE_TMP = 4 };
 
 constexpr int RED_THREADS = 256;
 
@@ -64,20 +65,20 @@ __global__ void __launch_bounds__(RED_THREADS) k_finish(const double* __restrict
       case OP_STORE_BB: sc[SC_BB] = acc; break;
       // an exactly zero residual (or <p, Gp> <= 0) stops the update instead of 0 / 0
       case OP_ALPHA: sc[SC_PQ] = acc; sc[SC_ALPHA] = acc > 0.0 ? sc[SC_RR] / acc : 0.0; break;
-      case OP_BETA: sc[SC_BETA] = sc[SC_RR] > 0.0 ? acc / sc[SC_RR] : 0.0; sc[SC_RR] = acc; break;
       case OP_STORE_TMP: sc[SC_TMP] = acc; break;
     }
   }
 }
 
-// x += alpha p; r -= alpha q; partial <r, r>  (4 elements per thread step)
+// x += alpha p; r -= alpha q; partial <r, r> (4 elements per thread step); the last CTA
+// forms beta = <r, r>_new / <r, r> (0 for an exactly zero residual) and stores <r, r>_new
 template <typename T> struct V4;
 template <> struct V4<float> { typedef float4 t; };
 template <> struct V4<double> { typedef double4 t; };
 
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_xr_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-                                                           const T* __restrict__ q, const double* __restrict__ sc, long n,
+                                                           const T* __restrict__ q, double* __restrict__ sc, long n,
                                                            double* __restrict__ part) {
   typedef typename V4<T>::t v4;
   const T alpha = T(sc[SC_ALPHA]);
@@ -103,6 +104,11 @@ __global__ void __launch_bounds__(RED_THREADS) k_xr_update(T* __restrict__ x, T*
   }
   acc = block_sum(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  __shared__ double lb_ws[RED_THREADS];
+  last_block_sum(part, sc_counter(sc, SC_CNT_RR), lb_ws, [&](double rr) {
+    sc[SC_BETA] = sc[SC_RR] > 0.0 ? rr / sc[SC_RR] : 0.0;
+    sc[SC_RR] = rr;
+  });
 }
 
 template <typename T>
@@ -158,6 +164,7 @@ static int cg_begin_t(bsct_gram* g, const T* b, T* x, int x0_is_zero, cudaStream
   }
   k_init_r<T><<<nb, RED_THREADS, 0, st>>>(b, q, r, p, n, x0_is_zero ? 0 : 1);
   BSCT_CUDA_TRY(cudaMemsetAsync(g->scal + SC_BETA, 0, sizeof(double), st));  // first direction p = r
+  BSCT_CUDA_TRY(cudaMemsetAsync(g->scal + SC_CNT_PQ, 0, 2 * sizeof(double), st));  // reduction counters
   k_dot<T><<<nb, RED_THREADS, 0, st>>>(r, r, n, g->partials);
   k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_STORE_RR);
   k_dot<T><<<nb, RED_THREADS, 0, st>>>(b, b, n, g->partials);
@@ -179,12 +186,10 @@ static int cg_iter_t(bsct_gram* g, T* x, int n_iter, cudaStream_t st) {
   const T* Gt = (g->precision == BSCT_F32) ? (const T*)(const void*)g->Gt32 : (const T*)(const void*)g->Gt64;
   if (o.cg_partials > g->n_partials) return BSCT_ERR_UNSUPPORTED_SIZE;
   for (int it = 0; it < n_iter; ++it) {
-    int rc = o.apply_cg(r, p, q, g->scal + SC_BETA, g->partials, (cpx<T>*)g->S, Gt, (const cpx<T>*)g->tw, st);
+    int rc = o.apply_cg(r, p, q, g->scal, g->partials, (cpx<T>*)g->S, Gt, (const cpx<T>*)g->tw, st);
     if (rc != BSCT_OK) return rc;
-    k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, o.cg_partials, g->scal, OP_ALPHA);
     k_xr_update<T><<<nb, RED_THREADS, 0, st>>>(x, r, p, q, g->scal, n, g->partials);
-    k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_BETA);
-    count_launch(3);
+    count_launch(1);
   }
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
@@ -299,8 +304,7 @@ extern "C" int bsct_cg_solve_mixed(bsct_gram* g, const void* d_b, void* d_x, int
     k_dot<float><<<nb, RED_THREADS, 0, st>>>(p, q, n, g->partials);
     k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_ALPHA);
     k_xr_update<float><<<nb, RED_THREADS, 0, st>>>(x, r, p, q, g->scal, n, g->partials);
-    k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_BETA);
-    count_launch(4);
+    count_launch(3);
   }
   BSCT_CUDA_TRY(cudaGetLastError());
   if (n_refine > 0) {

@@ -145,7 +145,7 @@ template <typename T, int LR, int RPC, bool CG = false>
 __global__ void __launch_bounds__(RPC * (LR / Plan<LR>::E))
 k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
            const cpx<T>* __restrict__ tsr, const cpx<T>* __restrict__ twc, const T* __restrict__ p = nullptr,
-           double* __restrict__ part = nullptr) {
+           double* __restrict__ part = nullptr, double* __restrict__ sc = nullptr) {
   constexpr int E = Plan<LR>::E, TT = LR / E, R1 = Plan<LR>::R[0], RL = Plan<LR>::R[Plan<LR>::NS - 1];
   constexpr int SME = row_region<T, LR, RPC>();
   static_assert(R1 % 2 == 0, "zero-padding / crop split needs an even first radix");
@@ -233,6 +233,11 @@ k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
         part[blockIdx.x] = t;
       }
     }
+    // the last CTA: <p, q> and alpha = <r, r> / <p, q> (0 when <p, q> <= 0)
+    last_block_sum(part, sc_counter(sc, SC_CNT_PQ), ws, [&](double pq) {
+      sc[SC_PQ] = pq;
+      sc[SC_ALPHA] = pq > 0.0 ? sc[SC_RR] / pq : 0.0;
+    });
   }
 }
 
@@ -523,7 +528,8 @@ static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw
   BSCT_CUDA_TRY(launch_overlap(kc, dim3(grid_c), dim3(TC), smc, st, S, Gt, t.cols_f, t.cols_r, N / CC::G));
   timer_mark(st, 2);
   BSCT_CUDA_TRY(launch_overlap(k_rows_c2r<T, LR, RPI>, dim3(N / RPI), dim3(TI), smi, st, (const cpx<T>*)S, y,
-                               (long)N, t.rows_r, t.untangle, (const T*)nullptr, (double*)nullptr));
+                               (long)N, t.rows_r, t.untangle, (const T*)nullptr, (double*)nullptr,
+                               (double*)nullptr));
   timer_mark(st, 3);
   count_launch(3);
   BSCT_CUDA_TRY(cudaGetLastError());
@@ -534,7 +540,7 @@ static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw
 //   K5: p = r + beta p (beta from the device), written back and transformed
 //   K7: q written, per-CTA partial sums of <p, q> into part[0 .. N/RPC)
 template <typename T, int N>
-static int apply_cg_impl(const T* r, T* p, T* q, const double* beta, double* part, cpx<T>* S, const T* Gt,
+static int apply_cg_impl(const T* r, T* p, T* q, double* sc, double* part, cpx<T>* S, const T* Gt,
                          const cpx<T>* tw, cudaStream_t st) {
   constexpr int LR = N, LC = 2 * N;
   constexpr int RPC = rows_per_cta<LR>(), RPI = rows_per_cta_inv<LR>();
@@ -560,10 +566,10 @@ static int apply_cg_impl(const T* r, T* p, T* q, const double* beta, double* par
   }
   const TwPtrs<T> t = tw_ptrs<T, N>(tw);
   BSCT_CUDA_TRY(launch_overlap(k_rows_r2c<T, LR, true, RPC, true>, dim3(N / RPC), dim3(TR), smr, st, r, (long)N, S,
-                               t.rows_f, t.untangle, (const T*)p, p, beta));
+                               t.rows_f, t.untangle, (const T*)p, p, (const double*)(sc + SC_BETA)));
   BSCT_CUDA_TRY(launch_overlap(kc, dim3(grid_c), dim3(TC), smc, st, S, Gt, t.cols_f, t.cols_r, N / CC::G));
   BSCT_CUDA_TRY(launch_overlap(k_rows_c2r<T, LR, RPI, true>, dim3(N / RPI), dim3(TI), smi, st, (const cpx<T>*)S, q,
-                               (long)N, t.rows_r, t.untangle, (const T*)p, part));
+                               (long)N, t.rows_r, t.untangle, (const T*)p, part, sc));
   count_launch(3);
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
