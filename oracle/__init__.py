@@ -18,11 +18,13 @@ that it follows):
                    piecewise Gauss-Legendre quadrature.
 * ``gram``       - Gram filter taps (Sec. 4, the Gram entry with and without blur),
                    explicit Gram matrix on tiny grids, Toeplitz spectrum, Gram apply
-                   (direct convolution and FFT).
+                   (direct convolution and FFT), the circulant preconditioner
+                   (the N x N section of the inverse of G's 2N-periodic circulant
+                   embedding, its symbol floored; not in the paper).
 * ``backproject``- correction filter (Eq. 5), B-spline sinogram interpolation and the
                    back projection H^T g (Sec. 5), forward sampling g_s = S H c.
 * ``cg``         - textbook conjugate gradients on G c = H^T g (normal equations of
-                   the least-squares problem of Sec. 2).
+                   the least-squares problem of Sec. 2), and its preconditioned form.
 
 Where the paper is silent or garbled the oracle takes one reading; every such
 reading is listed in DESIGN.md.

@@ -37,6 +37,39 @@ def cg(apply_G, b, x0=None, iters=20, tol=0.0):
     return x, np.array(hist), iterates
 
 
+def pcg(apply_G, apply_Minv, b, x0=None, iters=20, tol=0.0):
+    """Preconditioned CG with a fixed SPD preconditioner M^-1; returns (x, history of
+    ||r_k|| / ||b||, iterates).
+
+    The textbook recurrence: z = M^-1 r, rho = <r, z>, alpha = rho / <p, G p>,
+    beta = rho_new / rho, p = z + beta p.  With M^-1 = I it is ``cg``.  Stops after
+    ``iters`` iterations or when the residual ratio <= tol.
+    """
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    r = b - apply_G(x) if x0 is not None else b.copy()
+    z = apply_Minv(r)
+    p = z.copy()
+    rho = float(np.sum(r * z))
+    bnorm = float(np.sqrt(np.sum(b * b)))
+    hist = [float(np.sqrt(np.sum(r * r))) / bnorm]
+    iterates = []
+    for _ in range(iters):
+        if tol > 0.0 and hist[-1] <= tol:
+            break
+        q = apply_G(p)
+        alpha = rho / float(np.sum(p * q))
+        x = x + alpha * p
+        r = r - alpha * q
+        z = apply_Minv(r)
+        rho_new = float(np.sum(r * z))
+        p = z + (rho_new / rho) * p
+        rho = rho_new
+        hist.append(float(np.sqrt(np.sum(r * r))) / bnorm)
+        iterates.append(x.copy())
+    return x, np.array(hist), iterates
+
+
 def true_relative_residual(apply_G, b, x):
     """||b - G x|| / ||b|| recomputed from scratch (the judge of any solver's output)."""
     r = b - apply_G(x)

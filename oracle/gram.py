@@ -151,3 +151,35 @@ def gram_apply_sampled(G, x, points):
         sub = G[i2:i2 + N, i1:i1 + N][::-1, ::-1]
         out.append(float(np.sum(sub * x)))
     return np.array(out)
+
+
+def circulant_precond_symbol(G, eps):
+    """Fourier symbol of the circulant preconditioner: 1 / max(G^, eps G^(0)) on the 2N x 2N grid.
+
+    G is Toeplitz-block-Toeplitz (Sec. 4), so it is the N x N section of the 2N-periodic
+    circulant C whose eigenvalues are the spectrum G^ of the embedded filter.  The
+    preconditioner is the same section of C^-1.  G^ may dip slightly below zero for
+    sparse angle sets (the truncated filter is not a positive symbol), so the symbol is
+    floored at eps times its largest value G^(0) = sum of the taps (all taps are >= 0);
+    that keeps the preconditioner symmetric positive definite for any eps in (0, 1].
+    """
+    if not 0.0 < eps <= 1.0:
+        raise ValueError("eps must lie in (0, 1]")
+    Ghat, _ = gram_spectrum(G)
+    g0 = Ghat[0, 0]
+    return 1.0 / np.maximum(Ghat, eps * g0)
+
+
+def circulant_inverse_full(G, x, eps):
+    """F^-1 diag(symbol) F applied to x zero-padded to 2N x 2N; the whole periodic field."""
+    N = x.shape[0]
+    L = 2 * N
+    xp = np.zeros((L, L))
+    xp[:N, :N] = x
+    return np.fft.ifft2(np.fft.fft2(xp) * circulant_precond_symbol(G, eps)).real
+
+
+def circulant_precond_apply(G, x, eps):
+    """M^-1 x: the N x N crop of ``circulant_inverse_full`` (the section of C^-1)."""
+    N = x.shape[0]
+    return circulant_inverse_full(G, x, eps)[:N, :N]
