@@ -315,6 +315,18 @@ def run_ours(args):
     cg_ms = max_over_ranks(e0.elapsed_time(e1))
     cg_rate = world * n_cg / (cg_ms * 1e-3)
     cg_bytes = apply_bytes + 36 * N * N
+    pcg_info = None
+    if not args.quick:
+        # preconditioned CG: two applies (G, M^-1) and one vector update per iteration
+        g.pcg_solve(b, max_iter=3)
+        barrier()
+        e0.record(stream)
+        g.pcg_solve(b, max_iter=n_cg)
+        e1.record(stream)
+        barrier()
+        pcg_ms = max_over_ranks(e0.elapsed_time(e1))
+        pcg_info = {"iters": n_cg, "ms_per_iter": pcg_ms / n_cg, "eps": bsct.PRECOND_EPS,
+                    "timed": "one bsct_pcg_solve call from x = 0 (its start-up M^-1 apply included)"}
 
     # ---------------------------------------------------------------- end to end (host buffers)
     xh = torch.empty((N, N), dtype=torch.float32, pin_memory=True)
@@ -397,6 +409,14 @@ def run_ours(args):
               "plain_iters": [r["iterations"] for _, (_, r) in plain],
               "plain_true_rel_residual_max": max(r["true_rel_residual"] for _, (_, r) in plain),
               "learned_ms_median": None}
+        # preconditioned CG with the circulant preconditioner (the non-learned comparator)
+        g5.pcg_solve(b5s[0], max_iter=5)
+        pcg = [timed(lambda: g5.pcg_solve(b, max_iter=2000, rel_tol=1e-4, check_every=2)) for b in b5s]
+        tt["pcg_circulant"] = {
+            "eps": bsct.PRECOND_EPS, "ms_median": float(np.median([t for t, _ in pcg])),
+            "iters": [r["iterations"] for _, (_, r) in pcg],
+            "true_rel_residual_max": max(r["true_rel_residual"] for _, (_, r) in pcg),
+            "speedup_vs_plain": tt["plain_ms_median"] / float(np.median([t for t, _ in pcg]))}
         if args.learned_pairs > 0:
             from paper_2005_13471_gb300 import learned
 
@@ -521,6 +541,7 @@ def run_ours(args):
         "cg": {"iters": n_cg, "ms_per_iter": cg_ms / n_cg, "algorithmic_bytes_per_iter": cg_bytes,
                "frac_of_hbm": cg_bytes / (cg_ms / n_cg * 1e-3) / 1e9 / hbm,
                "l2": "not flushed between iterations (135 MB working set)"},
+        "pcg": pcg_info,
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(launches),

@@ -181,6 +181,27 @@ int bsct_cg_solve_mixed(bsct_gram* g, const void* d_b, void* d_x, int n_low, int
 /* Copy the current recursive squared residual ||r||^2 and ||b||^2 to host (synchronous). */
 int bsct_cg_residual(const bsct_gram* g, double* rr, double* bb, void* stream);
 
+/* Circulant preconditioner of the Gram filter.  G is Toeplitz-block-Toeplitz (Sec. 4,
+ * closing remark): it is the N x N section of the 2N-periodic circulant C whose
+ * eigenvalues are the spectrum G^ of the zero-padded filter.  The preconditioner is the
+ * same section of C^-1, with C's symbol floored:
+ *     M^-1 x = crop_N( F^-1 [ F(pad_2N x) / max(G^, eps G^(0)) ] ),
+ * G^(0) = the sum of the taps = the largest |G^| (all taps are >= 0).  The floor keeps
+ * M^-1 symmetric positive definite where the truncated filter's symbol dips below zero
+ * (sparse angle sets, blur); eps must lie in (0, 1].  Not part of the paper: a
+ * non-learned preconditioner beside the learned one.
+ * bsct_precond_apply: d_y = M^-1 d_x, [N][N] in the handle's precision (the Gram apply
+ * with the reciprocal spectrum).  The first call, and any call with another eps, builds
+ * the reciprocal spectrum (one kernel); the first call also allocates it and one N x N
+ * vector in the handle.  Asynchronous on the stream; use one stream per handle.
+ * bsct_pcg_solve: preconditioned CG on G x = b with that M^-1; arguments, stopping rule
+ * (on the recursive ||r|| / ||b||, checked every check_every iterations), report and
+ * return codes as bsct_cg_solve.  Each iteration costs two applies (G and M^-1) and one
+ * vector update, seven kernels with no host synchronisation.  Synchronous. */
+int bsct_precond_apply(bsct_gram* g, double eps, const void* d_x, void* d_y, void* stream);
+int bsct_pcg_solve(bsct_gram* g, double eps, const void* d_b, void* d_x, int x0_is_zero, int max_iter,
+                   double rel_tol, int check_every, bsct_cg_report* report, void* stream);
+
 /* Batched reconstruction of many independent slices (FP32).  Each slice i has its own
  * geometry geoms[i] (sizes, views, detector, blur may all differ; slices with an
  * identical geometry share one Gram filter and one set of back-projection tables).

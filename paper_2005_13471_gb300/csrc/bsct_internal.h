@@ -57,7 +57,10 @@ inline cudaError_t launch_overlap(void (*k)(KP...), dim3 grid, dim3 block, size_
 
 // CG scalars in device memory (FP64), 16 slots per CG state; the last two hold the
 // arrival counters of the last-block reductions below (zero between launches).
-enum { SC_RR = 0, SC_PQ = 1, SC_ALPHA = 2, SC_BETA = 3, SC_BB = 4, SC_TMP = 5, SC_CNT_PQ = 14, SC_CNT_RR = 15 };
+// SC_RR holds <r, r> for CG and rho = <r, M^-1 r> for preconditioned CG, whose <r, r>
+// (the convergence measure) goes to SC_RRP
+enum { SC_RR = 0, SC_PQ = 1, SC_ALPHA = 2, SC_BETA = 3, SC_BB = 4, SC_TMP = 5, SC_RRP = 6,
+       SC_CNT_PQ = 14, SC_CNT_RR = 15 };
 __device__ __forceinline__ unsigned long long* sc_counter(double* sc, int slot) {
   return reinterpret_cast<unsigned long long*>(sc + slot);
 }
@@ -118,6 +121,11 @@ template <typename T> struct FftOps {
   int (*apply_cg)(const T* r, T* p, T* q, double* sc, double* part, cpx<T>* S, const T* Gt, const cpx<T>* tw,
                   cudaStream_t st);
   int cg_partials;
+  // preconditioner step z = M^-1 r, the apply with spectrum Mt: the last pass writes
+  // per-CTA partial sums of rho = <r, z> to part[0 .. cg_partials) and its last CTA forms
+  // sc[SC_BETA] = rho / sc[SC_RR] (0 when sc[SC_RR] <= 0) and sc[SC_RR] = rho
+  int (*apply_pc)(const T* r, T* z, double* sc, double* part, cpx<T>* S, const T* Mt, const cpx<T>* tw,
+                  cudaStream_t st);
   // emb: 2N x 2N real circulant kernel; S2: 2N x N complex scratch; writes Gt (scaled)
   int (*spectrum)(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* tw, cudaStream_t st);
 };
@@ -176,5 +184,9 @@ struct bsct_gram {
   int n_partials = 0;
   bool owns_filter = true;   // false for batch slices sharing another handle's taps/spectrum/twiddles
   void* dg_work = nullptr;   // DFT-GEMM scratch, allocated on first DFT-GEMM apply
+  void* z = nullptr;         // preconditioned residual (T, N*N), allocated on first use
+  double* Mt64 = nullptr;    // circulant preconditioner spectrum [N+1][2N], packed like Gt64
+  float* Mt32 = nullptr;     // same, FP32 (precision F32 only)
+  double m_eps = -1.0;       // floor the preconditioner spectrum was built with
   size_t dg_bytes = 0;
 };

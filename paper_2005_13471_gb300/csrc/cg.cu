@@ -14,7 +14,7 @@
 
 namespace bsct {
 
-enum { OP_STORE_RR = 0, OP_STORE_BB = 1, OP_ALPHA = 2, OP_STORE_TMP = 4 };
+enum { OP_STORE_RR = 0, OP_STORE_BB = 1, OP_ALPHA = 2, OP_STORE_TMP = 4, OP_STORE_RRP = 5 };
 
 constexpr int RED_THREADS = 256;
 
@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_finish(const double* __restrict
       // an exactly zero residual (or <p, Gp> <= 0) stops the update instead of 0 / 0
       case OP_ALPHA: sc[SC_PQ] = acc; sc[SC_ALPHA] = acc > 0.0 ? sc[SC_RR] / acc : 0.0; break;
       case OP_STORE_TMP: sc[SC_TMP] = acc; break;
+      case OP_STORE_RRP: sc[SC_RRP] = acc; break;
     }
   }
 }
@@ -76,7 +77,9 @@ template <typename T> struct V4;
 template <> struct V4<float> { typedef float4 t; };
 template <> struct V4<double> { typedef double4 t; };
 
-template <typename T>
+// PCG = true: the last CTA stores <r, r>_new in sc[SC_RRP] only (beta comes from the
+// preconditioner step)
+template <typename T, bool PCG = false>
 __global__ void __launch_bounds__(RED_THREADS) k_xr_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
                                                            const T* __restrict__ q, double* __restrict__ sc, long n,
                                                            double* __restrict__ part) {
@@ -106,8 +109,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_xr_update(T* __restrict__ x, T*
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
   __shared__ double lb_ws[RED_THREADS];
   last_block_sum(part, sc_counter(sc, SC_CNT_RR), lb_ws, [&](double rr) {
-    sc[SC_BETA] = sc[SC_RR] > 0.0 ? rr / sc[SC_RR] : 0.0;
-    sc[SC_RR] = rr;
+    if constexpr (PCG) {
+      sc[SC_RRP] = rr;
+    } else {
+      sc[SC_BETA] = sc[SC_RR] > 0.0 ? rr / sc[SC_RR] : 0.0;
+      sc[SC_RR] = rr;
+    }
   });
 }
 
@@ -126,6 +133,32 @@ __global__ void k_init_r(const T* __restrict__ b, const T* __restrict__ q, T* __
     const T v = has_x0 ? b[i] - q[i] : b[i];
     r[i] = v;
     p[i] = v;
+  }
+}
+
+// Preconditioner spectrum from the Gram spectrum, in the same packed, scaled layout
+// [N+1][2N]: rows 1 .. N-1 hold G^(u, v) / L^2, rows 0 and N hold (G^(u,0) +- G^(u,N)) / 2L^2.
+// Each value becomes 1 / max(G^, eps G^(0,0)) (L = 2N); one thread per (u, v < N), the
+// v = 0 thread also writes row N.
+__global__ void k_precond_spectrum(const double* __restrict__ Gt, int N, double eps, double* __restrict__ Mt,
+                                   float* __restrict__ Mt32) {
+  const int L = 2 * N;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)L * N) return;
+  const int v = (int)(i / L), u = (int)(i % L);
+  const double sc = (double)L * (double)L;
+  const double floor_ = eps * (Gt[0] + Gt[(long)N * L]) * sc;  // eps G^(0, 0)
+  if (v == 0) {
+    const double a = Gt[u], b = Gt[(long)N * L + u];
+    const double h0 = 1.0 / fmax((a + b) * sc, floor_), hN = 1.0 / fmax((a - b) * sc, floor_);
+    const double m0 = 0.5 * (h0 + hN) / sc, mN = 0.5 * (h0 - hN) / sc;
+    Mt[u] = m0;
+    Mt[(long)N * L + u] = mN;
+    if (Mt32) { Mt32[u] = (float)m0; Mt32[(long)N * L + u] = (float)mN; }
+  } else {
+    const double m = 1.0 / fmax(Gt[i] * sc, floor_) / sc;
+    Mt[i] = m;
+    if (Mt32) Mt32[i] = (float)m;
   }
 }
 
@@ -323,4 +356,159 @@ extern "C" int bsct_cg_solve_mixed(bsct_gram* g, const void* d_b, void* d_x, int
     report->true_rel_residual = tr;
   }
   return BSCT_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Preconditioned CG with the circulant preconditioner M^-1 = P C^-1 P^T: C is the
+// 2N-periodic circulant whose N x N section is G (G is Toeplitz-block-Toeplitz, Sec. 4),
+// P the zero-padding, and C's symbol floored at eps G^(0).  M^-1 r is the FFT apply with
+// the reciprocal spectrum.  One iteration is seven kernels:
+//   p = z + beta p; q = G p; alpha = rho / <p, q>       (apply_cg, z in place of r)
+//   x += alpha p; r -= alpha q; <r, r> -> SC_RRP         (k_xr_update<PCG>)
+//   z = M^-1 r; rho_new = <r, z>; beta = rho_new / rho   (apply_pc)
+// ------------------------------------------------------------------------------------
+static int precond_ready(bsct_gram* g, double eps, cudaStream_t st) {
+  if (!(eps > 0.0 && eps <= 1.0)) { bsct_set_last_message("eps must lie in (0, 1]"); return BSCT_ERR_INVALID_ARG; }
+  const int N = g->N, L = 2 * N;
+  const bool f32 = g->precision == BSCT_F32;
+  const size_t T = f32 ? sizeof(float) : sizeof(double);
+  if (!g->Mt64) BSCT_CUDA_TRY(cudaMalloc(&g->Mt64, (size_t)(N + 1) * L * sizeof(double)));
+  if (f32 && !g->Mt32) BSCT_CUDA_TRY(cudaMalloc(&g->Mt32, (size_t)(N + 1) * L * sizeof(float)));
+  if (!g->z) BSCT_CUDA_TRY(cudaMalloc(&g->z, (size_t)N * N * T));
+  if (g->m_eps != eps) {
+    const long n = (long)L * N;
+    k_precond_spectrum<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->Gt64, N, eps, g->Mt64, f32 ? g->Mt32 : nullptr);
+    count_launch();
+    BSCT_CUDA_TRY(cudaGetLastError());
+    g->m_eps = eps;
+  }
+  return BSCT_OK;
+}
+
+template <typename T> static const T* precond_spectrum(const bsct_gram* g) {
+  return (g->precision == BSCT_F32) ? (const T*)(const void*)g->Mt32 : (const T*)(const void*)g->Mt64;
+}
+
+template <typename T>
+static int precond_apply_t(bsct_gram* g, const T* x, T* y, cudaStream_t st) {
+  FftOps<T> o;
+  if (!fft_ops_for<T>(g->N, &o)) return BSCT_ERR_UNSUPPORTED_SIZE;
+  return o.apply(x, y, (cpx<T>*)g->S, precond_spectrum<T>(g), (const cpx<T>*)g->tw, st);
+}
+
+template <typename T>
+static int pcg_begin_t(bsct_gram* g, const T* b, T* x, int x0_is_zero, cudaStream_t st) {
+  const long n = (long)g->N * g->N;
+  const int nb = nblk(g, n);
+  T* r = (T*)g->r;
+  T* p = (T*)g->p;
+  T* q = (T*)g->q;
+  FftOps<T> o;
+  if (!fft_ops_for<T>(g->N, &o)) return BSCT_ERR_UNSUPPORTED_SIZE;
+  if (o.cg_partials > g->n_partials) return BSCT_ERR_UNSUPPORTED_SIZE;
+  if (x0_is_zero) {
+    k_zero<T><<<nb, RED_THREADS, 0, st>>>(x, n);
+    count_launch();
+  } else {
+    int rc = apply_g(g, x, q, st);
+    if (rc != BSCT_OK) return rc;
+  }
+  // r = b - G x0; p = r only keeps p finite for the first update p = z + 0 p
+  k_init_r<T><<<nb, RED_THREADS, 0, st>>>(b, q, r, p, n, x0_is_zero ? 0 : 1);
+  BSCT_CUDA_TRY(cudaMemsetAsync(g->scal, 0, 16 * sizeof(double), st));  // rho = beta = 0, counters
+  k_dot<T><<<nb, RED_THREADS, 0, st>>>(r, r, n, g->partials);
+  k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_STORE_RRP);
+  k_dot<T><<<nb, RED_THREADS, 0, st>>>(b, b, n, g->partials);
+  k_finish<<<1, RED_THREADS, 0, st>>>(g->partials, nb, g->scal, OP_STORE_BB);
+  count_launch(5);
+  // z = M^-1 r, rho = <r, z>; beta stays 0 because the stored rho is 0
+  return o.apply_pc(r, (T*)g->z, g->scal, g->partials, (cpx<T>*)g->S, precond_spectrum<T>(g),
+                    (const cpx<T>*)g->tw, st);
+}
+
+template <typename T>
+static int pcg_iter_t(bsct_gram* g, T* x, int n_iter, cudaStream_t st) {
+  const long n = (long)g->N * g->N;
+  const int nb = nblk(g, n);
+  T* r = (T*)g->r;
+  T* p = (T*)g->p;
+  T* q = (T*)g->q;
+  T* z = (T*)g->z;
+  FftOps<T> o;
+  if (!fft_ops_for<T>(g->N, &o)) return BSCT_ERR_UNSUPPORTED_SIZE;
+  const T* Gt = (g->precision == BSCT_F32) ? (const T*)(const void*)g->Gt32 : (const T*)(const void*)g->Gt64;
+  const T* Mt = precond_spectrum<T>(g);
+  for (int it = 0; it < n_iter; ++it) {
+    int rc = o.apply_cg(z, p, q, g->scal, g->partials, (cpx<T>*)g->S, Gt, (const cpx<T>*)g->tw, st);
+    if (rc != BSCT_OK) return rc;
+    k_xr_update<T, true><<<nb, RED_THREADS, 0, st>>>(x, r, p, q, g->scal, n, g->partials);
+    count_launch(1);
+    rc = o.apply_pc(r, z, g->scal, g->partials, (cpx<T>*)g->S, Mt, (const cpx<T>*)g->tw, st);
+    if (rc != BSCT_OK) return rc;
+  }
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+static int read_scalars(const bsct_gram* g, double* h, cudaStream_t st) {
+  BSCT_CUDA_TRY(cudaMemcpyAsync(h, g->scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  BSCT_CUDA_TRY(cudaStreamSynchronize(st));
+  return BSCT_OK;
+}
+
+extern "C" int bsct_precond_apply(bsct_gram* g, double eps, const void* d_x, void* d_y, void* stream) {
+  if (!g || !d_x || !d_y) { bsct_set_last_message("NULL argument"); return BSCT_ERR_INVALID_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = precond_ready(g, eps, st);
+  if (rc != BSCT_OK) return rc;
+  if (g->precision == BSCT_F32) return precond_apply_t<float>(g, (const float*)d_x, (float*)d_y, st);
+  return precond_apply_t<double>(g, (const double*)d_x, (double*)d_y, st);
+}
+
+extern "C" int bsct_pcg_solve(bsct_gram* g, double eps, const void* d_b, void* d_x, int x0_is_zero, int max_iter,
+                              double rel_tol, int check_every, bsct_cg_report* report, void* stream) {
+  if (!g || !d_b || !d_x || max_iter < 0) { bsct_set_last_message("invalid argument"); return BSCT_ERR_INVALID_ARG; }
+  if (check_every < 1) check_every = 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool f32 = g->precision == BSCT_F32;
+  int rc = precond_ready(g, eps, st);
+  if (rc != BSCT_OK) return rc;
+  rc = f32 ? pcg_begin_t<float>(g, (const float*)d_b, (float*)d_x, x0_is_zero, st)
+           : pcg_begin_t<double>(g, (const double*)d_b, (double*)d_x, x0_is_zero, st);
+  if (rc != BSCT_OK) return rc;
+  double h[16];
+  int it = 0, converged = 0;
+  if (rel_tol > 0.0) {
+    if ((rc = read_scalars(g, h, st)) != BSCT_OK) return rc;
+    if (h[SC_BB] == 0.0 || sqrt(h[SC_RRP] / h[SC_BB]) <= rel_tol) converged = 1;
+  }
+  while (!converged && it < max_iter) {
+    const int k = (rel_tol > 0.0) ? (check_every < max_iter - it ? check_every : max_iter - it) : max_iter - it;
+    rc = f32 ? pcg_iter_t<float>(g, (float*)d_x, k, st) : pcg_iter_t<double>(g, (double*)d_x, k, st);
+    if (rc != BSCT_OK) return rc;
+    it += k;
+    if (rel_tol > 0.0) {
+      if ((rc = read_scalars(g, h, st)) != BSCT_OK) return rc;
+      if (!isfinite(h[SC_RRP]) || !isfinite(h[SC_RR])) {
+        bsct_set_last_message("PCG residual is not finite");
+        return BSCT_ERR_NONFINITE;
+      }
+      if (sqrt(h[SC_RRP] / h[SC_BB]) <= rel_tol) converged = 1;
+    }
+  }
+  if ((rc = read_scalars(g, h, st)) != BSCT_OK) return rc;
+  const double rr = h[SC_RRP], bb = h[SC_BB];
+  double tr = -1.0;
+  if (rel_tol > 0.0) {
+    rc = f32 ? true_residual_t<float>(g, (const float*)d_b, (const float*)d_x, &tr, st)
+             : true_residual_t<double>(g, (const double*)d_b, (const double*)d_x, &tr, st);
+    if (rc != BSCT_OK) return rc;
+  }
+  if (report) {
+    report->iterations = it;
+    report->converged = converged;
+    report->rel_residual = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    report->true_rel_residual = tr;
+  }
+  return (rel_tol > 0.0 && !converged) ? BSCT_WARN_NOT_CONVERGED : BSCT_OK;
 }

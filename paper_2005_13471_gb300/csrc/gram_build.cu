@@ -409,6 +409,9 @@ extern "C" void bsct_gram_free(bsct_gram* g) {
   }
   cudaFree(g->S);
   cudaFree(g->dg_work);
+  cudaFree(g->z);
+  cudaFree(g->Mt64);
+  cudaFree(g->Mt32);
   cudaFree(g->r);
   cudaFree(g->p);
   cudaFree(g->q);

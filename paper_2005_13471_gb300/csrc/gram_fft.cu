@@ -140,8 +140,11 @@ k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
 // ------------------------------------------------------------------------------------
 // K7: packed half spectra -> real rows, first LR outputs of 2 LR (crop)
 // ------------------------------------------------------------------------------------
-// CG: also accumulate <p, y> over the block (p = the apply's input) into part[blockIdx.x]
-template <typename T, int LR, int RPC, bool CG = false>
+// RED != 0: also accumulate <p, y> over the block (p = the apply's input) into
+// part[blockIdx.x]; the last CTA turns the sum into the step scalars of CG (RED_ALPHA)
+// or of preconditioned CG (RED_RHO)
+enum { RED_NONE = 0, RED_ALPHA = 1, RED_RHO = 2 };
+template <typename T, int LR, int RPC, int RED = RED_NONE>
 __global__ void __launch_bounds__(RPC * (LR / Plan<LR>::E))
 k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
            const cpx<T>* __restrict__ tsr, const cpx<T>* __restrict__ twc, const T* __restrict__ p = nullptr,
@@ -202,13 +205,13 @@ k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
 #pragma unroll
     for (int r = 0; r < R1 / 2; ++r) {
       st_cpx(yr + j + r * (LR / R1), v[b * R1 + r]);
-      if constexpr (CG) {
+      if constexpr (RED != RED_NONE) {
         const cpx<T> pp = ld_cpx(reinterpret_cast<const cpx<T>*>(p + (long)(row0 + f) * ld_y) + j + r * (LR / R1));
         dot = fma(pp.x, v[b * R1 + r].x, fma(pp.y, v[b * R1 + r].y, dot));
       }
     }
   }
-  if constexpr (CG) {
+  if constexpr (RED != RED_NONE) {
     // block sum in FP64 (the per-thread part is <= 16 products)
     constexpr int NTH = RPC * TT;
     double d = (double)dot;
@@ -233,10 +236,16 @@ k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
         part[blockIdx.x] = t;
       }
     }
-    // the last CTA: <p, q> and alpha = <r, r> / <p, q> (0 when <p, q> <= 0)
-    last_block_sum(part, sc_counter(sc, SC_CNT_PQ), ws, [&](double pq) {
-      sc[SC_PQ] = pq;
-      sc[SC_ALPHA] = pq > 0.0 ? sc[SC_RR] / pq : 0.0;
+    last_block_sum(part, sc_counter(sc, SC_CNT_PQ), ws, [&](double t) {
+      if constexpr (RED == RED_ALPHA) {
+        // <p, q> and alpha = <r, r> / <p, q> (0 when <p, q> <= 0)
+        sc[SC_PQ] = t;
+        sc[SC_ALPHA] = t > 0.0 ? sc[SC_RR] / t : 0.0;
+      } else {
+        // rho_new = <r, M^-1 r>, beta = rho_new / rho (0 before the first step)
+        sc[SC_BETA] = sc[SC_RR] > 0.0 ? t / sc[SC_RR] : 0.0;
+        sc[SC_RR] = t;
+      }
     });
   }
 }
@@ -555,7 +564,7 @@ static int apply_cg_impl(const T* r, T* p, T* q, double* sc, double* part, cpx<T
   int& grid_c = grid_cs[device_slot()];
   if (grid_c == 0) {
     int rc = set_smem(k_rows_r2c<T, LR, true, RPC, true>, smr);
-    if (rc == BSCT_OK) rc = set_smem(k_rows_c2r<T, LR, RPI, true>, smi);
+    if (rc == BSCT_OK) rc = set_smem(k_rows_c2r<T, LR, RPI, RED_ALPHA>, smi);
     if (rc == BSCT_OK) rc = set_smem(kc, smc);
     if (rc != BSCT_OK) return rc;
     int per_sm = 0;
@@ -568,8 +577,45 @@ static int apply_cg_impl(const T* r, T* p, T* q, double* sc, double* part, cpx<T
   BSCT_CUDA_TRY(launch_overlap(k_rows_r2c<T, LR, true, RPC, true>, dim3(N / RPC), dim3(TR), smr, st, r, (long)N, S,
                                t.rows_f, t.untangle, (const T*)p, p, (const double*)(sc + SC_BETA)));
   BSCT_CUDA_TRY(launch_overlap(kc, dim3(grid_c), dim3(TC), smc, st, S, Gt, t.cols_f, t.cols_r, N / CC::G));
-  BSCT_CUDA_TRY(launch_overlap(k_rows_c2r<T, LR, RPI, true>, dim3(N / RPI), dim3(TI), smi, st, (const cpx<T>*)S, q,
+  BSCT_CUDA_TRY(launch_overlap(k_rows_c2r<T, LR, RPI, RED_ALPHA>, dim3(N / RPI), dim3(TI), smi, st, (const cpx<T>*)S, q,
                                (long)N, t.rows_r, t.untangle, (const T*)p, part, sc));
+  count_launch(3);
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+// z = M^-1 r for preconditioned CG: the plain apply with the preconditioner's spectrum,
+// <r, z> fused into the last pass, whose last CTA forms beta and rho
+template <typename T, int N>
+static int apply_pc_impl(const T* r, T* z, double* sc, double* part, cpx<T>* S, const T* Mt, const cpx<T>* tw,
+                         cudaStream_t st) {
+  constexpr int LR = N, LC = 2 * N;
+  constexpr int RPC = rows_per_cta<LR>(), RPI = rows_per_cta_inv<LR>();
+  typedef ColsCfg<T, LC> CC;
+  constexpr int TR = RPC * (LR / Plan<LR>::E), TI = RPI * (LR / Plan<LR>::E), TC = cols_threads<T, LC, CC::G>();
+  constexpr size_t smr = (size_t)RPC * row_region<T, LR, RPC>() * sizeof(cpx<T>);
+  constexpr size_t smi = (size_t)RPI * row_region<T, LR, RPI>() * sizeof(cpx<T>);
+  constexpr size_t smc = cols_smem<T, LC, CC::G>();
+  auto kc = k_cols_conv<T, LC, CC::G, CC::MINB>;
+  static int grid_cs[MAX_DEVICES] = {};
+  int& grid_c = grid_cs[device_slot()];
+  if (grid_c == 0) {
+    int rc = set_smem(k_rows_r2c<T, LR, true, RPC>, smr);
+    if (rc == BSCT_OK) rc = set_smem(k_rows_c2r<T, LR, RPI, RED_RHO>, smi);
+    if (rc == BSCT_OK) rc = set_smem(kc, smc);
+    if (rc != BSCT_OK) return rc;
+    int per_sm = 0;
+    BSCT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc, TC, smc));
+    if (per_sm < 1) per_sm = 1;
+    const int tiles = N / CC::G;
+    grid_c = per_sm * sm_count() < tiles ? per_sm * sm_count() : tiles;
+  }
+  const TwPtrs<T> t = tw_ptrs<T, N>(tw);
+  BSCT_CUDA_TRY(launch_overlap(k_rows_r2c<T, LR, true, RPC>, dim3(N / RPC), dim3(TR), smr, st, r, (long)N, S,
+                               t.rows_f, t.untangle, (const T*)nullptr, (T*)nullptr, (const double*)nullptr));
+  BSCT_CUDA_TRY(launch_overlap(kc, dim3(grid_c), dim3(TC), smc, st, S, Mt, t.cols_f, t.cols_r, N / CC::G));
+  BSCT_CUDA_TRY(launch_overlap(k_rows_c2r<T, LR, RPI, RED_RHO>, dim3(N / RPI), dim3(TI), smi, st, (const cpx<T>*)S,
+                               z, (long)N, t.rows_r, t.untangle, r, part, sc));
   count_launch(3);
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
@@ -603,6 +649,7 @@ template <typename T, int N> FftOps<T> fft_ops() {
   FftOps<T> o;
   o.apply = &apply_impl<T, N>;
   o.apply_cg = &apply_cg_impl<T, N>;
+  o.apply_pc = &apply_pc_impl<T, N>;
   o.cg_partials = N / rows_per_cta_inv<N>();
   o.spectrum = &spectrum_impl<T, N>;
   return o;
