@@ -156,3 +156,24 @@ def forward_sample(coeffs, angles_pi, M, lam, zeta):
         h = bs.blurred_footprint(ym[:, None] - t[None, nz], c, s, zeta)
         out[j] = h @ w[nz]
     return out
+
+
+def forward_sample_points(coeffs, angles_pi, M, lam, zeta, points):
+    """g_s[j, m] = (S H f)(theta_j, y_m) at selected (view index j, bin m) pairs only.
+
+    The same sum over every pixel as ``forward_sample`` (Sec. 2, Eq. 4), evaluated one
+    detector sample at a time so that large images can be checked at a few samples.
+    """
+    coeffs = np.asarray(coeffs, dtype=np.float64)
+    N = coeffs.shape[0]
+    c_all, s_all = cospi_sinpi(np.atleast_1d(angles_pi))
+    ym = bin_centres(M, lam)
+    w = coeffs.reshape(-1)
+    out = []
+    for j, m in points:
+        c, s = c_all[j], s_all[j]
+        t = pixel_projections(N, c, s).reshape(-1)
+        half = bs.footprint_support(c, s, zeta)
+        near = np.abs(ym[m] - t) < half
+        out.append(float(bs.blurred_footprint(ym[m] - t[near], c, s, zeta) @ w[near]))
+    return np.array(out)

@@ -115,3 +115,34 @@ def test_prefilter_only_on_degree_two_views():
     assert np.array_equal(out[0], sino[0]) and np.array_equal(out[2], sino[2])
     assert not np.allclose(out[1], sino[1])
     assert np.array_equal(bp.prefilter(sino, angles, 0.0), sino)
+
+
+def test_forward_partition_of_unity():
+    # zeta = 1 and lambda_y = 1: the footprint M_[|c|,|s|,1] contains a unit box, whose
+    # integer shifts sum to one, so every view's samples add up to the sum of the
+    # coefficients (the detector covers the whole image)
+    N, M = 9, 17
+    angles = np.array([0.0, 0.07, 0.25, 0.31, 0.5, 0.83])
+    c = np.random.default_rng(11).standard_normal((N, N))
+    sino = bp.forward_sample(c, angles, M, 1.0, 1.0)
+    assert np.max(np.abs(sino.sum(axis=1) - c.sum())) < 1e-12 * np.abs(c).sum()
+
+
+def test_forward_axis_views_are_line_sums():
+    # theta = 0 without blur, lambda_y = 1, M = N: bin m sees exactly column m (a unit
+    # box of the detector coordinate); theta = pi/2 sees row m
+    N = 8
+    c = np.random.default_rng(12).standard_normal((N, N))
+    sino = bp.forward_sample(c, np.array([0.0, 0.5]), N, 1.0, 0.0)
+    assert np.max(np.abs(sino[0] - c.sum(axis=0))) < 1e-13
+    assert np.max(np.abs(sino[1] - c.sum(axis=1))) < 1e-13
+
+
+def test_forward_sample_points_match_full_views():
+    N, M, lam, zeta = 11, 19, 0.8, 0.5
+    angles = np.array([0.13, 0.5, 0.77])
+    c = np.random.default_rng(13).standard_normal((N, N))
+    full = bp.forward_sample(c, angles, M, lam, zeta)
+    pts = [(0, 0), (0, 9), (1, 4), (2, 18), (2, 10)]
+    got = bp.forward_sample_points(c, angles, M, lam, zeta, pts)
+    assert np.max(np.abs(got - np.array([full[p] for p in pts]))) < 1e-14 * np.abs(full).max()
