@@ -154,6 +154,22 @@ int bsct_backproject_workspace(const bsct_geom* geom, int precision, size_t* byt
 int bsct_backproject(const bsct_geom* geom, const void* d_sino, void* d_b, int precision,
                      void* d_work, size_t work_bytes, void* stream);
 
+/* Forward projection g_s = S H c (Sec. 2, Eq. 3-4): detector samples of the blurred
+ * X-ray transform of the pixel-basis image,
+ *   g_s[j][m] = sum_k c_k M_[|cos theta_j|, |sin theta_j|, zeta](y_m - x_k . u_theta_j),
+ * the pixel footprint being the box spline of the pixel's projection (directions |cos|,
+ * |sin|, Eq. 3) averaged over the detector cell (one more direction zeta, Eq. 4), with
+ * the geometry conventions of bsct_geom.  d_coeffs: [N][N] image (row k2, column k1);
+ * d_sino: [n_angles][n_bins] (output, overwritten).  float for BSCT_F32, double for
+ * BSCT_F64.  d_work: device workspace of at least bsct_forward_project_workspace bytes
+ * (per-view tables and a transposed copy of the image).  Asynchronous on the stream.
+ * A sample exactly on the edge of an unblurred axis-aligned footprint (a box) counts the
+ * pixel as outside.  Errors: INVALID_ARG, UNSUPPORTED_SIZE (N > 16384,
+ * n_angles x n_bins >= 2^31, zeta_blur > 4), CUDA. */
+int bsct_forward_project_workspace(const bsct_geom* geom, int precision, size_t* bytes);
+int bsct_forward_project(const bsct_geom* geom, const void* d_coeffs, void* d_sino, int precision,
+                         void* d_work, size_t work_bytes, void* stream);
+
 /* Conjugate gradients on G x = b (normal equations of Sec. 2) with the handle's data
  * precision; inner products and step scalars in FP64 on the device.
  * d_b: right-hand side [N][N]; d_x: in = initial guess (ignored if x0_is_zero),

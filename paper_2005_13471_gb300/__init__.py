@@ -18,7 +18,7 @@ import os
 import numpy as np
 
 __all__ = [
-    "F32", "F64", "Geometry", "GramFilter", "gram_build", "gram_apply", "backproject", "cg_solve",
+    "F32", "F64", "Geometry", "GramFilter", "gram_build", "gram_apply", "backproject", "forward_project", "cg_solve",
     "library_path", "lib", "supported_size", "launch_count",
 ]
 
@@ -81,6 +81,8 @@ def _declare(L):
     L.bsct_cg_iterate.argtypes = [vp, vp, ctypes.c_int, vp]
     L.bsct_cg_residual.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp]
     L.bsct_precond_apply.argtypes = [vp, dbl, vp, vp, vp]
+    L.bsct_forward_project_workspace.argtypes = [gp, ctypes.c_int, ctypes.POINTER(sz)]
+    L.bsct_forward_project.argtypes = [gp, vp, vp, ctypes.c_int, vp, sz, vp]
     L.bsct_pcg_solve.argtypes = [vp, dbl, vp, vp, ctypes.c_int, ctypes.c_int, dbl, ctypes.c_int,
                                  ctypes.POINTER(_CGReport), vp]
     L.bsct_status_string.argtypes = [ctypes.c_int]
@@ -422,6 +424,30 @@ def backproject(geom, sino, precision=F32, out=None, work=None):
         work = torch.empty(nbytes, dtype=torch.uint8, device=sino.device)
     _check(lib().bsct_backproject(geom.cptr(), ps, pb, precision, ctypes.c_void_p(work.data_ptr()),
                                   ctypes.c_size_t(work.numel()), _stream()), "bsct_backproject")
+    return out
+
+
+def forward_project_workspace(geom, precision=F32):
+    n = ctypes.c_size_t()
+    _check(lib().bsct_forward_project_workspace(geom.cptr(), precision, ctypes.byref(n)),
+           "bsct_forward_project_workspace")
+    return int(n.value)
+
+
+def forward_project(geom, coeffs, precision=F32, out=None, work=None):
+    """g_s = S H c (Sec. 2, Eq. 3-4): the [n_angles, n_bins] detector samples of a device image [N, N]."""
+    import torch
+
+    dt = _dtype(precision)
+    pc = _dev(coeffs, (geom.N, geom.N), dt, "coeffs")
+    if out is None:
+        out = torch.empty((geom.n_angles, geom.n_bins), dtype=dt, device=coeffs.device)
+    ps = _dev(out, (geom.n_angles, geom.n_bins), dt, "out")
+    nbytes = forward_project_workspace(geom, precision)
+    if work is None or work.numel() < nbytes:
+        work = torch.empty(nbytes, dtype=torch.uint8, device=coeffs.device)
+    _check(lib().bsct_forward_project(geom.cptr(), pc, ps, precision, ctypes.c_void_p(work.data_ptr()),
+                                      ctypes.c_size_t(work.numel()), _stream()), "bsct_forward_project")
     return out
 
 
