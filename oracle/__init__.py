@@ -24,7 +24,8 @@ that it follows):
 * ``backproject``- correction filter (Eq. 5), B-spline sinogram interpolation and the
                    back projection H^T g (Sec. 5), forward sampling g_s = S H c.
 * ``cg``         - textbook conjugate gradients on G c = H^T g (normal equations of
-                   the least-squares problem of Sec. 2), and its preconditioned form.
+                   the least-squares problem of Sec. 2), its preconditioned form, and the
+                   steepest descent of the paper's reconstruction study (Sec. 6).
 
 Where the paper is silent or garbled the oracle takes one reading; every such
 reading is listed in DESIGN.md.

@@ -70,6 +70,30 @@ def pcg(apply_G, apply_Minv, b, x0=None, iters=20, tol=0.0):
     return x, np.array(hist), iterates
 
 
+def steepest_descent(apply_G, b, x0=None, iters=20, tol=0.0):
+    """Steepest descent on G x = b, the solver of the paper's reconstruction study (Sec. 6).
+
+    Each step moves along the residual r = b - G x by the exact line minimiser of the
+    quadratic, alpha = <r, r> / <r, G r>.  Returns (x, history of ||r_k|| / ||b||, iterates).
+    """
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    r = b - apply_G(x) if x0 is not None else b.copy()
+    bnorm = float(np.sqrt(np.sum(b * b)))
+    hist = [float(np.sqrt(np.sum(r * r))) / bnorm]
+    iterates = []
+    for _ in range(iters):
+        if tol > 0.0 and hist[-1] <= tol:
+            break
+        q = apply_G(r)
+        alpha = float(np.sum(r * r)) / float(np.sum(r * q))
+        x = x + alpha * r
+        r = r - alpha * q
+        hist.append(float(np.sqrt(np.sum(r * r))) / bnorm)
+        iterates.append(x.copy())
+    return x, np.array(hist), iterates
+
+
 def true_relative_residual(apply_G, b, x):
     """||b - G x|| / ||b|| recomputed from scratch (the judge of any solver's output)."""
     r = b - apply_G(x)

@@ -130,3 +130,31 @@ def test_pcg_needs_fewer_iterations_than_cg():
     x, h_p, _ = ocg.pcg(apply, lambda v: gram.circulant_precond_apply(G, v, 1e-4), b, iters=500, tol=1e-4)
     assert h_p[-1] <= 1e-4 and ocg.true_relative_residual(apply, b, x) < 2e-4
     assert len(h_p) * 2 < len(h_cg)
+
+
+def test_steepest_descent_scaled_identity_one_step():
+    b = np.array([1.0, -2.0, 3.0])
+    x, hist, _ = ocg.steepest_descent(lambda v: 4.0 * v, b, iters=1)
+    assert np.max(np.abs(x - b / 4.0)) < 1e-15 and hist[-1] < 1e-15
+
+
+def test_steepest_descent_textbook_rate():
+    # A = diag(1, kappa), x0 = 0, b = A (kappa, 1) (error along the worst direction):
+    # every step multiplies the A-norm of the error by exactly (kappa - 1) / (kappa + 1)
+    kappa = 9.0
+    A = np.diag([1.0, kappa])
+    xs = np.array([kappa, 1.0])
+    b = A @ xs
+    _, _, its = ocg.steepest_descent(lambda v: A @ v, b, iters=6)
+    en = lambda e: float(np.sqrt(e @ A @ e))
+    errs = [en(xs)] + [en(xs - x) for x in its]
+    ratios = np.array(errs[1:]) / np.array(errs[:-1])
+    assert np.allclose(ratios, (kappa - 1) / (kappa + 1), rtol=1e-12)
+
+
+def test_steepest_descent_converges_and_energy_decreases():
+    A, b = _spd(20, 9)
+    xs = np.linalg.solve(A, b)
+    x, _, its = ocg.steepest_descent(lambda v: A @ v, b, iters=400, tol=1e-13)
+    en = [float((xs - z) @ A @ (xs - z)) for z in its]
+    assert np.all(np.diff(en) < 0) and np.linalg.norm(x - xs) < 1e-11 * np.linalg.norm(xs)
