@@ -181,6 +181,12 @@ int bsct_forward_project(const bsct_geom* geom, const void* d_coeffs, void* d_si
 int bsct_cg_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero, int max_iter,
                   double rel_tol, int check_every, bsct_cg_report* report, void* stream);
 
+/* Steepest descent on G x = b, the unregularised solver of the paper's reconstruction
+ * study (Sec. 6): x += alpha r with alpha = <r, r> / <r, G r>.  Arguments, stopping rule,
+ * report and return codes as bsct_cg_solve; four kernels per iteration. */
+int bsct_sd_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero, int max_iter,
+                  double rel_tol, int check_every, bsct_cg_report* report, void* stream);
+
 /* Run exactly n_iter CG iterations without any host synchronisation (the body every
  * CG step of bsct_cg_solve runs; suitable for timing and CUDA-graph capture).  The
  * state (x, r, p and the scalars) lives in the handle: call bsct_cg_begin first. */

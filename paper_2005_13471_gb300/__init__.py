@@ -78,6 +78,8 @@ def _declare(L):
     L.bsct_cg_solve.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, dbl, ctypes.c_int,
                                 ctypes.POINTER(_CGReport), vp]
     L.bsct_cg_begin.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+    L.bsct_sd_solve.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, dbl, ctypes.c_int,
+                                ctypes.POINTER(_CGReport), vp]
     L.bsct_cg_iterate.argtypes = [vp, vp, ctypes.c_int, vp]
     L.bsct_cg_residual.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp]
     L.bsct_precond_apply.argtypes = [vp, dbl, vp, vp, vp]
@@ -379,6 +381,20 @@ class GramFilter:
         report = dict(iterations=rep.iterations, converged=bool(rep.converged), rel_residual=rep.rel_residual,
                       true_rel_residual=rep.true_rel_residual, status=rc)
         return x, report
+
+    def sd_solve(self, b, x0=None, max_iter=100, rel_tol=0.0, check_every=10):
+        """Steepest descent on G x = b (the paper's reconstruction solver)."""
+        import torch
+
+        n = self.N
+        pb = _dev(b, (n, n), self.dtype, "b")
+        x = torch.empty((n, n), dtype=self.dtype, device=b.device) if x0 is None else x0.clone()
+        rep = _CGReport()
+        rc = _check(lib().bsct_sd_solve(self._h, pb, _dev(x, (n, n), self.dtype, "x"), 1 if x0 is None else 0,
+                                        int(max_iter), float(rel_tol), int(check_every), ctypes.byref(rep),
+                                        _stream()), "bsct_sd_solve")
+        return x, dict(iterations=rep.iterations, converged=bool(rep.converged), rel_residual=rep.rel_residual,
+                       true_rel_residual=rep.true_rel_residual, status=rc)
 
     def cg_begin(self, b, x, x0_is_zero=True):
         n = self.N

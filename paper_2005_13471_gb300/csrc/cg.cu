@@ -10,6 +10,8 @@
 //   x += alpha p;  r -= alpha q;  <r, r> (k_xr_update; its last CTA forms
 //   beta = rr_new / rr;  rr = rr_new      beta and rr; beta = 0 before the first iteration)
 // so one iteration is four kernels and the scalar reductions need no launches of their own.
+// Steepest descent (the solver of the paper's reconstruction study, Sec. 6) is the same
+// iteration with beta held at 0, i.e. the direction is always the residual.
 #include "bsct_internal.h"
 
 namespace bsct {
@@ -77,9 +79,11 @@ template <typename T> struct V4;
 template <> struct V4<float> { typedef float4 t; };
 template <> struct V4<double> { typedef double4 t; };
 
-// PCG = true: the last CTA stores <r, r>_new in sc[SC_RRP] only (beta comes from the
-// preconditioner step)
-template <typename T, bool PCG = false>
+// What the last CTA does with <r, r>_new: CG forms beta = <r, r>_new / <r, r> and stores
+// <r, r>_new; PCG stores it in sc[SC_RRP] only (beta comes from the preconditioner
+// step); steepest descent stores it and keeps beta = 0 (the next direction is r)
+enum { UPD_CG = 0, UPD_PCG = 1, UPD_SD = 2 };
+template <typename T, int UPD = UPD_CG>
 __global__ void __launch_bounds__(RED_THREADS) k_xr_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
                                                            const T* __restrict__ q, double* __restrict__ sc, long n,
                                                            double* __restrict__ part) {
@@ -109,8 +113,11 @@ __global__ void __launch_bounds__(RED_THREADS) k_xr_update(T* __restrict__ x, T*
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
   __shared__ double lb_ws[RED_THREADS];
   last_block_sum(part, sc_counter(sc, SC_CNT_RR), lb_ws, [&](double rr) {
-    if constexpr (PCG) {
+    if constexpr (UPD == UPD_PCG) {
       sc[SC_RRP] = rr;
+    } else if constexpr (UPD == UPD_SD) {
+      sc[SC_BETA] = 0.0;
+      sc[SC_RR] = rr;
     } else {
       sc[SC_BETA] = sc[SC_RR] > 0.0 ? rr / sc[SC_RR] : 0.0;
       sc[SC_RR] = rr;
@@ -207,7 +214,7 @@ static int cg_begin_t(bsct_gram* g, const T* b, T* x, int x0_is_zero, cudaStream
   return BSCT_OK;
 }
 
-template <typename T>
+template <typename T, int UPD = UPD_CG>
 static int cg_iter_t(bsct_gram* g, T* x, int n_iter, cudaStream_t st) {
   const long n = (long)g->N * g->N;
   const int nb = nblk(g, n);
@@ -221,7 +228,7 @@ static int cg_iter_t(bsct_gram* g, T* x, int n_iter, cudaStream_t st) {
   for (int it = 0; it < n_iter; ++it) {
     int rc = o.apply_cg(r, p, q, g->scal, g->partials, (cpx<T>*)g->S, Gt, (const cpx<T>*)g->tw, st);
     if (rc != BSCT_OK) return rc;
-    k_xr_update<T><<<nb, RED_THREADS, 0, st>>>(x, r, p, q, g->scal, n, g->partials);
+    k_xr_update<T, UPD><<<nb, RED_THREADS, 0, st>>>(x, r, p, q, g->scal, n, g->partials);
     count_launch(1);
   }
   BSCT_CUDA_TRY(cudaGetLastError());
@@ -270,8 +277,10 @@ static int true_residual_t(bsct_gram* g, const T* b, const T* x, double* out, cu
   return BSCT_OK;
 }
 
-extern "C" int bsct_cg_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero, int max_iter, double rel_tol,
-                             int check_every, bsct_cg_report* report, void* stream) {
+// CG (steepest = false) or steepest descent (steepest = true): the same begin, state and
+// stopping rule; steepest descent is the CG iteration with beta held at 0
+static int krylov_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero, int max_iter, double rel_tol,
+                        int check_every, bsct_cg_report* report, void* stream, bool steepest) {
   if (!g || !d_b || !d_x || max_iter < 0) { bsct_set_last_message("invalid argument"); return BSCT_ERR_INVALID_ARG; }
   if (check_every < 1) check_every = 1;
   cudaStream_t st = (cudaStream_t)stream;
@@ -286,7 +295,11 @@ extern "C" int bsct_cg_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is
   }
   while (!converged && it < max_iter) {
     const int k = (rel_tol > 0.0) ? (check_every < max_iter - it ? check_every : max_iter - it) : max_iter - it;
-    rc = bsct_cg_iterate(g, d_x, k, stream);
+    if (steepest)
+      rc = g->precision == BSCT_F32 ? cg_iter_t<float, UPD_SD>(g, (float*)d_x, k, st)
+                                    : cg_iter_t<double, UPD_SD>(g, (double*)d_x, k, st);
+    else
+      rc = bsct_cg_iterate(g, d_x, k, stream);
     if (rc != BSCT_OK) return rc;
     it += k;
     if (rel_tol > 0.0) {
@@ -311,6 +324,16 @@ extern "C" int bsct_cg_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is
     report->true_rel_residual = tr;
   }
   return (rel_tol > 0.0 && !converged) ? BSCT_WARN_NOT_CONVERGED : BSCT_OK;
+}
+
+extern "C" int bsct_cg_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero, int max_iter, double rel_tol,
+                             int check_every, bsct_cg_report* report, void* stream) {
+  return krylov_solve(g, d_b, d_x, x0_is_zero, max_iter, rel_tol, check_every, report, stream, false);
+}
+
+extern "C" int bsct_sd_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero, int max_iter, double rel_tol,
+                             int check_every, bsct_cg_report* report, void* stream) {
+  return krylov_solve(g, d_b, d_x, x0_is_zero, max_iter, rel_tol, check_every, report, stream, true);
 }
 
 // CG whose operator is the split-BF16 DFT-GEMM apply (unfused: p update, apply, <p, q>),
@@ -364,7 +387,7 @@ extern "C" int bsct_cg_solve_mixed(bsct_gram* g, const void* d_b, void* d_x, int
 // P the zero-padding, and C's symbol floored at eps G^(0).  M^-1 r is the FFT apply with
 // the reciprocal spectrum.  One iteration is seven kernels:
 //   p = z + beta p; q = G p; alpha = rho / <p, q>       (apply_cg, z in place of r)
-//   x += alpha p; r -= alpha q; <r, r> -> SC_RRP         (k_xr_update<PCG>)
+//   x += alpha p; r -= alpha q; <r, r> -> SC_RRP         (k_xr_update<UPD_PCG>)
 //   z = M^-1 r; rho_new = <r, z>; beta = rho_new / rho   (apply_pc)
 // ------------------------------------------------------------------------------------
 static int precond_ready(bsct_gram* g, double eps, cudaStream_t st) {
@@ -441,7 +464,7 @@ static int pcg_iter_t(bsct_gram* g, T* x, int n_iter, cudaStream_t st) {
   for (int it = 0; it < n_iter; ++it) {
     int rc = o.apply_cg(z, p, q, g->scal, g->partials, (cpx<T>*)g->S, Gt, (const cpx<T>*)g->tw, st);
     if (rc != BSCT_OK) return rc;
-    k_xr_update<T, true><<<nb, RED_THREADS, 0, st>>>(x, r, p, q, g->scal, n, g->partials);
+    k_xr_update<T, UPD_PCG><<<nb, RED_THREADS, 0, st>>>(x, r, p, q, g->scal, n, g->partials);
     count_launch(1);
     rc = o.apply_pc(r, z, g->scal, g->partials, (cpx<T>*)g->S, Mt, (const cpx<T>*)g->tw, st);
     if (rc != BSCT_OK) return rc;

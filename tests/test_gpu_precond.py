@@ -143,3 +143,40 @@ def test_pcg_degenerate_and_errors(bsct):
         with pytest.raises(RuntimeError, match="invalid argument"):
             g.precond_apply(zero, eps=bad)
     g.close()
+
+
+def test_steepest_descent_follows_oracle(bsct):
+    cfg = get_config("fp64_n64")
+    angles, sino, _ = make_problem(cfg)
+    N = cfg["N"]
+    g = bsct.gram_build(bsct.Geometry(N, angles, cfg["n_bins"], cfg["lambda_y"], cfg["zeta"]), bsct.F64)
+    b_ref = obp.backproject(sino, N, angles, cfg["lambda_y"], cfg["zeta"])
+    b = torch.tensor(b_ref, device=DEV)
+    G = ogram.gram_taps(N, angles, cfg["zeta"])
+    apply = lambda v: ogram.gram_apply_fft(G, v)
+    _, hist, iters = ocg.steepest_descent(apply, b_ref, iters=20)
+    for k in (1, 2, 5, 20):
+        xk, rk = g.sd_solve(b, max_iter=k)
+        assert rk["iterations"] == k
+        assert rel(xk.cpu().numpy(), iters[k - 1]) < 1e-10
+        assert abs(rk["rel_residual"] - hist[k]) < 1e-9 * hist[k]
+    g.close()
+
+
+def test_steepest_descent_fp32_converges(bsct):
+    N, na = 128, 180
+    angles = np.arange(na) / na
+    sino = ellipse_sinogram(ellipse_params(N, 20, seed=2), angles, 184, 1.0, 1.0)
+    g = bsct.gram_build(bsct.Geometry(N, angles, 184, 1.0, 1.0), bsct.F32)
+    bd = obp.backproject(sino, N, angles, 1.0, 1.0).astype(np.float32).astype(np.float64)
+    b = torch.tensor(bd, dtype=torch.float32, device=DEV)
+    G = ogram.gram_taps(N, angles, 1.0)
+    apply = lambda v: ogram.gram_apply_fft(G, v)
+    _, hist, iters = ocg.steepest_descent(apply, bd, iters=5)
+    for k in (1, 5):
+        xk, _ = g.sd_solve(b, max_iter=k)
+        assert rel(xk.cpu().numpy(), iters[k - 1]) < 1e-5
+    x, rep = g.sd_solve(b, max_iter=3000, rel_tol=1e-3, check_every=10)
+    assert rep["converged"]
+    assert ocg.true_relative_residual(apply, bd, x.cpu().double().numpy()) < 1.2e-3
+    g.close()
