@@ -328,6 +328,20 @@ def run_ours(args):
         pcg_info = {"iters": n_cg, "ms_per_iter": pcg_ms / n_cg, "eps": bsct.PRECOND_EPS,
                     "timed": "one bsct_pcg_solve call from x = 0 (its start-up M^-1 apply included)"}
 
+    # ---------------------------------------------------------------- forward projection S H c
+    fwork = torch.empty(bsct.forward_project_workspace(geom, bsct.F32), dtype=torch.uint8, device=dev)
+    sino_f = torch.empty_like(sino)
+    bsct.forward_project(geom, x, bsct.F32, out=sino_f, work=fwork)
+    barrier()
+    e0.record(stream)
+    bsct.forward_project(geom, x, bsct.F32, out=sino_f, work=fwork)
+    e1.record(stream)
+    barrier()
+    fp_ms = max_over_ranks(e0.elapsed_time(e1))
+    forward_info = {"ms": fp_ms, "Gpairs_per_s": N * N * cfg["n_angles"] / (fp_ms * 1e-3) / 1e9,
+                    "pairs": "pixel-view pairs N^2 x views, as for the back projection",
+                    "launches": 3, "includes": "per-view tables, image transpose, gather"}
+
     # ---------------------------------------------------------------- end to end (host buffers)
     xh = torch.empty((N, N), dtype=torch.float32, pin_memory=True)
     xh.copy_(x.cpu())
@@ -375,18 +389,6 @@ def run_ours(args):
         t["backproject_fp32_frac"] = N * N * cfg["n_angles"] * 70.0 / (t["backproject_ms"] * 1e-3) / fp32
         t["backproject_flop_per_pair"] = "70, algorithmic: <= 7 bins x degree-5 Horner per pixel-view pair"
         extras["hot_path_pass"] = t
-        # forward projection S H c of the CG solution on the same geometry
-        fwork = torch.empty(bsct.forward_project_workspace(geom, bsct.F32), dtype=torch.uint8, device=dev)
-        sino_f = torch.empty_like(sino)
-        bsct.forward_project(geom, x2, bsct.F32, out=sino_f, work=fwork)
-        barrier()
-        e[0].record(stream)
-        bsct.forward_project(geom, x2, bsct.F32, out=sino_f, work=fwork)
-        e[1].record(stream)
-        barrier()
-        fp_ms = e[0].elapsed_time(e[1])
-        extras["forward_project"] = {"ms": fp_ms, "Gpairs_per_s": N * N * cfg["n_angles"] / (fp_ms * 1e-3) / 1e9,
-                                     "pairs": "pixel-view pairs N^2 x views, as for the back projection"}
         g2.close()
         # time to a 1e-4 relative residual on the learned-evaluation geometry: 20 held-out
         # seeds (phantoms generated on the device), medians and iteration counts
@@ -554,6 +556,7 @@ def run_ours(args):
                "frac_of_hbm": cg_bytes / (cg_ms / n_cg * 1e-3) / 1e9 / hbm,
                "l2": "not flushed between iterations (135 MB working set)"},
         "pcg": pcg_info,
+        "forward_project": forward_info,
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(launches),

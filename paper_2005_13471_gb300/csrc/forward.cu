@@ -33,12 +33,14 @@ namespace bsct {
 constexpr int FP_IMAX = 9;       // intervals of f per view (<= 8 kinks)
 constexpr int FP_RMAX = 8;       // integer offsets r per (sample, line): zeta <= 4
 constexpr int FP_FSTART = 16;    // interval starts, padded
-constexpr int FP_TAB = FP_FSTART + FP_IMAX * FP_RMAX * 4;  // T entries per view
-constexpr int FP_HDR = 8;        // doubles per view
+constexpr int FP_LUT = 64;       // cells of the interval lookup
+constexpr int FP_TAB = FP_FSTART + FP_IMAX * FP_RMAX * 4 + FP_LUT;  // T entries per view
+constexpr int FP_HDR = 9;        // doubles per view
 constexpr int FP_THREADS = 256;
 constexpr double FP_ZETA_MAX = 4.0;
 
-enum { FH_ALPHA0 = 0, FH_GAMMA = 1, FH_BETA = 2, FH_MODE = 3, FH_RLO = 4, FH_R = 5, FH_NI = 6, FH_OPEN = 7 };
+enum { FH_ALPHA0 = 0, FH_GAMMA = 1, FH_BETA = 2, FH_MODE = 3, FH_RLO = 4, FH_R = 5, FH_NI = 6, FH_OPEN = 7,
+       FH_LUT = 8 };
 
 // The footprint's factor M_[A, zeta] (zeta > 0: trapezoid; zeta = 0: box of width A) as
 // linear pieces a_p + b_p v between sorted kinks e[0..nk).
@@ -147,6 +149,24 @@ __global__ void k_fp_tables(const double* __restrict__ ang, int N, int M, double
     h[FH_R] = R;
     h[FH_NI] = ni;
     h[FH_OPEN] = (B == 0.0 && zeta == 0.0) ? 1.0 : 0.0;
+    // interval lookup on the starts as the gather kernel sees them (rounded to T):
+    // cell c of [0, 1) maps to the interval holding c / FP_LUT; the gather then steps
+    // over at most two more starts inside the cell, or searches them all when some
+    // cell holds more than two
+    T* lut = tab + (long)v * FP_TAB + FP_FSTART + FP_IMAX * FP_RMAX * 4;
+    bool ok = true;
+    for (int c = 0; c < FP_LUT; ++c) {
+      const double lo = (double)c / FP_LUT, hi = (double)(c + 1) / FP_LUT;
+      int I = 0, inside = 0;
+      for (int i = 1; i < ni; ++i) {
+        const double st = (double)T(s_f[i]);
+        I += st <= lo;
+        inside += (st > lo && st < hi);
+      }
+      lut[c] = T(I);
+      ok = ok && inside <= 2;
+    }
+    h[FH_LUT] = ok ? 1.0 : 0.0;
   }
   __syncthreads();
   T* tv = tab + (long)v * FP_TAB;
@@ -201,13 +221,15 @@ __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ 
   const int v = blockIdx.y;
   __shared__ T s_f[FP_FSTART];
   __shared__ V4 s_p[FP_IMAX * FP_RMAX];
+  __shared__ unsigned char s_lut[FP_LUT];
   const T* tv = tab + (long)v * FP_TAB;
   if (threadIdx.x < FP_FSTART) s_f[threadIdx.x] = tv[threadIdx.x];
   if (threadIdx.x < FP_IMAX * FP_RMAX) s_p[threadIdx.x] = reinterpret_cast<const V4*>(tv + FP_FSTART)[threadIdx.x];
+  if (threadIdx.x < FP_LUT) s_lut[threadIdx.x] = (unsigned char)tv[FP_FSTART + FP_IMAX * FP_RMAX * 4 + threadIdx.x];
   const double* h = hdr + (long)v * FP_HDR;
   const double alpha0 = h[FH_ALPHA0], gamma = h[FH_GAMMA], beta = h[FH_BETA];
   const int rlo = (int)h[FH_RLO], R = (int)h[FH_R];
-  const bool open_box = h[FH_OPEN] != 0.0;
+  const bool open_box = h[FH_OPEN] != 0.0, lut_ok = h[FH_LUT] != 0.0;
   const T* src = h[FH_MODE] == 0.0 ? img : imgT;
   __syncthreads();
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -230,6 +252,7 @@ __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ 
   if constexpr (sizeof(T) == 4) {
     const double ah = rint(alpha * grid) / grid, bh = rint(beta * grid) / grid;
     const float a_hi = (float)ah, a_lo = (float)(alpha - ah), b_hi = (float)bh, b_lo = (float)(beta - bh);
+#pragma unroll 2
     for (int k = k0; k <= k1; ++k) {
       const float kf = (float)k;
       const float kh = fmaf(-kf, b_hi, a_hi);  // exact: both terms on the 2^-g grid
@@ -240,16 +263,24 @@ __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ 
       K += Kf;
       f -= Kf;
       if (open_box && f == 0.5f) continue;  // a sample exactly on a pixel edge of the box
-      int I = 0;
+      int I;
+      if (lut_ok) {
+        I = s_lut[min((int)(f * (float)FP_LUT), FP_LUT - 1)];
+        I += (s_f[I + 1] <= f);
+        I += (s_f[I + 1] <= f);
+      } else {
+        I = 0;
 #pragma unroll
-      for (int i = 1; i < FP_IMAX; ++i) I += (s_f[i] <= f);
+        for (int i = 1; i < FP_IMAX; ++i) I += (s_f[i] <= f);
+      }
       const float t = f - s_f[I];
       const float* line = src + (long)k * N;
       const int kb = (int)K - rlo;
 #pragma unroll
       for (int rr = 0; rr < FP_RMAX; ++rr) {
+        if (rr >= R) break;
         const int j = kb - rr;
-        if (rr < R && (unsigned)j < (unsigned)N) {
+        if ((unsigned)j < (unsigned)N) {
           const float4 p = s_p[I * FP_RMAX + rr];
           acc = fmaf(__ldg(line + j), fmaf(fmaf(p.z, t, p.y), t, p.x), acc);
         }
@@ -261,16 +292,24 @@ __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ 
       double K = floor(kap);
       double f = kap - K;
       if (open_box && f == 0.5) continue;
-      int I = 0;
+      int I;
+      if (lut_ok) {
+        I = s_lut[min((int)(f * (double)FP_LUT), FP_LUT - 1)];
+        I += (s_f[I + 1] <= f);
+        I += (s_f[I + 1] <= f);
+      } else {
+        I = 0;
 #pragma unroll
-      for (int i = 1; i < FP_IMAX; ++i) I += (s_f[i] <= f);
+        for (int i = 1; i < FP_IMAX; ++i) I += (s_f[i] <= f);
+      }
       const double t = f - s_f[I];
       const double* line = src + (long)k * N;
       const int kb = (int)K - rlo;
 #pragma unroll
       for (int rr = 0; rr < FP_RMAX; ++rr) {
+        if (rr >= R) break;
         const int j = kb - rr;
-        if (rr < R && (unsigned)j < (unsigned)N) {
+        if ((unsigned)j < (unsigned)N) {
           const double4_32a p = s_p[I * FP_RMAX + rr];
           acc = fma(line[j], fma(fma(p.z, t, p.y), t, p.x), acc);
         }
