@@ -467,6 +467,19 @@ def run_ours(args):
         extras["time_to_1e-4"] = tt
         g5.close()
 
+    # ---------------------------------------------------------------- accuracy study (Sec. 6, box-spline curves)
+    if not args.quick:
+        from paper_2005_13471_gb300 import study
+
+        t_st = time.perf_counter()
+        rows = study.accuracy_sweep(bsct, N=256, n_views=180, zeta=1.0, lambdas=(0.25, 0.5, 1.0, 1.5, 2.0),
+                                    noise=(0.0, 0.01, 0.05), solver="sd", iters=100, n_ellipses=30, seed=rank)
+        extras["accuracy_study"] = {
+            "workload": "N=256, 180 views, zeta=1, 30-ellipse phantom, exact blurred sinogram, Gaussian noise "
+                        "sigma relative to the largest sample, 100 steepest-descent steps",
+            "rows": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()} for r in rows],
+            "wall_s": time.perf_counter() - t_st}
+
     # ---------------------------------------------------------------- split-BF16 DFT-GEMM apply (tensor cores)
     if not args.quick:
         yd = torch.empty_like(y)

@@ -35,12 +35,14 @@ constexpr int FP_RMAX = 8;       // integer offsets r per (sample, line): zeta <
 constexpr int FP_FSTART = 16;    // interval starts, padded
 constexpr int FP_LUT = 64;       // cells of the interval lookup
 constexpr int FP_TAB = FP_FSTART + FP_IMAX * FP_RMAX * 4 + FP_LUT;  // T entries per view
-constexpr int FP_HDR = 9;        // doubles per view
+constexpr int FP_HDR = 10;       // doubles per view
+constexpr int FP_PS = FP_RMAX + 1;  // shared-memory stride of a table row: rows of 36 floats
+                                    // put lanes in different intervals on different banks
 constexpr int FP_THREADS = 256;
 constexpr double FP_ZETA_MAX = 4.0;
 
 enum { FH_ALPHA0 = 0, FH_GAMMA = 1, FH_BETA = 2, FH_MODE = 3, FH_RLO = 4, FH_R = 5, FH_NI = 6, FH_OPEN = 7,
-       FH_LUT = 8 };
+       FH_LUT = 8, FH_IBETA = 9 };
 
 // The footprint's factor M_[A, zeta] (zeta > 0: trapezoid; zeta = 0: box of width A) as
 // linear pieces a_p + b_p v between sorted kinks e[0..nk).
@@ -115,6 +117,7 @@ __global__ void k_fp_tables(const double* __restrict__ ang, int N, int M, double
     h[FH_ALPHA0] = (y0 + half * minor) / major + half;
     h[FH_GAMMA] = lam / major;
     h[FH_BETA] = minor / major;
+    h[FH_IBETA] = minor != 0.0 ? major / minor : 0.0;
     h[FH_MODE] = rows ? 0.0 : 1.0;
     // kinks of h = M_[A, zeta] * box_B, in units of A, reduced to [0, 1)
     Lin L;
@@ -220,14 +223,15 @@ __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ 
   typedef typename Vec4<T>::t V4;
   const int v = blockIdx.y;
   __shared__ T s_f[FP_FSTART];
-  __shared__ V4 s_p[FP_IMAX * FP_RMAX];
+  __shared__ V4 s_p[FP_IMAX * FP_PS];
   __shared__ unsigned char s_lut[FP_LUT];
   const T* tv = tab + (long)v * FP_TAB;
   if (threadIdx.x < FP_FSTART) s_f[threadIdx.x] = tv[threadIdx.x];
-  if (threadIdx.x < FP_IMAX * FP_RMAX) s_p[threadIdx.x] = reinterpret_cast<const V4*>(tv + FP_FSTART)[threadIdx.x];
+  if (threadIdx.x < FP_IMAX * FP_RMAX)
+    s_p[(threadIdx.x / FP_RMAX) * FP_PS + threadIdx.x % FP_RMAX] = reinterpret_cast<const V4*>(tv + FP_FSTART)[threadIdx.x];
   if (threadIdx.x < FP_LUT) s_lut[threadIdx.x] = (unsigned char)tv[FP_FSTART + FP_IMAX * FP_RMAX * 4 + threadIdx.x];
   const double* h = hdr + (long)v * FP_HDR;
-  const double alpha0 = h[FH_ALPHA0], gamma = h[FH_GAMMA], beta = h[FH_BETA];
+  const double alpha0 = h[FH_ALPHA0], gamma = h[FH_GAMMA], beta = h[FH_BETA], ibeta = h[FH_IBETA];
   const int rlo = (int)h[FH_RLO], R = (int)h[FH_R];
   const bool open_box = h[FH_OPEN] != 0.0, lut_ok = h[FH_LUT] != 0.0;
   const T* src = h[FH_MODE] == 0.0 ? img : imgT;
@@ -237,20 +241,22 @@ __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ 
   const double alpha = alpha0 + (double)m * gamma;
   // lines whose kappa = alpha - k beta lies in [rlo, N + rlo + R): the others touch no pixel
   const double klo = (double)rlo, khi = (double)(N + rlo + R);
+  // (bounds widened by one line: 1 / beta is rounded)
   double lo = 0.0, hi = (double)(N - 1);
   if (beta > 0.0) {
-    lo = fmax(lo, floor((alpha - khi) / beta));
-    hi = fmin(hi, ceil((alpha - klo) / beta));
+    lo = fmax(lo, floor((alpha - khi) * ibeta) - 1.0);
+    hi = fmin(hi, ceil((alpha - klo) * ibeta) + 1.0);
   } else if (beta < 0.0) {
-    lo = fmax(lo, floor((alpha - klo) / beta));
-    hi = fmin(hi, ceil((alpha - khi) / beta));
+    lo = fmax(lo, floor((alpha - klo) * ibeta) - 1.0);
+    hi = fmin(hi, ceil((alpha - khi) * ibeta) + 1.0);
   } else if (!(alpha >= klo && alpha < khi)) {
     hi = -1.0;
   }
   const int k0 = (int)lo, k1 = hi < lo ? -1 : (int)hi;  // both clamped to [0, N - 1] first
   T acc = T(0);
   if constexpr (sizeof(T) == 4) {
-    const double ah = rint(alpha * grid) / grid, bh = rint(beta * grid) / grid;
+    const double ig = 1.0 / grid;  // a power of two: exact, and hoisted out of the threads
+    const double ah = rint(alpha * grid) * ig, bh = rint(beta * grid) * ig;
     const float a_hi = (float)ah, a_lo = (float)(alpha - ah), b_hi = (float)bh, b_lo = (float)(beta - bh);
 #pragma unroll 2
     for (int k = k0; k <= k1; ++k) {
@@ -274,15 +280,24 @@ __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ 
         for (int i = 1; i < FP_IMAX; ++i) I += (s_f[i] <= f);
       }
       const float t = f - s_f[I];
-      const float* line = src + (long)k * N;
       const int kb = (int)K - rlo;
+      const float* lp = src + (long)k * N + kb;  // pixel kb - rr of the line at lp[-rr]
+      const float4* pr = s_p + I * FP_PS;
+      if (kb >= R - 1 && kb < N) {  // all R pixels inside the line
 #pragma unroll
-      for (int rr = 0; rr < FP_RMAX; ++rr) {
-        if (rr >= R) break;
-        const int j = kb - rr;
-        if ((unsigned)j < (unsigned)N) {
-          const float4 p = s_p[I * FP_RMAX + rr];
-          acc = fmaf(__ldg(line + j), fmaf(fmaf(p.z, t, p.y), t, p.x), acc);
+        for (int rr = 0; rr < FP_RMAX; ++rr) {
+          if (rr >= R) break;
+          const float4 p = pr[rr];
+          acc = fmaf(__ldg(lp - rr), fmaf(fmaf(p.z, t, p.y), t, p.x), acc);
+        }
+      } else {
+#pragma unroll
+        for (int rr = 0; rr < FP_RMAX; ++rr) {
+          if (rr >= R) break;
+          if ((unsigned)(kb - rr) < (unsigned)N) {
+            const float4 p = pr[rr];
+            acc = fmaf(__ldg(lp - rr), fmaf(fmaf(p.z, t, p.y), t, p.x), acc);
+          }
         }
       }
     }
@@ -310,7 +325,7 @@ __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ 
         if (rr >= R) break;
         const int j = kb - rr;
         if ((unsigned)j < (unsigned)N) {
-          const double4_32a p = s_p[I * FP_RMAX + rr];
+          const double4_32a p = s_p[I * FP_PS + rr];
           acc = fma(line[j], fma(fma(p.z, t, p.y), t, p.x), acc);
         }
       }
