@@ -19,11 +19,10 @@
 // terms) leaves per pixel one table read, two FMAs of Horner, the pixel load and the
 // accumulate; the interval search is done once per line.
 //
-// FP32 coordinates: the line coordinate kappa = alpha - k beta (alpha per sample, beta
-// per view) reaches ~2N, where an FP32 rounding would move the footprint by ~1e-4
-// pixel.  alpha and beta are split into a part on a 2^-g grid, for which
-// alpha_hi - k beta_hi is exact in FP32, and a small remainder, so that f is accurate to
-// ~1e-7 whatever N.
+// FP32 path: the line coordinate kappa = alpha - k beta (alpha per sample, beta per
+// view) reaches ~2N, where an FP32 rounding would move the footprint by ~1e-4 pixel; it
+// is kept in 64-bit fixed point instead (40 fractional bits), which makes each line's
+// step an exact integer subtraction and leaves f accurate to 2^-23 whatever N.
 #include <cmath>
 
 #include "bsct_internal.h"
@@ -219,7 +218,7 @@ template <> struct Vec4<double> { typedef double4_32a t; };
 template <typename T>
 __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ img, const T* __restrict__ imgT,
                                                           const double* __restrict__ hdr, const T* __restrict__ tab,
-                                                          int N, int M, double grid, T* __restrict__ sino) {
+                                                          int N, int M, T* __restrict__ sino) {
   typedef typename Vec4<T>::t V4;
   const int v = blockIdx.y;
   __shared__ T s_f[FP_FSTART];
@@ -255,23 +254,23 @@ __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ 
   const int k0 = (int)lo, k1 = hi < lo ? -1 : (int)hi;  // both clamped to [0, N - 1] first
   T acc = T(0);
   if constexpr (sizeof(T) == 4) {
-    const double ig = 1.0 / grid;  // a power of two: exact, and hoisted out of the threads
-    const double ah = rint(alpha * grid) * ig, bh = rint(beta * grid) * ig;
-    const float a_hi = (float)ah, a_lo = (float)(alpha - ah), b_hi = (float)bh, b_lo = (float)(beta - bh);
+    // kappa in fixed point with 40 fractional bits (alpha and beta are doubles whose last
+    // bit is worth at most 2^-40 here, so the conversion is exact): the per-line step is
+    // one 64-bit subtraction, the pixel index is the integer part, and f (its top 23
+    // fraction bits) and the lookup cell come from the fraction bits with no conversion
+    const double two40 = 1099511627776.0;
+    const long long bfx = llrint(beta * two40);
+    long long kfx = llrint(alpha * two40) - (long long)k0 * bfx;
+    const long long half = 1LL << 39, fmask = (1LL << 40) - 1;
 #pragma unroll 2
-    for (int k = k0; k <= k1; ++k) {
-      const float kf = (float)k;
-      const float kh = fmaf(-kf, b_hi, a_hi);  // exact: both terms on the 2^-g grid
-      const float kl = fmaf(-kf, b_lo, a_lo);
-      float K = floorf(kh);
-      float f = (kh - K) + kl;
-      const float Kf = floorf(f);
-      K += Kf;
-      f -= Kf;
-      if (open_box && f == 0.5f) continue;  // a sample exactly on a pixel edge of the box
+    for (int k = k0; k <= k1; ++k, kfx -= bfx) {
+      if (open_box && (kfx & fmask) == half) continue;  // a sample exactly on a pixel edge of the box
+      const int K = (int)(kfx >> 40);
+      const unsigned fr = (unsigned)(kfx >> 8);  // fraction bits 2^-1 .. 2^-32
+      const float f = __int_as_float(0x3f800000u | (fr >> 9)) - 1.0f;
       int I;
       if (lut_ok) {
-        I = s_lut[min((int)(f * (float)FP_LUT), FP_LUT - 1)];
+        I = s_lut[fr >> 26];  // floor(64 f)
         I += (s_f[I + 1] <= f);
         I += (s_f[I + 1] <= f);
       } else {
@@ -280,7 +279,7 @@ __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ 
         for (int i = 1; i < FP_IMAX; ++i) I += (s_f[i] <= f);
       }
       const float t = f - s_f[I];
-      const int kb = (int)K - rlo;
+      const int kb = K - rlo;
       const float* lp = src + (long)k * N + kb;  // pixel kb - rr of the line at lp[-rr]
       const float4* pr = s_p + I * FP_PS;
       if (kb >= R - 1 && kb < N) {  // all R pixels inside the line
@@ -402,12 +401,8 @@ static int fp_run(const bsct_geom* geom, const T* c, T* sino, char* w, cudaStrea
   k_fp_tables<T><<<na, 128, 0, st>>>(ang, N, M, geom->lambda_y, geom->zeta_blur, hdr, tab);
   dim3 tb(32, 8), tg((N + 31) / 32, (N + 31) / 32);
   k_fp_transpose<T><<<tg, tb, 0, st>>>(c, N, ct);
-  // grid 2^g such that every line coordinate (|kappa| < N + 8) and k beta_hi (|.| <= N)
-  // are exact FP32 multiples of 2^-g: (2N + 8) 2^g < 2^24
-  const int g = 23 - (int)ceil(log2(2.0 * N + 8.0));
-  const double grid = ldexp(1.0, g);
   dim3 gg((M + FP_THREADS - 1) / FP_THREADS, na);
-  k_fp_gather<T><<<gg, FP_THREADS, 0, st>>>(c, ct, hdr, tab, N, M, grid, sino);
+  k_fp_gather<T><<<gg, FP_THREADS, 0, st>>>(c, ct, hdr, tab, N, M, sino);
   count_launch(3);
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;

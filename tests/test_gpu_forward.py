@@ -107,3 +107,17 @@ def test_forward_errors(bsct):
     geom = bsct.Geometry(16, np.array([0.1]), 20, 1.0, 1.0)
     with pytest.raises(ValueError):
         bsct.forward_project(geom, torch.zeros((16, 15), device=DEV), bsct.F32)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_forward_samples_on_box_edges(bsct, prec):
+    # axis views without blur, N even and M odd, lambda_y = 1: every sample falls exactly
+    # on a pixel edge, where the open box footprint is zero (the oracle agrees)
+    N, M = 12, 13
+    angles = np.array([0.0, 0.5, 1.0])
+    c = np.random.default_rng(1).standard_normal((N, N))
+    assert np.all(obp.forward_sample(c, angles, M, 1.0, 0.0) == 0.0)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    g = bsct.forward_project(bsct.Geometry(N, angles, M, 1.0, 0.0), torch.tensor(c, dtype=dt, device=DEV),
+                             bsct.F64 if prec == "f64" else bsct.F32)
+    assert float(g.abs().max()) == 0.0
