@@ -32,8 +32,8 @@ namespace bsct {
 constexpr int FP_IMAX = 9;       // intervals of f per view (<= 8 kinks)
 constexpr int FP_RMAX = 8;       // integer offsets r per (sample, line): zeta <= 4
 constexpr int FP_FSTART = 16;    // interval starts, padded
-constexpr int FP_LUT = 64;       // cells of the interval lookup
-constexpr int FP_TAB = FP_FSTART + FP_IMAX * FP_RMAX * 4 + FP_LUT;  // T entries per view
+constexpr int FP_LUT = 64;       // cells of the interval lookup, 4 T entries each
+constexpr int FP_TAB = FP_FSTART + FP_IMAX * FP_RMAX * 4 + FP_LUT * 4;  // T entries per view
 constexpr int FP_HDR = 10;       // doubles per view
 constexpr int FP_PS = FP_RMAX + 1;  // shared-memory stride of a table row: rows of 36 floats
                                     // put lanes in different intervals on different banks
@@ -152,10 +152,13 @@ __global__ void k_fp_tables(const double* __restrict__ ang, int N, int M, double
     h[FH_NI] = ni;
     h[FH_OPEN] = (B == 0.0 && zeta == 0.0) ? 1.0 : 0.0;
     // interval lookup on the starts as the gather kernel sees them (rounded to T):
-    // cell c of [0, 1) maps to the interval holding c / FP_LUT; the gather then steps
-    // over at most two more starts inside the cell, or searches them all when some
-    // cell holds more than two
+    // cell c of [0, 1) holds (I, s_I, s_I+1, s_I+2) for the interval I holding c / FP_LUT
+    // and the next two starts (2 past the last), so one load and two comparisons find
+    // the interval of any f in the cell - unless some cell holds more than two starts,
+    // when the gather searches them all.  For FP32, I is stored as the bit pattern of
+    // the integer I * FP_PS (the interval's row in the shared table)
     T* lut = tab + (long)v * FP_TAB + FP_FSTART + FP_IMAX * FP_RMAX * 4;
+    auto start = [&](int i) { return i < ni ? T(s_f[i]) : T(2); };
     bool ok = true;
     for (int c = 0; c < FP_LUT; ++c) {
       const double lo = (double)c / FP_LUT, hi = (double)(c + 1) / FP_LUT;
@@ -165,7 +168,11 @@ __global__ void k_fp_tables(const double* __restrict__ ang, int N, int M, double
         I += st <= lo;
         inside += (st > lo && st < hi);
       }
-      lut[c] = T(I);
+      if constexpr (sizeof(T) == 4) lut[4 * c] = __int_as_float(I * FP_PS);
+      else lut[4 * c] = T(I);
+      lut[4 * c + 1] = start(I);
+      lut[4 * c + 2] = start(I + 1);
+      lut[4 * c + 3] = start(I + 2);
       ok = ok && inside <= 2;
     }
     h[FH_LUT] = ok ? 1.0 : 0.0;
@@ -223,12 +230,12 @@ __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ 
   const int v = blockIdx.y;
   __shared__ T s_f[FP_FSTART];
   __shared__ V4 s_p[FP_IMAX * FP_PS];
-  __shared__ unsigned char s_lut[FP_LUT];
+  __shared__ V4 s_lut[FP_LUT];
   const T* tv = tab + (long)v * FP_TAB;
   if (threadIdx.x < FP_FSTART) s_f[threadIdx.x] = tv[threadIdx.x];
   if (threadIdx.x < FP_IMAX * FP_RMAX)
     s_p[(threadIdx.x / FP_RMAX) * FP_PS + threadIdx.x % FP_RMAX] = reinterpret_cast<const V4*>(tv + FP_FSTART)[threadIdx.x];
-  if (threadIdx.x < FP_LUT) s_lut[threadIdx.x] = (unsigned char)tv[FP_FSTART + FP_IMAX * FP_RMAX * 4 + threadIdx.x];
+  if (threadIdx.x < FP_LUT) s_lut[threadIdx.x] = reinterpret_cast<const V4*>(tv + FP_FSTART + FP_IMAX * FP_RMAX * 4)[threadIdx.x];
   const double* h = hdr + (long)v * FP_HDR;
   const double alpha0 = h[FH_ALPHA0], gamma = h[FH_GAMMA], beta = h[FH_BETA], ibeta = h[FH_IBETA];
   const int rlo = (int)h[FH_RLO], R = (int)h[FH_R];
@@ -268,20 +275,23 @@ __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ 
       const int K = (int)(kfx >> 40);
       const unsigned fr = (unsigned)(kfx >> 8);  // fraction bits 2^-1 .. 2^-32
       const float f = __int_as_float(0x3f800000u | (fr >> 9)) - 1.0f;
-      int I;
+      int Ir;    // the interval's row offset in s_p
+      float t;   // f - (start of the interval)
       if (lut_ok) {
-        I = s_lut[fr >> 26];  // floor(64 f)
-        I += (s_f[I + 1] <= f);
-        I += (s_f[I + 1] <= f);
+        const float4 L = s_lut[fr >> 26];  // cell floor(64 f)
+        const bool g1 = L.z <= f, g2 = L.w <= f;
+        Ir = __float_as_int(L.x) + (g1 ? FP_PS : 0) + (g2 ? FP_PS : 0);
+        t = f - (g2 ? L.w : (g1 ? L.z : L.y));
       } else {
-        I = 0;
+        int I = 0;
 #pragma unroll
         for (int i = 1; i < FP_IMAX; ++i) I += (s_f[i] <= f);
+        Ir = I * FP_PS;
+        t = f - s_f[I];
       }
-      const float t = f - s_f[I];
       const int kb = K - rlo;
-      const float* lp = src + (long)k * N + kb;  // pixel kb - rr of the line at lp[-rr]
-      const float4* pr = s_p + I * FP_PS;
+      const float* lp = src + (k * N + kb);  // pixel kb - rr of the line at lp[-rr] (N^2 < 2^31)
+      const float4* pr = s_p + Ir;
       if (kb >= R - 1 && kb < N) {  // all R pixels inside the line
 #pragma unroll
         for (int rr = 0; rr < FP_RMAX; ++rr) {
@@ -308,9 +318,8 @@ __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ 
       if (open_box && f == 0.5) continue;
       int I;
       if (lut_ok) {
-        I = s_lut[min((int)(f * (double)FP_LUT), FP_LUT - 1)];
-        I += (s_f[I + 1] <= f);
-        I += (s_f[I + 1] <= f);
+        const double4_32a L = s_lut[min((int)(f * (double)FP_LUT), FP_LUT - 1)];
+        I = (int)L.x + (L.z <= f) + (L.w <= f);
       } else {
         I = 0;
 #pragma unroll
