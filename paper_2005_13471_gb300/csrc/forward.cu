@@ -34,14 +34,14 @@ constexpr int FP_RMAX = 8;       // integer offsets r per (sample, line): zeta <
 constexpr int FP_FSTART = 16;    // interval starts, padded
 constexpr int FP_LUT = 64;       // cells of the interval lookup, 4 T entries each
 constexpr int FP_TAB = FP_FSTART + FP_IMAX * FP_RMAX * 4 + FP_LUT * 4;  // T entries per view
-constexpr int FP_HDR = 10;       // doubles per view
+constexpr int FP_HDR = 12;       // doubles per view
 constexpr int FP_PS = FP_RMAX + 1;  // shared-memory stride of a table row: rows of 36 floats
                                     // put lanes in different intervals on different banks
 constexpr int FP_THREADS = 256;
 constexpr double FP_ZETA_MAX = 4.0;
 
 enum { FH_ALPHA0 = 0, FH_GAMMA = 1, FH_BETA = 2, FH_MODE = 3, FH_RLO = 4, FH_R = 5, FH_NI = 6, FH_OPEN = 7,
-       FH_LUT = 8, FH_IBETA = 9 };
+       FH_LUT = 8, FH_IBETA = 9, FH_PHILO = 10, FH_PHIHI = 11 };
 
 // The footprint's factor M_[A, zeta] (zeta > 0: trapezoid; zeta = 0: box of width A) as
 // linear pieces a_p + b_p v between sorted kinks e[0..nk).
@@ -148,6 +148,10 @@ __global__ void k_fp_tables(const double* __restrict__ ang, int N, int M, double
     s_A = A;
     s_B = B;
     h[FH_RLO] = rlo;
+    // the first offset (r = rlo) is inside the support only for f > -D - rlo, the last
+    // (r = rhi) only for f < D - rhi; the ones between always are
+    h[FH_PHILO] = -D - rlo;
+    h[FH_PHIHI] = D - rhi;
     h[FH_R] = R;
     h[FH_NI] = ni;
     h[FH_OPEN] = (B == 0.0 && zeta == 0.0) ? 1.0 : 0.0;
@@ -240,6 +244,7 @@ __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ 
   const double alpha0 = h[FH_ALPHA0], gamma = h[FH_GAMMA], beta = h[FH_BETA], ibeta = h[FH_IBETA];
   const int rlo = (int)h[FH_RLO], R = (int)h[FH_R];
   const bool open_box = h[FH_OPEN] != 0.0, lut_ok = h[FH_LUT] != 0.0;
+  const T phi_lo = (T)h[FH_PHILO], phi_hi = (T)h[FH_PHIHI];
   const T* src = h[FH_MODE] == 0.0 ? img : imgT;
   __syncthreads();
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -292,18 +297,28 @@ __global__ void __launch_bounds__(FP_THREADS) k_fp_gather(const T* __restrict__ 
       const int kb = K - rlo;
       const float* lp = src + (k * N + kb);  // pixel kb - rr of the line at lp[-rr] (N^2 < 2^31)
       const float4* pr = s_p + Ir;
+      // offsets outside the footprint's support are skipped (their table rows are zero)
+      const bool first = f > phi_lo, last = f < phi_hi;
       if (kb >= R - 1 && kb < N) {  // all R pixels inside the line
+        if (first) {
+          const float4 p = pr[0];
+          acc = fmaf(__ldg(lp), fmaf(fmaf(p.z, t, p.y), t, p.x), acc);
+        }
 #pragma unroll
-        for (int rr = 0; rr < FP_RMAX; ++rr) {
-          if (rr >= R) break;
+        for (int rr = 1; rr < FP_RMAX - 1; ++rr) {
+          if (rr >= R - 1) break;
           const float4 p = pr[rr];
           acc = fmaf(__ldg(lp - rr), fmaf(fmaf(p.z, t, p.y), t, p.x), acc);
+        }
+        if (last) {
+          const float4 p = pr[R - 1];
+          acc = fmaf(__ldg(lp - (R - 1)), fmaf(fmaf(p.z, t, p.y), t, p.x), acc);
         }
       } else {
 #pragma unroll
         for (int rr = 0; rr < FP_RMAX; ++rr) {
           if (rr >= R) break;
-          if ((unsigned)(kb - rr) < (unsigned)N) {
+          if ((unsigned)(kb - rr) < (unsigned)N && (rr > 0 || first) && (rr < R - 1 || last)) {
             const float4 p = pr[rr];
             acc = fmaf(__ldg(lp - rr), fmaf(fmaf(p.z, t, p.y), t, p.x), acc);
           }
