@@ -448,11 +448,17 @@ def run_ours(args):
                                                       check_every=5)) for b in b5s]
             fcg = [timed(lambda: g5.fcg_solve_learned(net, b, 1.0 / na5, max_iter=2000, rel_tol=1e-4,
                                                       precond_every=4)) for b in b5s[:5]]
+            wpcg = [timed(lambda: g5.pcg_solve_learned(net, b, 1.0 / na5, max_iter=2000, rel_tol=1e-4))
+                    for b in b5s]
             tt.update({
                 "learned_ms_median": float(np.median([t for t, _ in warm])),
                 "learned_iters": [r["iterations"] for _, (_, r) in warm],
                 "learned_true_rel_residual_max": max(r["true_rel_residual"] for _, (_, r) in warm),
                 "warm_start_alpha": [r["alpha"] for _, (_, r) in warm][:5],
+                "learned_pcg": {"ms_median": float(np.median([t for t, _ in wpcg])),
+                                "iters": [r["iterations"] for _, (_, r) in wpcg],
+                                "true_rel_residual_max": max(r["true_rel_residual"] for _, (_, r) in wpcg),
+                                "note": "warm start, then circulant-preconditioned CG (against pcg_circulant)"},
                 "fcg_precond_every_4": {
                     "seeds": 5, "ms_median": float(np.median([t for t, _ in fcg])),
                     "iters": [r["iterations"] for _, (_, r) in fcg],

@@ -293,6 +293,12 @@ int bsct_mse_loss_grad(const float* d_pred, const float* d_target, int64_t n, fl
  * NULL) receives alpha.  F32 handle; N a multiple of 64.  Synchronous. */
 int bsct_cg_solve_learned(bsct_gram* g, bsct_unet* net, const void* d_b, void* d_x, float in_scale, int max_iter,
                           double rel_tol, int check_every, bsct_cg_report* report, double* alpha_out, void* stream);
+/* The same learned warm start followed by preconditioned CG with the circulant
+ * preconditioner of bsct_pcg_solve (floor eps); measures whether the warm start still
+ * helps once the preconditioner has removed the slow directions.  Synchronous. */
+int bsct_pcg_solve_learned(bsct_gram* g, bsct_unet* net, double eps, const void* d_b, void* d_x, float in_scale,
+                           int max_iter, double rel_tol, int check_every, bsct_cg_report* report,
+                           double* alpha_out, void* stream);
 
 /* Flexible CG with the network as preconditioner (a learned extension; the paper solves
  * with steepest descent, Sec. 6).  Truncated flexible CG, FCG(1), on G x = b from x0 = 0:

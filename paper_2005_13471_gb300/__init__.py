@@ -83,6 +83,8 @@ def _declare(L):
     L.bsct_cg_iterate.argtypes = [vp, vp, ctypes.c_int, vp]
     L.bsct_cg_residual.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp]
     L.bsct_precond_apply.argtypes = [vp, dbl, vp, vp, vp]
+    L.bsct_pcg_solve_learned.argtypes = [vp, vp, dbl, vp, vp, ctypes.c_float, ctypes.c_int, dbl, ctypes.c_int,
+                                         ctypes.POINTER(_CGReport), ctypes.POINTER(dbl), vp]
     L.bsct_forward_project_workspace.argtypes = [gp, ctypes.c_int, ctypes.POINTER(sz)]
     L.bsct_forward_project.argtypes = [gp, vp, vp, ctypes.c_int, vp, sz, vp]
     L.bsct_pcg_solve.argtypes = [vp, dbl, vp, vp, ctypes.c_int, ctypes.c_int, dbl, ctypes.c_int,
@@ -336,6 +338,21 @@ class GramFilter:
                                                 _dev(x, (n, n), self.dtype, "x"), float(in_scale), int(max_iter),
                                                 float(rel_tol), int(check_every), ctypes.byref(rep),
                                                 ctypes.byref(alpha), _stream()), "bsct_cg_solve_learned")
+        return x, dict(iterations=rep.iterations, converged=bool(rep.converged), rel_residual=rep.rel_residual,
+                       true_rel_residual=rep.true_rel_residual, alpha=alpha.value, status=rc)
+
+    def pcg_solve_learned(self, net, b, in_scale, max_iter=1000, rel_tol=1e-4, check_every=2, eps=PRECOND_EPS):
+        """Circulant-preconditioned CG from the learned warm start alpha * net(in_scale * b)."""
+        import torch
+
+        n = self.N
+        x = torch.empty((n, n), dtype=self.dtype, device=b.device)
+        rep = _CGReport()
+        alpha = ctypes.c_double()
+        rc = _check(lib().bsct_pcg_solve_learned(self._h, net._h, float(eps), _dev(b, (n, n), self.dtype, "b"),
+                                                 _dev(x, (n, n), self.dtype, "x"), float(in_scale), int(max_iter),
+                                                 float(rel_tol), int(check_every), ctypes.byref(rep),
+                                                 ctypes.byref(alpha), _stream()), "bsct_pcg_solve_learned")
         return x, dict(iterations=rep.iterations, converged=bool(rep.converged), rel_residual=rep.rel_residual,
                        true_rel_residual=rep.true_rel_residual, alpha=alpha.value, status=rc)
 

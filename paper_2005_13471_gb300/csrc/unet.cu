@@ -639,9 +639,9 @@ __global__ void k_dot2(const float* __restrict__ a, const float* __restrict__ b,
 }
 }  // namespace
 
-extern "C" int bsct_cg_solve_learned(bsct_gram* g, bsct_unet* net, const void* d_b, void* d_x, float in_scale,
-                                     int max_iter, double rel_tol, int check_every, bsct_cg_report* report,
-                                     double* alpha_out, void* stream) {
+// x0 = alpha net(in_scale b) into d_x; *x0_zero = 1 when alpha is unusable (x0 = 0 then)
+static int learned_warm_start(bsct_gram* g, bsct_unet* net, const void* d_b, void* d_x, float in_scale,
+                              double* alpha_out, int* x0_zero, void* stream) {
   if (!g || !net || !d_b || !d_x) { bsct_set_last_message("invalid argument"); return BSCT_ERR_INVALID_ARG; }
   if (g->precision != BSCT_F32) { bsct_set_last_message("learned warm start needs an F32 handle"); return BSCT_ERR_INVALID_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
@@ -664,13 +664,29 @@ extern "C" int bsct_cg_solve_learned(bsct_gram* g, bsct_unet* net, const void* d
   // x0 = alpha xhat minimises the G-norm error along xhat; plain CG (x0 = 0) if it is unusable
   const double alpha = (h[1] > 0.0 && isfinite(h[0]) && isfinite(h[1])) ? h[0] / h[1] : 0.0;
   if (alpha_out) *alpha_out = alpha;
-  int x0_zero = 1;
+  *x0_zero = 1;
   if (alpha > 0.0 && isfinite(alpha)) {
     k_scale_copy<<<nblk(n), TPB, 0, st>>>(xhat, (float)alpha, xhat, n);
     count_launch();
-    x0_zero = 0;
+    *x0_zero = 0;
   }
+  return BSCT_OK;
+}
+
+extern "C" int bsct_cg_solve_learned(bsct_gram* g, bsct_unet* net, const void* d_b, void* d_x, float in_scale,
+                                     int max_iter, double rel_tol, int check_every, bsct_cg_report* report,
+                                     double* alpha_out, void* stream) {
+  int x0_zero = 1;
+  UTRY(learned_warm_start(g, net, d_b, d_x, in_scale, alpha_out, &x0_zero, stream));
   return bsct_cg_solve(g, d_b, d_x, x0_zero, max_iter, rel_tol, check_every, report, stream);
+}
+
+extern "C" int bsct_pcg_solve_learned(bsct_gram* g, bsct_unet* net, double eps, const void* d_b, void* d_x,
+                                      float in_scale, int max_iter, double rel_tol, int check_every,
+                                      bsct_cg_report* report, double* alpha_out, void* stream) {
+  int x0_zero = 1;
+  UTRY(learned_warm_start(g, net, d_b, d_x, in_scale, alpha_out, &x0_zero, stream));
+  return bsct_pcg_solve(g, eps, d_b, d_x, x0_zero, max_iter, rel_tol, check_every, report, stream);
 }
 
 namespace {

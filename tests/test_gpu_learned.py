@@ -131,6 +131,15 @@ def test_learned_warm_start_gain(bsct):
     _, rf = g.fcg_solve_learned(bad, b, 1.0 / na, max_iter=2000, rel_tol=1e-4, precond_every=1)
     assert rf["converged"] and rf["n_fallback"] == rf["n_precond"] == rf["iterations"]
     assert abs(rf["iterations"] - rp1["iterations"]) <= 2
+    # warm start followed by circulant-preconditioned CG: reaches the tolerance; with the
+    # useless network it is PCG from x0 = 0 exactly
+    b = (Xe[2] * na).contiguous()
+    _, rz = g.pcg_solve(b, max_iter=500, rel_tol=1e-4, check_every=1)
+    _, rw = g.pcg_solve_learned(net, b, 1.0 / na, max_iter=500, rel_tol=1e-4, check_every=1)
+    assert rw["converged"] and rw["true_rel_residual"] <= 1.2e-4
+    print("PCG iterations from 0 / from the warm start:", rz["iterations"], rw["iterations"])
+    _, rb = g.pcg_solve_learned(bad, b, 1.0 / na, max_iter=500, rel_tol=1e-4, check_every=1)
+    assert rb["alpha"] == 0.0 and rb["iterations"] == rz["iterations"]
     g.close()
     net.close()
     bad.close()
