@@ -79,6 +79,32 @@ typedef struct bsct_cg_report {
 /* Supported image sizes N (the FFT lengths are N and 2N). */
 int bsct_supported_size(int32_t N);
 
+/* Launch shape of the three FFT passes of the Gram apply for one size N and precision:
+ * image rows per CTA of the forward row pass and of the inverse row pass, and whether
+ * the persistent column pass runs one CTA per SM (1) or as many as fit (0).  Every
+ * shape computes bit-identical results; only the speed differs.  The shape is kept per
+ * device (the current one), size and precision, and applies to every apply of that
+ * size: gram_apply, cg_solve, pcg_solve, the batch and the no-allocation apply. */
+typedef struct bsct_fft_shape {
+  int32_t rows_fwd;
+  int32_t rows_inv;
+  int32_t cols_one_per_sm;
+  int32_t reserved;
+} bsct_fft_shape;
+/* The three candidate row counts of each row pass (half, the built-in default, double;
+ * 0 where a candidate does not fit a CTA for this size).  Host arrays of 3. */
+int bsct_fft_shape_candidates(int32_t N, int precision, int32_t* rows_fwd, int32_t* rows_inv);
+int bsct_fft_get_shape(int32_t N, int precision, bsct_fft_shape* out);
+/* Errors: INVALID_ARG when a row count is not one of the valid candidates. */
+int bsct_fft_set_shape(int32_t N, int precision, const bsct_fft_shape* shape);
+/* Autotuner: times `reps` applies of every valid shape (up to 18) on scratch data of
+ * size N (allocated and freed inside; synchronous on the stream), keeps the fastest as
+ * the current shape and returns it in *best (may be NULL), its time per apply in µs in
+ * *best_us (may be NULL) and every candidate's time in all_us[18] (may be NULL; -1 for
+ * invalid shapes; index = 6 fwd + 2 inv + cols over candidate indices). */
+int bsct_fft_autotune(int32_t N, int precision, int reps, bsct_fft_shape* best, double* best_us,
+                      double* all_us, void* stream);
+
 /* Build the Gram filter of a geometry (Sec. 4): for every offset d,
  *   G[d] = sum_theta M_[c, c, s, s, zeta, zeta](d . u_theta)
  * (the unit-mass box spline of the Gram entry; zeta terms only when zeta > 0), then

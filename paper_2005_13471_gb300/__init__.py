@@ -62,6 +62,11 @@ class _CGReport(ctypes.Structure):
     ]
 
 
+class FftShape(ctypes.Structure):
+    _fields_ = [("rows_fwd", ctypes.c_int32), ("rows_inv", ctypes.c_int32), ("cols_one_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 def _declare(L):
     vp, i32, dbl, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_size_t
     gp = ctypes.POINTER(_Geom)
@@ -83,6 +88,11 @@ def _declare(L):
     L.bsct_cg_iterate.argtypes = [vp, vp, ctypes.c_int, vp]
     L.bsct_cg_residual.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp]
     L.bsct_precond_apply.argtypes = [vp, dbl, vp, vp, vp]
+    L.bsct_fft_shape_candidates.argtypes = [i32, ctypes.c_int, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.bsct_fft_get_shape.argtypes = [i32, ctypes.c_int, ctypes.POINTER(FftShape)]
+    L.bsct_fft_set_shape.argtypes = [i32, ctypes.c_int, ctypes.POINTER(FftShape)]
+    L.bsct_fft_autotune.argtypes = [i32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(FftShape), ctypes.POINTER(dbl),
+                                    ctypes.POINTER(dbl), vp]
     L.bsct_pcg_solve_learned.argtypes = [vp, vp, dbl, vp, vp, ctypes.c_float, ctypes.c_int, dbl, ctypes.c_int,
                                          ctypes.POINTER(_CGReport), ctypes.POINTER(dbl), vp]
     L.bsct_forward_project_workspace.argtypes = [gp, ctypes.c_int, ctypes.POINTER(sz)]
@@ -427,6 +437,33 @@ class GramFilter:
         rr, bb = ctypes.c_double(), ctypes.c_double()
         _check(lib().bsct_cg_residual(self._h, ctypes.byref(rr), ctypes.byref(bb), _stream()), "bsct_cg_residual")
         return rr.value, bb.value
+
+
+def fft_shape_candidates(N, precision=F32):
+    """(forward, inverse) row-count candidates of the FFT row passes for size N (0 = not valid)."""
+    f, v = (ctypes.c_int32 * 3)(), (ctypes.c_int32 * 3)()
+    _check(lib().bsct_fft_shape_candidates(int(N), int(precision), f, v), "bsct_fft_shape_candidates")
+    return list(f), list(v)
+
+
+def fft_shape(N, precision=F32):
+    """Current launch shape of the FFT apply for size N: (rows_fwd, rows_inv, cols_one_per_sm)."""
+    sh = FftShape()
+    _check(lib().bsct_fft_get_shape(int(N), int(precision), ctypes.byref(sh)), "bsct_fft_get_shape")
+    return sh.rows_fwd, sh.rows_inv, sh.cols_one_per_sm
+
+
+def set_fft_shape(N, rows_fwd, rows_inv, cols_one_per_sm=0, precision=F32):
+    sh = FftShape(int(rows_fwd), int(rows_inv), int(cols_one_per_sm), 0)
+    _check(lib().bsct_fft_set_shape(int(N), int(precision), ctypes.byref(sh)), "bsct_fft_set_shape")
+
+
+def fft_autotune(N, precision=F32, reps=20):
+    """Time every valid launch shape for size N, keep the fastest; returns (shape, us, all_us)."""
+    sh, best, allus = FftShape(), ctypes.c_double(), (ctypes.c_double * 18)()
+    _check(lib().bsct_fft_autotune(int(N), int(precision), int(reps), ctypes.byref(sh), ctypes.byref(best), allus,
+                                   _stream()), "bsct_fft_autotune")
+    return (sh.rows_fwd, sh.rows_inv, sh.cols_one_per_sm), best.value, list(allus)
 
 
 def gram_build(geom, precision=F32):

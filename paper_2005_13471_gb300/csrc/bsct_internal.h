@@ -126,6 +126,13 @@ template <typename T> struct FftOps {
   // sc[SC_BETA] = rho / sc[SC_RR] (0 when sc[SC_RR] <= 0) and sc[SC_RR] = rho
   int (*apply_pc)(const T* r, T* z, double* sc, double* part, cpx<T>* S, const T* Mt, const cpx<T>* tw,
                   cudaStream_t st);
+  // launch shapes of the three passes (rows per CTA of the forward and inverse row pass,
+  // CTAs per SM of the column pass): the row counts of the three candidates of each row
+  // pass (0 where not valid for this size), and the current choice as candidate indices
+  // (idx[2]: 0 = occupancy limit, 1 = one CTA per SM), read (set = 0) or set after
+  // validation (set = 1), per device and precision
+  void (*shape_cands)(int fwd[3], int inv[3]);
+  int (*shape_index)(int idx[3], int set);
   // emb: 2N x 2N real circulant kernel; S2: 2N x N complex scratch; writes Gt (scaled)
   int (*spectrum)(const T* emb, cpx<T>* S2, T* Gt, const cpx<T>* tw, cudaStream_t st);
 };

@@ -505,83 +505,123 @@ static int sm_count() {
   return n[d];
 }
 
-template <typename T, int N>
-static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw, cudaStream_t st) {
+// ------------------------------------------------------------------------------------
+// Launch shapes.  The forward row pass takes RPC image rows per CTA, the inverse row
+// pass RPI, the persistent column pass up to its occupancy limit of CTAs per SM (or
+// one).  Each row count has three candidates around the measured default (half, the
+// default, double; those that do not fit a CTA are invalid); bsct_fft_autotune times
+// them.  The choice is kept per device and precision; every shape computes the same
+// numbers (the rows are transformed identically, only their grouping changes).
+// ------------------------------------------------------------------------------------
+template <int D> __host__ __device__ constexpr int shape_cand(int i) { return i == 0 ? D / 2 : (i == 1 ? D : 2 * D); }
+template <typename T, int LR, int RP> __host__ __device__ constexpr bool rows_ok() {
+  return RP >= 2 && (RP == 2 || RP % 4 == 0) && LR % RP == 0 && RP * (LR / Plan<LR>::E) <= 1024 &&
+         (size_t)RP * row_region<T, LR, RP>() * sizeof(cpx<T>) <= 227 * 1024;
+}
+struct Shape {
+  int fwd = 1, inv = 1, cols = 0;  // candidate indices; cols: 0 = occupancy limit, 1 = one CTA per SM
+};
+static Shape g_shape[MAX_DEVICES][2];
+template <typename T> static Shape& cur_shape() { return g_shape[device_slot()][sizeof(T) == 4 ? 0 : 1]; }
+
+enum { AP_PLAIN = 0, AP_CG = 1, AP_PC = 2 };
+
+// One apply y = G x (or M^-1 x) in three passes.
+//   AP_PLAIN: out = G in.
+//   AP_CG:    K5 forms p = in + beta p (beta = sc[SC_BETA]), writes it back and transforms
+//             it; K7 writes out = G p and reduces <p, out> into alpha (RED_ALPHA).
+//   AP_PC:    out = M^-1 in with spectrum Gt = the preconditioner's; K7 reduces <in, out>
+//             into beta and rho (RED_RHO).
+template <typename T, int N, int MODE, int RPC, int RPI>
+static int run_apply(const T* in, T* p, T* out, double* sc, double* part, cpx<T>* S, const T* Gt,
+                     const cpx<T>* tw, int cols, cudaStream_t st) {
   constexpr int LR = N, LC = 2 * N;
-  constexpr int RPC = rows_per_cta<LR>(), RPI = rows_per_cta_inv<LR>();
   typedef ColsCfg<T, LC> CC;
-  static_assert(N % RPC == 0 && N % RPI == 0 && N % CC::G == 0, "tile must divide N");
+  static_assert(N % CC::G == 0, "tile must divide N");
   constexpr int TR = RPC * (LR / Plan<LR>::E), TI = RPI * (LR / Plan<LR>::E), TC = cols_threads<T, LC, CC::G>();
   constexpr size_t smr = (size_t)RPC * row_region<T, LR, RPC>() * sizeof(cpx<T>);
   constexpr size_t smi = (size_t)RPI * row_region<T, LR, RPI>() * sizeof(cpx<T>);
   constexpr size_t smc = cols_smem<T, LC, CC::G>();
+  constexpr int RED = MODE == AP_CG ? RED_ALPHA : (MODE == AP_PC ? RED_RHO : RED_NONE);
+  auto k5 = k_rows_r2c<T, LR, true, RPC, MODE == AP_CG>;
+  auto k7 = k_rows_c2r<T, LR, RPI, RED>;
   auto kc = k_cols_conv<T, LC, CC::G, CC::MINB>;
-  static int grid_cs[MAX_DEVICES] = {};
-  int& grid_c = grid_cs[device_slot()];
-  if (grid_c == 0) {
-    int rc = set_smem(k_rows_r2c<T, LR, true, RPC>, smr);
-    if (rc == BSCT_OK) rc = set_smem(k_rows_c2r<T, LR, RPI>, smi);
+  static int per_sm_max[MAX_DEVICES] = {};  // 0 until this instance's launch setup is done
+  const int d = device_slot();
+  if (per_sm_max[d] == 0) {
+    int rc = set_smem(k5, smr);
+    if (rc == BSCT_OK) rc = set_smem(k7, smi);
     if (rc == BSCT_OK) rc = set_smem(kc, smc);
     if (rc != BSCT_OK) return rc;
     int per_sm = 0;
     BSCT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc, TC, smc));
-    if (per_sm < 1) per_sm = 1;
-    const int tiles = N / CC::G;
-    grid_c = per_sm * sm_count() < tiles ? per_sm * sm_count() : tiles;
+    per_sm_max[d] = per_sm < 1 ? 1 : per_sm;
   }
+  const int per_sm = cols == 1 ? 1 : per_sm_max[d];
+  const int tiles = N / CC::G;
+  const int grid_c = per_sm * sm_count() < tiles ? per_sm * sm_count() : tiles;
   const TwPtrs<T> t = tw_ptrs<T, N>(tw);
-  timer_mark(st, 0);
-  BSCT_CUDA_TRY(launch_overlap(k_rows_r2c<T, LR, true, RPC>, dim3(N / RPC), dim3(TR), smr, st, x, (long)N, S,
-                               t.rows_f, t.untangle, (const T*)nullptr, (T*)nullptr, (const double*)nullptr));
-  timer_mark(st, 1);
+  const T* k7_in = MODE == AP_CG ? (const T*)p : (MODE == AP_PC ? in : (const T*)nullptr);
+  if (MODE == AP_PLAIN) timer_mark(st, 0);
+  if constexpr (MODE == AP_CG)
+    BSCT_CUDA_TRY(launch_overlap(k5, dim3(N / RPC), dim3(TR), smr, st, in, (long)N, S, t.rows_f, t.untangle,
+                                 (const T*)p, p, (const double*)(sc + SC_BETA)));
+  else
+    BSCT_CUDA_TRY(launch_overlap(k5, dim3(N / RPC), dim3(TR), smr, st, in, (long)N, S, t.rows_f, t.untangle,
+                                 (const T*)nullptr, (T*)nullptr, (const double*)nullptr));
+  if (MODE == AP_PLAIN) timer_mark(st, 1);
   BSCT_CUDA_TRY(launch_overlap(kc, dim3(grid_c), dim3(TC), smc, st, S, Gt, t.cols_f, t.cols_r, N / CC::G));
-  timer_mark(st, 2);
-  BSCT_CUDA_TRY(launch_overlap(k_rows_c2r<T, LR, RPI>, dim3(N / RPI), dim3(TI), smi, st, (const cpx<T>*)S, y,
-                               (long)N, t.rows_r, t.untangle, (const T*)nullptr, (double*)nullptr,
-                               (double*)nullptr));
-  timer_mark(st, 3);
+  if (MODE == AP_PLAIN) timer_mark(st, 2);
+  BSCT_CUDA_TRY(launch_overlap(k7, dim3(N / RPI), dim3(TI), smi, st, (const cpx<T>*)S, out, (long)N, t.rows_r,
+                               t.untangle, k7_in, MODE == AP_PLAIN ? (double*)nullptr : part,
+                               MODE == AP_PLAIN ? (double*)nullptr : sc));
+  if (MODE == AP_PLAIN) timer_mark(st, 3);
   count_launch(3);
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
 }
 
-// q = G p for CG with the direction update and <p, q> fused into the row passes:
-//   K5: p = r + beta p (beta from the device), written back and transformed
-//   K7: q written, per-CTA partial sums of <p, q> into part[0 .. N/RPC)
+template <typename T, int N, int MODE, int RPC, int RPI>
+static int run_if_ok(const T* in, T* p, T* out, double* sc, double* part, cpx<T>* S, const T* Gt, const cpx<T>* tw,
+                     int cols, cudaStream_t st) {
+  if constexpr (rows_ok<T, N, RPC>() && rows_ok<T, N, RPI>()) {
+    return run_apply<T, N, MODE, RPC, RPI>(in, p, out, sc, part, S, Gt, tw, cols, st);
+  } else {
+    bsct_set_last_message("FFT launch shape not valid for this size");
+    return BSCT_ERR_INVALID_ARG;
+  }
+}
+
+template <typename T, int N, int MODE>
+static int dispatch(const T* in, T* p, T* out, double* sc, double* part, cpx<T>* S, const T* Gt, const cpx<T>* tw,
+                    cudaStream_t st) {
+  constexpr int DF = rows_per_cta<N>(), DI = rows_per_cta_inv<N>();
+  const Shape sh = cur_shape<T>();
+#define BSCT_SHAPE(F_, I_)                                                                                      \
+  case F_ * 3 + I_:                                                                                             \
+    return run_if_ok<T, N, MODE, shape_cand<DF>(F_), shape_cand<DI>(I_)>(in, p, out, sc, part, S, Gt, tw, sh.cols, \
+                                                                        st);
+  switch (sh.fwd * 3 + sh.inv) {
+    BSCT_SHAPE(0, 0) BSCT_SHAPE(0, 1) BSCT_SHAPE(0, 2)
+    BSCT_SHAPE(1, 0) BSCT_SHAPE(1, 1) BSCT_SHAPE(1, 2)
+    BSCT_SHAPE(2, 0) BSCT_SHAPE(2, 1) BSCT_SHAPE(2, 2)
+  }
+#undef BSCT_SHAPE
+  bsct_set_last_message("FFT launch shape index out of range");
+  return BSCT_ERR_INVALID_ARG;
+}
+
+template <typename T, int N>
+static int apply_impl(const T* x, T* y, cpx<T>* S, const T* Gt, const cpx<T>* tw, cudaStream_t st) {
+  return dispatch<T, N, AP_PLAIN>(x, (T*)nullptr, y, (double*)nullptr, (double*)nullptr, S, Gt, tw, st);
+}
+
+// q = G p for CG with the direction update fused into the first pass (p = r + beta p) and
+// <p, q> into the last, whose last CTA forms alpha
 template <typename T, int N>
 static int apply_cg_impl(const T* r, T* p, T* q, double* sc, double* part, cpx<T>* S, const T* Gt,
                          const cpx<T>* tw, cudaStream_t st) {
-  constexpr int LR = N, LC = 2 * N;
-  constexpr int RPC = rows_per_cta<LR>(), RPI = rows_per_cta_inv<LR>();
-  typedef ColsCfg<T, LC> CC;
-  static_assert(N % RPC == 0 && N % RPI == 0 && N % CC::G == 0, "tile must divide N");
-  constexpr int TR = RPC * (LR / Plan<LR>::E), TI = RPI * (LR / Plan<LR>::E), TC = cols_threads<T, LC, CC::G>();
-  constexpr size_t smr = (size_t)RPC * row_region<T, LR, RPC>() * sizeof(cpx<T>);
-  constexpr size_t smi = (size_t)RPI * row_region<T, LR, RPI>() * sizeof(cpx<T>);
-  constexpr size_t smc = cols_smem<T, LC, CC::G>();
-  auto kc = k_cols_conv<T, LC, CC::G, CC::MINB>;
-  static int grid_cs[MAX_DEVICES] = {};
-  int& grid_c = grid_cs[device_slot()];
-  if (grid_c == 0) {
-    int rc = set_smem(k_rows_r2c<T, LR, true, RPC, true>, smr);
-    if (rc == BSCT_OK) rc = set_smem(k_rows_c2r<T, LR, RPI, RED_ALPHA>, smi);
-    if (rc == BSCT_OK) rc = set_smem(kc, smc);
-    if (rc != BSCT_OK) return rc;
-    int per_sm = 0;
-    BSCT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc, TC, smc));
-    if (per_sm < 1) per_sm = 1;
-    const int tiles = N / CC::G;
-    grid_c = per_sm * sm_count() < tiles ? per_sm * sm_count() : tiles;
-  }
-  const TwPtrs<T> t = tw_ptrs<T, N>(tw);
-  BSCT_CUDA_TRY(launch_overlap(k_rows_r2c<T, LR, true, RPC, true>, dim3(N / RPC), dim3(TR), smr, st, r, (long)N, S,
-                               t.rows_f, t.untangle, (const T*)p, p, (const double*)(sc + SC_BETA)));
-  BSCT_CUDA_TRY(launch_overlap(kc, dim3(grid_c), dim3(TC), smc, st, S, Gt, t.cols_f, t.cols_r, N / CC::G));
-  BSCT_CUDA_TRY(launch_overlap(k_rows_c2r<T, LR, RPI, RED_ALPHA>, dim3(N / RPI), dim3(TI), smi, st, (const cpx<T>*)S, q,
-                               (long)N, t.rows_r, t.untangle, (const T*)p, part, sc));
-  count_launch(3);
-  BSCT_CUDA_TRY(cudaGetLastError());
-  return BSCT_OK;
+  return dispatch<T, N, AP_CG>(r, p, q, sc, part, S, Gt, tw, st);
 }
 
 // z = M^-1 r for preconditioned CG: the plain apply with the preconditioner's spectrum,
@@ -589,35 +629,38 @@ static int apply_cg_impl(const T* r, T* p, T* q, double* sc, double* part, cpx<T
 template <typename T, int N>
 static int apply_pc_impl(const T* r, T* z, double* sc, double* part, cpx<T>* S, const T* Mt, const cpx<T>* tw,
                          cudaStream_t st) {
-  constexpr int LR = N, LC = 2 * N;
-  constexpr int RPC = rows_per_cta<LR>(), RPI = rows_per_cta_inv<LR>();
-  typedef ColsCfg<T, LC> CC;
-  constexpr int TR = RPC * (LR / Plan<LR>::E), TI = RPI * (LR / Plan<LR>::E), TC = cols_threads<T, LC, CC::G>();
-  constexpr size_t smr = (size_t)RPC * row_region<T, LR, RPC>() * sizeof(cpx<T>);
-  constexpr size_t smi = (size_t)RPI * row_region<T, LR, RPI>() * sizeof(cpx<T>);
-  constexpr size_t smc = cols_smem<T, LC, CC::G>();
-  auto kc = k_cols_conv<T, LC, CC::G, CC::MINB>;
-  static int grid_cs[MAX_DEVICES] = {};
-  int& grid_c = grid_cs[device_slot()];
-  if (grid_c == 0) {
-    int rc = set_smem(k_rows_r2c<T, LR, true, RPC>, smr);
-    if (rc == BSCT_OK) rc = set_smem(k_rows_c2r<T, LR, RPI, RED_RHO>, smi);
-    if (rc == BSCT_OK) rc = set_smem(kc, smc);
-    if (rc != BSCT_OK) return rc;
-    int per_sm = 0;
-    BSCT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc, TC, smc));
-    if (per_sm < 1) per_sm = 1;
-    const int tiles = N / CC::G;
-    grid_c = per_sm * sm_count() < tiles ? per_sm * sm_count() : tiles;
+  return dispatch<T, N, AP_PC>(r, (T*)nullptr, z, sc, part, S, Mt, tw, st);
+}
+
+// shapes: the three row-count candidates of each row pass (0 where not valid) ...
+template <typename T, int N> static void shape_cands(int fwd[3], int inv[3]) {
+  constexpr int DF = rows_per_cta<N>(), DI = rows_per_cta_inv<N>();
+  fwd[0] = rows_ok<T, N, shape_cand<DF>(0)>() ? shape_cand<DF>(0) : 0;
+  fwd[1] = rows_ok<T, N, shape_cand<DF>(1)>() ? shape_cand<DF>(1) : 0;
+  fwd[2] = rows_ok<T, N, shape_cand<DF>(2)>() ? shape_cand<DF>(2) : 0;
+  inv[0] = rows_ok<T, N, shape_cand<DI>(0)>() ? shape_cand<DI>(0) : 0;
+  inv[1] = rows_ok<T, N, shape_cand<DI>(1)>() ? shape_cand<DI>(1) : 0;
+  inv[2] = rows_ok<T, N, shape_cand<DI>(2)>() ? shape_cand<DI>(2) : 0;
+}
+// ... and the current choice as candidate indices (get, or set after validation)
+template <typename T, int N> static int shape_index(int idx[3], int set) {
+  Shape& sh = cur_shape<T>();
+  if (!set) {
+    idx[0] = sh.fwd;
+    idx[1] = sh.inv;
+    idx[2] = sh.cols;
+    return BSCT_OK;
   }
-  const TwPtrs<T> t = tw_ptrs<T, N>(tw);
-  BSCT_CUDA_TRY(launch_overlap(k_rows_r2c<T, LR, true, RPC>, dim3(N / RPC), dim3(TR), smr, st, r, (long)N, S,
-                               t.rows_f, t.untangle, (const T*)nullptr, (T*)nullptr, (const double*)nullptr));
-  BSCT_CUDA_TRY(launch_overlap(kc, dim3(grid_c), dim3(TC), smc, st, S, Mt, t.cols_f, t.cols_r, N / CC::G));
-  BSCT_CUDA_TRY(launch_overlap(k_rows_c2r<T, LR, RPI, RED_RHO>, dim3(N / RPI), dim3(TI), smi, st, (const cpx<T>*)S,
-                               z, (long)N, t.rows_r, t.untangle, r, part, sc));
-  count_launch(3);
-  BSCT_CUDA_TRY(cudaGetLastError());
+  int fwd[3], inv[3];
+  shape_cands<T, N>(fwd, inv);
+  if (idx[0] < 0 || idx[0] > 2 || idx[1] < 0 || idx[1] > 2 || idx[2] < 0 || idx[2] > 1 || !fwd[idx[0]] ||
+      !inv[idx[1]]) {
+    bsct_set_last_message("FFT launch shape not valid for this size");
+    return BSCT_ERR_INVALID_ARG;
+  }
+  sh.fwd = idx[0];
+  sh.inv = idx[1];
+  sh.cols = idx[2];
   return BSCT_OK;
 }
 
@@ -650,7 +693,9 @@ template <typename T, int N> FftOps<T> fft_ops() {
   o.apply = &apply_impl<T, N>;
   o.apply_cg = &apply_cg_impl<T, N>;
   o.apply_pc = &apply_pc_impl<T, N>;
-  o.cg_partials = N / rows_per_cta_inv<N>();
+  o.cg_partials = N / 2;  // the fewest rows per CTA any shape of the inverse pass takes
+  o.shape_cands = &shape_cands<T, N>;
+  o.shape_index = &shape_index<T, N>;
   o.spectrum = &spectrum_impl<T, N>;
   return o;
 }
