@@ -44,6 +44,7 @@ def parse():
     p.add_argument("--learned-pairs", type=int, default=512, help="training pairs for the learned warm start (0 = skip)")
     p.add_argument("--workload", default=WORKLOAD, help="named workload of the timed steps (profiling runs use smaller ones)")
     p.add_argument("--learned-epochs", type=int, default=2)
+    p.add_argument("--no-tune", action="store_true", help="keep the built-in FFT launch shapes (no autotuner)")
     return p.parse_args()
 
 
@@ -239,6 +240,14 @@ def run_ours(args):
     y = torch.empty_like(x)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+
+    # ---------------------------------------------------------------- launch shape (autotuner)
+    tune = None
+    if not args.no_tune:
+        shape, tune_us, all_us = bsct.fft_autotune(N, bsct.F32, reps=20)
+        tune = {"N": N, "shape": {"rows_fwd": shape[0], "rows_inv": shape[1], "cols_one_per_sm": shape[2]},
+                "us_per_apply": tune_us, "candidates_us": [round(t, 2) for t in all_us if t >= 0],
+                "how": "bsct_fft_autotune: 20 applies of every valid launch shape, fastest kept"}
 
     # ---------------------------------------------------------------- timed steps
     for _ in range(args.warmup):
@@ -517,6 +526,9 @@ def run_ours(args):
         from workloads.phantom import ellipse_params, ellipse_sinogram_torch
 
         sl = wcfg.batch_slices(args.batch_slices, seed=rank)
+        if not args.no_tune:
+            for n_b in sorted({d["N"] for d in sl}):
+                bsct.fft_autotune(n_b, bsct.F32, reps=10)
         geoms, sinos, cache = [], [], {}
         for i, d in enumerate(sl):
             key = (d["N"], d["n_angles"], d["zeta"])
@@ -575,6 +587,7 @@ def run_ours(args):
                "frac_of_hbm": cg_bytes / (cg_ms / n_cg * 1e-3) / 1e9 / hbm,
                "l2": "not flushed between iterations (135 MB working set)"},
         "pcg": pcg_info,
+        "autotune": tune,
         "forward_project": forward_info,
         "roofline": roofline,
         "e2e": e2e,

@@ -34,6 +34,15 @@ template <typename T> __device__ __forceinline__ cpx<T> ld_cpx(const cpx<T>* p) 
   typename vec2<T>::type v = *reinterpret_cast<const typename vec2<T>::type*>(p);
   return mk(v.x, v.y);
 }
+// Load through L2 only (ld.global.cg).  Kernels launched with programmatic dependent
+// launch start before their predecessor has finished, so the L1 invalidation that
+// separates dependent grids can come before the predecessor's stores; L1 may then still
+// hold an older copy of the line.  Every load of data another kernel writes goes through
+// this in those kernels (constant tables may use ld_cpx).
+template <typename T> __device__ __forceinline__ cpx<T> ld_cpx_cg(const cpx<T>* p) {
+  typename vec2<T>::type v = __ldcg(reinterpret_cast<const typename vec2<T>::type*>(p));
+  return mk(v.x, v.y);
+}
 template <typename T> __device__ __forceinline__ void st_cpx(cpx<T>* p, cpx<T> a) {
   typename vec2<T>::type v; v.x = a.x; v.y = a.y;
   *reinterpret_cast<typename vec2<T>::type*>(p) = v;

@@ -82,7 +82,7 @@ k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
   cpx<T>* zn = CG ? reinterpret_cast<cpx<T>*>(p_new + (long)(row0 + f) * ld_x) : nullptr;
   pdl_trigger();
   pdl_wait();
-  const T beta = CG ? T(*cg_beta) : T(0);
+  const T beta = CG ? T(__ldcg(cg_beta)) : T(0);
 
   cpx<T> v[E];
 #pragma unroll
@@ -94,12 +94,12 @@ k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
         v[b * R1 + r] = mk(T(0), T(0));  // z[n] = 0 for n >= LR/2 (never read)
       } else if constexpr (CG) {
         const int n = j + r * (LR / R1);
-        const cpx<T> a = ld_cpx(z + n), pp = ld_cpx(zp + n);
+        const cpx<T> a = ld_cpx_cg(z + n), pp = ld_cpx_cg(zp + n);
         const cpx<T> pn = mk(fma(beta, pp.x, a.x), fma(beta, pp.y, a.y));
         st_cpx(zn + n, pn);
         v[b * R1 + r] = pn;
       } else {
-        v[b * R1 + r] = ld_cpx(z + j + r * (LR / R1));
+        v[b * R1 + r] = ld_cpx_cg(z + j + r * (LR / R1));
       }
     }
   }
@@ -171,8 +171,8 @@ k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
     const int rr = e % RB, vv = (e / RB) % HL, lr = (e / RB) / HL * RB + rr, row = row0 + lr;
     const cpx<T>* ir = S + (long)(row >> 2) * LR * 4 + (row & 3);
     cpx<T>* smf = sm_all + lr * SME;
-    const cpx<T> Y = ld_cpx(ir + vv * 4);
-    const cpx<T> Yo = ld_cpx(ir + (vv == 0 ? HL : LR - vv) * 4);
+    const cpx<T> Y = ld_cpx_cg(ir + vv * 4);
+    const cpx<T> Yo = ld_cpx_cg(ir + (vv == 0 ? HL : LR - vv) * 4);
     if (vv == 0) {
       smf[spad(0)] = mk(Y.x + Y.y, Y.x - Y.y);
       smf[spad(HL)] = mk(Yo.x + Yo.x, -(Yo.y + Yo.y));
@@ -206,7 +206,7 @@ k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
     for (int r = 0; r < R1 / 2; ++r) {
       st_cpx(yr + j + r * (LR / R1), v[b * R1 + r]);
       if constexpr (RED != RED_NONE) {
-        const cpx<T> pp = ld_cpx(reinterpret_cast<const cpx<T>*>(p + (long)(row0 + f) * ld_y) + j + r * (LR / R1));
+        const cpx<T> pp = ld_cpx_cg(reinterpret_cast<const cpx<T>*>(p + (long)(row0 + f) * ld_y) + j + r * (LR / R1));
         dot = fma(pp.x, v[b * R1 + r].x, fma(pp.y, v[b * R1 + r].y, dot));
       }
     }
@@ -240,10 +240,11 @@ k_rows_c2r(const cpx<T>* __restrict__ S, T* __restrict__ y, long ld_y,
       if constexpr (RED == RED_ALPHA) {
         // <p, q> and alpha = <r, r> / <p, q> (0 when <p, q> <= 0)
         sc[SC_PQ] = t;
-        sc[SC_ALPHA] = t > 0.0 ? sc[SC_RR] / t : 0.0;
+        sc[SC_ALPHA] = t > 0.0 ? __ldcg(sc + SC_RR) / t : 0.0;
       } else {
         // rho_new = <r, M^-1 r>, beta = rho_new / rho (0 before the first step)
-        sc[SC_BETA] = sc[SC_RR] > 0.0 ? t / sc[SC_RR] : 0.0;
+        const double rho = __ldcg(sc + SC_RR);
+        sc[SC_BETA] = rho > 0.0 ? t / rho : 0.0;
         sc[SC_RR] = t;
       }
     });
