@@ -137,6 +137,18 @@ int bsct_gram_spectrum(const bsct_gram* g, double* d_out, void* stream);
  * d_x and d_y: N*N elements, may not alias. */
 int bsct_gram_apply(const bsct_gram* g, const void* d_x, void* d_y, int mode, void* stream);
 
+/* y_k = G x_k for n images held in HOST memory: h_x and h_y hold n consecutive [N][N]
+ * images in the handle's precision (pinned memory - cudaHostAlloc / cudaHostRegister -
+ * lets the copies overlap; pageable memory works but serialises them).  The copy in, the
+ * apply (the handle's FFT mode) and the copy out of consecutive images run on three
+ * library streams over two device images per direction, so the transfers of images
+ * k + 1 and k - 1 overlap the apply of image k.  The first call creates the streams,
+ * events and the 4 N^2 device images in the handle (freed by bsct_gram_free).  The work
+ * starts after what is queued on `stream`, and `stream` waits for the last copy out
+ * (asynchronous: synchronise `stream` before reading h_y).  Not to be called
+ * concurrently with other work on the same handle.  n = 0 is a no-op. */
+int bsct_gram_apply_host(bsct_gram* g, const void* h_x, void* h_y, int32_t n, void* stream);
+
 /* Largest N accepted by bsct_gram_apply_noalloc. */
 #define BSCT_NOALLOC_MAX_N 512
 

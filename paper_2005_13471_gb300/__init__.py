@@ -88,6 +88,7 @@ def _declare(L):
     L.bsct_cg_iterate.argtypes = [vp, vp, ctypes.c_int, vp]
     L.bsct_cg_residual.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp]
     L.bsct_precond_apply.argtypes = [vp, dbl, vp, vp, vp]
+    L.bsct_gram_apply_host.argtypes = [vp, vp, vp, i32, vp]
     L.bsct_fft_shape_candidates.argtypes = [i32, ctypes.c_int, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.bsct_fft_get_shape.argtypes = [i32, ctypes.c_int, ctypes.POINTER(FftShape)]
     L.bsct_fft_set_shape.argtypes = [i32, ctypes.c_int, ctypes.POINTER(FftShape)]
@@ -335,6 +336,22 @@ class GramFilter:
                                          ctypes.byref(rep), _stream()), "bsct_pcg_solve")
         return x, dict(iterations=rep.iterations, converged=bool(rep.converged), rel_residual=rep.rel_residual,
                        true_rel_residual=rep.true_rel_residual, status=rc)
+
+    def apply_host(self, x, out=None):
+        """y_k = G x_k for host tensors [n, N, N] (pinned for overlapped copies); asynchronous
+        on the current stream - synchronise before reading `out`."""
+        import torch
+
+        n = self.N
+        if x.is_cuda or x.dtype != self.dtype or x.dim() != 3 or tuple(x.shape[1:]) != (n, n) or not x.is_contiguous():
+            raise ValueError("x must be a contiguous host tensor [k, N, N] of the handle's dtype")
+        if out is None:
+            out = torch.empty(x.shape, dtype=self.dtype, pin_memory=x.is_pinned())
+        if out.is_cuda or out.shape != x.shape or out.dtype != self.dtype or not out.is_contiguous():
+            raise ValueError("out must be a contiguous host tensor like x")
+        _check(lib().bsct_gram_apply_host(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                          int(x.shape[0]), _stream()), "bsct_gram_apply_host")
+        return out
 
     def cg_solve_learned(self, net, b, in_scale, max_iter=1000, rel_tol=1e-4, check_every=5):
         """CG from the learned warm start alpha * net(in_scale * b) (plain CG if alpha <= 0)."""

@@ -175,6 +175,9 @@ int bsct_check_geom(const bsct_geom* g);
 int bsct_check_bp_geom(const bsct_geom* g);
 
 // Library-owned state of one geometry (see bsct_gram_build).
+struct bsct_host_pipe;  // streams, events and device images of bsct_gram_apply_host
+void bsct_host_pipe_free(bsct_host_pipe* p);
+
 struct bsct_gram {
   int N = 0, precision = 0, n_angles = 0;
   double zeta = 0.0, lambda = 1.0;
@@ -195,5 +198,6 @@ struct bsct_gram {
   double* Mt64 = nullptr;    // circulant preconditioner spectrum [N+1][2N], packed like Gt64
   float* Mt32 = nullptr;     // same, FP32 (precision F32 only)
   double m_eps = -1.0;       // floor the preconditioner spectrum was built with
+  bsct_host_pipe* pipe = nullptr;  // created on the first host-memory apply
   size_t dg_bytes = 0;
 };

@@ -410,6 +410,7 @@ extern "C" void bsct_gram_free(bsct_gram* g) {
   cudaFree(g->S);
   cudaFree(g->dg_work);
   cudaFree(g->z);
+  bsct_host_pipe_free(g->pipe);
   cudaFree(g->Mt64);
   cudaFree(g->Mt32);
   cudaFree(g->r);

@@ -360,3 +360,19 @@ def test_fma_peak_sane(bsct):
     assert 7e12 < f32 < 2e14
     assert 1e11 < f64 < 1.5e13
     assert f32 > 4 * f64
+
+
+@pytest.mark.parametrize("prec,n", [(0, 0), (0, 1), (0, 5), (1, 3)])
+def test_apply_host_pipeline(bsct, prec, n):
+    # host-memory apply with overlapped copies: bit-identical to the device apply per image
+    N = 256
+    dt = torch.float32 if prec == bsct.F32 else torch.float64
+    g = bsct.gram_build(bsct.Geometry.uniform(N, 40, 366, 1.0, 1.0), prec)
+    xs = torch.randn((max(n, 1), N, N), dtype=dt, generator=torch.Generator().manual_seed(9))[:n].contiguous()
+    xh = xs.pin_memory()
+    yh = torch.full(xh.shape, float("nan"), dtype=dt).pin_memory()
+    g.apply_host(xh, yh)
+    torch.cuda.synchronize()
+    for k in range(n):
+        assert torch.equal(yh[k], g.apply(xs[k].to(DEV)).cpu()), k
+    g.close()
