@@ -59,8 +59,9 @@ static int pipe_create(bsct_gram* g, size_t bytes) {
 }
 
 extern "C" int bsct_gram_apply_host(bsct_gram* g, const void* h_x, void* h_y, int32_t n, void* stream) {
-  if (!g || !h_x || !h_y || n < 0) { bsct_set_last_message("invalid argument"); return BSCT_ERR_INVALID_ARG; }
-  if (n == 0) return BSCT_OK;
+  if (!g || n < 0) { bsct_set_last_message("invalid argument"); return BSCT_ERR_INVALID_ARG; }
+  if (n == 0) return BSCT_OK;  // the image pointers may then be NULL
+  if (!h_x || !h_y) { bsct_set_last_message("NULL image pointer"); return BSCT_ERR_INVALID_ARG; }
   const size_t bytes = (size_t)g->N * g->N * (g->precision == BSCT_F32 ? sizeof(float) : sizeof(double));
   if (!g->pipe) {
     int rc = pipe_create(g, bytes);
