@@ -1,9 +1,9 @@
 // Gram apply of many images held in host memory, with the transfers overlapped.
 //
-// Image k goes through three stages, each on its own library stream:
-//   copy in  (host x_k -> device dx[k % 2]),
-//   apply    (dy[k % 2] = G dx[k % 2], the handle's FFT apply),
-//   copy out (dy[k % 2] -> host y_k),
+// Image k goes through three stages on library streams:
+//   copy in  (host x_k -> device dx[k % 2], in two parts on two streams),
+//   apply    (dy[k % 2] = G dx[k % 2], the handle's FFT apply, on one stream),
+//   copy out (dy[k % 2] -> host y_k, in two parts on two streams),
 // so that while image k is transformed, image k + 1 is copied in and image k - 1 out.
 // Two device images per direction (double buffering); events order the reuse of a
 // buffer after the stage that last read it.  In steady state one image takes as long as
@@ -12,26 +12,32 @@
 
 using namespace bsct;
 
+constexpr int HP_LANES = 2;  // copy streams per direction; each image is copied in HP_LANES parts
+
 struct bsct_host_pipe {
-  cudaStream_t s[3] = {nullptr, nullptr, nullptr};  // copy in, apply, copy out
-  cudaEvent_t in_done[2] = {}, comp_done[2] = {}, out_done[2] = {}, start = nullptr, done = nullptr;
+  cudaStream_t s[1 + 2 * HP_LANES] = {};  // apply, copy-in lanes, copy-out lanes
+  cudaEvent_t in_done[2][HP_LANES] = {}, out_done[2][HP_LANES] = {}, comp_done[2] = {};
+  cudaEvent_t start = nullptr, done[HP_LANES] = {};
   void* dx[2] = {nullptr, nullptr};
   void* dy[2] = {nullptr, nullptr};
 };
 
 void bsct_host_pipe_free(bsct_host_pipe* p) {
   if (!p) return;
-  for (int i = 0; i < 3; ++i)
-    if (p->s[i]) cudaStreamDestroy(p->s[i]);
+  for (cudaStream_t& st : p->s)
+    if (st) cudaStreamDestroy(st);
   for (int b = 0; b < 2; ++b) {
-    if (p->in_done[b]) cudaEventDestroy(p->in_done[b]);
+    for (int l = 0; l < HP_LANES; ++l) {
+      if (p->in_done[b][l]) cudaEventDestroy(p->in_done[b][l]);
+      if (p->out_done[b][l]) cudaEventDestroy(p->out_done[b][l]);
+    }
     if (p->comp_done[b]) cudaEventDestroy(p->comp_done[b]);
-    if (p->out_done[b]) cudaEventDestroy(p->out_done[b]);
     cudaFree(p->dx[b]);
     cudaFree(p->dy[b]);
   }
   if (p->start) cudaEventDestroy(p->start);
-  if (p->done) cudaEventDestroy(p->done);
+  for (cudaEvent_t& e : p->done)
+    if (e) cudaEventDestroy(e);
   delete p;
 }
 
@@ -43,16 +49,20 @@ static int pipe_create(bsct_gram* g, size_t bytes) {
     return BSCT_ERR_CUDA;
   };
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&p->s[i], cudaStreamNonBlocking);
+  for (cudaStream_t& st : p->s)
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-    e = cudaEventCreateWithFlags(&p->in_done[b], cudaEventDisableTiming);
+    for (int l = 0; l < HP_LANES && e == cudaSuccess; ++l) {
+      e = cudaEventCreateWithFlags(&p->in_done[b][l], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->out_done[b][l], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->comp_done[b], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->out_done[b], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&p->dx[b], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&p->dy[b], bytes);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->start, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
+  for (cudaEvent_t& ev : p->done)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   if (e != cudaSuccess) return fail(e);
   g->pipe = p;
   return BSCT_OK;
@@ -68,29 +78,44 @@ extern "C" int bsct_gram_apply_host(bsct_gram* g, const void* h_x, void* h_y, in
     if (rc != BSCT_OK) return rc;
   }
   bsct_host_pipe* p = g->pipe;
-  cudaStream_t st = (cudaStream_t)stream, si = p->s[0], sa = p->s[1], so = p->s[2];
+  cudaStream_t st = (cudaStream_t)stream, sa = p->s[0];
+  const cudaStream_t* si = p->s + 1;             // copy-in lanes
+  const cudaStream_t* so = p->s + 1 + HP_LANES;  // copy-out lanes
   const int mode = g->precision == BSCT_F32 ? BSCT_APPLY_FFT32 : BSCT_APPLY_F64;
+  // an image is copied as HP_LANES contiguous parts (16-byte multiples but the last)
+  size_t part = (bytes / HP_LANES + 15) & ~(size_t)15;
   // everything below runs after the work already queued on the caller's stream
   BSCT_CUDA_TRY(cudaEventRecord(p->start, st));
-  for (int i = 0; i < 3; ++i) BSCT_CUDA_TRY(cudaStreamWaitEvent(p->s[i], p->start, 0));
+  for (cudaStream_t s : p->s) BSCT_CUDA_TRY(cudaStreamWaitEvent(s, p->start, 0));
   const char* hx = (const char*)h_x;
   char* hy = (char*)h_y;
   for (int k = 0; k < n; ++k) {
     const int b = k & 1;
-    if (k >= 2) BSCT_CUDA_TRY(cudaStreamWaitEvent(si, p->comp_done[b], 0));  // dx[b] read by apply k - 2
-    BSCT_CUDA_TRY(cudaMemcpyAsync(p->dx[b], hx + (size_t)k * bytes, bytes, cudaMemcpyHostToDevice, si));
-    BSCT_CUDA_TRY(cudaEventRecord(p->in_done[b], si));
-    BSCT_CUDA_TRY(cudaStreamWaitEvent(sa, p->in_done[b], 0));
-    if (k >= 2) BSCT_CUDA_TRY(cudaStreamWaitEvent(sa, p->out_done[b], 0));  // dy[b] copied out (k - 2)
+    for (int l = 0; l < HP_LANES; ++l) {
+      const size_t off = (size_t)l * part, len = off >= bytes ? 0 : (bytes - off < part ? bytes - off : part);
+      if (k >= 2) BSCT_CUDA_TRY(cudaStreamWaitEvent(si[l], p->comp_done[b], 0));  // dx[b] read by apply k - 2
+      if (len) BSCT_CUDA_TRY(cudaMemcpyAsync((char*)p->dx[b] + off, hx + (size_t)k * bytes + off, len,
+                                             cudaMemcpyHostToDevice, si[l]));
+      BSCT_CUDA_TRY(cudaEventRecord(p->in_done[b][l], si[l]));
+      BSCT_CUDA_TRY(cudaStreamWaitEvent(sa, p->in_done[b][l], 0));
+      if (k >= 2) BSCT_CUDA_TRY(cudaStreamWaitEvent(sa, p->out_done[b][l], 0));  // dy[b] copied out (k - 2)
+    }
     int rc = bsct_gram_apply(g, p->dx[b], p->dy[b], mode, sa);
     if (rc != BSCT_OK) return rc;
     BSCT_CUDA_TRY(cudaEventRecord(p->comp_done[b], sa));
-    BSCT_CUDA_TRY(cudaStreamWaitEvent(so, p->comp_done[b], 0));
-    BSCT_CUDA_TRY(cudaMemcpyAsync(hy + (size_t)k * bytes, p->dy[b], bytes, cudaMemcpyDeviceToHost, so));
-    BSCT_CUDA_TRY(cudaEventRecord(p->out_done[b], so));
+    for (int l = 0; l < HP_LANES; ++l) {
+      const size_t off = (size_t)l * part, len = off >= bytes ? 0 : (bytes - off < part ? bytes - off : part);
+      BSCT_CUDA_TRY(cudaStreamWaitEvent(so[l], p->comp_done[b], 0));
+      if (len) BSCT_CUDA_TRY(cudaMemcpyAsync(hy + (size_t)k * bytes + off, (char*)p->dy[b] + off, len,
+                                             cudaMemcpyDeviceToHost, so[l]));
+      BSCT_CUDA_TRY(cudaEventRecord(p->out_done[b][l], so[l]));
+    }
   }
-  // the caller's stream continues once the last image is back (which orders after all)
-  BSCT_CUDA_TRY(cudaEventRecord(p->done, so));
-  BSCT_CUDA_TRY(cudaStreamWaitEvent(st, p->done, 0));
+  // the caller's stream continues once the last image is back on every lane (which
+  // orders after all the other work)
+  for (int l = 0; l < HP_LANES; ++l) {
+    BSCT_CUDA_TRY(cudaEventRecord(p->done[l], so[l]));
+    BSCT_CUDA_TRY(cudaStreamWaitEvent(st, p->done[l], 0));
+  }
   return BSCT_OK;
 }
