@@ -139,11 +139,11 @@ int bsct_gram_apply(const bsct_gram* g, const void* d_x, void* d_y, int mode, vo
 
 /* y_k = G x_k for n images held in HOST memory: h_x and h_y hold n consecutive [N][N]
  * images in the handle's precision (pinned memory - cudaHostAlloc / cudaHostRegister -
- * lets the copies overlap; pageable memory works but serialises them).  The copy in (in
- * two parts on two streams), the apply (the handle's FFT mode, one stream) and the copy
- * out (two parts, two streams) of consecutive images run on library streams over two
- * device images per direction, so the transfers of images k + 1 and k - 1 overlap the
- * apply of image k.  n = 0 accepts NULL image pointers.  The first call creates the streams,
+ * lets the copies overlap; pageable memory works but serialises them).  The copy in, the
+ * apply (the handle's FFT mode) and the copy out of consecutive images run on three
+ * library streams over two device images per direction, so the transfers of images
+ * k + 1 and k - 1 overlap the apply of image k.  n = 0 accepts NULL image pointers.
+ * The first call creates the streams,
  * events and the 4 N^2 device images in the handle (freed by bsct_gram_free).  The work
  * starts after what is queued on `stream`, and `stream` waits for the last copy out
  * (asynchronous: synchronise `stream` before reading h_y).  Not to be called

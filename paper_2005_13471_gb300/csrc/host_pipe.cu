@@ -1,9 +1,9 @@
 // Gram apply of many images held in host memory, with the transfers overlapped.
 //
 // Image k goes through three stages on library streams:
-//   copy in  (host x_k -> device dx[k % 2], in two parts on two streams),
-//   apply    (dy[k % 2] = G dx[k % 2], the handle's FFT apply, on one stream),
-//   copy out (dy[k % 2] -> host y_k, in two parts on two streams),
+//   copy in  (host x_k -> device dx[k % 2]),
+//   apply    (dy[k % 2] = G dx[k % 2], the handle's FFT apply),
+//   copy out (dy[k % 2] -> host y_k),
 // so that while image k is transformed, image k + 1 is copied in and image k - 1 out.
 // Two device images per direction (double buffering); events order the reuse of a
 // buffer after the stage that last read it.  In steady state one image takes as long as
@@ -12,7 +12,9 @@
 
 using namespace bsct;
 
-constexpr int HP_LANES = 2;  // copy streams per direction; each image is copied in HP_LANES parts
+// copy streams per direction (each image is copied in HP_LANES parts): at N = 2048 one
+// lane gave 9 133 images/s end to end and two lanes 8 135, so one
+constexpr int HP_LANES = 1;
 
 struct bsct_host_pipe {
   cudaStream_t s[1 + 2 * HP_LANES] = {};  // apply, copy-in lanes, copy-out lanes
