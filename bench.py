@@ -451,6 +451,17 @@ def run_ours(args):
             "iters": [r["iterations"] for _, (_, r) in pcg],
             "true_rel_residual_max": max(r["true_rel_residual"] for _, (_, r) in pcg),
             "speedup_vs_plain": tt["plain_ms_median"] / float(np.median([t for t, _ in pcg]))}
+        # the same two solvers as one CUDA graph each (device-side stopping test): one
+        # launch and one synchronisation per solve; the output buffer is reused so the
+        # executable graph is built once
+        xg = torch.empty_like(b5s[0])
+        for method, key in (("cg", "plain_graph"), ("pcg", "pcg_graph")):
+            g5.solve_graph(b5s[0], method=method, max_iter=2000, rel_tol=1e-4, out=xg)
+            runs = [timed(lambda: g5.solve_graph(b, method=method, max_iter=2000, rel_tol=1e-4, out=xg))
+                    for b in b5s]
+            tt[key] = {"ms_median": float(np.median([t for t, _ in runs])),
+                       "iters": [r["iterations"] for _, (_, r) in runs],
+                       "true_rel_residual_max": max(r["true_rel_residual"] for _, (_, r) in runs)}
         if args.learned_pairs > 0:
             from paper_2005_13471_gb300 import learned
 

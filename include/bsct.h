@@ -220,6 +220,18 @@ int bsct_forward_project(const bsct_geom* geom, const void* d_coeffs, void* d_si
 int bsct_cg_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero, int max_iter,
                   double rel_tol, int check_every, bsct_cg_report* report, void* stream);
 
+/* The whole solve from x = 0 as one CUDA graph: CG (method 0) or preconditioned CG with
+ * the circulant preconditioner of bsct_pcg_solve (method 1, floor eps).  The iterations
+ * run as the body of a conditional WHILE node; a one-thread kernel after each iteration
+ * decides on the device whether another follows (recursive ||r|| / ||b|| > rel_tol, or
+ * always when rel_tol <= 0, and fewer than max_iter iterations so far), so the solve
+ * needs one graph launch and one host synchronisation.  Same iterates, report and
+ * return codes as bsct_cg_solve / bsct_pcg_solve (report->iterations = iterations run).
+ * The executable graph is kept in the handle (rebuilt when method, d_x, max_iter or
+ * rel_tol change).  Synchronous. */
+int bsct_solve_graph(bsct_gram* g, int method, double eps, const void* d_b, void* d_x, int max_iter,
+                     double rel_tol, bsct_cg_report* report, void* stream);
+
 /* Steepest descent on G x = b, the unregularised solver of the paper's reconstruction
  * study (Sec. 6): x += alpha r with alpha = <r, r> / <r, G r>.  Arguments, stopping rule,
  * report and return codes as bsct_cg_solve; four kernels per iteration. */

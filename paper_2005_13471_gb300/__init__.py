@@ -88,6 +88,7 @@ def _declare(L):
     L.bsct_cg_iterate.argtypes = [vp, vp, ctypes.c_int, vp]
     L.bsct_cg_residual.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp]
     L.bsct_precond_apply.argtypes = [vp, dbl, vp, vp, vp]
+    L.bsct_solve_graph.argtypes = [vp, ctypes.c_int, dbl, vp, vp, ctypes.c_int, dbl, ctypes.POINTER(_CGReport), vp]
     L.bsct_gram_apply_host.argtypes = [vp, vp, vp, i32, vp]
     L.bsct_fft_shape_candidates.argtypes = [i32, ctypes.c_int, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.bsct_fft_get_shape.argtypes = [i32, ctypes.c_int, ctypes.POINTER(FftShape)]
@@ -425,6 +426,21 @@ class GramFilter:
         report = dict(iterations=rep.iterations, converged=bool(rep.converged), rel_residual=rep.rel_residual,
                       true_rel_residual=rep.true_rel_residual, status=rc)
         return x, report
+
+    def solve_graph(self, b, method="pcg", max_iter=1000, rel_tol=1e-4, eps=PRECOND_EPS, out=None):
+        """CG (method "cg") or circulant-preconditioned CG ("pcg") from x = 0 as one CUDA graph
+        whose iterations stop on the device."""
+        import torch
+
+        n = self.N
+        x = torch.empty((n, n), dtype=self.dtype, device=b.device) if out is None else out
+        rep = _CGReport()
+        m = {"cg": 0, "pcg": 1}[method]
+        rc = _check(lib().bsct_solve_graph(self._h, m, float(eps), _dev(b, (n, n), self.dtype, "b"),
+                                           _dev(x, (n, n), self.dtype, "x"), int(max_iter), float(rel_tol),
+                                           ctypes.byref(rep), _stream()), "bsct_solve_graph")
+        return x, dict(iterations=rep.iterations, converged=bool(rep.converged), rel_residual=rep.rel_residual,
+                       true_rel_residual=rep.true_rel_residual, status=rc)
 
     def sd_solve(self, b, x0=None, max_iter=100, rel_tol=0.0, check_every=10):
         """Steepest descent on G x = b (the paper's reconstruction solver)."""

@@ -59,7 +59,7 @@ inline cudaError_t launch_overlap(void (*k)(KP...), dim3 grid, dim3 block, size_
 // arrival counters of the last-block reductions below (zero between launches).
 // SC_RR holds <r, r> for CG and rho = <r, M^-1 r> for preconditioned CG, whose <r, r>
 // (the convergence measure) goes to SC_RRP
-enum { SC_RR = 0, SC_PQ = 1, SC_ALPHA = 2, SC_BETA = 3, SC_BB = 4, SC_TMP = 5, SC_RRP = 6,
+enum { SC_RR = 0, SC_PQ = 1, SC_ALPHA = 2, SC_BETA = 3, SC_BB = 4, SC_TMP = 5, SC_RRP = 6, /* 7: graph iterations */
        SC_CNT_PQ = 14, SC_CNT_RR = 15 };
 __device__ __forceinline__ unsigned long long* sc_counter(double* sc, int slot) {
   return reinterpret_cast<unsigned long long*>(sc + slot);
@@ -177,6 +177,8 @@ int bsct_check_bp_geom(const bsct_geom* g);
 // Library-owned state of one geometry (see bsct_gram_build).
 struct bsct_host_pipe;  // streams, events and device images of bsct_gram_apply_host
 void bsct_host_pipe_free(bsct_host_pipe* p);
+struct bsct_graph_solver;  // executable graph of bsct_solve_graph
+void bsct_graph_solver_free(bsct_graph_solver* s);
 
 struct bsct_gram {
   int N = 0, precision = 0, n_angles = 0;
@@ -199,5 +201,6 @@ struct bsct_gram {
   float* Mt32 = nullptr;     // same, FP32 (precision F32 only)
   double m_eps = -1.0;       // floor the preconditioner spectrum was built with
   bsct_host_pipe* pipe = nullptr;  // created on the first host-memory apply
+  bsct_graph_solver* sgraph = nullptr;  // created on the first graph solve
   size_t dg_bytes = 0;
 };

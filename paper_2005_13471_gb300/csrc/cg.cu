@@ -535,3 +535,150 @@ extern "C" int bsct_pcg_solve(bsct_gram* g, double eps, const void* d_b, void* d
   }
   return (rel_tol > 0.0 && !converged) ? BSCT_WARN_NOT_CONVERGED : BSCT_OK;
 }
+
+// ------------------------------------------------------------------------------------
+// Whole solve in one CUDA graph.  The iterations run as the body of a conditional WHILE
+// node; a one-thread kernel after every iteration counts it and decides on the device
+// whether another follows (residual above the tolerance, fewer than max_iter so far), so
+// a solve is one graph launch and one host synchronisation, not a host round trip per
+// convergence check.  The executable graph is kept in the handle and rebuilt when the
+// method, x, max_iter or the tolerance change.
+// ------------------------------------------------------------------------------------
+namespace bsct {
+constexpr int SC_IT = 7;  // iterations run by the graph (unsigned 64-bit)
+
+// after == 0: the decision before the first iteration; after == 1: after an iteration
+__global__ void k_loop_ctl(double* sc, cudaGraphConditionalHandle h, int max_iter, double tol2, int rr_slot,
+                           int after) {
+  unsigned long long* it = reinterpret_cast<unsigned long long*>(sc + SC_IT);
+  const unsigned long long n = after ? *it + 1ull : 0ull;
+  *it = n;
+  const double rr = __ldcg(sc + rr_slot), bb = __ldcg(sc + SC_BB);
+  const bool more = (long long)n < (long long)max_iter && bb > 0.0 && isfinite(rr) && (tol2 <= 0.0 || rr > tol2 * bb);
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+}  // namespace bsct
+
+struct bsct_graph_solver {
+  int method = -1, max_iter = -1;
+  const void* x = nullptr;
+  double tol2 = -1.0;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;  // capture stream
+};
+
+void bsct_graph_solver_free(bsct_graph_solver* s) {
+  if (!s) return;
+  if (s->exec) cudaGraphExecDestroy(s->exec);
+  if (s->cs) cudaStreamDestroy(s->cs);
+  delete s;
+}
+
+template <typename T>
+static int build_solve_graph(bsct_gram* g, int method, T* x, int max_iter, double tol2, bsct_graph_solver* sg) {
+  if (sg->exec) { cudaGraphExecDestroy(sg->exec); sg->exec = nullptr; }
+  if (!sg->cs) BSCT_CUDA_TRY(cudaStreamCreateWithFlags(&sg->cs, cudaStreamNonBlocking));
+  cudaGraph_t parent = nullptr;
+  BSCT_CUDA_TRY(cudaGraphCreate(&parent, 0));
+  auto fail = [&](cudaError_t e) {
+    bsct_set_last_cuda_error(e);
+    cudaGraphDestroy(parent);
+    return BSCT_ERR_CUDA;
+  };
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, parent, 0, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return fail(e);
+  int rr_slot = method == 1 ? SC_RRP : SC_RR, zero = 0;
+  double* scal = g->scal;
+  void* init_args[] = {&scal, &h, &max_iter, &tol2, &rr_slot, &zero};
+  cudaKernelNodeParams kp = {};
+  kp.func = (void*)k_loop_ctl;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(1);
+  kp.kernelParams = init_args;
+  cudaGraphNode_t n_init = nullptr, n_loop = nullptr;
+  if ((e = cudaGraphAddKernelNode(&n_init, parent, nullptr, 0, &kp)) != cudaSuccess) return fail(e);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if ((e = cudaGraphAddNode(&n_loop, parent, &n_init, nullptr, 1, &cp)) != cudaSuccess) return fail(e);
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(sg->cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+      cudaSuccess)
+    return fail(e);
+  int rc = method == 1 ? pcg_iter_t<T>(g, x, 1, sg->cs) : cg_iter_t<T, UPD_CG>(g, x, 1, sg->cs);
+  k_loop_ctl<<<1, 1, 0, sg->cs>>>(g->scal, h, max_iter, tol2, rr_slot, 1);
+  count_launch();
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(sg->cs, &captured);
+  if (rc != BSCT_OK) { cudaGraphDestroy(parent); return rc; }
+  if (e != cudaSuccess) return fail(e);
+  if ((e = cudaGraphInstantiate(&sg->exec, parent, 0)) != cudaSuccess) return fail(e);
+  cudaGraphDestroy(parent);
+  sg->method = method;
+  sg->x = x;
+  sg->max_iter = max_iter;
+  sg->tol2 = tol2;
+  return BSCT_OK;
+}
+
+template <typename T>
+static int solve_graph_t(bsct_gram* g, int method, double eps, const T* b, T* x, int max_iter, double rel_tol,
+                         bsct_cg_report* report, cudaStream_t st) {
+  int rc = BSCT_OK;
+  if (method == 1) {
+    rc = precond_ready(g, eps, st);
+    if (rc == BSCT_OK) rc = pcg_begin_t<T>(g, b, x, 1, st);
+  } else {
+    rc = cg_begin_t<T>(g, b, x, 1, st);
+  }
+  if (rc != BSCT_OK) return rc;
+  const double tol2 = rel_tol > 0.0 ? rel_tol * rel_tol : 0.0;
+  if (!g->sgraph) g->sgraph = new bsct_graph_solver();
+  bsct_graph_solver* sg = g->sgraph;
+  if (!sg->exec || sg->method != method || sg->x != x || sg->max_iter != max_iter || sg->tol2 != tol2) {
+    rc = build_solve_graph<T>(g, method, x, max_iter, tol2, sg);
+    if (rc != BSCT_OK && g_overlap) {
+      // a graph that cannot hold the programmatic launch edges is built without them
+      cudaGetLastError();
+      g_overlap = false;
+      rc = build_solve_graph<T>(g, method, x, max_iter, tol2, sg);
+      g_overlap = true;
+    }
+    if (rc != BSCT_OK) return rc;
+  }
+  BSCT_CUDA_TRY(cudaGraphLaunch(sg->exec, st));
+  double h[16];
+  if ((rc = read_scalars(g, h, st)) != BSCT_OK) return rc;
+  const double rr = h[method == 1 ? SC_RRP : SC_RR], bb = h[SC_BB];
+  unsigned long long its = 0;
+  memcpy(&its, &h[SC_IT], sizeof(its));
+  if (!isfinite(rr)) { bsct_set_last_message("residual is not finite"); return BSCT_ERR_NONFINITE; }
+  const int converged = rel_tol > 0.0 && (bb == 0.0 || rr <= tol2 * bb);
+  double tr = -1.0;
+  if (rel_tol > 0.0) {
+    rc = true_residual_t<T>(g, b, x, &tr, st);
+    if (rc != BSCT_OK) return rc;
+  }
+  if (report) {
+    report->iterations = (int)its;
+    report->converged = converged;
+    report->rel_residual = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    report->true_rel_residual = tr;
+  }
+  return (rel_tol > 0.0 && !converged) ? BSCT_WARN_NOT_CONVERGED : BSCT_OK;
+}
+
+extern "C" int bsct_solve_graph(bsct_gram* g, int method, double eps, const void* d_b, void* d_x, int max_iter,
+                                double rel_tol, bsct_cg_report* report, void* stream) {
+  if (!g || !d_b || !d_x || max_iter < 0 || (method != 0 && method != 1)) {
+    bsct_set_last_message("invalid argument");
+    return BSCT_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (g->precision == BSCT_F32)
+    return solve_graph_t<float>(g, method, eps, (const float*)d_b, (float*)d_x, max_iter, rel_tol, report, st);
+  return solve_graph_t<double>(g, method, eps, (const double*)d_b, (double*)d_x, max_iter, rel_tol, report, st);
+}

@@ -411,6 +411,7 @@ extern "C" void bsct_gram_free(bsct_gram* g) {
   cudaFree(g->dg_work);
   cudaFree(g->z);
   bsct_host_pipe_free(g->pipe);
+  bsct_graph_solver_free(g->sgraph);
   cudaFree(g->Mt64);
   cudaFree(g->Mt32);
   cudaFree(g->r);

@@ -180,3 +180,30 @@ def test_steepest_descent_fp32_converges(bsct):
     assert rep["converged"]
     assert ocg.true_relative_residual(apply, bd, x.cpu().double().numpy()) < 1.2e-3
     g.close()
+
+
+@pytest.mark.parametrize("method", ["cg", "pcg"])
+@pytest.mark.parametrize("N,prec", [(16, 0), (128, 0), (64, 1)])
+def test_solve_graph_matches_host_loop(bsct, method, N, prec):
+    # the graph-driven solve runs the same iterations as the host-driven one and stops on
+    # the device at the same iteration
+    dt = torch.float32 if prec == bsct.F32 else torch.float64
+    g = bsct.gram_build(bsct.Geometry.uniform(N, 60, int(1.42 * N) + 2, 1.0, 1.0), prec)
+    x = torch.randn((N, N), dtype=dt, device=DEV, generator=torch.Generator(device=DEV).manual_seed(N + 1))
+    b = g.apply(x)
+    tol = 1e-4 if prec == bsct.F32 else 1e-9
+    if method == "cg":
+        xr, rr = g.cg_solve(b, max_iter=3000, rel_tol=tol, check_every=1)
+    else:
+        xr, rr = g.pcg_solve(b, max_iter=3000, rel_tol=tol, check_every=1)
+    for _ in range(2):  # the second call replays the cached graph
+        xg, rg = g.solve_graph(b, method=method, max_iter=3000, rel_tol=tol)
+        assert rg["converged"] and rg["iterations"] == rr["iterations"]
+        assert float((xg - xr).norm() / xr.norm()) < (1e-6 if prec == bsct.F32 else 1e-12)
+        assert abs(rg["true_rel_residual"] - rr["true_rel_residual"]) < 0.05 * rr["true_rel_residual"]
+    # a fixed number of iterations (no tolerance) and max_iter = 0
+    xk, rk = g.solve_graph(b, method=method, max_iter=5, rel_tol=0.0)
+    assert rk["iterations"] == 5
+    _, r0 = g.solve_graph(b, method=method, max_iter=0, rel_tol=0.0)
+    assert r0["iterations"] == 0
+    g.close()
