@@ -641,7 +641,9 @@ static int solve_graph_t(bsct_gram* g, int method, double eps, const T* b, T* x,
   if (!sg->exec || sg->method != method || sg->x != x || sg->max_iter != max_iter || sg->tol2 != tol2) {
     rc = build_solve_graph<T>(g, method, x, max_iter, tol2, sg);
     if (rc != BSCT_OK && g_overlap) {
-      // a graph that cannot hold the programmatic launch edges is built without them
+      // a graph that cannot hold the programmatic launch edges is built without them (the
+      // switch is process-wide while the graph is captured: do not build solve graphs
+      // from several host threads at once)
       cudaGetLastError();
       g_overlap = false;
       rc = build_solve_graph<T>(g, method, x, max_iter, tol2, sg);

@@ -7,18 +7,17 @@
 using namespace bsct;
 
 namespace {
-template <typename T> int ops_for(int N, int precision, FftOps<T>* o) {
+template <typename T> int ops_for(int N, FftOps<T>* o) {
   if (!fft_ops_for<T>(N, o)) {
     bsct_set_last_message("unsupported N (see bsct_supported_size)");
     return BSCT_ERR_UNSUPPORTED_SIZE;
   }
-  (void)precision;
   return BSCT_OK;
 }
 
 template <typename T> int get_shape(int N, bsct_fft_shape* out) {
   FftOps<T> o;
-  int rc = ops_for<T>(N, 0, &o);
+  int rc = ops_for<T>(N, &o);
   if (rc != BSCT_OK) return rc;
   int fwd[3], inv[3], idx[3];
   o.shape_cands(fwd, inv);
@@ -32,7 +31,7 @@ template <typename T> int get_shape(int N, bsct_fft_shape* out) {
 
 template <typename T> int set_shape(int N, const bsct_fft_shape* s) {
   FftOps<T> o;
-  int rc = ops_for<T>(N, 0, &o);
+  int rc = ops_for<T>(N, &o);
   if (rc != BSCT_OK) return rc;
   int fwd[3], inv[3], idx[3] = {-1, -1, s->cols_one_per_sm ? 1 : 0};
   o.shape_cands(fwd, inv);
@@ -50,7 +49,7 @@ template <typename T> __global__ void k_fill(T* a, long n, T v) {
 template <typename T>
 int autotune(int N, int reps, bsct_fft_shape* best, double* best_us, double* all_us, cudaStream_t st) {
   FftOps<T> o;
-  int rc = ops_for<T>(N, 0, &o);
+  int rc = ops_for<T>(N, &o);
   if (rc != BSCT_OK) return rc;
   const long n = (long)N * N, ng = (long)(N + 1) * 2 * N;
   T *x = nullptr, *y = nullptr, *Gt = nullptr;
@@ -131,12 +130,12 @@ extern "C" int bsct_fft_shape_candidates(int32_t N, int precision, int32_t* rows
   int f[3], v[3];
   if (precision == BSCT_F32) {
     FftOps<float> o;
-    int rc = ops_for<float>(N, 0, &o);
+    int rc = ops_for<float>(N, &o);
     if (rc != BSCT_OK) return rc;
     o.shape_cands(f, v);
   } else {
     FftOps<double> o;
-    int rc = ops_for<double>(N, 0, &o);
+    int rc = ops_for<double>(N, &o);
     if (rc != BSCT_OK) return rc;
     o.shape_cands(f, v);
   }
