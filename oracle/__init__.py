@@ -27,6 +27,6 @@ that it follows):
                    the least-squares problem of Sec. 2), its preconditioned form, and the
                    steepest descent of the paper's reconstruction study (Sec. 6).
 
-Where the paper is silent or garbled the oracle takes one reading; every such
-reading is listed in DESIGN.md.
+Where the paper is silent or garbled the oracle takes one reading, the one the CUDA
+path takes as well; each function's docstring states the readings it depends on.
 """
