@@ -23,9 +23,6 @@
 
 #include "bsct_boxspline.cuh"
 #include "bsct_fft.cuh"
-#include <algorithm>
-#include <vector>
-
 #include "bsct_internal.h"
 
 namespace bsct {
@@ -291,56 +288,6 @@ __global__ void k_gram_taps(int N, int na, const double* __restrict__ th, const 
   G[(long)(-d2 + N - 1) * W + (-d1 + N - 1)] = acc;
 }
 
-// The same taps for a view set that is symmetric under theta -> pi - theta and
-// theta -> pi/2 - theta (checked on the host; e.g. any even number of uniform views):
-// then G(d1, d2) = G(+-d1, +-d2) = G(+-d2, +-d1), and only the triangle 0 <= d2 <= d1 is
-// evaluated (N (N + 1) / 2 taps, each written to its up to eight images).
-__global__ void k_gram_taps_sym(int N, int na, const double* __restrict__ th, const double2* __restrict__ cs,
-                                const double* __restrict__ tab, double zeta, double* __restrict__ G) {
-  const long H = (long)N * (N + 1) / 2;
-  const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (h >= H) return;
-  long a = (long)((sqrt(8.0 * (double)h + 1.0) - 1.0) * 0.5);  // row of the triangle
-  while (a * (a + 1) / 2 > h) --a;
-  while ((a + 1) * (a + 2) / 2 <= h) ++a;
-  const int d1 = (int)a, d2 = (int)(h - a * (a + 1) / 2);
-  const double wmax = 1.4142135623730951 + zeta;
-  const double r = hypot((double)d1, (double)d2);
-  double acc = 0.0;
-  auto visit = [&](int j0, int j1) {
-    for (int j = j0; j < j1; ++j) {
-      const double2 u = cs[j];
-      const double t = fabs(d1 * u.x + d2 * u.y);
-      const double* T = tab + (long)j * GT_STRIDE;
-      if (t < T[GT_S]) acc += gram_table_eval(T, t);
-    }
-  };
-  const double hw = (r > wmax) ? asin(wmax / r) * 0.31830988618379067154 + 1e-12 : 1.0;
-  if (hw >= 0.5) {
-    visit(0, na);
-  } else {
-    const double phi = atan2((double)d2, (double)d1) * 0.31830988618379067154;
-    double centre = phi + 0.5;
-    if (centre >= 1.0) centre -= 1.0;
-    const double lo = centre - hw, hi = centre + hw;
-    if (lo < 0.0) {
-      visit(lower_bound_d(th, na, lo + 1.0), na);
-      visit(0, lower_bound_d(th, na, hi));
-    } else if (hi > 1.0) {
-      visit(lower_bound_d(th, na, lo), na);
-      visit(0, lower_bound_d(th, na, hi - 1.0));
-    } else {
-      visit(lower_bound_d(th, na, lo), lower_bound_d(th, na, hi));
-    }
-  }
-  const int W = 2 * N - 1, c = N - 1;
-  const int p[2] = {d1, d2};
-  for (int sw = 0; sw < 2; ++sw)
-    for (int s1 = -1; s1 <= 1; s1 += 2)
-      for (int s2 = -1; s2 <= 1; s2 += 2)
-        G[(long)(s2 * p[1 - sw] + c) * W + (s1 * p[sw] + c)] = acc;
-}
-
 __global__ void k_embed(const double* __restrict__ G, int N, double* __restrict__ E) {
   const int L = 2 * N;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -451,28 +398,6 @@ int bsct_check_geom(const bsct_geom* g) {
   return BSCT_OK;
 }
 
-// Is the view set (angles in half turns, each taken mod 1) mapped onto itself by
-// a -> 1 - a and by a -> 1/2 - a (as multisets, to 1e-12)?  Then the Gram filter has the
-// eight-fold symmetry that k_gram_taps_sym uses.
-static bool views_symmetric(const double* ang, int na) {
-  std::vector<double> a(na), b(na), c(na);
-  auto wrap = [](double v) {
-    v -= floor(v);
-    return v > 1.0 - 1e-12 ? 0.0 : v;
-  };
-  for (int i = 0; i < na; ++i) {
-    a[i] = wrap(ang[i]);
-    b[i] = wrap(1.0 - a[i]);
-    c[i] = wrap(0.5 - a[i]);
-  }
-  std::sort(a.begin(), a.end());
-  std::sort(b.begin(), b.end());
-  std::sort(c.begin(), c.end());
-  for (int i = 0; i < na; ++i)
-    if (fabs(a[i] - b[i]) > 1e-12 || fabs(a[i] - c[i]) > 1e-12) return false;
-  return true;
-}
-
 extern "C" void bsct_gram_free(bsct_gram* g) {
   if (!g) return;
   cudaDeviceSynchronize();
@@ -551,12 +476,9 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
   CTRY(cudaMemcpyAsync(d_ang, geom->angles_pi, na * sizeof(double), cudaMemcpyHostToDevice, st));
 
   k_geometry<<<(na + 127) / 128, 128, 0, st>>>(d_ang, na, d_th, d_cs);
-  const long H = (long)(2 * N - 1) * (N - 1) + N, Hs = (long)N * (N + 1) / 2;
+  const long H = (long)(2 * N - 1) * (N - 1) + N;
   k_gram_tables<<<na, 32, 0, st>>>(d_cs, geom->zeta_blur, 1e-13, d_gtab);
-  if (views_symmetric(geom->angles_pi, na))
-    k_gram_taps_sym<<<(unsigned)((Hs + 127) / 128), 128, 0, st>>>(N, na, d_th, d_cs, d_gtab, geom->zeta_blur, g->taps);
-  else
-    k_gram_taps<<<(unsigned)((H + 127) / 128), 128, 0, st>>>(N, na, d_th, d_cs, d_gtab, geom->zeta_blur, g->taps);
+  k_gram_taps<<<(unsigned)((H + 127) / 128), 128, 0, st>>>(N, na, d_th, d_cs, d_gtab, geom->zeta_blur, g->taps);
   k_embed<<<(unsigned)(((long)L * L + 255) / 256), 256, 0, st>>>(g->taps, N, d_emb);
   count_launch(4);
   CTRY(cudaGetLastError());
