@@ -254,8 +254,13 @@ __global__ void k_gram_taps(int N, int na, const double* __restrict__ th, const 
     d2 = 1 + (int)(q / (2 * N - 1));
     d1 = (int)(q % (2 * N - 1)) - (N - 1);
   }
-  const double wmax = 1.4142135623730951 + zeta;  // >= |c| + |s| + zeta for every view
-  const double r = hypot((double)d1, (double)d2);
+  // Views visited: those whose strip |d . u| < |c| + |s| + zeta can reach d, bounded by
+  // the window |theta - (phi_d + pi/2)| <= asin(wmax / |d|).  The window only has to
+  // contain them (views outside the support are skipped below), so it is computed in
+  // FP32 and widened by 1e-4 half turns - far more than the FP32 error, which is at most
+  // ~1e-5 here because asin's argument stays below 0.9999 - while the taps stay FP64.
+  const float wmax = 1.41421356f + (float)zeta;  // >= |c| + |s| + zeta for every view
+  const float r = hypotf((float)d1, (float)d2);
   double acc = 0.0;
   auto visit = [&](int j0, int j1) {
     for (int j = j0; j < j1; ++j) {
@@ -265,11 +270,11 @@ __global__ void k_gram_taps(int N, int na, const double* __restrict__ th, const 
       if (t < T[GT_S]) acc += gram_table_eval(T, t);
     }
   };
-  const double hw = (r > wmax) ? asin(wmax / r) * 0.31830988618379067154 + 1e-12 : 1.0;
+  const double hw = (r > 1.0001f * wmax) ? (double)(asinf(wmax / r) * 0.318309886f) + 1e-4 : 1.0;
   if (hw >= 0.5) {
     visit(0, na);
   } else {
-    const double phi = atan2((double)d2, (double)d1) * 0.31830988618379067154;  // / pi, in [0, 1]
+    const double phi = (double)(atan2f((float)d2, (float)d1) * 0.318309886f);  // / pi, in [0, 1]
     double centre = phi + 0.5;
     if (centre >= 1.0) centre -= 1.0;
     const double lo = centre - hw, hi = centre + hw;
