@@ -72,3 +72,34 @@ def test_argument_validation_without_gpu(lib):
     assert nbytes.value > 64 * 90 * 4
     assert lib.bsct_backproject_workspace(m.Geometry(64, np.arange(10) / 10, 90).cptr(), 7, ctypes.byref(nbytes)) == -1
     assert lib.bsct_gram_apply(None, None, None, 0, None) == -1
+
+
+def test_new_entry_points_validate_on_the_host(lib):
+    import paper_2005_13471_gb300 as m
+
+    # forward projection: workspace size, blur and precision limits
+    nbytes = ctypes.c_size_t()
+    g64 = m.Geometry(64, np.arange(10) / 10, 90, 1.0, 1.0)
+    assert lib.bsct_forward_project_workspace(g64.cptr(), 0, ctypes.byref(nbytes)) == 0
+    assert nbytes.value >= 64 * 64 * 4 + 10 * 560 * 4
+    assert lib.bsct_forward_project_workspace(m.Geometry(64, np.arange(3) / 3, 90, 1.0, 4.5).cptr(), 0,
+                                              ctypes.byref(nbytes)) == -2
+    assert lib.bsct_forward_project_workspace(g64.cptr(), 7, ctypes.byref(nbytes)) == -1
+    assert lib.bsct_forward_project(None, None, None, 0, None, 0, None) == -1
+    # solvers and applies on a missing handle
+    rep = m._CGReport()
+    assert lib.bsct_pcg_solve(None, 1e-4, None, None, 1, 10, 0.0, 1, ctypes.byref(rep), None) == -1
+    assert lib.bsct_precond_apply(None, 1e-4, None, None, None) == -1
+    assert lib.bsct_sd_solve(None, None, None, 1, 10, 0.0, 1, ctypes.byref(rep), None) == -1
+    assert lib.bsct_solve_graph(None, 1, 1e-4, None, None, 10, 1e-4, ctypes.byref(rep), None) == -1
+    assert lib.bsct_gram_apply_host(None, None, None, 1, None) == -1
+    assert lib.bsct_pcg_solve_learned(None, None, 1e-4, None, None, 1.0, 10, 1e-4, 1, ctypes.byref(rep), None,
+                                      None) == -1
+    # launch shapes: candidates, the built-in default, and rejected shapes
+    f, v = m.fft_shape_candidates(256)
+    assert f[1] and v[1] and all(x == 0 or x >= 2 for x in f + v)
+    assert m.fft_shape(256) == (f[1], v[1], 0)
+    sh = m.FftShape(3, v[1], 0, 0)
+    assert lib.bsct_fft_set_shape(256, 0, ctypes.byref(sh)) == -1
+    assert lib.bsct_fft_get_shape(100, 0, ctypes.byref(sh)) == -2
+    assert lib.bsct_fft_autotune(256, 0, 0, None, None, None, None) == -1
