@@ -14,7 +14,8 @@ that it follows):
                    (Sec. 2 problem statement, Sec. 5 degree rule).
 * ``boxspline``  - univariate box splines (Eq. 1, Eq. 2): truncated-power formula in
                    FP64 and in mpmath, the pixel's projection as a chord length, the
-                   detector-blurred footprint and its autocorrelation by exact
+                   detector-blurred footprint (one box, or a convolution of several:
+                   the detector model of Sec. 2) and its autocorrelation by exact
                    piecewise Gauss-Legendre quadrature.
 * ``gram``       - Gram filter taps (Sec. 4, the Gram entry with and without blur),
                    explicit Gram matrix on tiny grids, Toeplitz spectrum, Gram apply

@@ -39,7 +39,12 @@ def correction_filter(degree, radius=Q_RADIUS):
     if degree == 2:
         z1 = 2.0 * math.sqrt(2.0) - 3.0
         return math.sqrt(2.0) * z1 ** np.abs(m)
-    raise ValueError("degree must be 0, 1 or 2")
+    if degree == 3:
+        # b = [1/6, 2/3, 1/6]: root of z + 4 + 1/z = 0 inside the unit circle, and the
+        # gain that makes q * b = delta (several detector boxes, oblique views)
+        z1 = math.sqrt(3.0) - 2.0
+        return math.sqrt(3.0) * z1 ** np.abs(m)
+    raise ValueError("degree must be 0, 1, 2 or 3")
 
 
 def prefilter(sino, angles_pi, zeta):
@@ -88,8 +93,9 @@ def _bp_view_quadrature(coef, t, c, s, zeta, lam, degree):
     knots = np.clip(knots, lo[..., None], hi[..., None])
     edges = np.sort(np.concatenate([knots, bp + t[..., None], lo[..., None], hi[..., None]], axis=-1), axis=-1)
     edges = np.clip(edges, lo[..., None], hi[..., None])
-    return bs.gl3_integrate(
-        edges, lambda y: interpolant(coef, y, lam, degree) * bs.blurred_footprint(y - t[..., None], c, s, zeta))
+    f = lambda y: interpolant(coef, y, lam, degree) * bs.blurred_footprint(y - t[..., None], c, s, zeta)
+    # several detector boxes raise both degrees past what 3-point GL integrates exactly
+    return bs.gl6_integrate(edges, f) if len(bs.blur_widths(zeta)) >= 2 else bs.gl3_integrate(edges, f)
 
 
 def backproject(sino, N, angles_pi, lam, zeta, method="quadrature"):

@@ -24,6 +24,25 @@ import numpy as np
 # 3-point Gauss-Legendre on [0, 1]: exact for polynomials of degree <= 5.
 _GL3_X = np.array([0.5 - math.sqrt(15.0) / 10.0, 0.5, 0.5 + math.sqrt(15.0) / 10.0])
 _GL3_W = np.array([5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0])
+# 6-point Gauss-Legendre on [0, 1] (numpy's nodes): exact for degree <= 11, used where
+# several detector boxes raise the degree of the integrands.
+_GL6_X, _GL6_W = np.polynomial.legendre.leggauss(6)
+_GL6_X, _GL6_W = 0.5 * (_GL6_X + 1.0), 0.5 * _GL6_W
+
+
+def blur_widths(zeta):
+    """The detector kernel's box widths: a number (one box, none if 0) or a sequence.
+
+    Sec. 2 models the detector cell as a convolution of boxes and uses one; a sequence
+    gives the convolution of unit-mass boxes of those widths (zeros dropped).
+    """
+    if np.ndim(zeta) == 0:
+        return (float(zeta),) if float(zeta) > 0.0 else ()
+    return tuple(float(w) for w in zeta if float(w) > 0.0)
+
+
+def _multi(zeta):
+    return np.ndim(zeta) != 0 and len(blur_widths(zeta)) >= 2
 
 
 def _clean_dirs(dirs):
@@ -132,6 +151,10 @@ def blurred_footprint(y, c, s, zeta):
     integrated by its midpoint value.
     """
     y = np.asarray(y, dtype=np.float64)
+    if _multi(zeta):
+        return _footprint_boxes(y, c, s, blur_widths(zeta))
+    if np.ndim(zeta) != 0:
+        zeta = blur_widths(zeta)[0] if blur_widths(zeta) else 0.0
     if zeta == 0.0:
         return pixel_projection(y, c, s)
     bp = projection_breakpoints(c, s)
@@ -147,16 +170,43 @@ def blurred_footprint(y, c, s, zeta):
     return np.sum(length * vals, axis=-1) / zeta
 
 
+def _footprint_boxes(y, c, s, widths):
+    """P averaged successively over boxes of the given widths: each average is the exact
+    integral of a piecewise polynomial over its window, split at the previous level's
+    kinks and summed by 6-point Gauss-Legendre (exact for the degrees that arise)."""
+    if not widths:
+        return pixel_projection(y, c, s)
+    w = widths[-1]
+    inner = widths[:-1]
+    bp = footprint_breakpoints(c, s, inner) if inner else projection_breakpoints(c, s)
+    lo = y - 0.5 * w
+    hi = y + 0.5 * w
+    edges = np.sort(np.concatenate([lo[..., None], np.clip(bp, lo[..., None], hi[..., None]), hi[..., None]],
+                                   axis=-1), axis=-1)
+    a = edges[..., :-1]
+    ln = edges[..., 1:] - a
+    total = 0.0
+    for xg, wg in zip(_GL6_X, _GL6_W):
+        total = total + np.sum(wg * ln * _footprint_boxes(a + xg * ln, c, s, inner), axis=-1)
+    return total / w
+
+
 def footprint_breakpoints(c, s, zeta):
     bp = projection_breakpoints(c, s)
+    if _multi(zeta):
+        for w in blur_widths(zeta):
+            bp = np.unique(np.concatenate([bp - 0.5 * w, bp + 0.5 * w]))
+        return bp
+    if np.ndim(zeta) != 0:
+        zeta = blur_widths(zeta)[0] if blur_widths(zeta) else 0.0
     if zeta == 0.0:
         return bp
     return np.sort(np.concatenate([bp - 0.5 * zeta, bp + 0.5 * zeta]))
 
 
 def footprint_support(c, s, zeta):
-    """Half-width of h's support: (|c| + |s| + zeta) / 2."""
-    return 0.5 * (abs(float(c)) + abs(float(s)) + float(zeta))
+    """Half-width of h's support: (|c| + |s| + zeta) / 2 (zeta: the sum of the box widths)."""
+    return 0.5 * (abs(float(c)) + abs(float(s)) + float(sum(blur_widths(zeta))))
 
 
 def gl3_integrate(edges, f):
@@ -182,8 +232,18 @@ def footprint_autocorrelation(t, c, s, zeta):
     bp = footprint_breakpoints(c, s, zeta)
     edges = np.sort(np.concatenate(
         [np.broadcast_to(bp, t.shape + bp.shape), bp + t[..., None]], axis=-1), axis=-1)
-    return gl3_integrate(edges, lambda y: blurred_footprint(y, c, s, zeta)
-                         * blurred_footprint(y - t[..., None], c, s, zeta))
+    f = lambda y: blurred_footprint(y, c, s, zeta) * blurred_footprint(y - t[..., None], c, s, zeta)
+    return gl6_integrate(edges, f) if _multi(zeta) else gl3_integrate(edges, f)
+
+
+def gl6_integrate(edges, f):
+    """As ``gl3_integrate`` with 6-point Gauss-Legendre: exact for degree <= 11."""
+    lo = edges[..., :-1]
+    w = edges[..., 1:] - lo
+    total = 0.0
+    for xg, wg in zip(_GL6_X, _GL6_W):
+        total = total + np.sum(wg * w * f(lo + xg * w), axis=-1)
+    return total
 
 
 # ----------------------------------------------------------------------------------
@@ -191,7 +251,7 @@ def footprint_autocorrelation(t, c, s, zeta):
 # ----------------------------------------------------------------------------------
 
 def bspline(x, d):
-    """Centred cardinal B-spline beta_d(x) of degree d in {0, 1, 2} (textbook pieces)."""
+    """Centred cardinal B-spline beta_d(x) of degree d in {0, 1, 2, 3} (textbook pieces)."""
     x = np.abs(np.asarray(x, dtype=np.float64))
     if d == 0:
         return np.where(x < 0.5, 1.0, np.where(x == 0.5, 0.5, 0.0))
@@ -200,14 +260,17 @@ def bspline(x, d):
     if d == 2:
         return np.where(x < 0.5, 0.75 - x * x,
                         np.where(x < 1.5, 0.5 * (x - 1.5) ** 2, 0.0))
-    raise ValueError("degree must be 0, 1 or 2")
+    if d == 3:
+        return np.where(x < 1.0, 2.0 / 3.0 - x * x + 0.5 * x ** 3,
+                        np.where(x < 2.0, (2.0 - x) ** 3 / 6.0, 0.0))
+    raise ValueError("degree must be 0, 1, 2 or 3")
 
 
 def directions_gram(c, s, zeta):
-    """Direction list of the Gram kernel: [c, c, s, s] (Sec. 4), plus [zeta, zeta] with blur."""
+    """Direction list of the Gram kernel: [c, c, s, s] (Sec. 4), plus [w, w] per detector box."""
     d = [c, c, s, s]
-    if zeta > 0.0:
-        d += [zeta, zeta]
+    for w in blur_widths(zeta):
+        d += [w, w]
     return d
 
 
@@ -218,7 +281,6 @@ def directions_backprojection(c, s, zeta, lam, degree):
     the footprint M_[c, s, zeta] gives the kernel that weighs sample m for a pixel.
     """
     d = [c, s]
-    if zeta > 0.0:
-        d.append(zeta)
+    d += list(blur_widths(zeta))
     d += [lam] * (degree + 1)
     return d

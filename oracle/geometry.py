@@ -62,4 +62,7 @@ def interp_degree(c, s, zeta):
     (number of non-zero directions) - 1: degree 1 in general, 0 for axis-aligned
     views without blur, 2 / 1 with blur.
     """
-    return int(c != 0.0) + int(s != 0.0) + int(zeta > 0.0) - 1
+    if np.ndim(zeta) == 0:
+        return int(c != 0.0) + int(s != 0.0) + int(zeta > 0.0) - 1
+    # several detector boxes: one more direction each
+    return int(c != 0.0) + int(s != 0.0) + sum(1 for w in zeta if float(w) > 0.0) - 1

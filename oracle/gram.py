@@ -34,7 +34,7 @@ def gram_taps(N, angles_pi, zeta, method="quadrature"):
     c_all, s_all = cospi_sinpi(angles_pi)
     for c, s in zip(np.atleast_1d(c_all), np.atleast_1d(s_all)):
         t = d1 * c + d2 * s
-        half = abs(c) + abs(s) + zeta
+        half = abs(c) + abs(s) + sum(bs.blur_widths(zeta))
         mask = np.abs(t) < half
         if not np.any(mask):
             continue
@@ -55,7 +55,7 @@ def gram_tap_values(offsets, angles_pi, zeta, method="quadrature"):
     c_all, s_all = cospi_sinpi(angles_pi)
     for c, s in zip(np.atleast_1d(c_all), np.atleast_1d(s_all)):
         t = offsets[:, 0] * c + offsets[:, 1] * s
-        mask = np.abs(t) < abs(c) + abs(s) + zeta
+        mask = np.abs(t) < abs(c) + abs(s) + sum(bs.blur_widths(zeta))
         if not np.any(mask):
             continue
         if method == "quadrature":
