@@ -262,8 +262,22 @@ __global__ void k_gram_taps(int N, int na, const double* __restrict__ th, const 
   const float wmax = 1.41421356f + (float)zeta;  // >= |c| + |s| + zeta for every view
   const float r = hypotf((float)d1, (float)d2);
   double acc = 0.0;
+  // two views per step as independent FP64 chains (the kernel waits on FP64 results,
+  // not on issue); a view outside its support is evaluated at the support edge and
+  // masked, and the sum keeps the view order, so the taps are unchanged
   auto visit = [&](int j0, int j1) {
-    for (int j = j0; j < j1; ++j) {
+    int j = j0;
+    for (; j + 1 < j1; j += 2) {
+      const double2 u0 = cs[j], u1 = cs[j + 1];
+      const double t0 = fabs(d1 * u0.x + d2 * u0.y), t1 = fabs(d1 * u1.x + d2 * u1.y);
+      const double* T0 = tab + (long)j * GT_STRIDE;
+      const double* T1 = T0 + GT_STRIDE;
+      const double s0 = T0[GT_S], s1 = T1[GT_S];
+      const double e0 = gram_table_eval(T0, fmin(t0, s0)), e1 = gram_table_eval(T1, fmin(t1, s1));
+      if (t0 < s0) acc += e0;
+      if (t1 < s1) acc += e1;
+    }
+    if (j < j1) {
       const double2 u = cs[j];
       const double t = fabs(d1 * u.x + d2 * u.y);
       const double* T = tab + (long)j * GT_STRIDE;
