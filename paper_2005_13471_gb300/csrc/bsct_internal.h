@@ -34,8 +34,10 @@ inline void timer_mark(cudaStream_t st, int i) {
 // launch_overlap() may be scheduled while the previous kernel of the stream is still
 // running its last CTAs.  Each such kernel calls pdl_trigger() first (its own successor
 // may then be scheduled once all of its CTAs have started) and pdl_wait() before its
-// first global-memory access; pdl_wait returns once the previous grid has completed and
-// its writes are visible, so the stream order of all memory effects is unchanged.
+// first global-memory access; pdl_wait returns once the previous grid has completed.
+// The L1 invalidation between dependent grids can then precede the predecessor's
+// stores, so these kernels read every datum another kernel wrote through L2 only
+// (ld_cpx_cg, __ldcg, cp.async.cg); only constant tables go through L1.
 // On by default; bsct_set_launch_overlap(0) launches them plainly.
 extern bool g_overlap;
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
