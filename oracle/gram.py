@@ -83,10 +83,9 @@ def explicit_gram_matrix(N, angles_pi, zeta):
             ti = t[i]
             edges = np.sort(np.concatenate(
                 [np.broadcast_to(bp + ti, (n, bp.size)), bp[None, :] + t[:, None]], axis=1), axis=1)
-            Gm[i, :] += bs.gl3_integrate(
-                edges,
-                lambda y: bs.blurred_footprint(y - ti, c, s, zeta)
-                * bs.blurred_footprint(y - t[:, None], c, s, zeta))
+            f = lambda y: bs.blurred_footprint(y - ti, c, s, zeta) * bs.blurred_footprint(y - t[:, None], c, s, zeta)
+            # several detector boxes raise the degree past 3-point Gauss-Legendre
+            Gm[i, :] += bs.gl6_integrate(edges, f) if len(bs.blur_widths(zeta)) >= 2 else bs.gl3_integrate(edges, f)
     return Gm
 
 
