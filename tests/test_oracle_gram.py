@@ -124,3 +124,17 @@ def test_spectrum_real_and_reported_sign():
     G1 = gram.gram_taps(8, np.array([0.1]), 0.0)
     re1, _ = gram.gram_spectrum(G1)
     assert np.min(re1) < 0  # not PSD for a single view: the embedding is not the operator
+
+
+def test_sampled_taps_match_the_full_filter():
+    # the per-offset evaluation used by the large-N GPU checks against the full filter
+    N = 12
+    angles = np.array([0.0, 0.11, 0.25, 0.47, 0.5, 0.73])
+    rng = np.random.default_rng(21)
+    offs = [(int(a), int(b)) for a, b in rng.integers(-(N - 1), N, (15, 2))] + [(0, 0), (N - 1, -(N - 1))]
+    for zeta in (0.0, 1.0):
+        for method in ("quadrature", "boxspline"):
+            G = gram.gram_taps(N, angles, zeta, method)
+            vals = gram.gram_tap_values(offs, angles, zeta, method)
+            ref = np.array([G[d2 + N - 1, d1 + N - 1] for d1, d2 in offs])
+            assert np.max(np.abs(vals - ref)) < 1e-14 * np.max(np.abs(G))
