@@ -17,7 +17,11 @@
 // h(|major| (f + r)) is ONE polynomial of f.  A per-view table of those polynomials
 // (built in FP64 from the footprint's piecewise-linear factor, without cancelling
 // terms) leaves per pixel one table read, two FMAs of Horner, the pixel load and the
-// accumulate; the interval search is done once per line.
+// accumulate.  Once per line: the interval of f, from a 64-cell lookup whose entries
+// carry the interval and its next two starts (one shared load and two comparisons), and
+// two comparisons that skip the first and last offsets when they fall outside the
+// support.  The table's rows are padded to 36 floats so that lanes in different
+// intervals read different banks.
 //
 // FP32 path: the line coordinate kappa = alpha - k beta (alpha per sample, beta per
 // view) reaches ~2N, where an FP32 rounding would move the footprint by ~1e-4 pixel; it
