@@ -8,9 +8,12 @@
 // until the process exits):
 //   g_na_scratch   - the N x N complex half-spectrum scratch of the three FFT passes,
 //   g_na_spectrum  - the packed, scaled spectrum the column pass reads,
-//   g_na_tw        - FFT twiddle tables for the current N.
+//   g_na_tw        - FFT twiddle tables of the call's N.
 // The size limit is BSCT_NOALLOC_MAX_N = 512 (2 MiB of scratch).  The kernels are the
-// ones bsct_gram_apply launches; only the buffers differ.
+// ones bsct_gram_apply launches; only the buffers differ.  Every call writes the
+// twiddle tables and the packed spectrum it reads before the three FFT passes (eight
+// small kernels beside the three passes), so no call depends on what an earlier call
+// left in the arrays, whatever N it had.
 #include "bsct_internal.h"
 
 namespace {
@@ -24,7 +27,6 @@ static __device__ __align__(256) bsct::cpx<float> g_na_tw[8 * NA_MAX_N];
 
 struct NaDevice {
   bool ready = false;
-  int tw_n = 0;  // N the twiddle tables currently hold
   bsct::cpx<float>* scratch = nullptr;
   float* spectrum = nullptr;
   bsct::cpx<float>* tw = nullptr;
@@ -81,11 +83,9 @@ extern "C" int bsct_gram_apply_noalloc(int32_t N, const double* d_spectrum, cons
     BSCT_CUDA_TRY(cudaGetSymbolAddress((void**)&d.tw, g_na_tw));
     d.ready = true;
   }
-  if (d.tw_n != N) {
-    const int rc = build_fft_tables<float>(d.tw, N, st);
-    if (rc != BSCT_OK) return rc;
-    d.tw_n = N;
-  }
+  // tables of this N, rebuilt on every call (8N entries: cheap beside the FFT passes)
+  const int rc = build_fft_tables<float>(d.tw, N, st);
+  if (rc != BSCT_OK) return rc;
   const long n = (long)(N + 1) * 2 * N;
   k_na_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_spectrum, N, d.spectrum);
   count_launch();

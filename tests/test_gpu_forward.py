@@ -59,7 +59,11 @@ def test_forward_matches_oracle(bsct, N, M, lam, zeta, angles, tol32, prec):
     cd = torch.tensor(c, dtype=torch.float64 if f64 else torch.float32, device=DEV)
     g = bsct.forward_project(geom, cd, bsct.F64 if f64 else bsct.F32).cpu().double().numpy()
     ref = obp.forward_sample(c, angles, M, lam, zeta)
-    assert np.max(np.abs(g - ref)) < (1e-11 if f64 else tol32) * np.max(np.abs(ref))
+    # FP64: 1e-12 of the largest sample; the near-axis unblurred case (FP32 gate 2e-4) keeps
+    # the ramp-slope allowance of 1e-11 (slope 1 / (|c| |s|) ~ 300 times FP64 coordinates)
+    err = np.max(np.abs(g - ref)) / np.max(np.abs(ref))
+    print(f"forward N={N} M={M} zeta={zeta} {prec}: {err:.2e}")
+    assert err < ((1e-11 if tol32 > 1e-5 else 1e-12) if f64 else tol32)
 
 
 def test_forward_bench_size_sampled_and_partition_of_unity(bsct):

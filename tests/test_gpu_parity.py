@@ -301,6 +301,32 @@ def test_cg_fp32_iterates_and_converges(bsct):
     g.close()
 
 
+@pytest.mark.parametrize("N", [1024, 2048])
+def test_cg_fp32_large_iterates_vs_oracle(bsct, N):
+    # the launch configuration of the timed CG at large N: the inverse row pass runs two
+    # rows per CTA, so <p, Gp> is summed over N / 2 per-CTA partials (512 / 1024) by the
+    # last CTA, and the vector update's partials likewise; iterates 1-3 element by element
+    # against the oracle's FP64 CG on the same FP32-rounded right-hand side
+    na = 12
+    angles = np.arange(na) / na
+    geom = bsct.Geometry(N, angles, int(1.42 * N) + 2, 1.0, 1.0)
+    g = bsct.gram_build(geom, bsct.F32)
+    G = ogram.gram_taps(N, angles, 1.0)
+    apply = lambda v: ogram.gram_apply_fft(G, v)
+    from workloads import ellipse_image
+
+    phantom = ellipse_image(ellipse_params(N, 40, seed=N), N, supersample=1)
+    bd = apply(phantom).astype(np.float32).astype(np.float64)
+    b = torch.tensor(bd, dtype=torch.float32, device=DEV)
+    _, hist, iters = ocg.cg(apply, bd, iters=3)
+    for k in (1, 2, 3):
+        xk, rep = g.cg_solve(b, max_iter=k)
+        assert rep["iterations"] == k
+        assert rel(xk.cpu().numpy(), iters[k - 1]) < 1e-5, k
+        assert abs(rep["rel_residual"] - hist[k]) < 1e-4 * hist[k], k
+    g.close()
+
+
 def test_cg_warm_start(bsct):
     N = 64
     geom = bsct.Geometry.uniform(N, 60, 92, 1.0, 0.0)

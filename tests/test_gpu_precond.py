@@ -5,8 +5,18 @@ section of the inverse of G's 2N-periodic circulant embedding (G is Toeplitz-blo
 Toeplitz, Sec. 4).  Small sizes are compared element by element with the oracle; at the
 bench size N = 2048 properties that hold at any size are checked: eps = 1 gives the
 scaled identity, M^-1 is symmetric and positive, and PCG reaches its tolerance with a
-true residual to match.  Tolerances: FP64 1e-11 (relative L2), FP32 2e-5.
+true residual to match.
+
+Tolerances (relative L2).  FP32 apply: 1e-5 (a CPU emulation with complex64 FFTs differs
+from FP64 by ~1e-7 on these inputs).  FP64 apply: the FP64 spectrum carries absolute
+rounding of ~u log2(4N^2) G^(0), which the floored reciprocal turns into relative error
+up to that / eps in M^-1's symbol, so the gate is 10 u log2(4N^2) / eps, at least 1e-12
+and at most 1e-11.  FP32 PCG iterates: the oracle's own FP64 PCG moves iterates 1 and 3
+of the N = 128 problem by 2.7e-6 and 1.1e-5 when b is perturbed at the FP32 rounding
+level (6e-8 relative; the circulant preconditioner amplifies it), so they are gated at
+about four times that: 1e-5 and 4e-5.
 """
+import math
 import numpy as np
 import pytest
 
@@ -53,7 +63,11 @@ def test_precond_apply_matches_oracle(bsct, N, na, zeta, eps, prec):
     xd = torch.tensor(x, dtype=torch.float64 if f64 else torch.float32, device=DEV)
     y = g.precond_apply(xd, eps=eps).cpu().double().numpy()
     ref = ogram.circulant_precond_apply(G, x, eps)
-    assert rel(y, ref) < (1e-11 if f64 else 2e-5)
+    u64 = 2.0 ** -53
+    tol64 = min(1e-11, max(1e-12, 10.0 * u64 * math.log2(4.0 * N * N) / eps))
+    err = rel(y, ref)
+    print(f"precond apply N={N} eps={eps} {prec}: {err:.2e}")
+    assert err < (tol64 if f64 else 1e-5)
     # the spectrum is rebuilt when eps changes
     y2 = g.precond_apply(xd, eps=1.0).cpu().double().numpy()
     assert rel(y2, x / G.sum()) < (1e-12 if f64 else 2e-6)
@@ -94,9 +108,11 @@ def test_pcg_fp32_converges(bsct):
     G = ogram.gram_taps(N, angles, 1.0)
     apply = lambda v: ogram.gram_apply_fft(G, v)
     _, _, iters = ocg.pcg(apply, lambda v: ogram.circulant_precond_apply(G, v, 1e-4), bd, iters=3)
-    for k in (1, 3):
+    for k, tol in ((1, 1e-5), (3, 4e-5)):
         xk, _ = g.pcg_solve(b, max_iter=k)
-        assert rel(xk.cpu().numpy(), iters[k - 1]) < 1e-5
+        err = rel(xk.cpu().numpy(), iters[k - 1])
+        print(f"FP32 PCG iterate {k}: {err:.2e}")
+        assert err < tol
     x, rep = g.pcg_solve(b, max_iter=500, rel_tol=1e-4, check_every=1)
     assert rep["converged"] and rep["rel_residual"] <= 1e-4
     r_final = ocg.true_relative_residual(apply, bd, x.cpu().double().numpy())

@@ -59,6 +59,34 @@ def test_noalloc_matches_gram_apply_twice(bsct, N, zeta):
     g.close()
 
 
+def test_noalloc_sizes_in_any_order_and_against_the_oracle(bsct):
+    """Calls with N = 64, then 512, then 64 again: each call writes the twiddle tables of
+    its own N, so returning to an earlier size reads no stale tables.  The N = 64 results
+    are also compared with the FP64 oracle's FFT convolution of the same taps."""
+    from oracle import gram as ogram
+
+    handles = {}
+    for N in (64, 512):
+        geom = bsct.Geometry.uniform(N, 90, int(1.42 * N), 1.0, 1.0)
+        g = bsct.gram_build(geom, bsct.F32)
+        handles[N] = (g, g.spectrum())
+    gen = torch.Generator(device=DEV).manual_seed(7)
+    for N in (64, 512, 64):
+        g, spec = handles[N]
+        x = torch.randn((N, N), device=DEV, generator=gen)
+        y = torch.full((N, N), float("nan"), device=DEV)
+        assert _noalloc(bsct, N, spec, x, y) == 0
+        torch.cuda.synchronize()
+        assert rel(y, g.apply(x)) < 1e-5, f"N = {N}"
+        if N == 64:
+            taps = g.taps().cpu().numpy()
+            y_ref = ogram.gram_apply_fft(taps, x.cpu().double().numpy())
+            err = np.linalg.norm(y.cpu().double().numpy() - y_ref) / np.linalg.norm(y_ref)
+            assert err < 1e-5, f"oracle, N = {N}: {err:.2e}"
+    for g, _ in handles.values():
+        g.close()
+
+
 def test_noalloc_rejects_sizes_beyond_its_limit(bsct):
     N = 1024  # supported by bsct_gram_apply, above BSCT_NOALLOC_MAX_N = 512
     spec = torch.zeros((2 * N, N + 1), dtype=torch.float64, device=DEV)
