@@ -163,6 +163,125 @@ def cpu_oracle_apply_rate(n_applies):
     return n_applies / dt, dt
 
 
+# ---------------------------------------------------------------- host-core baselines of the oracle
+# Workers of a "spawn" process pool (module level so that they pickle); every one calls
+# the oracle as it stands on its own unit of work.
+def _w_apply(args):
+    import numpy as np
+
+    from oracle import gram as ogram
+
+    seed, reps = args
+    N = 2048
+    rng = np.random.default_rng(seed)
+    G = rng.random((2 * N - 1, 2 * N - 1))  # the apply's cost does not depend on the tap values
+    x = rng.standard_normal((N, N))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        ogram.gram_apply_fft(G, x)
+    return time.perf_counter() - t0
+
+
+def _w_taps(args):
+    import numpy as np
+
+    from oracle import gram as ogram
+
+    N, views, zeta = args
+    t0 = time.perf_counter()
+    G = ogram.gram_taps(N, np.asarray(views), zeta)
+    return time.perf_counter() - t0, G
+
+
+def _w_bp(args):
+    import numpy as np
+
+    from oracle import backproject as obp
+
+    N, views, M, pts, seed = args
+    sino = np.random.default_rng(seed).standard_normal((len(views), M))
+    t0 = time.perf_counter()
+    obp.backproject_sampled(sino, N, np.asarray(views), 1.0, 1.0, pts)
+    return time.perf_counter() - t0
+
+
+def cpu_suite(cores):
+    """The FP64 oracle on the host cores, per workload of the bench (bounded samples).
+
+    Single-threaded figures call the oracle directly; the multi-core figures run independent
+    units (applies, view subsets, pixel samples) in a spawn process pool of `cores` workers
+    and divide the work done by the wall time.  Gram build and back projection are sampled
+    (a subset of views / pixels) and scaled to the full workload by the work they cover.
+    """
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import numpy as np
+
+    from oracle import cg as ocg
+    from oracle import gram as ogram
+    from workloads import ellipse_image, ellipse_params, get_config
+
+    out = {"cores": cores}
+    # spawn: the pool starts no child from a process that holds a CUDA context; a worker that
+    # dies raises BrokenProcessPool instead of leaving the map waiting
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
+        list(pool.map(_w_apply, [(k, 1) for k in range(cores)]))  # start-up, imports, first touch: untimed
+        # Gram apply at N = 2048: two per worker, all workers at once
+        t0 = time.perf_counter()
+        list(pool.map(_w_apply, [(100 + k, 2) for k in range(cores)]))
+        dt = time.perf_counter() - t0
+        out["gram_apply_n2048"] = {"applies_per_s_1core": None, "applies_per_s_all": 2 * cores / dt,
+                                   "sample": f"{2 * cores} applies, two per worker ({dt:.1f} s)"}
+        # Gram build at N = 2048, 1800 views, zeta = 1: a sample of views per worker
+        cfg = get_config("fp32_n2048")
+        N, na = cfg["N"], cfg["n_angles"]
+        views = np.arange(na) / na
+        per = 2
+        sample = [(N, views[(k * 97 + np.arange(per)) % na].tolist(), cfg["zeta"]) for k in range(cores)]
+        t1 = time.perf_counter()
+        res = list(pool.map(_w_taps, sample))
+        dt = time.perf_counter() - t1
+        t_view = float(np.mean([r[0] for r in res])) / per
+        out["gram_build_n2048"] = {"ms_1core": 1e3 * t_view * na, "ms_all": 1e3 * dt * na / (per * cores),
+                                   "sample": f"{per * cores} of {na} views ({per} per worker), scaled by views"}
+        # back projection at N = 2048, 1800 views: sampled pixels x views per worker
+        npx, nv = 250, 24
+        rng = np.random.default_rng(0)
+        jobs = [(N, views[(k * 53 + np.arange(nv) * 75) % na].tolist(), cfg["n_bins"],
+                 [tuple(int(v) for v in p) for p in rng.integers(0, N, size=(npx, 2))], k) for k in range(cores)]
+        t2 = time.perf_counter()
+        times = list(pool.map(_w_bp, jobs))
+        dt = time.perf_counter() - t2
+        pairs = npx * nv
+        out["backproject_n2048"] = {"pairs_per_s_1core": pairs / float(np.mean(times)),
+                                    "pairs_per_s_all": pairs * cores / dt,
+                                    "sample": f"{npx} pixels x {nv} views per worker (pixel-view pairs / s)"}
+        # time to a 1e-4 relative residual (N = 512, 720 views, zeta = 1): taps over the pool,
+        # then the oracle's CG on one core; right-hand side G x of a 40-ellipse phantom (the
+        # back projection is measured on its own above)
+        c5 = get_config("learned_eval_n512")
+        N5, na5 = c5["N"], c5["n_angles"]
+        v5 = np.arange(na5) / na5
+        chunks = [(N5, v5[k::cores].tolist(), c5["zeta"]) for k in range(cores)]
+        t3 = time.perf_counter()
+        parts = list(pool.map(_w_taps, chunks))
+        t_taps = time.perf_counter() - t3
+    G5 = sum(p[1] for p in parts)
+    x5 = ellipse_image(ellipse_params(N5, 40, seed=7), N5, supersample=1)
+    apply5 = lambda v: ogram.gram_apply_fft(G5, v)
+    b5 = apply5(x5)
+    t4 = time.perf_counter()
+    _, hist, _ = ocg.cg(apply5, b5, iters=2000, tol=1e-4)
+    t_cg = time.perf_counter() - t4
+    out["time_to_1e-4_n512"] = {"cg_s_1core": t_cg, "cg_iters": len(hist) - 1, "gram_build_s_all": t_taps,
+                                "rhs": "G x of a 40-ellipse phantom (FP64 oracle)"}
+    # the single-core apply rate (the reference arm's unit)
+    rate, dt = cpu_oracle_apply_rate(2)
+    out["gram_apply_n2048"]["applies_per_s_1core"] = rate
+    return out
+
+
 def reduce_max(v, device):
     """Maximum of v over the ranks of the default process group (v itself without one)."""
     import torch
@@ -586,14 +705,71 @@ def run_ours(args):
         batch.close()
         del sinos, xs
 
+    # ---------------------------------------------------------------- host link (pinned copies)
+    # one cudaMemcpyAsync per copy of one N x N FP32 image, host-to-device and device-to-host
+    # at the same time on two streams: the peak the end-to-end rate is divided by
+    nb = 4 * N * N
+    hsrc = torch.empty(N * N, dtype=torch.float32, pin_memory=True)
+    hdst = torch.empty(N * N, dtype=torch.float32, pin_memory=True)
+    dsrc = torch.empty(N * N, dtype=torch.float32, device=dev)
+    ddst = torch.empty(N * N, dtype=torch.float32, device=dev)
+    s_h2d, s_d2h = torch.cuda.Stream(), torch.cuda.Stream()
+    reps = 20
+    for _ in range(3):
+        ddst.copy_(hsrc, non_blocking=True)
+        hdst.copy_(dsrc, non_blocking=True)
+    torch.cuda.synchronize()
+    link = {}
+    for name, pairs in (("h2d", [(s_h2d, ddst, hsrc)]), ("d2h", [(s_d2h, hdst, dsrc)]),
+                        ("both", [(s_h2d, ddst, hsrc), (s_d2h, hdst, dsrc)])):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for st_, dst, src in pairs:
+                with torch.cuda.stream(st_):
+                    dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        link[name] = reps * nb / (time.perf_counter() - t0) / 1e9  # GB/s per direction
+    e2e_link_gbs = e2e["value"] * nb / 1e9  # per direction
+    e2e["host_link"] = {"h2d_GBs": link["h2d"], "d2h_GBs": link["d2h"], "both_per_direction_GBs": link["both"],
+                        "e2e_GBs_per_direction": e2e_link_gbs, "frac": e2e_link_gbs / link["both"],
+                        "how": f"pinned {nb >> 20} MiB image, one cudaMemcpyAsync per copy, {reps} copies per "
+                               "direction, both directions on two streams for the concurrent figure"}
+    del hsrc, hdst, dsrc, ddst
+
+    # ---------------------------------------------------------------- FP64 apply (context)
+    fp64_info = None
+    if not args.quick:
+        g64 = bsct.gram_build(geom, bsct.F64)
+        x64 = x.double()
+        y64 = torch.empty_like(x64)
+        for _ in range(3):
+            g64.apply(x64, y64)
+        barrier()
+        e0.record(stream)
+        for _ in range(10):
+            g64.apply(x64, y64)
+        e1.record(stream)
+        barrier()
+        ms64 = e0.elapsed_time(e1) / 10
+        fp64_info = {"ms_per_apply": ms64, "applies_per_s": 1e3 / ms64,
+                     "algorithmic_bytes": 2 * apply_bytes,
+                     "frac_of_hbm": 2 * apply_bytes / (ms64 * 1e-3) / 1e9 / hbm,
+                     "rel_l2_vs_fp32": float((y64 - g.apply(x).double()).norm() / y64.norm()),
+                     "l2": "not flushed between applies"}
+        g64.close()
+        del x64, y64
+
     # ---------------------------------------------------------------- CPU baseline (rank 0, N=1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n_cpu = 3
-        rate_cpu, dt_cpu = cpu_oracle_apply_rate(n_cpu)
-        cpu = {"value": rate_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{n_cpu} applies of the numpy FP64 oracle gram_apply_fft at N=2048 "
-                         f"({dt_cpu:.1f} s; taps of a 12-view geometry, apply cost independent of the view count)"}
+        cores = os.cpu_count() or 1
+        suite = cpu_suite(cores)
+        ga = suite["gram_apply_n2048"]
+        cpu = {"value": ga["applies_per_s_all"], "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle gram_apply_fft at N=2048 on {cores} host cores: {ga['sample']}",
+               "single_core_value": ga["applies_per_s_1core"],
+               "per_workload": suite}
 
     clocks = clk.summary()
     line = {
@@ -609,6 +785,7 @@ def run_ours(args):
                "frac_of_hbm": cg_bytes / (cg_ms / n_cg * 1e-3) / 1e9 / hbm,
                "l2": "not flushed between iterations (135 MB working set)"},
         "pcg": pcg_info,
+        "fp64_apply": fp64_info,
         "autotune": tune,
         "forward_project": forward_info,
         "roofline": roofline,

@@ -132,7 +132,7 @@ int bsct_gram_spectrum(const bsct_gram* g, double* d_out, void* stream);
  * handle and float buffers, BSCT_APPLY_F64 a BSCT_F64 handle and double buffers.
  * BSCT_APPLY_DFTGEMM_BF16 (F32 handle, float buffers) computes the same convolution
  * with every length-2N DFT as two split-BF16 GEMMs on the tensor cores (operands split
- * into BF16 high + low parts, FP32 accumulation; relative error ~1e-5 to 1e-4); its
+ * into BF16 high + low parts, FP32 accumulation; relative error ~5e-6 to 1e-5); its
  * ~12 (2N)^2-float scratch is allocated in the handle on the first such call.
  * d_x and d_y: N*N elements, may not alias. */
 int bsct_gram_apply(const bsct_gram* g, const void* d_x, void* d_y, int mode, void* stream);
@@ -169,10 +169,12 @@ int bsct_gram_apply_host(bsct_gram* g, const void* h_x, void* h_y, int32_t n, vo
  *   d_x, d_y   : [N][N] float on the device, may not alias.
  * The first call on a device looks up the device addresses of those arrays (no
  * allocation); make that first call before any stream capture.  All calls share the
- * arrays and leave the last call's contents in them; every element a call reads is
- * written by the same call first, so nothing has to be cleared.  Calls that overlap
- * on the GPU (two streams, or two host threads) race on the shared arrays: serialise
- * them.  Calls no cudaMalloc, cudaFree or allocating library routine.
+ * arrays and leave the last call's contents in them; every element a call reads
+ * (twiddle tables of its N, packed spectrum, scratch) is written by the same call
+ * first, so nothing has to be cleared and calls with different N may follow one
+ * another in any order.  Calls that overlap on the GPU (two streams, or two host
+ * threads) race on the shared arrays: serialise them.  Calls no cudaMalloc, cudaFree
+ * or allocating library routine.
  * Returns BSCT_OK or a negative error. */
 int bsct_gram_apply_noalloc(int32_t N, const double* d_spectrum, const float* d_x, float* d_y,
                             void* stream);
@@ -303,6 +305,12 @@ void bsct_batch_free(bsct_batch* b);
  * Batch b advances A, B, C by stride_a, stride_b, stride_c elements.  K, lda, ldb and
  * the A/B strides must be multiples of 8, A and B 16-byte aligned; trans_a needs
  * M % 8 == 0 and !trans_b needs N % 8 == 0.  All pointers device. */
+/* Which tensor-core GEMM bsct_gemm_bf16 (and every GEMM inside the library) runs:
+ * 0 (default) the fifth-generation tensor cores - tcgen05.mma with the accumulator in
+ * tensor memory and operand tiles copied into shared memory by the tensor-memory
+ * accelerator; 1 the warp-level mma.sync kernel (the comparison path).  Process-wide.
+ * Errors: INVALID_ARG. */
+int bsct_set_gemm_path(int path);
 int bsct_gemm_bf16(int trans_a, int trans_b, int32_t M, int32_t N, int32_t K, float alpha, const void* d_A,
                    int64_t lda, int64_t stride_a, const void* d_B, int64_t ldb, int64_t stride_b, float beta,
                    float* d_C, int64_t ldc, int64_t stride_c, int32_t batch, void* stream);
@@ -337,6 +345,44 @@ void bsct_unet_free(bsct_unet* net);
 int bsct_mse_loss_grad(const float* d_pred, const float* d_target, int64_t n, float* d_grad, double* d_loss,
                        void* stream);
 
+/* Single layers of that network (no counterpart in the paper), for checking them one by
+ * one: the same kernels and BF16 tensor-core GEMMs the network runs, with FP32 data.
+ * Activations are [C][n][H][W] FP32; n*H*W and cout must be multiples of 8.
+ * bsct_conv3x3_forward: out = act(conv3x3(bf16(in), bf16(w)) + b), zero padding 1, act =
+ *   ReLU when relu != 0, else identity; w [cout][kpad] with column ci*9 + ky*3 + kx and
+ *   kpad = 9 cin rounded up to a multiple of 8 (padding columns must be zero).
+ * bsct_conv3x3_backward: from d_gout = dLoss/d out, with d = bf16(gout masked by out > 0
+ *   when relu != 0): gw = d x im2col(bf16(in))^T ([cout][kpad], overwritten), gb = sum of
+ *   the unrounded masked gradient (overwritten), gin = col2im(bf16(w)^T d) (overwritten;
+ *   NULL skips it).  d_out (the forward output) is read only when relu != 0.
+ * bsct_tconv2x2_forward: 2x2 stride-2 transposed convolution [cin][n][H][W] ->
+ *   [cout][n][2H][2W], out[co][n][2y+dy][2x+dx] = sum_ci w[co*4+dy*2+dx][ci] bf16(in) + b;
+ *   cin a multiple of 8.  bsct_tconv2x2_backward: gw ([cout*4][cin]), gb, gin (NULL skips
+ *   it) from gout, rounded to BF16 before both products.
+ * Scratch comes from the stream-ordered allocator (cudaMallocAsync / cudaFreeAsync on the
+ * stream).  Asynchronous.  Errors: INVALID_ARG, CUDA. */
+int bsct_conv3x3_forward(int32_t n, int32_t cin, int32_t cout, int32_t H, int32_t W, const float* d_in,
+                         const float* d_w, const float* d_b, int relu, float* d_out, void* stream);
+int bsct_conv3x3_backward(int32_t n, int32_t cin, int32_t cout, int32_t H, int32_t W, const float* d_in,
+                          const float* d_w, const float* d_out, const float* d_gout, int relu, float* d_gin,
+                          float* d_gw, float* d_gb, void* stream);
+int bsct_tconv2x2_forward(int32_t n, int32_t cin, int32_t cout, int32_t H, int32_t W, const float* d_in,
+                          const float* d_w, const float* d_b, float* d_out, void* stream);
+int bsct_tconv2x2_backward(int32_t n, int32_t cin, int32_t cout, int32_t H, int32_t W, const float* d_in,
+                           const float* d_w, const float* d_gout, float* d_gin, float* d_gw, float* d_gb,
+                           void* stream);
+
+/* G-norm training loss of the learned warm start (no counterpart in the paper): for n
+ * images of the handle's size N (d_pred, d_target, d_grad: [n][N][N] FP32, device),
+ *   *d_loss += (1/n) sum_i w_i <e_i, G e_i>,   d_grad_i = (2 w_i / n) G e_i,
+ * with e_i = pred_i - target_i and G the handle's Gram filter (FP32 FFT apply); the error
+ * is measured in the norm CG minimises.  d_weight: n per-image weights (device FP64) or
+ * NULL for 1.  d_loss: one device FP64 value, accumulated (not cleared).  F32 handle.
+ * Scratch (n N^2 floats) from the stream-ordered allocator.  Asynchronous.  The sum runs in
+ * a fixed order (reproducible). */
+int bsct_gnorm_loss_grad(const bsct_gram* g, const float* d_pred, const float* d_target, int32_t n,
+                         const double* d_weight, float* d_grad, double* d_loss, void* stream);
+
 /* CG with a learned warm start: x_hat = net(in_scale * b); x0 = alpha x_hat with
  * alpha = <x_hat, b> / <x_hat, G x_hat> (the G-norm-optimal scaling); if alpha is not
  * positive and finite, x0 = 0 (plain CG).  Then bsct_cg_solve from x0 with the given
@@ -368,6 +414,21 @@ int bsct_pcg_solve_learned(bsct_gram* g, bsct_unet* net, double eps, const void*
 int bsct_fcg_solve_learned(bsct_gram* g, bsct_unet* net, const void* d_b, void* d_x, float in_scale, int max_iter,
                            double rel_tol, int precond_every, bsct_cg_report* report, int32_t* n_precond,
                            int32_t* n_fallback, void* stream);
+
+/* Non-finite input values (NaN, +-Inf).  The synchronous solvers (cg_solve, sd_solve,
+ * pcg_solve, solve_graph, cg_solve_mixed and the learned variants) find a non-finite
+ * right-hand side or initial guess in <b, b> / <r, r> before their first iteration and
+ * a non-finite residual at their synchronisation points, and return BSCT_ERR_NONFINITE.
+ * The asynchronous calls cannot return what their kernels find: bsct_gram_apply,
+ * bsct_backproject and bsct_forward_project set a per-device input status when their
+ * input (x, the sinogram, the coefficients) holds a non-finite value, and still run.
+ * bsct_input_status synchronises `stream`, then reads and clears that status: it returns
+ * BSCT_ERR_NONFINITE if such an input was seen by work completed since the last call,
+ * else BSCT_OK.  (The status is shared by all streams of the device.)
+ * bsct_check_finite checks n values of a caller buffer (float for BSCT_F32, double for
+ * BSCT_F64) and returns BSCT_ERR_NONFINITE or BSCT_OK (synchronous). */
+int bsct_input_status(void* stream);
+int bsct_check_finite(const void* d_buf, int64_t n, int precision, void* stream);
 
 /* Human-readable text of a status code, and of the last failure on this thread. */
 const char* bsct_status_string(int status);

@@ -67,6 +67,43 @@ class _Conv3(torch.autograd.Function):
         return dx, dw, db
 
 
+class _Conv3Linear(torch.autograd.Function):
+    """The 3x3 convolution without its ReLU (the same rounding points as _Conv3)."""
+
+    @staticmethod
+    def forward(ctx, x, w, b):
+        xr, wr = bf16(x), bf16(w)
+        ctx.save_for_backward(xr, wr)
+        return F.conv2d(xr, wr, b, padding=1)
+
+    @staticmethod
+    def backward(ctx, g):
+        xr, wr = ctx.saved_tensors
+        db = g.sum(dim=(0, 2, 3))
+        dr = bf16(g)
+        dx = torch.nn.grad.conv2d_input(xr.shape, wr, dr, padding=1)
+        dw = torch.nn.grad.conv2d_weight(xr, wr.shape, dr, padding=1)
+        return dx, dw, db
+
+
+def layer_grads(kind, x, w, b, gout, relu=True):
+    """One layer of the network on its own (kind "conv3" or "tconv2"): returns
+    (out, d x, d w, d b) for the output gradient gout, all float64, with the library's
+    rounding points.  x [n, cin, H, W]; w in torch layout ([cout, cin, 3, 3] or
+    [cin, cout, 2, 2]); b [cout]."""
+    xv = x.detach().clone().requires_grad_()
+    wv = w.detach().clone().requires_grad_()
+    bv = b.detach().clone().requires_grad_()
+    if kind == "conv3":
+        out = (_Conv3 if relu else _Conv3Linear).apply(xv, wv, bv)
+    elif kind == "tconv2":
+        out = _TConv.apply(xv, wv, bv)
+    else:
+        raise ValueError(kind)
+    out.backward(gout)
+    return out.detach(), xv.grad, wv.grad, bv.grad
+
+
 class _TConv(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x, w, b):

@@ -19,7 +19,7 @@ import numpy as np
 
 __all__ = [
     "F32", "F64", "Geometry", "GramFilter", "gram_build", "gram_apply", "backproject", "forward_project", "cg_solve",
-    "library_path", "lib", "supported_size", "launch_count",
+    "library_path", "lib", "supported_size", "launch_count", "input_status", "check_finite",
 ]
 
 F32 = 0
@@ -149,6 +149,21 @@ def _declare(L):
     L.bsct_set_launch_overlap.restype = ctypes.c_int
     L.bsct_launch_count.argtypes = []
     L.bsct_launch_count.restype = ctypes.c_uint64
+    L.bsct_conv3x3_forward.argtypes = [i32, i32, i32, i32, i32, vp, vp, vp, ctypes.c_int, vp, vp]
+    L.bsct_conv3x3_backward.argtypes = [i32, i32, i32, i32, i32, vp, vp, vp, vp, ctypes.c_int, vp, vp, vp, vp]
+    L.bsct_tconv2x2_forward.argtypes = [i32, i32, i32, i32, i32, vp, vp, vp, vp, vp]
+    L.bsct_tconv2x2_backward.argtypes = [i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
+    for name in ("bsct_conv3x3_forward", "bsct_conv3x3_backward", "bsct_tconv2x2_forward",
+                 "bsct_tconv2x2_backward"):
+        getattr(L, name).restype = ctypes.c_int
+    L.bsct_gnorm_loss_grad.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
+    L.bsct_gnorm_loss_grad.restype = ctypes.c_int
+    L.bsct_set_gemm_path.argtypes = [ctypes.c_int]
+    L.bsct_set_gemm_path.restype = ctypes.c_int
+    L.bsct_input_status.argtypes = [vp]
+    L.bsct_input_status.restype = ctypes.c_int
+    L.bsct_check_finite.argtypes = [vp, ctypes.c_int64, ctypes.c_int, vp]
+    L.bsct_check_finite.restype = ctypes.c_int
     for name in ("bsct_gram_build", "bsct_gram_taps", "bsct_gram_spectrum", "bsct_gram_apply",
                  "bsct_backproject_workspace", "bsct_backproject", "bsct_cg_solve", "bsct_cg_begin",
                  "bsct_cg_iterate", "bsct_cg_residual"):
@@ -182,6 +197,85 @@ def supported_size(N):
 
 def launch_count():
     return int(lib().bsct_launch_count())
+
+
+ERR_NONFINITE = -5
+
+
+def input_status():
+    """Read and clear the library's input status (synchronises the current stream):
+    ERR_NONFINITE if a Gram apply, back projection or forward projection whose work has
+    completed met a non-finite input value since the last call, else OK."""
+    return int(lib().bsct_input_status(_stream()))
+
+
+def check_finite(t):
+    """True if every value of the CUDA tensor t (float32 or float64) is finite (synchronous)."""
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype not in (torch.float32, torch.float64):
+        raise TypeError("check_finite needs a float32 / float64 CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("check_finite needs a contiguous tensor")
+    prec = F32 if t.dtype == torch.float32 else F64
+    rc = lib().bsct_check_finite(ctypes.c_void_p(t.data_ptr()), int(t.numel()), prec, _stream())
+    if rc == ERR_NONFINITE:
+        return False
+    _check(rc, "bsct_check_finite")
+    return True
+
+
+def set_gemm_path(path):
+    """0: tcgen05 tensor-core GEMMs (default); 1: the warp-level mma.sync comparison path."""
+    _check(lib().bsct_set_gemm_path(int(path)), "bsct_set_gemm_path")
+
+
+def _fptr(t, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def conv3x3_layer(x, w, b, relu=True, gout=None):
+    """One 3x3 convolution layer of the learned CNN (bsct_conv3x3_forward / _backward).
+
+    x [cin, n, H, W], w [cout, kpad], b [cout] (float32 CUDA).  Returns out, and with gout
+    also (gin, gw, gb)."""
+    import torch
+
+    cin, n, H, W = x.shape
+    cout = w.shape[0]
+    out = torch.empty((cout, n, H, W), dtype=torch.float32, device=x.device)
+    _check(lib().bsct_conv3x3_forward(n, cin, cout, H, W, _fptr(x, "x"), _fptr(w, "w"), _fptr(b, "b"),
+                                      1 if relu else 0, _fptr(out, "out"), _stream()), "bsct_conv3x3_forward")
+    if gout is None:
+        return out
+    gin, gw, gb = torch.empty_like(x), torch.empty_like(w), torch.empty_like(b)
+    _check(lib().bsct_conv3x3_backward(n, cin, cout, H, W, _fptr(x, "x"), _fptr(w, "w"), _fptr(out, "out"),
+                                       _fptr(gout, "gout"), 1 if relu else 0, _fptr(gin, "gin"), _fptr(gw, "gw"),
+                                       _fptr(gb, "gb"), _stream()), "bsct_conv3x3_backward")
+    return out, gin, gw, gb
+
+
+def tconv2x2_layer(x, w, b, gout=None):
+    """One 2x2 stride-2 transposed convolution of the learned CNN: x [cin, n, H, W],
+    w [cout * 4, cin], b [cout].  Returns out [cout, n, 2H, 2W], and with gout (gin, gw, gb)."""
+    import torch
+
+    cin, n, H, W = x.shape
+    cout = w.shape[0] // 4
+    out = torch.empty((cout, n, 2 * H, 2 * W), dtype=torch.float32, device=x.device)
+    _check(lib().bsct_tconv2x2_forward(n, cin, cout, H, W, _fptr(x, "x"), _fptr(w, "w"), _fptr(b, "b"),
+                                       _fptr(out, "out"), _stream()), "bsct_tconv2x2_forward")
+    if gout is None:
+        return out
+    gin, gw, gb = torch.empty_like(x), torch.empty_like(w), torch.empty_like(b)
+    _check(lib().bsct_tconv2x2_backward(n, cin, cout, H, W, _fptr(x, "x"), _fptr(w, "w"), _fptr(gout, "gout"),
+                                        _fptr(gin, "gin"), _fptr(gw, "gw"), _fptr(gb, "gb"), _stream()),
+           "bsct_tconv2x2_backward")
+    return out, gin, gw, gb
 
 
 def set_kernel_timing(on):
@@ -676,6 +770,19 @@ def mse_loss_grad(pred, target, grad, loss_acc):
     _check(lib().bsct_mse_loss_grad(ctypes.c_void_p(pred.data_ptr()), ctypes.c_void_p(target.data_ptr()), n,
                                     ctypes.c_void_p(grad.data_ptr()), _dev(loss_acc, (1,), torch.float64, "loss"),
                                     _stream()), "bsct_mse_loss_grad")
+
+
+def gnorm_loss_grad(gram, pred, target, grad, loss_acc, weight=None):
+    """G-norm loss of a batch [n, N, N]: loss_acc += (1/n) sum_i w_i <e_i, G e_i>, grad_i = (2 w_i / n) G e_i
+    (e = pred - target, G the handle's Gram filter; weight: n FP64 device values or None)."""
+    import torch
+
+    n, N = pred.shape[0], gram.N
+    pw = ctypes.c_void_p(0) if weight is None else _dev(weight, (n,), torch.float64, "weight")
+    _check(lib().bsct_gnorm_loss_grad(gram._h, _dev(pred, (n, N, N), torch.float32, "pred"),
+                                      _dev(target, (n, N, N), torch.float32, "target"), n, pw,
+                                      _dev(grad, (n, N, N), torch.float32, "grad"),
+                                      _dev(loss_acc, (1,), torch.float64, "loss"), _stream()), "bsct_gnorm_loss_grad")
 
 
 class Batch:

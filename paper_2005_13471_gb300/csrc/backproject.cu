@@ -690,6 +690,11 @@ extern "C" int bsct_backproject(const bsct_geom* geom, const void* d_sino, void*
   if (rc != BSCT_OK) return rc;
   if (work_bytes < bp_workspace(geom, precision)) { bsct_set_last_message("workspace too small"); return BSCT_ERR_INVALID_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
-  if (precision == BSCT_F32) return bp_run<float>(geom, (const float*)d_sino, (float*)d_b, (char*)d_work, st);
-  return bp_run<double>(geom, (const double*)d_sino, (double*)d_b, (char*)d_work, st);
+  const long ns = (long)geom->n_angles * geom->n_bins;  // non-finite samples set the input status
+  if (precision == BSCT_F32) {
+    rc = check_finite_async<float>((const float*)d_sino, ns, st);
+    return rc != BSCT_OK ? rc : bp_run<float>(geom, (const float*)d_sino, (float*)d_b, (char*)d_work, st);
+  }
+  rc = check_finite_async<double>((const double*)d_sino, ns, st);
+  return rc != BSCT_OK ? rc : bp_run<double>(geom, (const double*)d_sino, (double*)d_b, (char*)d_work, st);
 }

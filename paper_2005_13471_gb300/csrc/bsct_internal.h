@@ -142,6 +142,13 @@ template <typename T, int N> FftOps<T> fft_ops();
 template <typename T> bool fft_ops_for(int N, FftOps<T>* out);
 
 inline long fft_table_elems(int N) { return 8L * N; }
+
+// Non-finite input detection (status.cu): the device address of this device's status
+// words (word 0: the sticky flag read by bsct_input_status), and a check of n values of
+// p that sets status word `word` when one is not finite (asynchronous).
+unsigned int* input_status_ptr();
+unsigned int* timeout_status_ptr();  // word 2: a kernel's bounded wait gave up
+template <typename T> int check_finite_async(const T* p, long n, cudaStream_t st, int word = 0);
 // fill the 8N-entry twiddle array of size N (see FftOps)
 template <typename T> int build_fft_tables(cpx<T>* d_tw, int N, cudaStream_t st);
 
@@ -170,6 +177,11 @@ int dftgemm_apply(int N, const float* x, float* y, const float* Gt, const float2
                   cudaStream_t st);
 int gemm_bf16(bool ta, bool tb, int M, int N, int K, float alpha, const void* A, long lda, long sA, const void* B,
               long ldb, long sB, float beta, float* C, long ldc, long sC, int batch, cudaStream_t st);
+// the tcgen05 path (gemm_tc.cu); BSCT_ERR_UNSUPPORTED_SIZE when the copy engine cannot
+// describe the operands
+int gemm_bf16_tc(bool ta, bool tb, int M, int N, int K, float alpha, const void* A, long lda, long sA, const void* B,
+                 long ldb, long sB, float beta, float* C, long ldc, long sC, int batch, cudaStream_t st);
+extern int g_gemm_path;  // 0: tcgen05 (default), 1: warp-level mma.sync
 
 }  // namespace bsct
 

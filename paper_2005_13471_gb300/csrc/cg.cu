@@ -277,6 +277,20 @@ static int true_residual_t(bsct_gram* g, const T* b, const T* x, double* out, cu
   return BSCT_OK;
 }
 
+// A right-hand side or an initial guess holding a non-finite value shows in <b, b> or in
+// the initial <r, r>: the synchronous solvers stop before their first iteration.
+static int check_start(double rr, double bb) {
+  if (!isfinite(bb)) {
+    bsct_set_last_message("the right-hand side b holds a non-finite value");
+    return BSCT_ERR_NONFINITE;
+  }
+  if (!isfinite(rr)) {
+    bsct_set_last_message("the initial residual is not finite (x0 holds a non-finite value)");
+    return BSCT_ERR_NONFINITE;
+  }
+  return BSCT_OK;
+}
+
 // CG (steepest = false) or steepest descent (steepest = true): the same begin, state and
 // stopping rule; steepest descent is the CG iteration with beta held at 0
 static int krylov_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero, int max_iter, double rel_tol,
@@ -288,11 +302,10 @@ static int krylov_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero
   if (rc != BSCT_OK) return rc;
   double rr = 0.0, bb = 0.0;
   int it = 0, converged = 0;
-  if (rel_tol > 0.0) {
-    rc = bsct_cg_residual(g, &rr, &bb, stream);
-    if (rc != BSCT_OK) return rc;
-    if (bb == 0.0 || sqrt(rr / bb) <= rel_tol) converged = 1;
-  }
+  rc = bsct_cg_residual(g, &rr, &bb, stream);
+  if (rc != BSCT_OK) return rc;
+  if ((rc = check_start(rr, bb)) != BSCT_OK) return rc;
+  if (rel_tol > 0.0 && (bb == 0.0 || sqrt(rr / bb) <= rel_tol)) converged = 1;
   while (!converged && it < max_iter) {
     const int k = (rel_tol > 0.0) ? (check_every < max_iter - it ? check_every : max_iter - it) : max_iter - it;
     if (steepest)
@@ -311,6 +324,7 @@ static int krylov_solve(bsct_gram* g, const void* d_b, void* d_x, int x0_is_zero
   }
   rc = bsct_cg_residual(g, &rr, &bb, stream);
   if (rc != BSCT_OK) return rc;
+  if (!isfinite(rr)) { bsct_set_last_message("CG residual is not finite"); return BSCT_ERR_NONFINITE; }
   double tr = -1.0;
   if (rel_tol > 0.0) {
     rc = (g->precision == BSCT_F32) ? true_residual_t<float>(g, (const float*)d_b, (const float*)d_x, &tr, st)
@@ -352,6 +366,11 @@ extern "C" int bsct_cg_solve_mixed(bsct_gram* g, const void* d_b, void* d_x, int
   float* q = (float*)g->q;
   int rc = bsct_cg_begin(g, d_b, d_x, 1, stream);
   if (rc != BSCT_OK) return rc;
+  {
+    double rr0 = 0.0, bb0 = 0.0;
+    if ((rc = bsct_cg_residual(g, &rr0, &bb0, stream)) != BSCT_OK) return rc;
+    if ((rc = check_start(rr0, bb0)) != BSCT_OK) return rc;
+  }
   for (int it = 0; it < n_low; ++it) {
     k_p_update<float><<<nb, RED_THREADS, 0, st>>>(p, r, g->scal, n);
     count_launch();
@@ -372,6 +391,7 @@ extern "C" int bsct_cg_solve_mixed(bsct_gram* g, const void* d_b, void* d_x, int
   rc = bsct_cg_residual(g, &rr, &bb, stream);
   if (rc == BSCT_OK) rc = true_residual_t<float>(g, (const float*)d_b, (const float*)d_x, &tr, st);
   if (rc != BSCT_OK) return rc;
+  if (!isfinite(rr) || !isfinite(tr)) { bsct_set_last_message("residual is not finite"); return BSCT_ERR_NONFINITE; }
   if (report) {
     report->iterations = n_low + n_refine;
     report->converged = 0;
@@ -501,10 +521,9 @@ extern "C" int bsct_pcg_solve(bsct_gram* g, double eps, const void* d_b, void* d
   if (rc != BSCT_OK) return rc;
   double h[16];
   int it = 0, converged = 0;
-  if (rel_tol > 0.0) {
-    if ((rc = read_scalars(g, h, st)) != BSCT_OK) return rc;
-    if (h[SC_BB] == 0.0 || sqrt(h[SC_RRP] / h[SC_BB]) <= rel_tol) converged = 1;
-  }
+  if ((rc = read_scalars(g, h, st)) != BSCT_OK) return rc;
+  if ((rc = check_start(h[SC_RRP], h[SC_BB])) != BSCT_OK) return rc;
+  if (rel_tol > 0.0 && (h[SC_BB] == 0.0 || sqrt(h[SC_RRP] / h[SC_BB]) <= rel_tol)) converged = 1;
   while (!converged && it < max_iter) {
     const int k = (rel_tol > 0.0) ? (check_every < max_iter - it ? check_every : max_iter - it) : max_iter - it;
     rc = f32 ? pcg_iter_t<float>(g, (float*)d_x, k, st) : pcg_iter_t<double>(g, (double*)d_x, k, st);
@@ -521,6 +540,7 @@ extern "C" int bsct_pcg_solve(bsct_gram* g, double eps, const void* d_b, void* d
   }
   if ((rc = read_scalars(g, h, st)) != BSCT_OK) return rc;
   const double rr = h[SC_RRP], bb = h[SC_BB];
+  if (!isfinite(rr)) { bsct_set_last_message("PCG residual is not finite"); return BSCT_ERR_NONFINITE; }
   double tr = -1.0;
   if (rel_tol > 0.0) {
     rc = f32 ? true_residual_t<float>(g, (const float*)d_b, (const float*)d_x, &tr, st)
@@ -657,6 +677,7 @@ static int solve_graph_t(bsct_gram* g, int method, double eps, const T* b, T* x,
   const double rr = h[method == 1 ? SC_RRP : SC_RR], bb = h[SC_BB];
   unsigned long long its = 0;
   memcpy(&its, &h[SC_IT], sizeof(its));
+  if ((rc = check_start(0.0, bb)) != BSCT_OK) return rc;
   if (!isfinite(rr)) { bsct_set_last_message("residual is not finite"); return BSCT_ERR_NONFINITE; }
   const int converged = rel_tol > 0.0 && (bb == 0.0 || rr <= tol2 * bb);
   double tr = -1.0;

@@ -443,6 +443,11 @@ extern "C" int bsct_forward_project(const bsct_geom* geom, const void* d_coeffs,
   if (!d_coeffs || !d_sino || !d_work) { bsct_set_last_message("NULL device pointer"); return BSCT_ERR_INVALID_ARG; }
   if (work_bytes < fp_workspace(geom, precision)) { bsct_set_last_message("workspace too small"); return BSCT_ERR_INVALID_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
-  if (precision == BSCT_F32) return fp_run<float>(geom, (const float*)d_coeffs, (float*)d_sino, (char*)d_work, st);
-  return fp_run<double>(geom, (const double*)d_coeffs, (double*)d_sino, (char*)d_work, st);
+  const long nc = (long)geom->N * geom->N;  // non-finite coefficients set the input status
+  if (precision == BSCT_F32) {
+    rc = check_finite_async<float>((const float*)d_coeffs, nc, st);
+    return rc != BSCT_OK ? rc : fp_run<float>(geom, (const float*)d_coeffs, (float*)d_sino, (char*)d_work, st);
+  }
+  rc = check_finite_async<double>((const double*)d_coeffs, nc, st);
+  return rc != BSCT_OK ? rc : fp_run<double>(geom, (const double*)d_coeffs, (double*)d_sino, (char*)d_work, st);
 }

@@ -177,6 +177,8 @@ __global__ void __launch_bounds__(256) k_gemm_bf16(int M, int N, int K, float al
       }
 }
 
+int g_gemm_path = 0;
+
 int gemm_bf16(bool ta, bool tb, int M, int N, int K, float alpha, const void* A, long lda, long sA, const void* B,
               long ldb, long sB, float beta, float* C, long ldc, long sC, int batch, cudaStream_t st) {
   if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return BSCT_OK;
@@ -185,6 +187,10 @@ int gemm_bf16(bool ta, bool tb, int M, int N, int K, float alpha, const void* A,
     bsct_set_last_message("gemm_bf16: K, leading dimensions, batch strides (and M if trans_a, N unless trans_b) "
                           "must be multiples of 8");
     return BSCT_ERR_INVALID_ARG;
+  }
+  if (g_gemm_path == 0) {
+    const int rc = gemm_bf16_tc(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, st);
+    if (rc != BSCT_ERR_UNSUPPORTED_SIZE) return rc;
   }
   dim3 grid((N + GB_N - 1) / GB_N, (M + GB_M - 1) / GB_M, batch);
   const __nv_bfloat16* a = (const __nv_bfloat16*)A;
@@ -209,4 +215,13 @@ extern "C" int bsct_gemm_bf16(int trans_a, int trans_b, int32_t M, int32_t N, in
   }
   return bsct::gemm_bf16(trans_a != 0, trans_b != 0, M, N, K, alpha, d_A, lda, stride_a, d_B, ldb, stride_b, beta, d_C,
                          ldc, stride_c, batch, (cudaStream_t)stream);
+}
+
+extern "C" int bsct_set_gemm_path(int path) {
+  if (path != 0 && path != 1) {
+    bsct_set_last_message("GEMM path must be 0 (tcgen05) or 1 (mma.sync)");
+    return BSCT_ERR_INVALID_ARG;
+  }
+  bsct::g_gemm_path = path;
+  return BSCT_OK;
 }

@@ -576,6 +576,8 @@ extern "C" int bsct_gram_apply(const bsct_gram* g, const void* d_x, void* d_y, i
       BSCT_CUDA_TRY(cudaMalloc(&gm->dg_work, bytes));
       gm->dg_bytes = bytes;
     }
+    const int rc = check_finite_async<float>((const float*)d_x, (long)g->N * g->N, st);
+    if (rc != BSCT_OK) return rc;
     return dftgemm_apply(g->N, (const float*)d_x, (float*)d_y, g->Gt32, (const float2*)g->tw, gm->dg_work, st);
   }
   return fail(BSCT_ERR_INVALID_ARG, "unknown apply mode");

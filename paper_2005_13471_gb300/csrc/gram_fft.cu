@@ -17,6 +17,7 @@
 // ((row/4) * N + v) * 4 + row%4, so K5/K7 stream whole 4-row blocks and K6 reads
 // 32-byte row segments per column.
 #include "bsct_fft.cuh"
+#include "bsct_fft2.cuh"
 #include "bsct_internal.h"
 
 #ifndef BSCT_FFT_N
@@ -64,11 +65,13 @@ __device__ __forceinline__ long blk_index(int row, int col, int ncols) {
 // ------------------------------------------------------------------------------------
 // CG: the row is p_new = x + beta * p_old (x = the CG residual r), written to p_new
 // and transformed (the CG direction update fused into the first FFT pass)
+// status (may be null): a non-finite input value sets *status = 1 (the input check of
+// the public apply; one FMA per loaded value and a warp vote)
 template <typename T, int LR, bool PADDED, int RPC, bool CG = false>
 __global__ void __launch_bounds__(RPC * (LR / Plan<LR>::E))
 k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
            const cpx<T>* __restrict__ tsf, const cpx<T>* __restrict__ twc, const T* p_old = nullptr,
-           T* p_new = nullptr, const double* __restrict__ cg_beta = nullptr) {
+           T* p_new = nullptr, const double* __restrict__ cg_beta = nullptr, unsigned int* status = nullptr) {
   constexpr int E = Plan<LR>::E, TT = LR / E, R1 = Plan<LR>::R[0], RL = Plan<LR>::R[Plan<LR>::NS - 1];
   constexpr int SME = row_region<T, LR, RPC>();
   static_assert(R1 % 2 == 0, "zero-padding / crop split needs an even first radix");
@@ -85,6 +88,7 @@ k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
   const T beta = CG ? T(__ldcg(cg_beta)) : T(0);
 
   cpx<T> v[E];
+  T chk = T(0);  // stays 0 unless an input value is infinite or NaN (x * 0 = NaN)
 #pragma unroll
   for (int b = 0; b < E / R1; ++b) {
     const int j = tid + b * TT;
@@ -100,8 +104,12 @@ k_rows_r2c(const T* __restrict__ x, long ld_x, cpx<T>* __restrict__ S,
         v[b * R1 + r] = pn;
       } else {
         v[b * R1 + r] = ld_cpx_cg(z + j + r * (LR / R1));
+        if (status) chk = fma(v[b * R1 + r].y, T(0), fma(v[b * R1 + r].x, T(0), chk));
       }
     }
+  }
+  if (!CG && status) {
+    if (__any_sync(__activemask(), chk != chk) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);
   }
   fft<T, LR, false, false, PADDED>(v, sm, tid, tsf);
 #pragma unroll
@@ -457,6 +465,408 @@ k_cols_fwd_real(const cpx<T>* __restrict__ S2, T* __restrict__ Gt, const cpx<T>*
 }
 
 // ------------------------------------------------------------------------------------
+// FP32 path: the same three passes on the paired FFT of bsct_fft2.cuh.  Row passes
+// transform two image rows per group of threads (rows r, r+1 in the two lanes); the
+// column pass transforms columns v and v + N/2 of the half spectra together.  The half
+// spectra live as column pairs: S2[p * N + row] (p < N/2) holds (X_row[p], X_row[p + N/2])
+// in the lanes of one 16-byte value, X_row[0] being the packed (DC, Nyquist) pair.  The
+// untangling pairs bins v and LR - v (LR = N), and the set {v, LR - v, N/2 - v, N/2 + v}
+// is closed, so one item of the row passes produces or consumes whole column pairs.
+// ------------------------------------------------------------------------------------
+
+// shared words per image row in the row passes: the FFT buffer of a row pair (RS values of
+// 16 bytes) holds the two rows' regions of RS complex values each during the untangling;
+// RS = 16/RPC (mod 16) puts the RPC rows of one item group on distinct banks
+template <int LR, int RPC> __host__ __device__ constexpr int row_stride2() {
+  return smem_elems<LR>() + (((16 / RPC) % 16 - smem_elems<LR>() % 16) % 16 + 16) % 16;
+}
+template <int LR, int RPC> __host__ __device__ constexpr size_t rows_smem2() {
+  return (size_t)RPC * row_stride2<LR, RPC>() * sizeof(cpx<float>);
+}
+
+// untangling of one bin pair (v, LR - v) of a row, 0 < v < LR/2: Z = FFT(x_even + i x_odd)
+// -> X[v], X[LR - v] (half spectrum of the real row)
+__device__ __forceinline__ void untangle_fwd(cpx<float> Z, cpx<float> Zo, cpx<float> w, cpx<float>& Xv,
+                                             cpx<float>& Xm) {
+  const cpx<float> Zm = conj(Zo);
+  const cpx<float> Ev = scale(Z + Zm, 0.5f);
+  const cpx<float> WO = cmul(scale(mul_mi<float, false>(Z - Zm), 0.5f), w);
+  Xv = Ev + WO;
+  Xm = conj(Ev - WO);
+}
+// the inverse: half spectrum bins Y[v], Y[LR - v] -> row FFT inputs Zp[v], Zp[LR - v]
+__device__ __forceinline__ void untangle_inv(cpx<float> Y, cpx<float> Yo, cpx<float> w, cpx<float>& Zv,
+                                             cpx<float>& Zm) {
+  const cpx<float> Ym = conj(Yo);
+  const cpx<float> Ev = Y + Ym;
+  const cpx<float> iOd = mul_mi<float, true>(cmulc(Y - Ym, w));
+  Zv = Ev + iOd;
+  Zm = conj(Ev - iOd);
+}
+__device__ __forceinline__ void st_c2_lanes(c2* p, cpx<float> a, cpx<float> b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, b.x, a.y, b.y);
+}
+__device__ __forceinline__ void ld_c2_lanes(const c2* p, cpx<float>& a, cpx<float>& b) {
+  const float4 t = __ldcg(reinterpret_cast<const float4*>(p));
+  a = mk(t.x, t.z);
+  b = mk(t.y, t.w);
+}
+
+// K5 (FP32): real rows -> column-pair half spectra.  CG: the rows are p_new = x + beta p_old
+// (written back), as in k_rows_r2c.  status: see k_rows_r2c.
+template <int LR, int RPC, bool CG = false>
+__global__ void __launch_bounds__((RPC / 2) * (LR / Plan<LR>::E))
+k2_rows_r2c(const float* __restrict__ x, c2* __restrict__ S2, const cpx<float>* __restrict__ tsf,
+            const cpx<float>* __restrict__ twc, const float* p_old, float* p_new, const double* __restrict__ cg_beta,
+            unsigned int* status) {
+  constexpr int E = Plan<LR>::E, TT = LR / E, R1 = Plan<LR>::R[0], RL = Plan<LR>::R[Plan<LR>::NS - 1];
+  constexpr int RS = row_stride2<LR, RPC>(), NT = (RPC / 2) * TT, NR = LR;  // image rows = LR
+  static_assert(R1 % 2 == 0, "zero-padding split needs an even first radix");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  c2* smp = reinterpret_cast<c2*>(smraw);
+  cpx<float>* smr = reinterpret_cast<cpx<float>*>(smraw);
+  const int f = threadIdx.x / TT, tid = threadIdx.x % TT;
+  const int row0 = blockIdx.x * RPC;
+  c2* sm = smp + f * RS;
+  const cpx<float>* z0 = reinterpret_cast<const cpx<float>*>(x + (long)(row0 + 2 * f) * NR);
+  const cpx<float>* z1 = z0 + NR / 2;
+  pdl_trigger();
+  pdl_wait();
+  const float beta = CG ? float(__ldcg(cg_beta)) : 0.f;
+
+  c2 v[E];
+  float2 chk = make_float2(0.f, 0.f);  // stays 0 unless an input is infinite or NaN
+#pragma unroll
+  for (int b = 0; b < E / R1; ++b) {
+    const int j = tid + b * TT;
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      const int n = j + r * (LR / R1);
+      if (r >= R1 / 2) {
+        v[b * R1 + r] = c2zero();  // z[n] = 0 for n >= LR/2 (never read)
+      } else if constexpr (CG) {
+        const cpx<float>* q0 = reinterpret_cast<const cpx<float>*>(p_old + (long)(row0 + 2 * f) * NR);
+        cpx<float>* n0 = reinterpret_cast<cpx<float>*>(p_new + (long)(row0 + 2 * f) * NR);
+        const c2 a = c2pack(ld_cpx_cg(z0 + n), ld_cpx_cg(z1 + n));
+        const c2 pp = c2pack(ld_cpx_cg(q0 + n), ld_cpx_cg(q0 + NR / 2 + n));
+        const c2 pn = c2{fma2(bc2(beta), pp.re, a.re), fma2(bc2(beta), pp.im, a.im)};
+        st_cpx(n0 + n, c2lane0(pn));
+        st_cpx(n0 + NR / 2 + n, c2lane1(pn));
+        v[b * R1 + r] = pn;
+      } else {
+        v[b * R1 + r] = c2pack(ld_cpx_cg(z0 + n), ld_cpx_cg(z1 + n));
+        chk = fma2(v[b * R1 + r].im, bc2(0.f), fma2(v[b * R1 + r].re, bc2(0.f), chk));
+      }
+    }
+  }
+  if (!CG && status) {
+    const bool bad = chk.x != chk.x || chk.y != chk.y;
+    if (__any_sync(__activemask(), bad) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);
+  }
+  fft2<LR, false, false, true>(v, sm, tid, tsf);
+  // outputs in natural order, one region per row
+  cpx<float>* ra = smr + (2 * f) * RS;
+  cpx<float>* rb = ra + RS;
+#pragma unroll
+  for (int b = 0; b < E / RL; ++b) {
+    const int j = tid + b * TT;
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int k = spad(j + r * (LR / RL));
+      ra[k] = c2lane0(v[b * RL + r]);
+      rb[k] = c2lane1(v[b * RL + r]);
+    }
+  }
+  __syncthreads();
+  // items (row, v), v < LR/4: v = 0 makes column pairs 0 and LR/4, v > 0 makes pairs v and
+  // LR/2 - v; consecutive threads take consecutive rows (coalesced 16-byte stores)
+  constexpr int H = LR / 2, Q = LR / 4;
+#pragma unroll
+  for (int it = 0; it < E / 2; ++it) {
+    const int e = threadIdx.x + it * NT;
+    const int lr = e % RPC, vv = e / RPC, row = row0 + lr;
+    const cpx<float>* zr = smr + lr * RS;
+    if (vv == 0) {
+      const cpx<float> Z0 = zr[spad(0)], Zh = zr[spad(H)];
+      st_c2_lanes(S2 + row, mk(Z0.x + Z0.y, Z0.x - Z0.y), conj(Zh));  // (X[0], X[LR]) and X[LR/2]
+      cpx<float> Xq, X3q;
+      untangle_fwd(zr[spad(Q)], zr[spad(3 * Q)], ld_cpx(twc + Q), Xq, X3q);
+      st_c2_lanes(S2 + (long)Q * NR + row, Xq, X3q);
+    } else {
+      const int u = H - vv;
+      cpx<float> Xv, Xmv, Xu, Xmu;  // X[v], X[LR - v], X[u], X[LR - u] (LR - u = v + LR/2)
+      untangle_fwd(zr[spad(vv)], zr[spad(LR - vv)], ld_cpx(twc + vv), Xv, Xmv);
+      untangle_fwd(zr[spad(u)], zr[spad(LR - u)], ld_cpx(twc + u), Xu, Xmu);
+      st_c2_lanes(S2 + (long)vv * NR + row, Xv, Xmu);
+      st_c2_lanes(S2 + (long)u * NR + row, Xu, Xmv);
+    }
+  }
+}
+
+// K7 (FP32): column-pair half spectra -> real rows (first LR outputs of 2 LR).  RED as in
+// k_rows_c2r (p = the apply's input, for <p, y>).
+template <int LR, int RPC, int RED = RED_NONE>
+__global__ void __launch_bounds__((RPC / 2) * (LR / Plan<LR>::E))
+k2_rows_c2r(const c2* __restrict__ S2, float* __restrict__ y, const cpx<float>* __restrict__ tsr,
+            const cpx<float>* __restrict__ twc, const float* __restrict__ p, double* __restrict__ part,
+            double* __restrict__ sc) {
+  constexpr int E = Plan<LR>::E, TT = LR / E, R1 = Plan<LR>::R[0], RL = Plan<LR>::R[Plan<LR>::NS - 1];
+  constexpr int RS = row_stride2<LR, RPC>(), NT = (RPC / 2) * TT, NR = LR;
+  static_assert(R1 % 2 == 0, "crop split needs an even first radix");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  c2* smp = reinterpret_cast<c2*>(smraw);
+  cpx<float>* smr = reinterpret_cast<cpx<float>*>(smraw);
+  const int f = threadIdx.x / TT, tid = threadIdx.x % TT;
+  const int row0 = blockIdx.x * RPC;
+  c2* sm = smp + f * RS;
+  constexpr int H = LR / 2, Q = LR / 4;
+  pdl_trigger();
+  pdl_wait();
+  // inverse untangling straight from the column pairs (the loop is unrolled so that all
+  // loads of a thread are in flight together)
+#pragma unroll
+  for (int it = 0; it < E / 2; ++it) {
+    const int e = threadIdx.x + it * NT;
+    const int lr = e % RPC, vv = e / RPC, row = row0 + lr;
+    cpx<float>* zr = smr + lr * RS;
+    if (vv == 0) {
+      cpx<float> Y0, Yh, Yq, Y3q;
+      ld_c2_lanes(S2 + row, Y0, Yh);
+      ld_c2_lanes(S2 + (long)Q * NR + row, Yq, Y3q);
+      zr[spad(0)] = mk(Y0.x + Y0.y, Y0.x - Y0.y);
+      zr[spad(H)] = mk(Yh.x + Yh.x, -(Yh.y + Yh.y));
+      cpx<float> Zq, Z3q;
+      untangle_inv(Yq, Y3q, ld_cpx(twc + Q), Zq, Z3q);
+      zr[spad(Q)] = Zq;
+      zr[spad(3 * Q)] = Z3q;
+    } else {
+      const int u = H - vv;
+      cpx<float> Yv, Ymu, Yu, Ymv;  // pair v holds (Y[v], Y[LR - u]), pair u holds (Y[u], Y[LR - v])
+      ld_c2_lanes(S2 + (long)vv * NR + row, Yv, Ymu);
+      ld_c2_lanes(S2 + (long)u * NR + row, Yu, Ymv);
+      cpx<float> Zv, Zmv, Zu, Zmu;
+      untangle_inv(Yv, Ymv, ld_cpx(twc + vv), Zv, Zmv);
+      untangle_inv(Yu, Ymu, ld_cpx(twc + u), Zu, Zmu);
+      zr[spad(vv)] = Zv;
+      zr[spad(LR - vv)] = Zmv;
+      zr[spad(u)] = Zu;
+      zr[spad(LR - u)] = Zmu;
+    }
+  }
+  __syncthreads();
+  // the inverse runs the plan reversed: first radix RL, last radix R1 (crop: r < R1/2)
+  constexpr int RF = RL;
+  const cpx<float>* ra = smr + (2 * f) * RS;
+  const cpx<float>* rb = ra + RS;
+  c2 v[E];
+#pragma unroll
+  for (int b = 0; b < E / RF; ++b) {
+    const int j = tid + b * TT;
+#pragma unroll
+    for (int r = 0; r < RF; ++r) {
+      const int k = spad(j + r * (LR / RF));
+      v[b * RF + r] = c2pack(ra[k], rb[k]);
+    }
+  }
+  __syncthreads();
+  fft2<LR, true, true>(v, sm, tid, tsr);
+  cpx<float>* y0 = reinterpret_cast<cpx<float>*>(y + (long)(row0 + 2 * f) * NR);
+  cpx<float>* y1 = y0 + NR / 2;
+  float dot = 0.f;
+#pragma unroll
+  for (int b = 0; b < E / R1; ++b) {
+    const int j = tid + b * TT;
+#pragma unroll
+    for (int r = 0; r < R1 / 2; ++r) {
+      const int n = j + r * (LR / R1);
+      const cpx<float> a = c2lane0(v[b * R1 + r]), c = c2lane1(v[b * R1 + r]);
+      st_cpx(y0 + n, a);
+      st_cpx(y1 + n, c);
+      if constexpr (RED != RED_NONE) {
+        const cpx<float>* p0 = reinterpret_cast<const cpx<float>*>(p + (long)(row0 + 2 * f) * NR);
+        const cpx<float> pa = ld_cpx_cg(p0 + n), pc = ld_cpx_cg(p0 + NR / 2 + n);
+        dot = fmaf(pa.x, a.x, fmaf(pa.y, a.y, dot));
+        dot = fmaf(pc.x, c.x, fmaf(pc.y, c.y, dot));
+      }
+    }
+  }
+  if constexpr (RED != RED_NONE) {
+    double d = (double)dot;
+    __syncthreads();  // the exchange buffer is free: reuse it for the partial sums
+    double* ws = reinterpret_cast<double*>(smraw);
+    if constexpr (NT % 32 == 0) {
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+      if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = d;
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        constexpr int NW = NT / 32;
+        double t = threadIdx.x < NW ? ws[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+      }
+    } else {
+      ws[threadIdx.x] = d;  // blocks of fewer than 32 threads
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < NT; ++i) t += ws[i];
+        part[blockIdx.x] = t;
+      }
+    }
+    last_block_sum(part, sc_counter(sc, SC_CNT_PQ), ws, [&](double t) {
+      if constexpr (RED == RED_ALPHA) {
+        sc[SC_PQ] = t;
+        sc[SC_ALPHA] = t > 0.0 ? __ldcg(sc + SC_RR) / t : 0.0;
+      } else {
+        const double rho = __ldcg(sc + SC_RR);
+        sc[SC_BETA] = rho > 0.0 ? t / rho : 0.0;
+        sc[SC_RR] = t;
+      }
+    });
+  }
+}
+
+// K6 (FP32): per column pair (v, v + N/2): forward 2N FFT of the N non-zero rows, times
+// the spectrum columns, inverse, keep rows < N; in place on S2.  Persistent CTAs walk over
+// tiles of G pairs; the spectrum rows of the next tile are copied into shared memory
+// (cp.async) while the current tile's inverse transform runs, and column data is read from
+// L2 (the row pass has just written it).
+template <int LC, int G> __host__ __device__ constexpr size_t cols_smem2() {
+  return (size_t)G * smem_elems<LC>() * sizeof(c2) + (size_t)G * 2 * LC * sizeof(float);
+}
+template <int LC, int G, int MINB>
+__global__ void __launch_bounds__(G*(LC / Plan<LC>::E), MINB)
+k2_cols_conv(c2* __restrict__ S2, const float* __restrict__ Gt, const cpx<float>* __restrict__ tsf,
+             const cpx<float>* __restrict__ tsr, int ntiles) {
+  constexpr int E = Plan<LC>::E, TT = LC / E, R1 = Plan<LC>::R[0], RL = Plan<LC>::R[Plan<LC>::NS - 1];
+  constexpr int NT = G * TT, NR = LC / 2, NP = LC / 4;  // image rows, column pairs
+  constexpr int SME = smem_elems<LC>();
+  static_assert(R1 % 2 == 0, "zero-padding / crop split needs an even first radix");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  c2* xsm = reinterpret_cast<c2*>(smraw);
+  float* stg = reinterpret_cast<float*>(xsm + G * SME);  // [G][2][LC]: spectrum rows v, v + N/2
+  const int g = threadIdx.x / TT, tid = threadIdx.x % TT;
+  c2* sm = xsm + g * SME;
+
+  auto prefetch_spec = [&](int tile) {
+    if (tile < ntiles) {
+      for (int q = threadIdx.x; q < G * 2 * (LC / 4); q += NT) {
+        const int c = q / (LC / 4), k = q % (LC / 4);  // c = 2 * gp + lane
+        const int pp = tile * G + c / 2;
+        const float* src = Gt + (long)(pp + (c & 1) * NP) * LC + 4 * k;
+        cp_async16(stg + (long)c * LC + 4 * k, src);
+      }
+    }
+    cp_async_commit();
+  };
+
+  // column data of a tile -> this group's exchange buffer at the padded positions the
+  // first stage reads (cp.async; every thread copies the 16-byte values it will read)
+  auto prefetch_cols = [&](int t) {
+    if (t < ntiles) {
+      const c2* src = S2 + (long)(t * G + g) * NR;
+#pragma unroll
+      for (int b = 0; b < E / R1; ++b) {
+        const int j = tid + b * TT;
+#pragma unroll
+        for (int r = 0; r < R1 / 2; ++r) cp_async16(sm + spad(j + r * (LC / R1)), src + j + r * (LC / R1));
+      }
+    }
+    cp_async_commit();
+  };
+
+  int tile = blockIdx.x;
+  pdl_trigger();
+  constexpr bool TWREG = plan_palindrome<LC>();
+  TwCache<float, LC> twr;
+  if constexpr (TWREG) tw_cache_load<float, LC, false>(twr, tid, tsf);
+  pdl_wait();
+  prefetch_cols(tile);
+  prefetch_spec(tile);
+  // cp.async groups in commit order: cols(t0), spec(t0), then per tile spec(t+1), cols(t+1).
+  // The first tile waits for its column data only (its spectrum arrives during the forward
+  // transform); later tiles' groups both had the previous inverse transform to arrive.
+  bool first = true;
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int pr = tile * G + g;  // column pair of this thread group
+    if (first) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    first = false;
+    __syncthreads();
+    c2 v[E];
+#pragma unroll
+    for (int b = 0; b < E / R1; ++b) {
+      const int j = tid + b * TT;
+#pragma unroll
+      for (int r = 0; r < R1; ++r)
+        v[b * R1 + r] = r < R1 / 2 ? ld_c2(sm + spad(j + r * (LC / R1))) : c2zero();  // rows >= N are zero
+    }
+    __syncthreads();  // the buffer is the first exchange's
+    if constexpr (TWREG) fft2_cached<LC, false, false, true>(v, sm, tid, tsf, twr);
+    else fft2<LC, false, false, true>(v, sm, tid, tsf);
+    cp_async_wait<0>();  // spectrum rows of this tile (already complete after the first tile)
+    __syncthreads();
+    const float* gs0 = stg + (long)(2 * g) * LC;
+    const float* gs1 = gs0 + LC;
+    if (tile == 0) {
+      // pair 0 (group 0 of tile 0): lane 0 is the packed (DC + i Nyquist) column and needs
+      // its value at -u; every group stages its values so that the barrier is uniform
+#pragma unroll
+      for (int b = 0; b < E / RL; ++b) {
+        const int j = tid + b * TT;
+#pragma unroll
+        for (int r = 0; r < RL; ++r) st_c2(sm + spad(j + r * (LC / RL)), v[b * RL + r]);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int b = 0; b < E / RL; ++b) {
+        const int j = tid + b * TT;
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const int u = j + r * (LC / RL);
+          const c2 Z = v[b * RL + r];
+          if (pr == 0) {
+            const int um = (u == 0) ? 0 : LC - u;
+            const c2 Zn = ld_c2(sm + spad(um));
+            const float P = gs0[u], Qv = Gt[(long)NR * LC + u], g1 = gs1[u];
+            v[b * RL + r] = c2{make_float2(P * Z.re.x + Qv * Zn.re.x, g1 * Z.re.y),
+                               make_float2(P * Z.im.x - Qv * Zn.im.x, g1 * Z.im.y)};
+          } else {
+            const float2 gv = make_float2(gs0[u], gs1[u]);
+            v[b * RL + r] = c2{mul2(Z.re, gv), mul2(Z.im, gv)};
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int b = 0; b < E / RL; ++b) {
+        const int j = tid + b * TT;
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const int u = j + r * (LC / RL);
+          const float2 gv = make_float2(gs0[u], gs1[u]);
+          v[b * RL + r] = c2{mul2(v[b * RL + r].re, gv), mul2(v[b * RL + r].im, gv)};
+        }
+      }
+    }
+    __syncthreads();  // spectrum staging (and, for pair 0, the exchange buffer) consumed
+    prefetch_spec(tile + gridDim.x);
+    // the next tile's column data starts arriving while the last inverse stage runs
+    auto next_cols = [&]() { prefetch_cols(tile + gridDim.x); };
+    if constexpr (TWREG) fft2_cached<LC, true, true>(v, sm, tid, tsr, twr, next_cols);
+    else fft2<LC, true, true>(v, sm, tid, tsr, next_cols);
+    c2* out = S2 + (long)pr * NR;
+#pragma unroll
+    for (int b = 0; b < E / R1; ++b) {
+      const int j = tid + b * TT;
+#pragma unroll
+      for (int r = 0; r < R1 / 2; ++r) st_c2(out + j + r * (LC / R1), v[b * R1 + r]);
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// ------------------------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------------------------
 template <typename K> static int set_smem(K kern, size_t bytes) {
@@ -519,6 +929,34 @@ template <typename T, int LR, int RP> __host__ __device__ constexpr bool rows_ok
   return RP >= 2 && (RP == 2 || RP % 4 == 0) && LR % RP == 0 && RP * (LR / Plan<LR>::E) <= 1024 &&
          (size_t)RP * row_region<T, LR, RP>() * sizeof(cpx<T>) <= 227 * 1024;
 }
+// FP32 (paired) row passes: about 256 threads per CTA forward (two rows per LR/E threads);
+// long rows go one pair per CTA in the inverse pass
+template <int LR> __host__ __device__ constexpr int rows_per_cta2() {
+  return (512 / (LR / Plan<LR>::E)) < 2 ? 2 : ((512 / (LR / Plan<LR>::E)) > LR ? LR : (512 / (LR / Plan<LR>::E)));
+}
+template <int LR> __host__ __device__ constexpr int rows_per_cta_inv2() {
+  return (LR / Plan<LR>::E) >= 64 ? 2 : rows_per_cta2<LR>();
+}
+template <int LR, int RP> __host__ __device__ constexpr bool rows_ok2() {
+  return RP >= 2 && (RP == 2 || RP % 4 == 0) && LR % RP == 0 && (RP / 2) * (LR / Plan<LR>::E) <= 1024 &&
+         rows_smem2<LR, RP>() <= 227 * 1024;
+}
+template <typename T, int LR> __host__ __device__ constexpr int def_rows_fwd() {
+  return sizeof(T) == 4 ? rows_per_cta2<LR>() : rows_per_cta<LR>();
+}
+template <typename T, int LR> __host__ __device__ constexpr int def_rows_inv() {
+  return sizeof(T) == 4 ? rows_per_cta_inv2<LR>() : rows_per_cta_inv<LR>();
+}
+template <typename T, int LR, int RP> __host__ __device__ constexpr bool rows_valid() {
+  if constexpr (sizeof(T) == 4) return rows_ok2<LR, RP>();
+  else return rows_ok<T, LR, RP>();
+}
+template <int LC> struct ColsCfg2 {
+  static constexpr int TT = LC / Plan<LC>::E;
+  static constexpr int G = TT >= 256 ? 1 : (256 / TT > LC / 4 ? LC / 4 : 256 / TT);
+  static constexpr int MINB = cols_smem2<LC, G>() * 2 <= 227 * 1024 ? 2 : 1;
+};
+
 struct Shape {
   int fwd = 1, inv = 1, cols = 0;  // candidate indices; cols: 0 = occupancy limit, 1 = one CTA per SM
 };
@@ -566,10 +1004,11 @@ static int run_apply(const T* in, T* p, T* out, double* sc, double* part, cpx<T>
   if (MODE == AP_PLAIN) timer_mark(st, 0);
   if constexpr (MODE == AP_CG)
     BSCT_CUDA_TRY(launch_overlap(k5, dim3(N / RPC), dim3(TR), smr, st, in, (long)N, S, t.rows_f, t.untangle,
-                                 (const T*)p, p, (const double*)(sc + SC_BETA)));
+                                 (const T*)p, p, (const double*)(sc + SC_BETA), (unsigned int*)nullptr));
   else
     BSCT_CUDA_TRY(launch_overlap(k5, dim3(N / RPC), dim3(TR), smr, st, in, (long)N, S, t.rows_f, t.untangle,
-                                 (const T*)nullptr, (T*)nullptr, (const double*)nullptr));
+                                 (const T*)nullptr, (T*)nullptr, (const double*)nullptr,
+                                 MODE == AP_PLAIN ? input_status_ptr() : (unsigned int*)nullptr));
   if (MODE == AP_PLAIN) timer_mark(st, 1);
   BSCT_CUDA_TRY(launch_overlap(kc, dim3(grid_c), dim3(TC), smc, st, S, Gt, t.cols_f, t.cols_r, N / CC::G));
   if (MODE == AP_PLAIN) timer_mark(st, 2);
@@ -582,11 +1021,64 @@ static int run_apply(const T* in, T* p, T* out, double* sc, double* part, cpx<T>
   return BSCT_OK;
 }
 
+// FP32: the paired kernels (column-pair layout of S)
+template <int N, int MODE, int RPC, int RPI>
+static int run_apply2(const float* in, float* p, float* out, double* sc, double* part, cpx<float>* S, const float* Gt,
+                      const cpx<float>* tw, int cols, cudaStream_t st) {
+  constexpr int LR = N, LC = 2 * N;
+  typedef ColsCfg2<LC> CC;
+  static_assert((N / 2) % CC::G == 0, "tile must divide the column pairs");
+  constexpr int TR = (RPC / 2) * (LR / Plan<LR>::E), TI = (RPI / 2) * (LR / Plan<LR>::E);
+  constexpr int TC = CC::G * (LC / Plan<LC>::E);
+  constexpr size_t smr = rows_smem2<LR, RPC>(), smi = rows_smem2<LR, RPI>(), smc = cols_smem2<LC, CC::G>();
+  constexpr int RED = MODE == AP_CG ? RED_ALPHA : (MODE == AP_PC ? RED_RHO : RED_NONE);
+  auto k5 = k2_rows_r2c<LR, RPC, MODE == AP_CG>;
+  auto k7 = k2_rows_c2r<LR, RPI, RED>;
+  auto kc = k2_cols_conv<LC, CC::G, CC::MINB>;
+  static int per_sm_max[MAX_DEVICES] = {};
+  const int d = device_slot();
+  if (per_sm_max[d] == 0) {
+    int rc = set_smem(k5, smr);
+    if (rc == BSCT_OK) rc = set_smem(k7, smi);
+    if (rc == BSCT_OK) rc = set_smem(kc, smc);
+    if (rc != BSCT_OK) return rc;
+    int per_sm = 0;
+    BSCT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc, TC, smc));
+    per_sm_max[d] = per_sm < 1 ? 1 : per_sm;
+  }
+  const int per_sm = cols == 1 ? 1 : per_sm_max[d];
+  const int tiles = (N / 2) / CC::G;
+  const int grid_c = per_sm * sm_count() < tiles ? per_sm * sm_count() : tiles;
+  const TwPtrs<float> t = tw_ptrs<float, N>(tw);
+  c2* S2 = reinterpret_cast<c2*>(S);
+  const float* k7_in = MODE == AP_CG ? (const float*)p : (MODE == AP_PC ? in : (const float*)nullptr);
+  if (MODE == AP_PLAIN) timer_mark(st, 0);
+  if constexpr (MODE == AP_CG)
+    BSCT_CUDA_TRY(launch_overlap(k5, dim3(N / RPC), dim3(TR), smr, st, in, S2, t.rows_f, t.untangle, (const float*)p,
+                                 p, (const double*)(sc + SC_BETA), (unsigned int*)nullptr));
+  else
+    BSCT_CUDA_TRY(launch_overlap(k5, dim3(N / RPC), dim3(TR), smr, st, in, S2, t.rows_f, t.untangle,
+                                 (const float*)nullptr, (float*)nullptr, (const double*)nullptr,
+                                 MODE == AP_PLAIN ? input_status_ptr() : (unsigned int*)nullptr));
+  if (MODE == AP_PLAIN) timer_mark(st, 1);
+  BSCT_CUDA_TRY(launch_overlap(kc, dim3(grid_c), dim3(TC), smc, st, S2, Gt, t.cols_f, t.cols_r, tiles));
+  if (MODE == AP_PLAIN) timer_mark(st, 2);
+  BSCT_CUDA_TRY(launch_overlap(k7, dim3(N / RPI), dim3(TI), smi, st, (const c2*)S2, out, t.rows_r, t.untangle, k7_in,
+                               MODE == AP_PLAIN ? (double*)nullptr : part, MODE == AP_PLAIN ? (double*)nullptr : sc));
+  if (MODE == AP_PLAIN) timer_mark(st, 3);
+  count_launch(3);
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
 template <typename T, int N, int MODE, int RPC, int RPI>
 static int run_if_ok(const T* in, T* p, T* out, double* sc, double* part, cpx<T>* S, const T* Gt, const cpx<T>* tw,
                      int cols, cudaStream_t st) {
-  if constexpr (rows_ok<T, N, RPC>() && rows_ok<T, N, RPI>()) {
-    return run_apply<T, N, MODE, RPC, RPI>(in, p, out, sc, part, S, Gt, tw, cols, st);
+  if constexpr (rows_valid<T, N, RPC>() && rows_valid<T, N, RPI>()) {
+    if constexpr (sizeof(T) == 4)
+      return run_apply2<N, MODE, RPC, RPI>(in, p, out, sc, part, S, Gt, tw, cols, st);
+    else
+      return run_apply<T, N, MODE, RPC, RPI>(in, p, out, sc, part, S, Gt, tw, cols, st);
   } else {
     bsct_set_last_message("FFT launch shape not valid for this size");
     return BSCT_ERR_INVALID_ARG;
@@ -596,7 +1088,7 @@ static int run_if_ok(const T* in, T* p, T* out, double* sc, double* part, cpx<T>
 template <typename T, int N, int MODE>
 static int dispatch(const T* in, T* p, T* out, double* sc, double* part, cpx<T>* S, const T* Gt, const cpx<T>* tw,
                     cudaStream_t st) {
-  constexpr int DF = rows_per_cta<N>(), DI = rows_per_cta_inv<N>();
+  constexpr int DF = def_rows_fwd<T, N>(), DI = def_rows_inv<T, N>();
   const Shape sh = cur_shape<T>();
 #define BSCT_SHAPE(F_, I_)                                                                                      \
   case F_ * 3 + I_:                                                                                             \
@@ -635,13 +1127,13 @@ static int apply_pc_impl(const T* r, T* z, double* sc, double* part, cpx<T>* S, 
 
 // shapes: the three row-count candidates of each row pass (0 where not valid) ...
 template <typename T, int N> static void shape_cands(int fwd[3], int inv[3]) {
-  constexpr int DF = rows_per_cta<N>(), DI = rows_per_cta_inv<N>();
-  fwd[0] = rows_ok<T, N, shape_cand<DF>(0)>() ? shape_cand<DF>(0) : 0;
-  fwd[1] = rows_ok<T, N, shape_cand<DF>(1)>() ? shape_cand<DF>(1) : 0;
-  fwd[2] = rows_ok<T, N, shape_cand<DF>(2)>() ? shape_cand<DF>(2) : 0;
-  inv[0] = rows_ok<T, N, shape_cand<DI>(0)>() ? shape_cand<DI>(0) : 0;
-  inv[1] = rows_ok<T, N, shape_cand<DI>(1)>() ? shape_cand<DI>(1) : 0;
-  inv[2] = rows_ok<T, N, shape_cand<DI>(2)>() ? shape_cand<DI>(2) : 0;
+  constexpr int DF = def_rows_fwd<T, N>(), DI = def_rows_inv<T, N>();
+  fwd[0] = rows_valid<T, N, shape_cand<DF>(0)>() ? shape_cand<DF>(0) : 0;
+  fwd[1] = rows_valid<T, N, shape_cand<DF>(1)>() ? shape_cand<DF>(1) : 0;
+  fwd[2] = rows_valid<T, N, shape_cand<DF>(2)>() ? shape_cand<DF>(2) : 0;
+  inv[0] = rows_valid<T, N, shape_cand<DI>(0)>() ? shape_cand<DI>(0) : 0;
+  inv[1] = rows_valid<T, N, shape_cand<DI>(1)>() ? shape_cand<DI>(1) : 0;
+  inv[2] = rows_valid<T, N, shape_cand<DI>(2)>() ? shape_cand<DI>(2) : 0;
 }
 // ... and the current choice as candidate indices (get, or set after validation)
 template <typename T, int N> static int shape_index(int idx[3], int set) {

@@ -114,14 +114,15 @@ __device__ __forceinline__ float block_reduce(float v) {
   return t;
 }
 constexpr int CHUNK = 8192;
+// relu = 0: no mask (a layer without its ReLU)
 __global__ void k_relu_bwd(const float* __restrict__ g, const float* __restrict__ out, long P, bf16* __restrict__ dpre,
-                           float* __restrict__ db) {
+                           float* __restrict__ db, int relu = 1) {
   const int c = blockIdx.y;
   const long p0 = (long)blockIdx.x * CHUNK, p1 = p0 + CHUNK < P ? p0 + CHUNK : P;
   float acc = 0.f;
   for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     const long i = (long)c * P + p;
-    const float d = out[i] > 0.f ? g[i] : 0.f;
+    const float d = (!relu || out[i] > 0.f) ? g[i] : 0.f;
     dpre[i] = __float2bfloat16_rn(d);
     acc += d;
   }
@@ -232,6 +233,26 @@ __global__ void k_adam(float* __restrict__ w, float* __restrict__ g, float* __re
   w[i] = wi;
   wb[i] = __float2bfloat16_rn(wi);
   g[i] = 0.f;
+}
+
+// stream-ordered scratch of one call (freed at scope exit), and the layer shape checks
+struct LayerScratch {
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  bool ok = true;
+  template <typename T> T* get(long n) {
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, (size_t)(n > 0 ? n : 1) * sizeof(T), st) != cudaSuccess) { ok = false; return nullptr; }
+    ptrs.push_back(p);
+    return (T*)p;
+  }
+  ~LayerScratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+  }
+};
+bool layer_dims_ok(int n, int cin, int cout, int H, int W) {
+  return n >= 1 && cin >= 1 && cout >= 1 && H >= 1 && W >= 1 && cout % 8 == 0 && (long)n * H * W % 8 == 0 &&
+         (long)n * H * W * 9 * cin < (1L << 31);
 }
 
 // ---------------------------------------------------------------------------- network
@@ -876,6 +897,73 @@ extern "C" int bsct_mse_loss_grad(const float* d_pred, const float* d_target, in
   return BSCT_OK;
 }
 
+// G-norm loss of a batch of images (a training loss matched to what CG needs):
+//   loss += (1/n) sum_i w_i <e_i, G e_i>,  grad_i = (2 w_i / n) G e_i,  e_i = pred_i - target_i
+namespace {
+constexpr int GN_BLOCKS = 64;
+__global__ void k_sub(const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ c, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) c[i] = a[i] - b[i];
+}
+// part[img][blk] = partial <e_img, ge_img> (grid: GN_BLOCKS x n_img)
+__global__ void k_gn_dot(const float* __restrict__ e, const float* __restrict__ ge, long m, double* __restrict__ part) {
+  const long off = (long)blockIdx.y * m;
+  double acc = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long)gridDim.x * blockDim.x)
+    acc += (double)e[off + i] * (double)ge[off + i];
+  __shared__ double red[TPB / 32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < TPB / 32; ++w) t += red[w];
+    part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+// one thread: loss += (1/n) sum_i w_i sum_b part[i][b] (fixed order: reproducible)
+__global__ void k_gn_fin(const double* __restrict__ part, const double* __restrict__ w, int n, double* __restrict__ loss) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double tot = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int b = 0; b < GN_BLOCKS; ++b) s += part[i * GN_BLOCKS + b];
+    tot += (w ? w[i] : 1.0) * s;
+  }
+  *loss += tot / n;
+}
+__global__ void k_gn_scale(float* __restrict__ g, const double* __restrict__ w, long m, int n) {
+  const long total = m * n;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x)
+    g[i] *= (float)(2.0 * (w ? w[i / m] : 1.0) / n);
+}
+}  // namespace
+
+extern "C" int bsct_gnorm_loss_grad(const bsct_gram* g, const float* d_pred, const float* d_target, int32_t n,
+                                    const double* d_weight, float* d_grad, double* d_loss, void* stream) {
+  if (!g || !d_pred || !d_target || !d_grad || !d_loss || n < 1 || g->precision != BSCT_F32) {
+    bsct_set_last_message("invalid argument (F32 handle, n >= 1, non-NULL buffers)");
+    return BSCT_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const long m = (long)g->N * g->N;
+  LayerScratch sc{st};
+  float* e = sc.get<float>(m * n);
+  double* part = sc.get<double>((long)GN_BLOCKS * n);
+  if (!sc.ok) { bsct_set_last_message("out of device memory"); return BSCT_ERR_CUDA; }
+  k_sub<<<nblk(m * n) < 4096 ? nblk(m * n) : 4096, TPB, 0, st>>>(d_pred, d_target, e, m * n);
+  count_launch();
+  for (int i = 0; i < n; ++i) {
+    const int rc = bsct_gram_apply(g, e + (long)i * m, d_grad + (long)i * m, BSCT_APPLY_FFT32, stream);
+    if (rc != BSCT_OK) return rc;
+  }
+  k_gn_dot<<<dim3(GN_BLOCKS, n), TPB, 0, st>>>(e, d_grad, m, part);
+  k_gn_fin<<<1, 32, 0, st>>>(part, d_weight, n, d_loss);
+  k_gn_scale<<<nblk(m * n) < 4096 ? nblk(m * n) : 4096, TPB, 0, st>>>(d_grad, d_weight, m, n);
+  count_launch(3);
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
 // copy the FP32 parameters (which = 0) or gradients (which = 1) to / from caller memory
 extern "C" int bsct_unet_copy(bsct_unet* u, int which, int to_net, float* d_buf, void* stream) {
   if (!u || !d_buf || which < 0 || which > 1) { bsct_set_last_message("invalid argument"); return BSCT_ERR_INVALID_ARG; }
@@ -887,5 +975,113 @@ extern "C" int bsct_unet_copy(bsct_unet* u, int which, int to_net, float* d_buf,
   } else {
     BSCT_CUDA_TRY(cudaMemcpyAsync(d_buf, net, u->n_params * 4, cudaMemcpyDeviceToDevice, st));
   }
+  return BSCT_OK;
+}
+
+// ---------------------------------------------------------------------------- single layers
+// The network's layers on their own (for checking them one by one against the oracle):
+// the same kernels and GEMMs, with scratch from the stream-ordered allocator.
+
+extern "C" int bsct_conv3x3_forward(int32_t n, int32_t cin, int32_t cout, int32_t H, int32_t W, const float* d_in,
+                                    const float* d_w, const float* d_b, int relu, float* d_out, void* stream) {
+  if (!d_in || !d_w || !d_b || !d_out || !layer_dims_ok(n, cin, cout, H, W)) {
+    bsct_set_last_message("invalid layer arguments (cout and n H W must be multiples of 8)");
+    return BSCT_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int kpad = ((9 * cin + 7) / 8) * 8;
+  const long P = (long)n * H * W;
+  LayerScratch sc{st};
+  bf16* wb = sc.get<bf16>((long)cout * kpad);
+  bf16* col = sc.get<bf16>((long)kpad * P);
+  if (!sc.ok) { bsct_set_last_message("out of device memory"); return BSCT_ERR_CUDA; }
+  k_to_bf16<<<nblk((long)cout * kpad), TPB, 0, st>>>(d_w, wb, (long)cout * kpad);
+  k_im2col3<<<nblk((long)kpad * P), TPB, 0, st>>>(d_in, cin, n, H, W, kpad, col);
+  count_launch(2);
+  UTRY(bsct::gemm_bf16(false, false, cout, (int)P, kpad, 1.f, wb, kpad, 0, col, P, 0, 0.f, d_out, P, 0, 1, st));
+  k_bias_relu<<<nblk((long)cout * P), TPB, 0, st>>>(d_out, d_b, cout, P, relu ? 1 : 0);
+  count_launch();
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+extern "C" int bsct_conv3x3_backward(int32_t n, int32_t cin, int32_t cout, int32_t H, int32_t W, const float* d_in,
+                                     const float* d_w, const float* d_out, const float* d_gout, int relu, float* d_gin,
+                                     float* d_gw, float* d_gb, void* stream) {
+  if (!d_in || !d_w || !d_gout || !d_gw || !d_gb || (relu && !d_out) || !layer_dims_ok(n, cin, cout, H, W)) {
+    bsct_set_last_message("invalid layer arguments (cout and n H W must be multiples of 8)");
+    return BSCT_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int kpad = ((9 * cin + 7) / 8) * 8;
+  const long P = (long)n * H * W;
+  LayerScratch sc{st};
+  bf16* wb = sc.get<bf16>((long)cout * kpad);
+  bf16* col = sc.get<bf16>((long)kpad * P);
+  bf16* dpre = sc.get<bf16>((long)cout * P);
+  float* dcol = d_gin ? sc.get<float>((long)kpad * P) : nullptr;
+  if (!sc.ok) { bsct_set_last_message("out of device memory"); return BSCT_ERR_CUDA; }
+  BSCT_CUDA_TRY(cudaMemsetAsync(d_gb, 0, (size_t)cout * sizeof(float), st));
+  k_to_bf16<<<nblk((long)cout * kpad), TPB, 0, st>>>(d_w, wb, (long)cout * kpad);
+  k_relu_bwd<<<chan_grid(P, cout), TPB, 0, st>>>(d_gout, relu ? d_out : d_gout, P, dpre, d_gb, relu ? 1 : 0);
+  k_im2col3<<<nblk((long)kpad * P), TPB, 0, st>>>(d_in, cin, n, H, W, kpad, col);
+  count_launch(3);
+  UTRY(bsct::gemm_bf16(false, true, cout, kpad, (int)P, 1.f, dpre, P, 0, col, P, 0, 0.f, d_gw, kpad, 0, 1, st));
+  if (d_gin) {
+    UTRY(bsct::gemm_bf16(true, false, kpad, (int)P, cout, 1.f, wb, kpad, 0, dpre, P, 0, 0.f, dcol, P, 0, 1, st));
+    k_col2im3<<<nblk((long)cin * P), TPB, 0, st>>>(dcol, cin, n, H, W, d_gin);
+    count_launch();
+  }
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+extern "C" int bsct_tconv2x2_forward(int32_t n, int32_t cin, int32_t cout, int32_t H, int32_t W, const float* d_in,
+                                     const float* d_w, const float* d_b, float* d_out, void* stream) {
+  if (!d_in || !d_w || !d_b || !d_out || !layer_dims_ok(n, cin, cout, H, W) || cin % 8) {
+    bsct_set_last_message("invalid layer arguments (cin, cout and n H W must be multiples of 8)");
+    return BSCT_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const long P = (long)n * H * W;
+  LayerScratch sc{st};
+  bf16* wb = sc.get<bf16>((long)cout * 4 * cin);
+  bf16* inb = sc.get<bf16>((long)cin * P);
+  float* tmp = sc.get<float>((long)cout * 4 * P);
+  if (!sc.ok) { bsct_set_last_message("out of device memory"); return BSCT_ERR_CUDA; }
+  k_to_bf16<<<nblk((long)cout * 4 * cin), TPB, 0, st>>>(d_w, wb, (long)cout * 4 * cin);
+  k_to_bf16<<<nblk((long)cin * P), TPB, 0, st>>>(d_in, inb, (long)cin * P);
+  count_launch(2);
+  UTRY(bsct::gemm_bf16(false, false, cout * 4, (int)P, cin, 1.f, wb, cin, 0, inb, P, 0, 0.f, tmp, P, 0, 1, st));
+  k_tconv_scatter<<<nblk((long)cout * 4 * P), TPB, 0, st>>>(tmp, d_b, cout, n, H, W, d_out);
+  count_launch();
+  BSCT_CUDA_TRY(cudaGetLastError());
+  return BSCT_OK;
+}
+
+extern "C" int bsct_tconv2x2_backward(int32_t n, int32_t cin, int32_t cout, int32_t H, int32_t W, const float* d_in,
+                                      const float* d_w, const float* d_gout, float* d_gin, float* d_gw, float* d_gb,
+                                      void* stream) {
+  if (!d_in || !d_w || !d_gout || !d_gw || !d_gb || !layer_dims_ok(n, cin, cout, H, W) || cin % 8) {
+    bsct_set_last_message("invalid layer arguments (cin, cout and n H W must be multiples of 8)");
+    return BSCT_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const long P = (long)n * H * W;
+  LayerScratch sc{st};
+  bf16* wb = sc.get<bf16>((long)cout * 4 * cin);
+  bf16* gg = sc.get<bf16>((long)cout * 4 * P);
+  bf16* inb = sc.get<bf16>((long)cin * P);
+  if (!sc.ok) { bsct_set_last_message("out of device memory"); return BSCT_ERR_CUDA; }
+  BSCT_CUDA_TRY(cudaMemsetAsync(d_gb, 0, (size_t)cout * sizeof(float), st));
+  k_to_bf16<<<nblk((long)cout * 4 * cin), TPB, 0, st>>>(d_w, wb, (long)cout * 4 * cin);
+  k_tconv_gather<<<nblk((long)cout * 4 * P), TPB, 0, st>>>(d_gout, cout, n, H, W, gg);
+  k_to_bf16<<<nblk((long)cin * P), TPB, 0, st>>>(d_in, inb, (long)cin * P);
+  k_chan_sum<<<chan_grid(4 * P, cout), TPB, 0, st>>>(d_gout, 4 * P, d_gb);
+  count_launch(4);
+  UTRY(bsct::gemm_bf16(false, true, cout * 4, cin, (int)P, 1.f, gg, P, 0, inb, P, 0, 0.f, d_gw, cin, 0, 1, st));
+  if (d_gin)
+    UTRY(bsct::gemm_bf16(true, false, cin, (int)P, cout * 4, 1.f, wb, cin, 0, gg, P, 0, 0.f, d_gin, P, 0, 1, st));
+  BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
 }

@@ -60,10 +60,31 @@ def generate_pairs(n_pairs, N=256, n_angles=360, n_bins=364, zeta=1.0, I0=1e5, c
     return X, Y
 
 
-def train(net, X, Y, epochs=1, batch_size=8, lr=1e-3, lr_final=1e-4, seed=0, log_every=0):
-    """Adam on the mean-squared error; returns the list of per-step losses."""
+def gnorm_weights(gram, Y, chunk=64):
+    """Per-target weights 1 / <y, G y> (FP64, device) that make the G-norm loss relative."""
     import torch
 
+    n = Y.shape[0]
+    w = torch.empty(n, dtype=torch.float64, device=Y.device)
+    zero = torch.zeros((min(chunk, n),) + tuple(Y.shape[1:]), dtype=torch.float32, device=Y.device)
+    grad = torch.empty_like(zero)
+    acc = torch.zeros(1, dtype=torch.float64, device=Y.device)
+    for i in range(n):
+        acc.zero_()
+        bsct.gnorm_loss_grad(gram, Y[i:i + 1], zero[:1], grad[:1], acc)
+        w[i] = 1.0 / acc[0].clamp_min(1e-300)
+    return w
+
+
+def train(net, X, Y, epochs=1, batch_size=8, lr=1e-3, lr_final=1e-4, seed=0, log_every=0, loss="mse", gram=None,
+          weights=None):
+    """Adam on the mean-squared error (loss="mse") or on the relative G-norm error
+    <e, G e> / <y, G y> (loss="gnorm": the norm CG minimises; gram = the Gram filter of the
+    training geometry, weights = gnorm_weights(gram, Y)); returns the per-step losses."""
+    import torch
+
+    if loss not in ("mse", "gnorm") or (loss == "gnorm" and (gram is None or weights is None)):
+        raise ValueError("loss must be 'mse', or 'gnorm' with gram and weights")
     n = X.shape[0]
     gen = torch.Generator(device="cpu").manual_seed(seed)
     steps_per_epoch = n // batch_size
@@ -80,7 +101,10 @@ def train(net, X, Y, epochs=1, batch_size=8, lr=1e-3, lr_final=1e-4, seed=0, log
             yb = Y.index_select(0, idx)
             pred = net.forward(xb)
             loss_acc.zero_()
-            bsct.mse_loss_grad(pred, yb, grad, loss_acc)
+            if loss == "mse":
+                bsct.mse_loss_grad(pred, yb, grad, loss_acc)
+            else:
+                bsct.gnorm_loss_grad(gram, pred.contiguous(), yb, grad, loss_acc, weights.index_select(0, idx))
             net.backward(grad)
             step += 1
             # cosine decay from lr to lr_final

@@ -103,3 +103,10 @@ def test_new_entry_points_validate_on_the_host(lib):
     assert lib.bsct_fft_set_shape(256, 0, ctypes.byref(sh)) == -1
     assert lib.bsct_fft_get_shape(100, 0, ctypes.byref(sh)) == -2
     assert lib.bsct_fft_autotune(256, 0, 0, None, None, None, None) == -1
+
+
+def test_check_finite_validates_on_the_host(lib):
+    # argument errors are returned before any CUDA call
+    assert lib.bsct_check_finite(None, 10, 0, None) == -1   # NULL buffer with values to check
+    assert lib.bsct_check_finite(None, -1, 0, None) == -1   # negative count
+    assert lib.bsct_check_finite(ctypes.c_void_p(16), 4, 7, None) == -1  # unknown precision

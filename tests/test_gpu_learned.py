@@ -143,3 +143,33 @@ def test_learned_warm_start_gain(bsct):
     g.close()
     net.close()
     bad.close()
+
+
+def test_gnorm_loss_against_oracle(bsct):
+    # the G-norm training loss: loss = (1/n) sum_i w_i <e_i, G e_i>, grad_i = (2 w_i / n) G e_i,
+    # e = pred - target, against the FP64 oracle's Gram apply on the same FP32 inputs
+    from oracle import gram as ogram
+
+    N, na, n = 64, 30, 3
+    angles = np.arange(na) / na
+    g = bsct.gram_build(bsct.Geometry(N, angles, 92, 1.0, 1.0), bsct.F32)
+    G = ogram.gram_taps(N, angles, 1.0)
+    gen = torch.Generator().manual_seed(11)
+    pred = torch.randn((n, N, N), generator=gen)
+    target = torch.randn((n, N, N), generator=gen)
+    w = torch.tensor([0.5, 1.0, 2.0], dtype=torch.float64)
+    grad = torch.empty((n, N, N), device=DEV)
+    loss = torch.zeros(1, dtype=torch.float64, device=DEV)
+    bsct.gnorm_loss_grad(g, pred.to(DEV), target.to(DEV), grad, loss, w.to(DEV))
+    e = (pred - target).double().numpy()
+    ge = np.stack([ogram.gram_apply_fft(G, e[i]) for i in range(n)])
+    ref_loss = sum(float(w[i]) * float((e[i] * ge[i]).sum()) for i in range(n)) / n
+    ref_grad = np.stack([2.0 * float(w[i]) / n * ge[i] for i in range(n)])
+    assert abs(float(loss.item()) - ref_loss) < 1e-5 * abs(ref_loss)
+    err = np.linalg.norm(grad.cpu().double().numpy() - ref_grad) / np.linalg.norm(ref_grad)
+    assert err < 1e-5
+    # accumulates, and runs in a fixed order: a second call adds the same value exactly
+    first = float(loss.item())
+    bsct.gnorm_loss_grad(g, pred.to(DEV), target.to(DEV), grad, loss, w.to(DEV))
+    assert float(loss.item()) == 2 * first
+    g.close()

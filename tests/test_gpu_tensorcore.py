@@ -1,9 +1,11 @@
 """Tensor-core paths: the BF16 GEMM building block and the split-BF16 DFT-GEMM Gram apply.
 
 GEMM: against an FP64 CPU product of the same BF16-rounded operands (FP32-accumulate
-tolerance 1e-5).  DFT-GEMM apply: error against the FP64 oracle is reported and gated
-at 2e-4 relative L2 (operands carry ~17 significant bits after the hi/lo split);
-refinement by FP32 residual CG steps must reach the FP32 path's residual.
+tolerance 1e-5).  DFT-GEMM apply: error against the FP64 oracle, gated at 2e-5
+relative L2: the hi/lo split keeps ~16 significant bits per operand (the dropped lo x lo
+product and the lo parts' own rounding are ~2^-16 relative per GEMM), and measured
+errors are 5-7e-6 over four GEMM stages; refinement by FP32 residual CG steps must reach
+the FP32 path's residual.
 """
 import numpy as np
 import pytest
@@ -27,19 +29,33 @@ def bsct():
     return m
 
 
+GEMM_SHAPES = [(128, 128, 64, 1),  # one CTA, one K tile: the smallest case of the tcgen05 kernel
+               (200, 136, 72, 2), (128, 256, 384, 1), (16, 8, 24, 3), (264, 520, 40, 1),
+               (32, 1024, 288, 1),  # U-Net level 0 (M < 128: the roles of A and B are exchanged)
+               (128, 2048, 384, 1),  # a DFT-GEMM stage (M = 2P, K = 6P)
+               (520, 392, 1032, 2)]  # ragged tiles in M, N and K, several K tiles, batches
+
+
+@pytest.mark.parametrize("path", [0, 1])  # 0: tcgen05 tensor cores, 1: warp-level mma.sync
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
-@pytest.mark.parametrize("M,N,K,batch", [(200, 136, 72, 2), (128, 256, 384, 1), (16, 8, 24, 3), (264, 520, 40, 1)])
-def test_gemm_bf16(bsct, ta, tb, M, N, K, batch):
+@pytest.mark.parametrize("M,N,K,batch", GEMM_SHAPES)
+def test_gemm_bf16(bsct, path, ta, tb, M, N, K, batch):
     g = torch.Generator().manual_seed(M * N + K)
     a = torch.randn((batch, K, M) if ta else (batch, M, K), generator=g).to(torch.bfloat16)
     b = torch.randn((batch, N, K) if tb else (batch, K, N), generator=g).to(torch.bfloat16)
     c0 = torch.randn((batch, M, N), generator=g)
-    c = bsct.gemm_bf16(a.to(DEV), b.to(DEV), c0.clone().to(DEV), trans_a=ta, trans_b=tb, alpha=0.5, beta=2.0)
+    bsct.set_gemm_path(path)
+    try:
+        c = bsct.gemm_bf16(a.to(DEV), b.to(DEV), c0.clone().to(DEV), trans_a=ta, trans_b=tb, alpha=0.5, beta=2.0)
+        torch.cuda.synchronize()
+    finally:
+        bsct.set_gemm_path(0)
     A = a.double().transpose(1, 2) if ta else a.double()
     B = b.double().transpose(1, 2) if tb else b.double()
     ref = 0.5 * torch.bmm(A, B) + 2.0 * c0.double()
     err = float((c.cpu().double() - ref).norm() / ref.norm())
     assert err < 1e-5
+    assert bsct.input_status() == bsct.OK  # no bounded wait gave up
 
 
 def test_gemm_rejects_misaligned(bsct):
@@ -61,7 +77,7 @@ def test_dftgemm_apply_error_vs_oracle(bsct, N):
     ref = ogram.gram_apply_fft(G, x.astype(np.float64))
     err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
     print(f"N={N} split-BF16 DFT-GEMM apply rel-L2 error vs FP64 oracle: {err:.3e}")
-    assert err < 2e-4
+    assert err < 2e-5
     y32 = g.apply(xd).cpu().numpy()
     assert np.linalg.norm(y32 - ref) / np.linalg.norm(ref) < err  # FP32 FFT is the more accurate path
     g.close()
@@ -77,7 +93,7 @@ def test_dftgemm_full_size_sampled(bsct):
     pts = [tuple(p) for p in np.random.default_rng(2).integers(0, N, size=(10, 2))]
     ref = ogram.gram_apply_sampled(G, x.astype(np.float64), pts)
     got = np.array([y[p] for p in pts])
-    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-4
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-5
     g.close()
 
 

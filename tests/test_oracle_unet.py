@@ -53,3 +53,42 @@ def test_whole_network_gradients(no_rounding):
         tm, hm = ounet.unpack(params - e, base)
         fd = float(((ounet.forward(x, tp, hp) - ounet.forward(x, tm, hm)) * gout).sum() / 2e-6)
         assert abs(fd - float(g[i])) < 1e-5 * max(1.0, abs(fd))
+
+
+def test_linear_conv_backward_matches_autograd(no_rounding):
+    g = torch.Generator().manual_seed(6)
+    x = torch.randn((2, 3, 5, 6), dtype=torch.float64, generator=g, requires_grad=True)
+    w = torch.randn((2, 3, 3, 3), dtype=torch.float64, generator=g, requires_grad=True)
+    b = torch.randn(2, dtype=torch.float64, generator=g, requires_grad=True)
+    assert torch.autograd.gradcheck(ounet._Conv3Linear.apply, (x, w, b))
+
+
+def test_layer_grads_by_finite_differences(no_rounding):
+    # the per-layer entry of the oracle against central differences of <out, gout>
+    g = torch.Generator().manual_seed(7)
+    for kind, wshape, relu in (("conv3", (3, 2, 3, 3), False), ("conv3", (3, 2, 3, 3), True),
+                               ("tconv2", (2, 3, 2, 2), False)):
+        x = torch.randn((2, 2, 4, 5), dtype=torch.float64, generator=g)
+        w = torch.randn(wshape, dtype=torch.float64, generator=g)
+        b = torch.randn(3, dtype=torch.float64, generator=g)
+        o = ounet.layer_grads(kind, x, w, b, torch.zeros(_out_shape(kind, x, w)), relu)[0]
+        gout = torch.randn(o.shape, dtype=torch.float64, generator=g)
+        _, dx, dw, db = ounet.layer_grads(kind, x, w, b, gout, relu)
+        f = lambda xx, ww, bb: float((ounet.layer_grads(kind, xx, ww, bb, torch.zeros(o.shape), relu)[0] * gout).sum())
+        for t, grad, name in ((x, dx, "x"), (w, dw, "w"), (b, db, "b")):
+            flat = t.reshape(-1)
+            for i in (0, flat.numel() // 2, flat.numel() - 1):
+                e = torch.zeros_like(flat)
+                e[i] = 1e-6
+                args = {"x": x, "w": w, "b": b}
+                args[name] = (flat + e).reshape(t.shape)
+                fp = f(args["x"], args["w"], args["b"])
+                args[name] = (flat - e).reshape(t.shape)
+                fm = f(args["x"], args["w"], args["b"])
+                fd = (fp - fm) / 2e-6
+                assert abs(fd - float(grad.reshape(-1)[i])) < 1e-6 * max(1.0, abs(fd)), (kind, name, i)
+
+
+def _out_shape(kind, x, w):
+    n, _, H, W = x.shape
+    return (n, w.shape[0], H, W) if kind == "conv3" else (n, w.shape[1], 2 * H, 2 * W)
