@@ -41,7 +41,10 @@ def parse():
     p.add_argument("--quick", action="store_true", help="skip the hot-path pass, batch and time-to-1e-4 extras")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--batch-slices", type=int, default=256)
-    p.add_argument("--learned-pairs", type=int, default=512, help="training pairs for the learned warm start (0 = skip)")
+    p.add_argument("--learned-pairs", type=int, default=10000,
+                   help="training pairs for the learned warm start (0 = skip; 10000 = the configured set)")
+    p.add_argument("--learned-loss", choices=["gnorm", "mse"], default="gnorm",
+                   help="training loss: relative G-norm error (the norm CG minimises) or mean squared error")
     p.add_argument("--workload", default=WORKLOAD, help="named workload of the timed steps (profiling runs use smaller ones)")
     p.add_argument("--learned-epochs", type=int, default=2)
     p.add_argument("--no-tune", action="store_true", help="keep the built-in FFT launch shapes (no autotuner)")
@@ -589,10 +592,26 @@ def run_ours(args):
                                             cg_iters=200, chunk=256, seed=rank)
             t_gen = time.perf_counter() - t_tr
             net = bsct.UNet(32, seed=rank)
+            g_tr, w_tr = None, None
+            if args.learned_loss == "gnorm":
+                g_tr = bsct.gram_build(bsct.Geometry.uniform(256, 360, 364, 1.0, 1.0), bsct.F32)
+                w_tr = learned.gnorm_weights(g_tr, Yl)
             losses = learned.train(net, Xl, Yl, epochs=args.learned_epochs, batch_size=8, lr=1e-3, lr_final=5e-5,
-                                   log_every=25)
+                                   log_every=25, loss=args.learned_loss, gram=g_tr, weights=w_tr)
             t_train = time.perf_counter() - t_tr - t_gen
+            if g_tr is not None:
+                g_tr.close()
             del Xl, Yl
+            # network inference alone (the warm start's fixed cost per solve)
+            xin = (b5s[0] / na5).unsqueeze(0).contiguous()
+            net.forward(xin)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(5):
+                net.forward(xin)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            infer_ms = e0.elapsed_time(e1) / 5
             g5.cg_solve_learned(net, b5s[0], 1.0 / na5, max_iter=5, rel_tol=0.0)
             warm = [timed(lambda: g5.cg_solve_learned(net, b, 1.0 / na5, max_iter=2000, rel_tol=1e-4,
                                                       check_every=5)) for b in b5s]
@@ -615,8 +634,9 @@ def run_ours(args):
                     "network_applications": [r["n_precond"] for _, (_, r) in fcg],
                     "fallbacks": [r["n_fallback"] for _, (_, r) in fcg],
                     "true_rel_residual_max": max(r["true_rel_residual"] for _, (_, r) in fcg)},
+                "inference_ms_n512": infer_ms,
                 "training": {"pairs": args.learned_pairs, "geometry": "N=256, 360 views, 364 bins, zeta=1",
-                             "target": "200-iteration CG", "epochs": args.learned_epochs,
+                             "target": "200-iteration CG", "epochs": args.learned_epochs, "loss": args.learned_loss,
                              "generate_s": t_gen, "train_s": t_train,
                              "loss_first_last": [losses[0], losses[-1]] if losses else None}})
             net.close()

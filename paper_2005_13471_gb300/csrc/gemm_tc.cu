@@ -30,9 +30,11 @@ namespace bsct {
 
 namespace tc {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4, THREADS = 128;
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3, THREADS = 128;
 constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+// (the epilogue reuses the stage ring for its per-warp 32 x 33 transposition tiles)
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+static_assert(4 * 32 * 33 * 4 <= STAGES * STAGE_BYTES, "epilogue tiles fit in the stage ring");
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -121,7 +123,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 // A_MN / B_MN: the operand tile is MN-major (M / N contiguous in memory); TRANS_C: the
 // accumulator rows are columns of C (roles of A and B exchanged by the host)
 template <bool A_MN, bool B_MN, bool TRANS_C>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS, 2)
 k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N, int K,
           float alpha, float beta, float* __restrict__ C, long ldc, long sC, int a_bcast, int b_bcast,
           unsigned int* status) {
@@ -221,29 +223,23 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
       if (!TRANS_C) {
-        const int m = m0 + row;
-        float* p = Cb + (long)m * ldc + n0 + c0;
-        if (m < M && n0 + c0 + 32 <= N && ((uintptr_t)p & 15) == 0) {
+        // transpose the warp's 32 x 32 chunk through shared memory (the free stage ring) so
+        // that every store instruction writes one row segment of 32 consecutive floats
+        float* t = reinterpret_cast<float*>(base) + warp * (32 * 33);
 #pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            float4 o = make_float4(alpha * v[j], alpha * v[j + 1], alpha * v[j + 2], alpha * v[j + 3]);
-            if (beta != 0.f) {
-              const float4 c = *reinterpret_cast<const float4*>(p + j);
-              o.x = fmaf(beta, c.x, o.x); o.y = fmaf(beta, c.y, o.y);
-              o.z = fmaf(beta, c.z, o.z); o.w = fmaf(beta, c.w, o.w);
-            }
-            *reinterpret_cast<float4*>(p + j) = o;
-          }
-        } else if (m < M) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int n = n0 + c0 + j;
-            if (n < N) {
-              float* p = Cb + (long)m * ldc + n;
-              *p = beta != 0.f ? fmaf(alpha, v[j], beta * *p) : alpha * v[j];
-            }
+        for (int j = 0; j < 32; ++j) t[lane * 33 + j] = v[j];
+        __syncwarp();
+        const int n = n0 + c0 + lane;
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+          const int m = m0 + warp * 32 + r;
+          if (m < M && n < N) {
+            float* p = Cb + (long)m * ldc + n;
+            const float o = alpha * t[r * 33 + lane];
+            *p = beta != 0.f ? fmaf(beta, *p, o) : o;
           }
         }
+        __syncwarp();
       } else {
         // accumulator (row = n, column = m): C[m][n]
         const int n = m0 + row;

@@ -52,51 +52,77 @@ __global__ void k_to_bf16(const float* __restrict__ a, bf16* __restrict__ b, lon
   if (i < n) b[i] = __float2bfloat16_rn(a[i]);
 }
 
-// col[(ci*9 + ky*3 + kx)][(n, y, x)] = in[ci][n][y+ky-1][x+kx-1] (zero outside), rows >= 9*C zero
-__global__ void k_im2col3(const float* __restrict__ in, int C, int NB, int H, int W, int Kpad, bf16* __restrict__ col) {
+// col[(ci*9 + ky*3 + kx)][(n, y, x)] = in[ci][n][y+ky-1][x+kx-1] (zero outside), rows >= 9*C zero.
+// Grid (NB*H, Kpad): one image row of one col row per block (indices from the block, no
+// per-element division); two x per thread, stored as one BF16 pair (W even)
+__global__ void k_im2col3(const float* __restrict__ in, int C, int NB, int H, int W, bf16* __restrict__ col) {
+  const int k = blockIdx.y, row = blockIdx.x;  // row = n H + y
   const long P = (long)NB * H * W;
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long)Kpad * P) return;
-  const int k = (int)(i / P);
-  const long p = i % P;
-  float v = 0.f;
-  if (k < 9 * C) {
-    const int ci = k / 9, ky = (k % 9) / 3, kx = k % 3;
-    const int x = (int)(p % W), y = (int)((p / W) % H);
-    const long nb = p / ((long)H * W);
-    const int yy = y + ky - 1, xx = x + kx - 1;
-    if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = in[((long)ci * NB + nb) * H * W + (long)yy * W + xx];
+  __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(col + (long)k * P + (long)row * W);
+  const int W2 = W >> 1;
+  if (k >= 9 * C) {
+    for (int x2 = threadIdx.x; x2 < W2; x2 += blockDim.x) dst[x2] = __floats2bfloat162_rn(0.f, 0.f);
+    return;
   }
-  col[i] = __float2bfloat16_rn(v);
+  const int ci = k / 9, r = k - 9 * ci, ky = r / 3, kx = r - 3 * ky;
+  const int nb = row / H, y = row - nb * H, yy = y + ky - 1;
+  const bool rowok = yy >= 0 && yy < H;
+  const float* src = in + ((long)ci * NB + nb) * H * W + (long)(rowok ? yy : 0) * W;
+  for (int x2 = threadIdx.x; x2 < W2; x2 += blockDim.x) {
+    const int xa = 2 * x2 + kx - 1, xb = xa + 1;
+    const float a = (rowok && xa >= 0 && xa < W) ? src[xa] : 0.f;
+    const float b = (rowok && xb >= 0 && xb < W) ? src[xb] : 0.f;
+    dst[x2] = __floats2bfloat162_rn(a, b);
+  }
+}
+inline int row_threads(int n) { return n >= 256 ? 256 : ((n + 31) / 32) * 32; }
+inline void launch_im2col3(const float* in, int C, int NB, int H, int W, int Kpad, bf16* col, cudaStream_t st) {
+  k_im2col3<<<dim3((unsigned)(NB * H), (unsigned)Kpad), row_threads(W / 2), 0, st>>>(in, C, NB, H, W, col);
 }
 
-// gin[ci][n][y][x] = sum_{ky,kx} dcol[(ci,ky,kx)][n][y-ky+1][x-kx+1]
+// gin[ci][n][y][x] = sum_{ky,kx} dcol[(ci,ky,kx)][n][y-ky+1][x-kx+1]; grid (NB*H, C), one image
+// row per block
 __global__ void k_col2im3(const float* __restrict__ dcol, int C, int NB, int H, int W, float* __restrict__ gin) {
+  const int ci = blockIdx.y, row = blockIdx.x;
+  const int nb = row / H, y = row - nb * H;
   const long P = (long)NB * H * W;
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long)C * P) return;
-  const int ci = (int)(i / P);
-  const long p = i % P;
-  const int x = (int)(p % W), y = (int)((p / W) % H);
-  const long base = p - (long)y * W - x;  // (n, 0, 0)
-  float acc = 0.f;
-  for (int ky = 0; ky < 3; ++ky) {
-    const int yy = y - ky + 1;
-    if (yy < 0 || yy >= H) continue;
-    for (int kx = 0; kx < 3; ++kx) {
-      const int xx = x - kx + 1;
-      if (xx < 0 || xx >= W) continue;
-      acc += dcol[(long)(ci * 9 + ky * 3 + kx) * P + base + (long)yy * W + xx];
+  const long base = (long)nb * H * W;
+  float* out = gin + (long)ci * P + (long)row * W;
+  for (int x = threadIdx.x; x < W; x += blockDim.x) {
+    float acc = 0.f;
+    for (int ky = 0; ky < 3; ++ky) {
+      const int yy = y - ky + 1;
+      if (yy < 0 || yy >= H) continue;
+      for (int kx = 0; kx < 3; ++kx) {
+        const int xx = x - kx + 1;
+        if (xx < 0 || xx >= W) continue;
+        acc += dcol[(long)(ci * 9 + ky * 3 + kx) * P + base + (long)yy * W + xx];
+      }
     }
+    out[x] = acc;
   }
-  gin[i] = acc;
+}
+inline void launch_col2im3(const float* dcol, int C, int NB, int H, int W, float* gin, cudaStream_t st) {
+  k_col2im3<<<dim3((unsigned)(NB * H), (unsigned)C), row_threads(W), 0, st>>>(dcol, C, NB, H, W, gin);
 }
 
+// a[c][p] = act(a[c][p] + b[c]); grid (chunks, C), four values per thread (P % 4 == 0)
 __global__ void k_bias_relu(float* __restrict__ a, const float* __restrict__ b, int C, long P, int relu) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long)C * P) return;
-  float v = a[i] + b[i / P];
-  a[i] = relu ? fmaxf(v, 0.f) : v;
+  const int c = blockIdx.y;
+  const float bc = b[c];
+  float4* row = reinterpret_cast<float4*>(a + (long)c * P);
+  const long P4 = P >> 2;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < P4; i += (long)gridDim.x * blockDim.x) {
+    float4 v = row[i];
+    v.x += bc; v.y += bc; v.z += bc; v.w += bc;
+    if (relu) { v.x = fmaxf(v.x, 0.f); v.y = fmaxf(v.y, 0.f); v.z = fmaxf(v.z, 0.f); v.w = fmaxf(v.w, 0.f); }
+    row[i] = v;
+  }
+}
+inline void launch_bias_relu(float* a, const float* b, int C, long P, int relu, cudaStream_t st) {
+  long bx = (P / 4 + TPB - 1) / TPB;
+  if (bx > 1024) bx = 1024;
+  k_bias_relu<<<dim3((unsigned)bx, (unsigned)C), TPB, 0, st>>>(a, b, C, P, relu);
 }
 
 // dpre = g * (out > 0) (BF16 for the GEMMs); db[c] += sum over the channel
@@ -167,31 +193,34 @@ __global__ void k_maxpool2_bwd(const float* __restrict__ in, const float* __rest
   gin[t] += gout[i];
 }
 
-// tmp[(co,dy,dx)][(n,y,x)] (+ b[co]) -> out[co][n][2y+dy][2x+dx]
+// tmp[(co,dy,dx)][(n,y,x)] (+ b[co]) -> out[co][n][2y+dy][2x+dx]; grid (NB*2H, Co), one output
+// row per block
 __global__ void k_tconv_scatter(const float* __restrict__ tmp, const float* __restrict__ b, int Co, int NB, int H,
                                 int W, float* __restrict__ out) {
+  const int co = blockIdx.y, orow = blockIdx.x;  // orow = n 2H + Y
+  const int nb = orow / (2 * H), Y = orow - nb * 2 * H, y = Y >> 1, dy = Y & 1;
   const long P = (long)NB * H * W;
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;  // over out
-  const long Pout = P * 4;
-  if (i >= (long)Co * Pout) return;
-  const int co = (int)(i / Pout);
-  const long q = i % Pout;
-  const int X = (int)(q % (2 * W)), Y = (int)((q / (2 * W)) % (2 * H));
-  const long nb = q / ((long)4 * H * W);
-  const int dy = Y & 1, dx = X & 1, y = Y >> 1, x = X >> 1;
-  out[i] = tmp[(long)(co * 4 + dy * 2 + dx) * P + nb * H * W + (long)y * W + x] + b[co];
+  const float bc = b[co];
+  const float* t0 = tmp + (long)(co * 4 + dy * 2) * P + (long)nb * H * W + (long)y * W;  // dx = 1: + P
+  float* o = out + (long)co * 4 * P + (long)orow * 2 * W;
+  for (int X = threadIdx.x; X < 2 * W; X += blockDim.x) o[X] = t0[(long)(X & 1) * P + (X >> 1)] + bc;
 }
-// gathered[(co,dy,dx)][(n,y,x)] = bf16(gout[co][n][2y+dy][2x+dx])
+inline void launch_tconv_scatter(const float* tmp, const float* b, int Co, int NB, int H, int W, float* out,
+                                 cudaStream_t st) {
+  k_tconv_scatter<<<dim3((unsigned)(NB * 2 * H), (unsigned)Co), row_threads(2 * W), 0, st>>>(tmp, b, Co, NB, H, W, out);
+}
+// gathered[(co,dy,dx)][(n,y,x)] = bf16(gout[co][n][2y+dy][2x+dx]); grid (NB*H, Co*4)
 __global__ void k_tconv_gather(const float* __restrict__ gout, int Co, int NB, int H, int W, bf16* __restrict__ g) {
+  const int r = blockIdx.y, row = blockIdx.x;  // row = n H + y
+  const int co = r >> 2, dy = (r >> 1) & 1, dx = r & 1;
+  const int nb = row / H, y = row - nb * H;
   const long P = (long)NB * H * W;
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long)Co * 4 * P) return;
-  const int r = (int)(i / P);
-  const long p = i % P;
-  const int co = r / 4, dy = (r % 4) / 2, dx = r % 2;
-  const int x = (int)(p % W), y = (int)((p / W) % H);
-  const long nb = p / ((long)H * W);
-  g[i] = __float2bfloat16_rn(gout[(long)co * 4 * P + nb * 4 * H * W + (long)(2 * y + dy) * (2 * W) + 2 * x + dx]);
+  const float* src = gout + (long)co * 4 * P + ((long)nb * 2 * H + 2 * y + dy) * 2 * W + dx;
+  bf16* d = g + (long)r * P + (long)row * W;
+  for (int x = threadIdx.x; x < W; x += blockDim.x) d[x] = __float2bfloat16_rn(src[2 * x]);
+}
+inline void launch_tconv_gather(const float* gout, int Co, int NB, int H, int W, bf16* g, cudaStream_t st) {
+  k_tconv_gather<<<dim3((unsigned)(NB * H), (unsigned)(Co * 4)), row_threads(W), 0, st>>>(gout, Co, NB, H, W, g);
 }
 
 // head: out[p] = sum_c w[c] a[c][p] + b
@@ -251,7 +280,7 @@ struct LayerScratch {
   }
 };
 bool layer_dims_ok(int n, int cin, int cout, int H, int W) {
-  return n >= 1 && cin >= 1 && cout >= 1 && H >= 1 && W >= 1 && cout % 8 == 0 && (long)n * H * W % 8 == 0 &&
+  return n >= 1 && cin >= 1 && cout >= 1 && H >= 1 && W >= 2 && W % 2 == 0 && cout % 8 == 0 && (long)n * H * W % 8 == 0 &&
          (long)n * H * W * 9 * cin < (1L << 31);
 }
 
@@ -380,11 +409,11 @@ int alloc_acts(bsct_unet* u, int NB, int H, int W) {
 
 int conv_fwd(bsct_unet* u, const Conv3& c, const float* in, int NB, int H, int W, float* out, cudaStream_t st) {
   const long P = (long)NB * H * W;
-  k_im2col3<<<nblk((long)c.kpad * P), TPB, 0, st>>>(in, c.cin, NB, H, W, c.kpad, u->col);
+  launch_im2col3(in, c.cin, NB, H, W, c.kpad, u->col, st);
   count_launch();
   UTRY(bsct::gemm_bf16(false, false, c.cout, (int)P, c.kpad, 1.f, u->wb + c.w, c.kpad, 0, u->col, P, 0, 0.f, out, P,
                        0, 1, st));
-  k_bias_relu<<<nblk((long)c.cout * P), TPB, 0, st>>>(out, u->w + c.b, c.cout, P, 1);
+  launch_bias_relu(out, u->w + c.b, c.cout, P, 1, st);
   count_launch();
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
@@ -395,7 +424,7 @@ int conv_bwd(bsct_unet* u, const Conv3& c, const float* in, const float* out, co
              float* gin, cudaStream_t st) {
   const long P = (long)NB * H * W;
   k_relu_bwd<<<chan_grid(P, c.cout), TPB, 0, st>>>(gout, out, P, u->dpre, u->g + c.b);
-  k_im2col3<<<nblk((long)c.kpad * P), TPB, 0, st>>>(in, c.cin, NB, H, W, c.kpad, u->col);
+  launch_im2col3(in, c.cin, NB, H, W, c.kpad, u->col, st);
   count_launch(2);
   // dW[cout][kpad] += dpre[cout][P] col[kpad][P]^T
   UTRY(bsct::gemm_bf16(false, true, c.cout, c.kpad, (int)P, 1.f, u->dpre, P, 0, u->col, P, 0, 1.f, u->g + c.w, c.kpad,
@@ -404,7 +433,7 @@ int conv_bwd(bsct_unet* u, const Conv3& c, const float* in, const float* out, co
     // dcol[kpad][P] = W^T dpre
     UTRY(bsct::gemm_bf16(true, false, c.kpad, (int)P, c.cout, 1.f, u->wb + c.w, c.kpad, 0, u->dpre, P, 0, 0.f, u->dcol,
                          P, 0, 1, st));
-    k_col2im3<<<nblk((long)c.cin * P), TPB, 0, st>>>(u->dcol, c.cin, NB, H, W, gin);
+    launch_col2im3(u->dcol, c.cin, NB, H, W, gin, st);
     count_launch();
   }
   BSCT_CUDA_TRY(cudaGetLastError());
@@ -418,7 +447,7 @@ int tconv_fwd(bsct_unet* u, const TConv& t, const float* in, int NB, int H, int 
   count_launch();
   UTRY(bsct::gemm_bf16(false, false, t.cout * 4, (int)P, t.cin, 1.f, u->wb + t.w, t.cin, 0, u->dpre, P, 0, 0.f, u->tmp,
                        P, 0, 1, st));
-  k_tconv_scatter<<<nblk((long)t.cout * 4 * P), TPB, 0, st>>>(u->tmp, u->w + t.b, t.cout, NB, H, W, out);
+  launch_tconv_scatter(u->tmp, u->w + t.b, t.cout, NB, H, W, out, st);
   count_launch();
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
@@ -429,7 +458,7 @@ int tconv_bwd(bsct_unet* u, const TConv& t, const float* in, const float* gout, 
   const long P = (long)NB * H * W;
   bf16* gg = u->dpre;                          // gathered gradient [(cout*4)][P]
   bf16* inb = u->col;                          // BF16 copy of the input [cin][P]
-  k_tconv_gather<<<nblk((long)t.cout * 4 * P), TPB, 0, st>>>(gout, t.cout, NB, H, W, gg);
+  launch_tconv_gather(gout, t.cout, NB, H, W, gg, st);
   k_to_bf16<<<nblk((long)t.cin * P), TPB, 0, st>>>(in, inb, (long)t.cin * P);
   k_chan_sum<<<chan_grid(4 * P, t.cout), TPB, 0, st>>>(gout, 4 * P, u->g + t.b);
   count_launch(3);
@@ -996,10 +1025,10 @@ extern "C" int bsct_conv3x3_forward(int32_t n, int32_t cin, int32_t cout, int32_
   bf16* col = sc.get<bf16>((long)kpad * P);
   if (!sc.ok) { bsct_set_last_message("out of device memory"); return BSCT_ERR_CUDA; }
   k_to_bf16<<<nblk((long)cout * kpad), TPB, 0, st>>>(d_w, wb, (long)cout * kpad);
-  k_im2col3<<<nblk((long)kpad * P), TPB, 0, st>>>(d_in, cin, n, H, W, kpad, col);
+  launch_im2col3(d_in, cin, n, H, W, kpad, col, st);
   count_launch(2);
   UTRY(bsct::gemm_bf16(false, false, cout, (int)P, kpad, 1.f, wb, kpad, 0, col, P, 0, 0.f, d_out, P, 0, 1, st));
-  k_bias_relu<<<nblk((long)cout * P), TPB, 0, st>>>(d_out, d_b, cout, P, relu ? 1 : 0);
+  launch_bias_relu(d_out, d_b, cout, P, relu ? 1 : 0, st);
   count_launch();
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
@@ -1024,12 +1053,12 @@ extern "C" int bsct_conv3x3_backward(int32_t n, int32_t cin, int32_t cout, int32
   BSCT_CUDA_TRY(cudaMemsetAsync(d_gb, 0, (size_t)cout * sizeof(float), st));
   k_to_bf16<<<nblk((long)cout * kpad), TPB, 0, st>>>(d_w, wb, (long)cout * kpad);
   k_relu_bwd<<<chan_grid(P, cout), TPB, 0, st>>>(d_gout, relu ? d_out : d_gout, P, dpre, d_gb, relu ? 1 : 0);
-  k_im2col3<<<nblk((long)kpad * P), TPB, 0, st>>>(d_in, cin, n, H, W, kpad, col);
+  launch_im2col3(d_in, cin, n, H, W, kpad, col, st);
   count_launch(3);
   UTRY(bsct::gemm_bf16(false, true, cout, kpad, (int)P, 1.f, dpre, P, 0, col, P, 0, 0.f, d_gw, kpad, 0, 1, st));
   if (d_gin) {
     UTRY(bsct::gemm_bf16(true, false, kpad, (int)P, cout, 1.f, wb, kpad, 0, dpre, P, 0, 0.f, dcol, P, 0, 1, st));
-    k_col2im3<<<nblk((long)cin * P), TPB, 0, st>>>(dcol, cin, n, H, W, d_gin);
+    launch_col2im3(dcol, cin, n, H, W, d_gin, st);
     count_launch();
   }
   BSCT_CUDA_TRY(cudaGetLastError());
@@ -1053,7 +1082,7 @@ extern "C" int bsct_tconv2x2_forward(int32_t n, int32_t cin, int32_t cout, int32
   k_to_bf16<<<nblk((long)cin * P), TPB, 0, st>>>(d_in, inb, (long)cin * P);
   count_launch(2);
   UTRY(bsct::gemm_bf16(false, false, cout * 4, (int)P, cin, 1.f, wb, cin, 0, inb, P, 0, 0.f, tmp, P, 0, 1, st));
-  k_tconv_scatter<<<nblk((long)cout * 4 * P), TPB, 0, st>>>(tmp, d_b, cout, n, H, W, d_out);
+  launch_tconv_scatter(tmp, d_b, cout, n, H, W, d_out, st);
   count_launch();
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
@@ -1075,7 +1104,7 @@ extern "C" int bsct_tconv2x2_backward(int32_t n, int32_t cin, int32_t cout, int3
   if (!sc.ok) { bsct_set_last_message("out of device memory"); return BSCT_ERR_CUDA; }
   BSCT_CUDA_TRY(cudaMemsetAsync(d_gb, 0, (size_t)cout * sizeof(float), st));
   k_to_bf16<<<nblk((long)cout * 4 * cin), TPB, 0, st>>>(d_w, wb, (long)cout * 4 * cin);
-  k_tconv_gather<<<nblk((long)cout * 4 * P), TPB, 0, st>>>(d_gout, cout, n, H, W, gg);
+  launch_tconv_gather(d_gout, cout, n, H, W, gg, st);
   k_to_bf16<<<nblk((long)cin * P), TPB, 0, st>>>(d_in, inb, (long)cin * P);
   k_chan_sum<<<chan_grid(4 * P, cout), TPB, 0, st>>>(d_gout, 4 * P, d_gb);
   count_launch(4);
