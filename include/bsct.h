@@ -104,6 +104,11 @@ int bsct_fft_set_shape(int32_t N, int precision, const bsct_fft_shape* shape);
  * invalid shapes; index = 6 fwd + 2 inv + cols over candidate indices). */
 int bsct_fft_autotune(int32_t N, int precision, int reps, bsct_fft_shape* best, double* best_us,
                       double* all_us, void* stream);
+/* The same with a cold L2 for every timed apply: before each of the `reps` applies a write
+ * of flush_bytes bytes (allocated and freed inside) evicts the previous apply's data, and
+ * only the applies are timed (one by one).  flush_bytes = 0 is bsct_fft_autotune. */
+int bsct_fft_autotune_flushed(int32_t N, int precision, int reps, int64_t flush_bytes, bsct_fft_shape* best,
+                              double* best_us, double* all_us, void* stream);
 
 /* Build the Gram filter of a geometry (Sec. 4): for every offset d,
  *   G[d] = sum_theta M_[c, c, s, s, zeta, zeta](d . u_theta)

@@ -156,6 +156,9 @@ def _declare(L):
     for name in ("bsct_conv3x3_forward", "bsct_conv3x3_backward", "bsct_tconv2x2_forward",
                  "bsct_tconv2x2_backward"):
         getattr(L, name).restype = ctypes.c_int
+    L.bsct_fft_autotune_flushed.argtypes = [i32, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                            ctypes.POINTER(FftShape), ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp]
+    L.bsct_fft_autotune_flushed.restype = ctypes.c_int
     L.bsct_gnorm_loss_grad.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
     L.bsct_gnorm_loss_grad.restype = ctypes.c_int
     L.bsct_set_gemm_path.argtypes = [ctypes.c_int]
@@ -585,11 +588,16 @@ def set_fft_shape(N, rows_fwd, rows_inv, cols_one_per_sm=0, precision=F32):
     _check(lib().bsct_fft_set_shape(int(N), int(precision), ctypes.byref(sh)), "bsct_fft_set_shape")
 
 
-def fft_autotune(N, precision=F32, reps=20):
-    """Time every valid launch shape for size N, keep the fastest; returns (shape, us, all_us)."""
+def fft_autotune(N, precision=F32, reps=20, flush_bytes=0):
+    """Time every valid launch shape for size N, keep the fastest; returns (shape, us, all_us).
+    flush_bytes > 0 evicts L2 before every timed apply (bsct_fft_autotune_flushed)."""
     sh, best, allus = FftShape(), ctypes.c_double(), (ctypes.c_double * 18)()
-    _check(lib().bsct_fft_autotune(int(N), int(precision), int(reps), ctypes.byref(sh), ctypes.byref(best), allus,
-                                   _stream()), "bsct_fft_autotune")
+    if flush_bytes:
+        _check(lib().bsct_fft_autotune_flushed(int(N), int(precision), int(reps), int(flush_bytes), ctypes.byref(sh),
+                                               ctypes.byref(best), allus, _stream()), "bsct_fft_autotune_flushed")
+    else:
+        _check(lib().bsct_fft_autotune(int(N), int(precision), int(reps), ctypes.byref(sh), ctypes.byref(best),
+                                       allus, _stream()), "bsct_fft_autotune")
     return (sh.rows_fwd, sh.rows_inv, sh.cols_one_per_sm), best.value, list(allus)
 
 

@@ -50,74 +50,85 @@ __global__ void k_dft_matrix(__nv_bfloat16* A3, int P, int inverse) {
   A3[i] = (s == 2) ? lo : hi;  // operand order [B_hi; B_lo; B_hi] pairs with [A_hi, A_hi, A_lo]
 }
 
-// first operand of the row-index DFT: zero-padded real image x (N x N) as T[ri][L][L]
+// first operand of the row-index DFT: zero-padded real image x (N x N) as T[ri][L][L];
+// grid (rows L, planes 2), threads over the columns of a row
 __global__ void k_split_pad(const float* __restrict__ x, int N, __nv_bfloat16* __restrict__ B) {
   const int L = 2 * N;
   const long plane = (long)L * L;
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * plane) return;
-  const int ri = (int)(i / plane);
-  const long e = i % plane;
-  const int r = (int)(e / L), c = (int)(e % L);
-  const float v = (ri == 0 && r < N && c < N) ? x[(long)r * N + c] : 0.f;
-  __nv_bfloat16 hi, lo;
-  split_bf16(v, hi, lo);
-  B[i] = hi;
-  B[2 * plane + i] = lo;
-  B[4 * plane + i] = hi;
+  const int r = blockIdx.x, ri = blockIdx.y;
+  for (int c = threadIdx.x; c < L; c += blockDim.x) {
+    const long i = (long)ri * plane + (long)r * L + c;
+    const float v = (ri == 0 && r < N && c < N) ? x[(long)r * N + c] : 0.f;
+    __nv_bfloat16 hi, lo;
+    split_bf16(v, hi, lo);
+    B[i] = hi;
+    B[2 * plane + i] = lo;
+    B[4 * plane + i] = hi;
+  }
 }
 
-// D1[ri][k1][n2][rest] * W_L^(+-n2 k1) -> split operand [s][ri][n2][k1][rest]
+// D1[ri][k1][n2][rest] * W_L^(+-n2 k1) -> split operand [s][ri][n2][k1][rest]; grid (Q, P):
+// one (k1, n2) row of R values per block
 __global__ void k_twiddle_split(const float* __restrict__ D, int P, int Q, long R, const float2* __restrict__ tw,
                                 int inverse, __nv_bfloat16* __restrict__ B) {
   const long L = (long)P * Q;
   const long plane = L * R;
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;  // over [k1][n2][rest]
-  if (i >= plane) return;
-  const long rest = i % R;
-  const int n2 = (int)((i / R) % Q), k1 = (int)(i / (R * Q));
+  const int n2 = blockIdx.x, k1 = blockIdx.y;
   const float2 w = tw[((long)n2 * k1) % L];
   const float wi = inverse ? -w.y : w.y;
-  const float re = D[i], im = D[plane + i];
-  const float yr = re * w.x - im * wi, yi = re * wi + im * w.x;
-  const long o = ((long)n2 * P + k1) * R + rest;
-  __nv_bfloat16 hr, lr, hi_, li;
-  split_bf16(yr, hr, lr);
-  split_bf16(yi, hi_, li);
-  B[o] = hr; B[plane + o] = hi_;
-  B[2 * plane + o] = lr; B[3 * plane + o] = li;
-  B[4 * plane + o] = hr; B[5 * plane + o] = hi_;
+  const float* dre = D + ((long)k1 * Q + n2) * R;
+  const long o0 = ((long)n2 * P + k1) * R;
+  for (long rest = threadIdx.x; rest < R; rest += blockDim.x) {
+    const float re = dre[rest], im = dre[plane + rest];
+    const float yr = re * w.x - im * wi, yi = re * wi + im * w.x;
+    const long o = o0 + rest;
+    __nv_bfloat16 hr, lr, hi_, li;
+    split_bf16(yr, hr, lr);
+    split_bf16(yi, hi_, li);
+    B[o] = hr; B[plane + o] = hi_;
+    B[2 * plane + o] = lr; B[3 * plane + o] = li;
+    B[4 * plane + o] = hr; B[5 * plane + o] = hi_;
+  }
 }
 
 // D[ri][a][b] (L x L) -> split operand of the transposed tensor [s][ri][b][a]; optionally
 // multiplied by the real spectrum first (Gt layout of the FFT path, scaled by 1/L^2):
-// element (a, b) = (v, u) column frequency v, row frequency u
+// element (a, b) = (v, u) column frequency v, row frequency u.  32 x 32 tiles through
+// shared memory (grid (L/32, L/32), block 32 x 8): reads and writes both coalesced.
 __global__ void k_transpose_split(const float* __restrict__ D, int N, const float* __restrict__ Gt,
                                   __nv_bfloat16* __restrict__ B) {
   const int L = 2 * N;
   const long plane = (long)L * L;
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;  // output index [b][a]
-  if (i >= plane) return;
-  const int b = (int)(i / L), a = (int)(i % L);
-  const long src = (long)a * L + b;
-  float re = D[src], im = D[plane + src];
-  if (Gt) {
-    // element at (v = a, u = b) before the transpose
-    const int v = a, u = b;
-    float g;
-    if (v == 0) g = Gt[u] + Gt[(long)N * L + u];
-    else if (v == N) g = Gt[u] - Gt[(long)N * L + u];
-    else if (v < N) g = Gt[(long)v * L + u];
-    else g = Gt[(long)(L - v) * L + (u == 0 ? 0 : L - u)];
-    re *= g;
-    im *= g;
+  __shared__ float tre[32][33], tim[32][33];
+  const int a0 = blockIdx.y * 32, b0 = blockIdx.x * 32;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int a = a0 + dy, b = b0 + threadIdx.x;
+    const long src = (long)a * L + b;
+    float re = D[src], im = D[plane + src];
+    if (Gt) {
+      const int v = a, u = b;
+      float g;
+      if (v == 0) g = Gt[u] + Gt[(long)N * L + u];
+      else if (v == N) g = Gt[u] - Gt[(long)N * L + u];
+      else if (v < N) g = Gt[(long)v * L + u];
+      else g = Gt[(long)(L - v) * L + (u == 0 ? 0 : L - u)];
+      re *= g;
+      im *= g;
+    }
+    tre[dy][threadIdx.x] = re;
+    tim[dy][threadIdx.x] = im;
   }
-  __nv_bfloat16 hr, lr, hi_, li;
-  split_bf16(re, hr, lr);
-  split_bf16(im, hi_, li);
-  B[i] = hr; B[plane + i] = hi_;
-  B[2 * plane + i] = lr; B[3 * plane + i] = li;
-  B[4 * plane + i] = hr; B[5 * plane + i] = hi_;
+  __syncthreads();
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int b = b0 + dy, a = a0 + threadIdx.x;
+    const long i = (long)b * L + a;
+    __nv_bfloat16 hr, lr, hi_, li;
+    split_bf16(tre[threadIdx.x][dy], hr, lr);
+    split_bf16(tim[threadIdx.x][dy], hi_, li);
+    B[i] = hr; B[plane + i] = hi_;
+    B[2 * plane + i] = lr; B[3 * plane + i] = li;
+    B[4 * plane + i] = hr; B[5 * plane + i] = hi_;
+  }
 }
 
 // y[r][c] = Re D[c][r] for r, c < N (the last DFT ran over the column index, leading)
@@ -155,8 +166,7 @@ static int dft_leading(int L, int P, int Q, long R, const __nv_bfloat16* Ap, con
   // stage 1: M = 2P, K = 6P, N = Q R
   int rc = gemm_bf16(false, false, 2 * P, (int)(Q * R), 6 * P, 1.f, Ap, 6 * P, 0, B, Q * R, 0, 0.f, Dtmp, Q * R, 0, 1, st);
   if (rc != BSCT_OK) return rc;
-  const long plane = (long)L * R;
-  k_twiddle_split<<<(unsigned)((plane + 255) / 256), 256, 0, st>>>(Dtmp, P, Q, R, tw, inverse, B);
+  k_twiddle_split<<<dim3((unsigned)Q, (unsigned)P), 256, 0, st>>>(Dtmp, P, Q, R, tw, inverse, B);
   count_launch();
   BSCT_CUDA_TRY(cudaGetLastError());
   // stage 2: M = 2Q, K = 6Q, N = P R
@@ -187,22 +197,22 @@ int dftgemm_apply(int N, const float* x, float* y, const float* Gt, const float2
   k_dft_matrix<<<(12 * P * P + 255) / 256, 256, 0, st>>>(Api, P, 1);
   k_dft_matrix<<<(12 * Q * Q + 255) / 256, 256, 0, st>>>(Aqf, Q, 0);
   k_dft_matrix<<<(12 * Q * Q + 255) / 256, 256, 0, st>>>(Aqi, Q, 1);
-  const unsigned gb = (unsigned)((plane + 255) / 256);
-  k_split_pad<<<(unsigned)((2 * plane + 255) / 256), 256, 0, st>>>(x, N, B);
+  const dim3 gt((unsigned)(L / 32), (unsigned)(L / 32)), bt(32, 8);
+  k_split_pad<<<dim3((unsigned)L, 2), 256, 0, st>>>(x, N, B);
   count_launch(5);
   BSCT_CUDA_TRY(cudaGetLastError());
   int rc;
   // forward over the row index r (leading), then over the column index
   if ((rc = dft_leading(L, P, Q, L, Apf, Aqf, B, D1, D2, tw_untangle, 0, st)) != BSCT_OK) return rc;
-  k_transpose_split<<<gb, 256, 0, st>>>(D2, N, nullptr, B);
+  k_transpose_split<<<gt, bt, 0, st>>>(D2, N, nullptr, B);
   count_launch();
   if ((rc = dft_leading(L, P, Q, L, Apf, Aqf, B, D1, D2, tw_untangle, 0, st)) != BSCT_OK) return rc;
   // D2[ri][v][u]: multiply by the spectrum, transpose to [u][v] -> inverse over u first
-  k_transpose_split<<<gb, 256, 0, st>>>(D2, N, Gt, B);
+  k_transpose_split<<<gt, bt, 0, st>>>(D2, N, Gt, B);
   count_launch();
   if ((rc = dft_leading(L, P, Q, L, Api, Aqi, B, D1, D2, tw_untangle, 1, st)) != BSCT_OK) return rc;
   // D2[ri][r][v] -> [v][r] -> inverse over v
-  k_transpose_split<<<gb, 256, 0, st>>>(D2, N, nullptr, B);
+  k_transpose_split<<<gt, bt, 0, st>>>(D2, N, nullptr, B);
   count_launch();
   if ((rc = dft_leading(L, P, Q, L, Api, Aqi, B, D1, D2, tw_untangle, 1, st)) != BSCT_OK) return rc;
   // D2[ri][c][r]: crop the transposed result

@@ -2,7 +2,8 @@
 //
 //   C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b]   (same contract as k_gemm_bf16)
 //
-// One CTA of four warps computes a 128 x BN tile of C (BN = 128):
+// One CTA of four warps computes a 128 x BN tile of C (BN = 128; 64 or 32 when the B operand
+// is K-major and has at most that many columns, as for the CNN's narrow layers):
 //   * warp 0, one lane: producer - the tensor-memory accelerator copies 128 x 64 (A) and
 //     64 x BN (B) operand tiles into a ring of STAGES shared-memory stages
 //     (cp.async.bulk.tensor, 128-byte swizzle, zero fill outside the matrices), each
@@ -30,11 +31,16 @@ namespace bsct {
 
 namespace tc {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3, THREADS = 128;
-constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int BM = 128, BK = 64, STAGES = 3, THREADS = 128;
+constexpr int A_BYTES = BM * BK * 2;
+// tile width BN (128, or 64 / 32 for narrow K-major B operands): bytes of a B tile and of a stage
+template <int BN> __host__ __device__ constexpr int b_bytes() { return BN * BK * 2; }
+template <int BN> __host__ __device__ constexpr int stage_bytes() { return A_BYTES + b_bytes<BN>(); }
 // (the epilogue reuses the stage ring for its per-warp 32 x 33 transposition tiles)
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
-static_assert(4 * 32 * 33 * 4 <= STAGES * STAGE_BYTES, "epilogue tiles fit in the stage ring");
+template <int BN> __host__ __device__ constexpr int smem_bytes() {
+  return STAGES * stage_bytes<BN>() + 1024 /* alignment */ + 256 /* barriers */;
+}
+static_assert(4 * 32 * 33 * 4 <= STAGES * stage_bytes<32>(), "epilogue tiles fit in the stage ring");
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -122,7 +128,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 // A_MN / B_MN: the operand tile is MN-major (M / N contiguous in memory); TRANS_C: the
 // accumulator rows are columns of C (roles of A and B exchanged by the host)
-template <bool A_MN, bool B_MN, bool TRANS_C>
+template <bool A_MN, bool B_MN, bool TRANS_C, int BN>
 __global__ void __launch_bounds__(THREADS, 2)
 k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N, int K,
           float alpha, float beta, float* __restrict__ C, long ldc, long sC, int a_bcast, int b_bcast,
@@ -130,6 +136,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   extern __shared__ __align__(1024) unsigned char smraw[];
   // 1024-byte aligned stage ring (the swizzle atoms), barriers and the TMEM address after it
   unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  static_assert(BN == 128 || (!B_MN && (BN == 64 || BN == 32)), "narrow tiles need a K-major B operand");
+  constexpr int B_BYTES = b_bytes<BN>(), STAGE_BYTES = stage_bytes<BN>();
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(base + STAGES * STAGE_BYTES);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -302,7 +310,7 @@ static bool make_map(CUtensorMap* map, const void* ptr, long rows, long cols, lo
 }  // namespace tc
 
 // one instantiation: shared-memory opt-in once per device, then the launch
-template <bool XMN, bool YMN, bool TC>
+template <bool XMN, bool YMN, bool TC, int BN>
 static int launch_tc(dim3 grid, const CUtensorMap& mx, const CUtensorMap& my, int M, int N, int K, float alpha,
                      float beta, float* C, long ldc, long sC, int x_bc, int y_bc, unsigned int* status,
                      cudaStream_t st) {
@@ -311,15 +319,15 @@ static int launch_tc(dim3 grid, const CUtensorMap& mx, const CUtensorMap& my, in
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
   if (!attr[dev]) {
-    const cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<XMN, YMN, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               SMEM_BYTES);
+    const cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<XMN, YMN, TC, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               smem_bytes<BN>());
     if (e != cudaSuccess) {
       bsct_set_last_cuda_error(e);
       return BSCT_ERR_CUDA;
     }
     attr[dev] = true;
   }
-  k_gemm_tc<XMN, YMN, TC><<<grid, THREADS, SMEM_BYTES, st>>>(mx, my, M, N, K, alpha, beta, C, ldc, sC, x_bc, y_bc,
+  k_gemm_tc<XMN, YMN, TC, BN><<<grid, THREADS, smem_bytes<BN>(), st>>>(mx, my, M, N, K, alpha, beta, C, ldc, sC, x_bc, y_bc,
                                                               status);
   count_launch();
   const cudaError_t e = cudaGetLastError();
@@ -352,23 +360,33 @@ int gemm_bf16_tc(bool ta, bool tb, int M, int N, int K, float alpha, const void*
     return BSCT_ERR_UNSUPPORTED_SIZE;
   CUtensorMap mx, my;
   // K-major: rows = M or N, cols = K; MN-major: rows = K, cols = M or N
+  // narrow K-major B operands (N = 32 or 64 columns, the CNN's small channel counts) use
+  // a tile of that width so that the MMA and its tensor memory do no padding work
+  const int BNsel = y_mn ? 128 : (NY <= 32 ? 32 : (NY <= 64 ? 64 : 128));
   const bool okx = x_mn ? make_map(&mx, X, K, MX, ldx, sx, batch, BK) : make_map(&mx, X, MX, K, ldx, sx, batch, BM);
-  const bool oky = y_mn ? make_map(&my, Y, K, NY, ldy, sy, batch, BK) : make_map(&my, Y, NY, K, ldy, sy, batch, BN);
+  const bool oky = y_mn ? make_map(&my, Y, K, NY, ldy, sy, batch, BK) : make_map(&my, Y, NY, K, ldy, sy, batch, BNsel);
   if (!okx || !oky) return BSCT_ERR_UNSUPPORTED_SIZE;
   unsigned int* status = timeout_status_ptr();
   if (!status) return BSCT_ERR_CUDA;
   const int x_bc = (swap ? sB : sA) == 0 && batch > 1, y_bc = (swap ? sA : sB) == 0 && batch > 1;
-  dim3 grid((NY + BN - 1) / BN, (MX + BM - 1) / BM, batch);
-  if (!swap) {
-    if (!x_mn && !y_mn) return launch_tc<false, false, false>(grid, mx, my, M, N, K, alpha, beta, C, ldc, sC, x_bc, y_bc, status, st);
-    if (!x_mn && y_mn) return launch_tc<false, true, false>(grid, mx, my, M, N, K, alpha, beta, C, ldc, sC, x_bc, y_bc, status, st);
-    if (x_mn && !y_mn) return launch_tc<true, false, false>(grid, mx, my, M, N, K, alpha, beta, C, ldc, sC, x_bc, y_bc, status, st);
-    return launch_tc<true, true, false>(grid, mx, my, M, N, K, alpha, beta, C, ldc, sC, x_bc, y_bc, status, st);
+  dim3 grid((NY + BNsel - 1) / BNsel, (MX + BM - 1) / BM, batch);
+#define BSCT_TC(XM, YM, TCV, BNV) \
+  return launch_tc<XM, YM, TCV, BNV>(grid, mx, my, M, N, K, alpha, beta, C, ldc, sC, x_bc, y_bc, status, st)
+  if (y_mn) {
+    if (!swap) { if (x_mn) BSCT_TC(true, true, false, 128); else BSCT_TC(false, true, false, 128); }
+    if (x_mn) BSCT_TC(true, true, true, 128); else BSCT_TC(false, true, true, 128);
   }
-  if (!x_mn && !y_mn) return launch_tc<false, false, true>(grid, mx, my, M, N, K, alpha, beta, C, ldc, sC, x_bc, y_bc, status, st);
-  if (!x_mn && y_mn) return launch_tc<false, true, true>(grid, mx, my, M, N, K, alpha, beta, C, ldc, sC, x_bc, y_bc, status, st);
-  if (x_mn && !y_mn) return launch_tc<true, false, true>(grid, mx, my, M, N, K, alpha, beta, C, ldc, sC, x_bc, y_bc, status, st);
-  return launch_tc<true, true, true>(grid, mx, my, M, N, K, alpha, beta, C, ldc, sC, x_bc, y_bc, status, st);
+  if (BNsel == 32) {
+    if (!swap) { if (x_mn) BSCT_TC(true, false, false, 32); else BSCT_TC(false, false, false, 32); }
+    if (x_mn) BSCT_TC(true, false, true, 32); else BSCT_TC(false, false, true, 32);
+  }
+  if (BNsel == 64) {
+    if (!swap) { if (x_mn) BSCT_TC(true, false, false, 64); else BSCT_TC(false, false, false, 64); }
+    if (x_mn) BSCT_TC(true, false, true, 64); else BSCT_TC(false, false, true, 64);
+  }
+  if (!swap) { if (x_mn) BSCT_TC(true, false, false, 128); else BSCT_TC(false, false, false, 128); }
+  if (x_mn) BSCT_TC(true, false, true, 128); else BSCT_TC(false, false, true, 128);
+#undef BSCT_TC
 }
 
 }  // namespace bsct

@@ -46,8 +46,11 @@ template <typename T> __global__ void k_fill(T* a, long n, T v) {
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) a[i] = v;
 }
 
+// flush_bytes > 0: before every timed apply, a write of that many bytes evicts the data of
+// the previous one from L2 (the applies are then timed one by one, the writes excluded)
 template <typename T>
-int autotune(int N, int reps, bsct_fft_shape* best, double* best_us, double* all_us, cudaStream_t st) {
+int autotune(int N, int reps, bsct_fft_shape* best, double* best_us, double* all_us, cudaStream_t st,
+             long flush_bytes = 0) {
   FftOps<T> o;
   int rc = ops_for<T>(N, &o);
   if (rc != BSCT_OK) return rc;
@@ -55,8 +58,9 @@ int autotune(int N, int reps, bsct_fft_shape* best, double* best_us, double* all
   T *x = nullptr, *y = nullptr, *Gt = nullptr;
   cpx<T>*S = nullptr, *tw = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  unsigned char* fl = nullptr;
   auto cleanup = [&]() {
-    cudaFree(x); cudaFree(y); cudaFree(Gt); cudaFree(S); cudaFree(tw);
+    cudaFree(x); cudaFree(y); cudaFree(Gt); cudaFree(S); cudaFree(tw); cudaFree(fl);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
   };
@@ -72,6 +76,7 @@ int autotune(int N, int reps, bsct_fft_shape* best, double* best_us, double* all
   TTRY(cudaMalloc(&tw, fft_table_elems(N) * sizeof(cpx<T>)));
   TTRY(cudaEventCreate(&e0));
   TTRY(cudaEventCreate(&e1));
+  if (flush_bytes > 0) TTRY(cudaMalloc(&fl, (size_t)flush_bytes));
   k_fill<T><<<256, 256, 0, st>>>(x, n, T(1));
   k_fill<T><<<256, 256, 0, st>>>(Gt, ng, T(1e-6));
   count_launch(2);
@@ -91,13 +96,29 @@ int autotune(int N, int reps, bsct_fft_shape* best, double* best_us, double* all
       rc = o.apply(x, y, S, Gt, tw, st);
       if (rc != BSCT_OK) { o.shape_index(keep, 1); cleanup(); return rc; }
     }
-    TTRY(cudaEventRecord(e0, st));
-    for (int r = 0; r < reps; ++r) o.apply(x, y, S, Gt, tw, st);
-    TTRY(cudaEventRecord(e1, st));
-    TTRY(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    TTRY(cudaEventElapsedTime(&ms, e0, e1));
-    const double us = 1e3 * ms / reps;
+    double tot_ms = 0.0;
+    if (!fl) {
+      TTRY(cudaEventRecord(e0, st));
+      for (int r = 0; r < reps; ++r) o.apply(x, y, S, Gt, tw, st);
+      TTRY(cudaEventRecord(e1, st));
+      TTRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      TTRY(cudaEventElapsedTime(&ms, e0, e1));
+      tot_ms = ms;
+    } else {
+      for (int r = 0; r < reps; ++r) {
+        k_fill<unsigned char><<<1024, 256, 0, st>>>(fl, flush_bytes, (unsigned char)r);
+        count_launch();
+        TTRY(cudaEventRecord(e0, st));
+        o.apply(x, y, S, Gt, tw, st);
+        TTRY(cudaEventRecord(e1, st));
+        TTRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        TTRY(cudaEventElapsedTime(&ms, e0, e1));
+        tot_ms += ms;
+      }
+    }
+    const double us = 1e3 * tot_ms / reps;
     if (all_us) all_us[i] = us;
     if (us < best_t) {
       best_t = us;
@@ -141,6 +162,17 @@ extern "C" int bsct_fft_shape_candidates(int32_t N, int precision, int32_t* rows
   }
   for (int i = 0; i < 3; ++i) { rows_fwd[i] = f[i]; rows_inv[i] = v[i]; }
   return BSCT_OK;
+}
+
+extern "C" int bsct_fft_autotune_flushed(int32_t N, int precision, int reps, int64_t flush_bytes,
+                                         bsct_fft_shape* best, double* best_us, double* all_us, void* stream) {
+  if (reps < 1 || flush_bytes < 0 || (precision != BSCT_F32 && precision != BSCT_F64)) {
+    bsct_set_last_message("invalid argument");
+    return BSCT_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  return precision == BSCT_F32 ? autotune<float>(N, reps, best, best_us, all_us, st, (long)flush_bytes)
+                               : autotune<double>(N, reps, best, best_us, all_us, st, (long)flush_bytes);
 }
 
 extern "C" int bsct_fft_autotune(int32_t N, int precision, int reps, bsct_fft_shape* best, double* best_us,

@@ -53,31 +53,43 @@ __global__ void k_to_bf16(const float* __restrict__ a, bf16* __restrict__ b, lon
 }
 
 // col[(ci*9 + ky*3 + kx)][(n, y, x)] = in[ci][n][y+ky-1][x+kx-1] (zero outside), rows >= 9*C zero.
-// Grid (NB*H, Kpad): one image row of one col row per block (indices from the block, no
-// per-element division); two x per thread, stored as one BF16 pair (W even)
-__global__ void k_im2col3(const float* __restrict__ in, int C, int NB, int H, int W, bf16* __restrict__ col) {
-  const int k = blockIdx.y, row = blockIdx.x;  // row = n H + y
+// Grid (NB*H, C + 1): block (image row, input channel) stages the three input rows y-1..y+1
+// (with a zero halo) in shared memory and writes the nine col rows of that channel, two x
+// per thread as one BF16 pair (W even); blocks with blockIdx.y == C write the zero rows
+__global__ void k_im2col3(const float* __restrict__ in, int C, int NB, int H, int W, int Kpad,
+                          bf16* __restrict__ col) {
+  extern __shared__ float srow[];  // 3 (W + 2)
+  const int row = blockIdx.x, ci = blockIdx.y;  // row = n H + y
   const long P = (long)NB * H * W;
-  __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(col + (long)k * P + (long)row * W);
   const int W2 = W >> 1;
-  if (k >= 9 * C) {
-    for (int x2 = threadIdx.x; x2 < W2; x2 += blockDim.x) dst[x2] = __floats2bfloat162_rn(0.f, 0.f);
+  if (ci == C) {
+    for (int k = 9 * C; k < Kpad; ++k) {
+      __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(col + (long)k * P + (long)row * W);
+      for (int x2 = threadIdx.x; x2 < W2; x2 += blockDim.x) dst[x2] = __floats2bfloat162_rn(0.f, 0.f);
+    }
     return;
   }
-  const int ci = k / 9, r = k - 9 * ci, ky = r / 3, kx = r - 3 * ky;
-  const int nb = row / H, y = row - nb * H, yy = y + ky - 1;
-  const bool rowok = yy >= 0 && yy < H;
-  const float* src = in + ((long)ci * NB + nb) * H * W + (long)(rowok ? yy : 0) * W;
-  for (int x2 = threadIdx.x; x2 < W2; x2 += blockDim.x) {
-    const int xa = 2 * x2 + kx - 1, xb = xa + 1;
-    const float a = (rowok && xa >= 0 && xa < W) ? src[xa] : 0.f;
-    const float b = (rowok && xb >= 0 && xb < W) ? src[xb] : 0.f;
-    dst[x2] = __floats2bfloat162_rn(a, b);
+  const int nb = row / H, y = row - nb * H;
+  const float* src = in + ((long)ci * NB + nb) * H * W;
+  const int WS = W + 2;
+  for (int t = threadIdx.x; t < 3 * WS; t += blockDim.x) {
+    const int r = t / WS, xx = t - r * WS - 1, yy = y - 1 + r;
+    srow[t] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? src[(long)yy * W + xx] : 0.f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) {
+    const int ky = tap / 3, kx = tap - 3 * ky;
+    __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(col + (long)(ci * 9 + tap) * P + (long)row * W);
+    const float* s2 = srow + ky * WS + kx;  // s2[x] = in[y + ky - 1][x + kx - 1]
+    for (int x2 = threadIdx.x; x2 < W2; x2 += blockDim.x) dst[x2] = __floats2bfloat162_rn(s2[2 * x2], s2[2 * x2 + 1]);
   }
 }
 inline int row_threads(int n) { return n >= 256 ? 256 : ((n + 31) / 32) * 32; }
 inline void launch_im2col3(const float* in, int C, int NB, int H, int W, int Kpad, bf16* col, cudaStream_t st) {
-  k_im2col3<<<dim3((unsigned)(NB * H), (unsigned)Kpad), row_threads(W / 2), 0, st>>>(in, C, NB, H, W, col);
+  const unsigned gy = (unsigned)(C + (Kpad > 9 * C ? 1 : 0));
+  k_im2col3<<<dim3((unsigned)(NB * H), gy), row_threads(W / 2), (size_t)3 * (W + 2) * sizeof(float), st>>>(
+      in, C, NB, H, W, Kpad, col);
 }
 
 // gin[ci][n][y][x] = sum_{ky,kx} dcol[(ci,ky,kx)][n][y-ky+1][x-kx+1]; grid (NB*H, C), one image

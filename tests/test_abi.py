@@ -103,6 +103,7 @@ def test_new_entry_points_validate_on_the_host(lib):
     assert lib.bsct_fft_set_shape(256, 0, ctypes.byref(sh)) == -1
     assert lib.bsct_fft_get_shape(100, 0, ctypes.byref(sh)) == -2
     assert lib.bsct_fft_autotune(256, 0, 0, None, None, None, None) == -1
+    assert lib.bsct_fft_autotune_flushed(256, 0, 5, -1, None, None, None, None) == -1
 
 
 def test_check_finite_validates_on_the_host(lib):

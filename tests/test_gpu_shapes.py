@@ -65,14 +65,15 @@ def test_every_shape_same_apply(bsct, N, prec):
         g.close()
 
 
-def test_autotune_keeps_a_valid_shape(bsct):
+@pytest.mark.parametrize("flush", [0, 256 << 20])
+def test_autotune_keeps_a_valid_shape(bsct, flush):
     N = 512
     g = bsct.gram_build(bsct.Geometry.uniform(N, 60, 730, 1.0, 1.0), bsct.F32)
     x = torch.randn((N, N), device=DEV, generator=torch.Generator(device=DEV).manual_seed(3))
     restore(bsct, N, bsct.F32)
     ref = g.apply(x).clone()
     try:
-        best, us, all_us = bsct.fft_autotune(N, bsct.F32, reps=5)
+        best, us, all_us = bsct.fft_autotune(N, bsct.F32, reps=5, flush_bytes=flush)
         assert best in shapes(bsct, N, bsct.F32) and bsct.fft_shape(N, bsct.F32) == best
         timed = [t for t in all_us if t >= 0]
         assert len(timed) == len(shapes(bsct, N, bsct.F32)) and us == pytest.approx(min(timed))

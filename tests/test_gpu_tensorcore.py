@@ -33,7 +33,8 @@ GEMM_SHAPES = [(128, 128, 64, 1),  # one CTA, one K tile: the smallest case of t
                (200, 136, 72, 2), (128, 256, 384, 1), (16, 8, 24, 3), (264, 520, 40, 1),
                (32, 1024, 288, 1),  # U-Net level 0 (M < 128: the roles of A and B are exchanged)
                (128, 2048, 384, 1),  # a DFT-GEMM stage (M = 2P, K = 6P)
-               (520, 392, 1032, 2)]  # ragged tiles in M, N and K, several K tiles, batches
+               (520, 392, 1032, 2),  # ragged tiles in M, N and K, several K tiles, batches
+               (256, 48, 200, 2), (136, 24, 64, 1)]  # narrow N: 64- and 32-column tiles for K-major B
 
 
 @pytest.mark.parametrize("path", [0, 1])  # 0: tcgen05 tensor cores, 1: warp-level mma.sync
