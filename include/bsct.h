@@ -56,15 +56,21 @@ extern "C" {
 /* Problem geometry (Sec. 2: coefficients c_k on an N x N grid, n_angles views, a
  * detector of n_bins samples with step lambda_y, blur width zeta_blur).
  * angles_pi: HOST array of n_angles values theta_j / pi (any real values; theta and
- * theta + pi are distinct views).  Read during the call only. */
+ * theta + pi are distinct views).  Read during the call only.
+ * Detector kernel (Sec. 2 allows a convolution of several boxes): with n_blur = 0 it is one
+ * unit-mass box of width zeta_blur (0 = none); with n_blur = 1 or 2 it is the convolution of
+ * the unit-mass boxes of widths blur_widths[0 .. n_blur) (HOST array, each in [0.2, 4]) and
+ * zeta_blur must be 0.  Two boxes are supported by bsct_gram_build, bsct_backproject and
+ * bsct_forward_project (FP32 and FP64); the batch takes one box. */
 typedef struct bsct_geom {
   int32_t N;
   int32_t n_angles;
   int32_t n_bins;
-  int32_t reserved;
+  int32_t n_blur;
   const double* angles_pi;
   double lambda_y;
   double zeta_blur;
+  const double* blur_widths;
 } bsct_geom;
 
 typedef struct bsct_gram bsct_gram; /* opaque, library-owned */

@@ -46,10 +46,11 @@ class _Geom(ctypes.Structure):
         ("N", ctypes.c_int32),
         ("n_angles", ctypes.c_int32),
         ("n_bins", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("n_blur", ctypes.c_int32),
         ("angles_pi", ctypes.POINTER(ctypes.c_double)),
         ("lambda_y", ctypes.c_double),
         ("zeta_blur", ctypes.c_double),
+        ("blur_widths", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -338,15 +339,24 @@ class Geometry:
     """
 
     def __init__(self, N, angles_pi, n_bins, lambda_y=1.0, zeta_blur=0.0):
+        """zeta_blur: one detector box width, or a sequence of box widths (the detector kernel is
+        then the convolution of those unit-mass boxes, Sec. 2)."""
         self.N = int(N)
         self.angles_pi = np.ascontiguousarray(np.asarray(angles_pi, dtype=np.float64).reshape(-1))
         self.n_angles = int(self.angles_pi.size)
         self.n_bins = int(n_bins)
         self.lambda_y = float(lambda_y)
-        self.zeta_blur = float(zeta_blur)
-        self._c = _Geom(self.N, self.n_angles, self.n_bins, 0,
+        if np.ndim(zeta_blur) == 0:
+            self.zeta_blur = float(zeta_blur)
+            self.blur_widths = np.zeros(0)
+        else:
+            self.zeta_blur = 0.0
+            w = np.asarray(zeta_blur, dtype=np.float64).reshape(-1)
+            self.blur_widths = np.ascontiguousarray(w[w != 0.0])  # zero widths are no box
+        wp = self.blur_widths.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if self.blur_widths.size else None
+        self._c = _Geom(self.N, self.n_angles, self.n_bins, int(self.blur_widths.size),
                         self.angles_pi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                        self.lambda_y, self.zeta_blur)
+                        self.lambda_y, self.zeta_blur, wp)
 
     @classmethod
     def uniform(cls, N, n_angles, n_bins, lambda_y=1.0, zeta_blur=0.0):

@@ -567,6 +567,8 @@ using namespace bsct;
 int bsct_check_geom(const bsct_geom* g);
 
 static size_t bp_workspace(const bsct_geom* g, int precision) {
+  double wb[2];
+  if (bsct_blur_boxes(g, wb) == 2) return mb_bp_workspace(g, precision);
   const size_t T = precision == BSCT_F32 ? 4 : 8;
   size_t b = 0;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -646,7 +648,9 @@ static int bp_run(const bsct_geom* g, const T* sino, T* b, char* work, cudaStrea
   const int na = g->n_angles, M = g->n_bins, N = g->N;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   BpPlan p;
-  p.N = N; p.na = na; p.M = M; p.lambda = g->lambda_y; p.zeta = g->zeta_blur;
+  double wb[2];
+  bsct_blur_boxes(g, wb);  // one box (or none) here
+  p.N = N; p.na = na; p.M = M; p.lambda = g->lambda_y; p.zeta = wb[0];
   p.ang = (double*)work;
   work += al((size_t)na * sizeof(double));
   p.p00 = (double*)work;
@@ -668,8 +672,10 @@ static int bp_run(const bsct_geom* g, const T* sino, T* b, char* work, cudaStrea
 
 int bsct_check_bp_geom(const bsct_geom* geom) {
   if (geom->N < 1 || geom->N > 16384) { bsct_set_last_message("N out of range"); return BSCT_ERR_UNSUPPORTED_SIZE; }
+  double wb[2];
+  if (bsct_blur_boxes(geom, wb) == 2) return mb_check_bp(geom);
   // widest kernel: |c| + |s| <= sqrt(2), degree <= 2
-  const double W = 1.4142135623730951 + geom->zeta_blur + 3.0 * geom->lambda_y;
+  const double W = 1.4142135623730951 + wb[0] + 3.0 * geom->lambda_y;
   int J0, nJ;
   bp_jrange(W, geom->lambda_y, &J0, &nJ);
   if (nJ > BP_NJMAX) { bsct_set_last_message("lambda_y too small: too many samples per pixel"); return BSCT_ERR_UNSUPPORTED_SIZE; }
@@ -691,10 +697,16 @@ extern "C" int bsct_backproject(const bsct_geom* geom, const void* d_sino, void*
   if (work_bytes < bp_workspace(geom, precision)) { bsct_set_last_message("workspace too small"); return BSCT_ERR_INVALID_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
   const long ns = (long)geom->n_angles * geom->n_bins;  // non-finite samples set the input status
+  double wb[2];
+  const bool two = bsct_blur_boxes(geom, wb) == 2;
   if (precision == BSCT_F32) {
     rc = check_finite_async<float>((const float*)d_sino, ns, st);
-    return rc != BSCT_OK ? rc : bp_run<float>(geom, (const float*)d_sino, (float*)d_b, (char*)d_work, st);
+    if (rc != BSCT_OK) return rc;
+    return two ? mb_bp_run<float>(geom, (const float*)d_sino, (float*)d_b, (char*)d_work, st)
+               : bp_run<float>(geom, (const float*)d_sino, (float*)d_b, (char*)d_work, st);
   }
   rc = check_finite_async<double>((const double*)d_sino, ns, st);
-  return rc != BSCT_OK ? rc : bp_run<double>(geom, (const double*)d_sino, (double*)d_b, (char*)d_work, st);
+  if (rc != BSCT_OK) return rc;
+  return two ? mb_bp_run<double>(geom, (const double*)d_sino, (double*)d_b, (char*)d_work, st)
+             : bp_run<double>(geom, (const double*)d_sino, (double*)d_b, (char*)d_work, st);
 }

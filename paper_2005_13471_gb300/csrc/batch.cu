@@ -109,18 +109,29 @@ extern "C" int bsct_batch_create(int n_slices, const bsct_geom* geoms, bsct_batc
       bsct_set_last_message("unsupported N in batch");
       return BSCT_ERR_UNSUPPORTED_SIZE;
     }
+    double w[2];
+    if (bsct_blur_boxes(&geoms[i], w) == 2) {
+      bsct_set_last_message("batch: two detector boxes are not supported (the back projection tables hold one)");
+      return BSCT_ERR_UNSUPPORTED_SIZE;
+    }
   }
   cudaStream_t st = (cudaStream_t)stream;
   bsct_batch* bt = new bsct_batch();
   bt->slices.resize(n_slices);
   for (int i = 0; i < n_slices; ++i) {
+    // a one-entry box list is the single detector box zeta_blur
+    bsct_geom gi_geom = geoms[i];
+    double w[2];
+    gi_geom.zeta_blur = bsct_blur_boxes(&geoms[i], w) == 1 ? w[0] : 0.0;
+    gi_geom.n_blur = 0;
+    gi_geom.blur_widths = nullptr;
     int gi = -1;
     for (size_t k = 0; k < bt->geoms.size(); ++k)
-      if (same_geom(bt->geoms[k].g, geoms[i])) { gi = (int)k; break; }
+      if (same_geom(bt->geoms[k].g, gi_geom)) { gi = (int)k; break; }
     if (gi < 0) {
       bt->geoms.emplace_back();
       BatchGeom& G = bt->geoms.back();
-      G.g = geoms[i];
+      G.g = gi_geom;
       G.angles.assign(geoms[i].angles_pi, geoms[i].angles_pi + geoms[i].n_angles);
       G.g.angles_pi = G.angles.data();
       gi = (int)bt->geoms.size() - 1;

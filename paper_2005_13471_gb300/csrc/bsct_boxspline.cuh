@@ -138,4 +138,96 @@ __device__ inline double box_eval(double x, const BoxDirs& D, int small) {
 // Relative length below which the short direction goes through box_stable.
 #define BSCT_SHORT_DIR 0.2
 
+// Kinks of M_D: -sum m a / 2 + sum_g k_g a_g (0 <= k_g <= m_g); returns how many (<= cap).
+__device__ inline int box_kinks(const BoxDirs& D, double* out, int cap) {
+  double tot = 0.0;
+  for (int g = 0; g < D.ng; ++g) tot += D.m[g] * D.a[g];
+  const int m0 = D.ng > 0 ? D.m[0] : 0, m1 = D.ng > 1 ? D.m[1] : 0;
+  const int m2 = D.ng > 2 ? D.m[2] : 0, m3 = D.ng > 3 ? D.m[3] : 0;
+  int n = 0;
+  for (int k0 = 0; k0 <= m0; ++k0)
+    for (int k1 = 0; k1 <= m1; ++k1)
+      for (int k2 = 0; k2 <= m2; ++k2)
+        for (int k3 = 0; k3 <= m3; ++k3) {
+          double k = -0.5 * tot;
+          if (k0) k += k0 * D.a[0];
+          if (k1) k += k1 * D.a[1];
+          if (k2) k += k2 * D.a[2];
+          if (k3) k += k3 * D.a[3];
+          if (n < cap) out[n++] = k;
+        }
+  return n;
+}
+
+// Convolution of two box splines, M_[P, Q](x) = int M_P(x - v) M_Q(v) dv, for direction lists
+// too long for the truncated-power form (several detector boxes): 4-point Gauss-Legendre on
+// every piece between the kinks of both factors inside the overlap of their supports (exact
+// for deg M_P + deg M_Q <= 7).  M_P is evaluated with the short-direction split of group
+// small_p (or -1), M_Q by truncated powers (its directions - detector boxes and sample
+// spacings - are never short).  Both factors are centred and symmetric, so each is evaluated
+// at -|argument|, where its truncated powers are smallest.  Every term is non-negative.
+#define BSCT_CONV_CUTS 96
+__device__ inline double box_conv(double x, const BoxDirs& P, int small_p, const BoxDirs& Q) {
+  double cut[BSCT_CONV_CUTS];
+  double qt = 0.0, pt = 0.0;
+  for (int g = 0; g < Q.ng; ++g) qt += Q.m[g] * Q.a[g];
+  for (int g = 0; g < P.ng; ++g) pt += P.m[g] * P.a[g];
+  const double lo = fmax(-0.5 * qt, x - 0.5 * pt), hi = fmin(0.5 * qt, x + 0.5 * pt);
+  if (!(hi > lo)) return 0.0;
+  int nc = 0;
+  cut[nc++] = lo;
+  cut[nc++] = hi;
+  double kq[48], kp[48];
+  const int nq = box_kinks(Q, kq, 48), np = box_kinks(P, kp, 48);
+  for (int i = 0; i < nq && nc < BSCT_CONV_CUTS; ++i)
+    if (kq[i] > lo && kq[i] < hi) cut[nc++] = kq[i];
+  for (int i = 0; i < np && nc < BSCT_CONV_CUTS; ++i) {
+    const double v = x - kp[i];
+    if (v > lo && v < hi) cut[nc++] = v;
+  }
+  for (int i = 1; i < nc; ++i) {  // insertion sort
+    const double t = cut[i];
+    int j = i - 1;
+    while (j >= 0 && cut[j] > t) { cut[j + 1] = cut[j]; --j; }
+    cut[j + 1] = t;
+  }
+  // Gauss-Legendre, 4 points on [0, 1]
+  const double gx[4] = {0.06943184420297371239, 0.33000947820757186760, 0.66999052179242813240,
+                        0.93056815579702628761};
+  const double gw[4] = {0.17392742256872692869, 0.32607257743127307131, 0.32607257743127307131,
+                        0.17392742256872692869};
+  double acc = 0.0;
+  for (int i = 0; i + 1 < nc; ++i) {
+    const double a = cut[i], w = cut[i + 1] - cut[i];
+    if (w <= 0.0) continue;
+    double piece = 0.0;
+    for (int q = 0; q < 4; ++q) {
+      const double v = a + gx[q] * w;
+      piece += gw[q] * box_eval(-fabs(x - v), P, small_p) * box_tp(-fabs(v), Q);
+    }
+    acc += piece * w;
+  }
+  return acc;
+}
+
+// Monomial coefficients c[0..7] (in v on [-1, 1]) of the polynomial of degree <= 7 through
+// the values fv[i] at the Chebyshev nodes cos(pi (2i + 1) / 16): the discrete Chebyshev
+// transform, then T_0..T_7 written out in powers of v.
+__device__ inline void cheb8_monomials(const double fv[8], double c[8]) {
+  double ch[8];
+  for (int k = 0; k < 8; ++k) {
+    double acc = 0.0;
+    for (int i = 0; i < 8; ++i) acc += fv[i] * cospi(k * (2.0 * i + 1.0) / 16.0);
+    ch[k] = acc * (k == 0 ? 1.0 / 8.0 : 2.0 / 8.0);
+  }
+  c[0] = ch[0] - ch[2] + ch[4] - ch[6];
+  c[1] = ch[1] - 3.0 * ch[3] + 5.0 * ch[5] - 7.0 * ch[7];
+  c[2] = 2.0 * ch[2] - 8.0 * ch[4] + 18.0 * ch[6];
+  c[3] = 4.0 * ch[3] - 20.0 * ch[5] + 56.0 * ch[7];
+  c[4] = 8.0 * ch[4] - 48.0 * ch[6];
+  c[5] = 16.0 * ch[5] - 112.0 * ch[7];
+  c[6] = 32.0 * ch[6];
+  c[7] = 64.0 * ch[7];
+}
+
 }  // namespace bsct

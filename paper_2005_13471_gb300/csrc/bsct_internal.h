@@ -186,7 +186,18 @@ extern int g_gemm_path;  // 0: tcgen05 (default), 1: warp-level mma.sync
 }  // namespace bsct
 
 int bsct_check_geom(const bsct_geom* g);
+// detector boxes of a geometry (checked): their number (0, 1 or 2) and widths
+int bsct_blur_boxes(const bsct_geom* g, double w[2]);
 int bsct_check_bp_geom(const bsct_geom* g);
+
+namespace bsct {
+// two detector boxes (multibox.cu): back projection and forward projection of a checked geometry
+int mb_check_bp(const bsct_geom* g);
+size_t mb_bp_workspace(const bsct_geom* g, int precision);
+template <typename T> int mb_bp_run(const bsct_geom* g, const T* sino, T* b, char* work, cudaStream_t st);
+size_t mb_fp_workspace(const bsct_geom* g, int precision);
+template <typename T> int mb_fp_run(const bsct_geom* g, const T* c, T* sino, char* work, cudaStream_t st);
+}  // namespace bsct
 
 // Library-owned state of one geometry (see bsct_gram_build).
 struct bsct_host_pipe;  // streams, events and device images of bsct_gram_apply_host

@@ -386,6 +386,8 @@ int bsct_check_geom(const bsct_geom* g);
 static size_t fp_al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static size_t fp_workspace(const bsct_geom* g, int precision) {
+  double wb[2];
+  if (bsct_blur_boxes(g, wb) == 2) return mb_fp_workspace(g, precision);
   const size_t T = precision == BSCT_F32 ? 4 : 8;
   return fp_al((size_t)g->n_angles * sizeof(double)) + fp_al((size_t)g->n_angles * FP_HDR * sizeof(double)) +
          fp_al((size_t)g->n_angles * FP_TAB * T) + fp_al((size_t)g->N * g->N * T);
@@ -426,7 +428,9 @@ static int fp_run(const bsct_geom* geom, const T* c, T* sino, char* w, cudaStrea
   w += fp_al((size_t)na * FP_TAB * sizeof(T));
   T* ct = (T*)w;
   BSCT_CUDA_TRY(cudaMemcpyAsync(ang, geom->angles_pi, (size_t)na * sizeof(double), cudaMemcpyHostToDevice, st));
-  k_fp_tables<T><<<na, 128, 0, st>>>(ang, N, M, geom->lambda_y, geom->zeta_blur, hdr, tab);
+  double wb[2];
+  bsct_blur_boxes(geom, wb);  // one box (or none) here
+  k_fp_tables<T><<<na, 128, 0, st>>>(ang, N, M, geom->lambda_y, wb[0], hdr, tab);
   dim3 tb(32, 8), tg((N + 31) / 32, (N + 31) / 32);
   k_fp_transpose<T><<<tg, tb, 0, st>>>(c, N, ct);
   dim3 gg((M + FP_THREADS - 1) / FP_THREADS, na);
@@ -444,10 +448,16 @@ extern "C" int bsct_forward_project(const bsct_geom* geom, const void* d_coeffs,
   if (work_bytes < fp_workspace(geom, precision)) { bsct_set_last_message("workspace too small"); return BSCT_ERR_INVALID_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
   const long nc = (long)geom->N * geom->N;  // non-finite coefficients set the input status
+  double wb[2];
+  const bool two = bsct_blur_boxes(geom, wb) == 2;
   if (precision == BSCT_F32) {
     rc = check_finite_async<float>((const float*)d_coeffs, nc, st);
-    return rc != BSCT_OK ? rc : fp_run<float>(geom, (const float*)d_coeffs, (float*)d_sino, (char*)d_work, st);
+    if (rc != BSCT_OK) return rc;
+    return two ? mb_fp_run<float>(geom, (const float*)d_coeffs, (float*)d_sino, (char*)d_work, st)
+               : fp_run<float>(geom, (const float*)d_coeffs, (float*)d_sino, (char*)d_work, st);
   }
   rc = check_finite_async<double>((const double*)d_coeffs, nc, st);
-  return rc != BSCT_OK ? rc : fp_run<double>(geom, (const double*)d_coeffs, (double*)d_sino, (char*)d_work, st);
+  if (rc != BSCT_OK) return rc;
+  return two ? mb_fp_run<double>(geom, (const double*)d_coeffs, (double*)d_sino, (char*)d_work, st)
+             : fp_run<double>(geom, (const double*)d_coeffs, (double*)d_sino, (char*)d_work, st);
 }

@@ -160,9 +160,19 @@ __device__ __forceinline__ int lower_bound_d(const double* __restrict__ v, int n
 // stored as monomials in v = (t - mid) / halfwidth in [-1, 1], obtained by Chebyshev
 // interpolation at 6 nodes of exact FP64 values (gram_kernel, with the short-direction
 // split near the axes).  Taps then cost a 4-step search and a 6-term Horner per view.
-constexpr int GT_KMAX = 16;
-constexpr int GT_S = 0, GT_NK = 1, GT_KN = 2, GT_MID = GT_KN + GT_KMAX, GT_IHW = GT_MID + GT_KMAX,
-              GT_COEF = GT_IHW + GT_KMAX, GT_STRIDE = GT_COEF + 6 * GT_KMAX;
+// Table layout per view: S, piece count, KMAX piece starts (padded with 1e300), centres,
+// inverse half widths, then NC monomial coefficients per piece.  One detector box (or none):
+// <= 13 pieces of degree <= 5; two boxes (Sec. 2's series of boxes): <= 41 pieces of degree 7.
+template <int KMAX_, int NC_> struct GTab {
+  static constexpr int KMAX = KMAX_, NC = NC_;
+  static constexpr int S = 0, NK = 1, KN = 2, MID = KN + KMAX, IHW = MID + KMAX, COEF = IHW + KMAX,
+                       STRIDE = COEF + NC * KMAX;
+};
+typedef GTab<16, 6> GT1;
+typedef GTab<64, 8> GT2;
+constexpr int GT_KMAX = GT1::KMAX;
+constexpr int GT_S = GT1::S, GT_NK = GT1::NK, GT_KN = GT1::KN, GT_MID = GT1::MID, GT_IHW = GT1::IHW,
+              GT_COEF = GT1::COEF, GT_STRIDE = GT1::STRIDE;
 
 __global__ void __launch_bounds__(32) k_gram_tables(const double2* __restrict__ cs, double zeta, double merge_tol,
                                                     double* __restrict__ tab) {
@@ -227,21 +237,99 @@ __global__ void __launch_bounds__(32) k_gram_tables(const double2* __restrict__ 
   T[GT_IHW + q] = 1.0 / hw;
 }
 
+template <typename L = GT1>
 __device__ __forceinline__ double gram_table_eval(const double* __restrict__ T, double t) {
   int q = 0;
 #pragma unroll
-  for (int step = 8; step > 0; step >>= 1)
-    if (T[GT_KN + q + step] <= t) q += step;
-  const double v = (t - T[GT_MID + q]) * T[GT_IHW + q];
-  const double* c = T + GT_COEF + 6 * q;
-  double r = c[5];
-  r = fma(r, v, c[4]);
-  r = fma(r, v, c[3]);
-  r = fma(r, v, c[2]);
-  r = fma(r, v, c[1]);
-  return fma(r, v, c[0]);
+  for (int step = L::KMAX / 2; step > 0; step >>= 1)
+    if (T[L::KN + q + step] <= t) q += step;
+  const double v = (t - T[L::MID + q]) * T[L::IHW + q];
+  const double* c = T + L::COEF + L::NC * q;
+  double r = c[L::NC - 1];
+#pragma unroll
+  for (int k = L::NC - 2; k >= 0; --k) r = fma(r, v, c[k]);
+  return r;
 }
 
+// Two detector boxes: the per-view Gram kernel A = M_[c,c,s,s,w1,w1,w2,w2] as the convolution
+// of M_[c,c,s,s] (with the short-direction split near the axes) and M_[w1,w1,w2,w2]; its
+// kinks -S + i|c| + j|s| + k w1 + l w2 (i, j, k, l in 0..2) cut [0, S] into <= 41 pieces of
+// degree 7, fitted by Chebyshev interpolation at 8 nodes (one thread per piece).
+__device__ inline double gram_kernel2(double t, double a, double b, double w1, double w2) {
+  BoxDirs P, Q;
+  P.ng = 0;
+  if (a > 0.0) { P.a[P.ng] = a; P.m[P.ng] = 2; ++P.ng; }
+  if (b > 0.0) { P.a[P.ng] = b; P.m[P.ng] = 2; ++P.ng; }
+  for (int g = P.ng; g < 4; ++g) { P.a[g] = 0.0; P.m[g] = 0; }
+  int small = -1;
+  if (a > 0.0 && b > 0.0) {
+    if (b < BSCT_SHORT_DIR * a) small = 1;
+    else if (a < BSCT_SHORT_DIR * b) small = 0;
+  }
+  Q.ng = 0;
+  if (w1 == w2) { Q.a[0] = w1; Q.m[0] = 4; Q.ng = 1; }
+  else { Q.a[0] = w1; Q.m[0] = 2; Q.a[1] = w2; Q.m[1] = 2; Q.ng = 2; }
+  for (int g = Q.ng; g < 4; ++g) { Q.a[g] = 0.0; Q.m[g] = 0; }
+  return box_conv(t, P, small, Q);
+}
+
+__global__ void __launch_bounds__(64) k_gram_tables2(const double2* __restrict__ cs, double w1, double w2,
+                                                     double merge_tol, double* __restrict__ tab) {
+  typedef GT2 L;
+  const int j = blockIdx.x;
+  const double a = fabs(cs[j].x), b = fabs(cs[j].y);
+  const double S = a + b + w1 + w2;
+  __shared__ double kn[96];
+  __shared__ int nk_s;
+  double* T = tab + (long)j * L::STRIDE;
+  if (threadIdx.x == 0) {
+    int n = 0;
+    kn[n++] = 0.0;
+    for (int i = 0; i <= 2; ++i)
+      for (int jj = 0; jj <= 2; ++jj)
+        for (int k = 0; k <= 2; ++k)
+          for (int l = 0; l <= 2; ++l) {
+            const double x = -S + i * a + jj * b + k * w1 + l * w2;
+            if (x > 0.0 && x < S && n < 94) kn[n++] = x;
+          }
+    kn[n++] = S;
+    for (int i = 1; i < n; ++i) {  // sort
+      const double t = kn[i];
+      int q = i - 1;
+      while (q >= 0 && kn[q] > t) { kn[q + 1] = kn[q]; --q; }
+      kn[q + 1] = t;
+    }
+    int m = 1;  // merge kinks closer than merge_tol (keep S as the last one)
+    for (int i = 1; i < n; ++i)
+      if (kn[i] - kn[m - 1] > merge_tol) kn[m++] = kn[i];
+      else if (i == n - 1) kn[m - 1] = kn[i];
+    if (m > L::KMAX) m = L::KMAX;  // cannot happen: at most 41 distinct kinks in [0, S]
+    nk_s = m;
+    T[L::S] = S;
+    T[L::NK] = m;
+    for (int i = 0; i < L::KMAX; ++i) T[L::KN + i] = i < m ? kn[i] : 1e300;
+  }
+  __syncthreads();
+  const int nk = nk_s;
+  const int q = threadIdx.x;
+  if (q >= L::KMAX) return;
+  if (q >= nk - 1) {
+    T[L::MID + q] = 0.0;
+    T[L::IHW + q] = 0.0;
+    for (int i = 0; i < L::NC; ++i) T[L::COEF + L::NC * q + i] = 0.0;
+    return;
+  }
+  const double lo = kn[q], hi = kn[q + 1];
+  const double mid = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
+  double fv[8];
+  for (int i = 0; i < 8; ++i) fv[i] = gram_kernel2(mid + hw * cospi((2.0 * i + 1.0) / 16.0), a, b, w1, w2);
+  cheb8_monomials(fv, T + L::COEF + L::NC * q);
+  T[L::MID + q] = mid;
+  T[L::IHW + q] = 1.0 / hw;
+}
+
+// zeta: the sum of the detector box widths (bounds the strip of views that reach a tap)
+template <typename L>
 __global__ void k_gram_taps(int N, int na, const double* __restrict__ th, const double2* __restrict__ cs,
                             const double* __restrict__ tab, double zeta, double* __restrict__ G) {
   const long H = (long)(2 * N - 1) * (N - 1) + N;
@@ -270,18 +358,18 @@ __global__ void k_gram_taps(int N, int na, const double* __restrict__ th, const 
     for (; j + 1 < j1; j += 2) {
       const double2 u0 = cs[j], u1 = cs[j + 1];
       const double t0 = fabs(d1 * u0.x + d2 * u0.y), t1 = fabs(d1 * u1.x + d2 * u1.y);
-      const double* T0 = tab + (long)j * GT_STRIDE;
-      const double* T1 = T0 + GT_STRIDE;
-      const double s0 = T0[GT_S], s1 = T1[GT_S];
-      const double e0 = gram_table_eval(T0, fmin(t0, s0)), e1 = gram_table_eval(T1, fmin(t1, s1));
+      const double* T0 = tab + (long)j * L::STRIDE;
+      const double* T1 = T0 + L::STRIDE;
+      const double s0 = T0[L::S], s1 = T1[L::S];
+      const double e0 = gram_table_eval<L>(T0, fmin(t0, s0)), e1 = gram_table_eval<L>(T1, fmin(t1, s1));
       if (t0 < s0) acc += e0;
       if (t1 < s1) acc += e1;
     }
     if (j < j1) {
       const double2 u = cs[j];
       const double t = fabs(d1 * u.x + d2 * u.y);
-      const double* T = tab + (long)j * GT_STRIDE;
-      if (t < T[GT_S]) acc += gram_table_eval(T, t);
+      const double* T = tab + (long)j * L::STRIDE;
+      if (t < T[L::S]) acc += gram_table_eval<L>(T, t);
     }
   };
   const double hw = (r > 1.0001f * wmax) ? (double)(asinf(wmax / r) * 0.318309886f) + 1e-4 : 1.0;
@@ -414,7 +502,28 @@ int bsct_check_geom(const bsct_geom* g) {
     return fail(BSCT_ERR_INVALID_ARG, "0 < zeta_blur < 0.2 is not supported (short blur direction)");
   for (int i = 0; i < g->n_angles; ++i)
     if (!isfinite(g->angles_pi[i])) return fail(BSCT_ERR_INVALID_ARG, "angles_pi holds a non-finite value");
+  if (g->n_blur < 0 || g->n_blur > 2) return fail(BSCT_ERR_INVALID_ARG, "n_blur must be 0, 1 or 2");
+  if (g->n_blur > 0) {
+    if (!g->blur_widths) return fail(BSCT_ERR_INVALID_ARG, "blur_widths is NULL");
+    if (g->zeta_blur != 0.0) return fail(BSCT_ERR_INVALID_ARG, "zeta_blur must be 0 when blur_widths is given");
+    for (int i = 0; i < g->n_blur; ++i)
+      if (!isfinite(g->blur_widths[i]) || g->blur_widths[i] < BSCT_SHORT_DIR || g->blur_widths[i] > 4.0)
+        return fail(BSCT_ERR_INVALID_ARG, "detector box widths must lie in [0.2, 4]");
+  }
   return BSCT_OK;
+}
+
+int bsct_blur_boxes(const bsct_geom* g, double w[2]) {
+  w[0] = w[1] = 0.0;
+  if (g->n_blur > 0) {
+    for (int i = 0; i < g->n_blur; ++i) w[i] = g->blur_widths[i];
+    return g->n_blur;
+  }
+  if (g->zeta_blur > 0.0) {
+    w[0] = g->zeta_blur;
+    return 1;
+  }
+  return 0;
 }
 
 extern "C" void bsct_gram_free(bsct_gram* g) {
@@ -471,7 +580,11 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
   g->N = N;
   g->precision = precision;
   g->n_angles = na;
-  g->zeta = geom->zeta_blur;
+  {
+    double w[2];
+    bsct_blur_boxes(geom, w);
+    g->zeta = w[0] + w[1];  // total detector width (informational)
+  }
   g->lambda = geom->lambda_y;
   double *d_ang = nullptr, *d_th = nullptr, *d_emb = nullptr, *d_gtab = nullptr;
   double2* d_cs = nullptr;
@@ -486,7 +599,9 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
   CTRY(cudaMalloc(&d_ang, na * sizeof(double)));
   CTRY(cudaMalloc(&d_th, na * sizeof(double)));
   CTRY(cudaMalloc(&d_cs, na * sizeof(double2)));
-  CTRY(cudaMalloc(&d_gtab, (size_t)na * GT_STRIDE * sizeof(double)));
+  double wb[2];
+  const int nbox = bsct_blur_boxes(geom, wb);
+  CTRY(cudaMalloc(&d_gtab, (size_t)na * (nbox == 2 ? GT2::STRIDE : GT1::STRIDE) * sizeof(double)));
   CTRY(cudaMalloc(&g->taps, ntap * sizeof(double)));
   CTRY(cudaMalloc(&d_emb, (size_t)L * L * sizeof(double)));
   CTRY(cudaMalloc(&d_S2, (size_t)L * N * 2 * sizeof(double)));
@@ -496,8 +611,13 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
 
   k_geometry<<<(na + 127) / 128, 128, 0, st>>>(d_ang, na, d_th, d_cs);
   const long H = (long)(2 * N - 1) * (N - 1) + N;
-  k_gram_tables<<<na, 32, 0, st>>>(d_cs, geom->zeta_blur, 1e-13, d_gtab);
-  k_gram_taps<<<(unsigned)((H + 127) / 128), 128, 0, st>>>(N, na, d_th, d_cs, d_gtab, geom->zeta_blur, g->taps);
+  if (nbox == 2) {
+    k_gram_tables2<<<na, 64, 0, st>>>(d_cs, wb[0], wb[1], 1e-13, d_gtab);
+    k_gram_taps<GT2><<<(unsigned)((H + 127) / 128), 128, 0, st>>>(N, na, d_th, d_cs, d_gtab, wb[0] + wb[1], g->taps);
+  } else {
+    k_gram_tables<<<na, 32, 0, st>>>(d_cs, wb[0], 1e-13, d_gtab);
+    k_gram_taps<GT1><<<(unsigned)((H + 127) / 128), 128, 0, st>>>(N, na, d_th, d_cs, d_gtab, wb[0], g->taps);
+  }
   k_embed<<<(unsigned)(((long)L * L + 255) / 256), 256, 0, st>>>(g->taps, N, d_emb);
   count_launch(4);
   CTRY(cudaGetLastError());

@@ -111,3 +111,40 @@ def test_check_finite_validates_on_the_host(lib):
     assert lib.bsct_check_finite(None, 10, 0, None) == -1   # NULL buffer with values to check
     assert lib.bsct_check_finite(None, -1, 0, None) == -1   # negative count
     assert lib.bsct_check_finite(ctypes.c_void_p(16), 4, 7, None) == -1  # unknown precision
+
+
+def test_detector_box_list_validates_on_the_host(lib):
+    import paper_2005_13471_gb300 as m
+
+    nbytes = ctypes.c_size_t()
+    ang = np.arange(6) / 6
+    one = m.Geometry(64, ang, 90, 1.0, 0.8)
+    two = m.Geometry(64, ang, 90, 1.0, (0.8, 1.3))
+    assert m.Geometry(64, ang, 90, 1.0, (0.8, 0.0)).blur_widths.tolist() == [0.8]  # zero widths dropped
+    # workspaces: two boxes take the wider tables of their own path
+    for f in (lib.bsct_backproject_workspace, lib.bsct_forward_project_workspace):
+        assert f(one.cptr(), 0, ctypes.byref(nbytes)) == 0
+        n1 = nbytes.value
+        assert f(two.cptr(), 0, ctypes.byref(nbytes)) == 0
+        assert nbytes.value > 0 and nbytes.value != n1
+    # rejected before any CUDA call: widths outside [0.2, 4], more than two boxes, a box
+    # list together with zeta_blur, n_blur > 0 without widths
+    bad = [m.Geometry(64, ang, 90, 1.0, (0.8, 0.1)), m.Geometry(64, ang, 90, 1.0, (0.8, 4.5)),
+           m.Geometry(64, ang, 90, 1.0, (0.5, 0.6, 0.7))]
+    for g in bad:
+        assert lib.bsct_backproject_workspace(g.cptr(), 0, ctypes.byref(nbytes)) == -1
+    g = m.Geometry(64, ang, 90, 1.0, (0.8, 1.3))
+    g._c.zeta_blur = 0.5
+    assert lib.bsct_forward_project_workspace(g.cptr(), 0, ctypes.byref(nbytes)) == -1
+    g = m.Geometry(64, ang, 90, 1.0, 0.0)
+    g._c.n_blur = 2
+    assert lib.bsct_backproject_workspace(g.cptr(), 0, ctypes.byref(nbytes)) == -1
+    # two boxes too wide for the sample spacing: more samples per pixel than the tables hold
+    wide = m.Geometry(64, ang, 90, 0.2, (4.0, 4.0))
+    assert lib.bsct_backproject(wide.cptr(), ctypes.c_void_p(16), ctypes.c_void_p(16), 0, ctypes.c_void_p(16),
+                                1 << 40, None) == -2
+    # the batch takes one box
+    arr = (m._Geom * 1)(two._c)
+    h = ctypes.c_void_p()
+    assert lib.bsct_batch_create(1, arr, ctypes.byref(h), None) == -2
+    assert not h
