@@ -75,7 +75,7 @@ def measured_bf16_tflops():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("gram_fft.cu", "bsct_fft.cuh", "bsct_common.cuh"):
+    for name in ("gram_fft.cu", "bsct_fft.cuh", "bsct_fft2.cuh", "bsct_common.cuh"):
         with open(os.path.join(ROOT, "paper_2005_13471_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -413,10 +413,11 @@ def run_ours(args):
 
     # ---------------------------------------------------------------- roofline (dominant kernel)
     hbm, peak_kind = measured_peaks()
+    # the FP32 apply's three kernels (paired-FFT forms): algorithmic bytes per launch
     kernel_bytes = {
-        "k_rows_r2c": 4 * N * N + 8 * N * N,
-        "k_cols_conv": 8 * N * N + 8 * N * (N + 1) + 8 * N * N,
-        "k_rows_c2r": 8 * N * N + 4 * N * N,
+        "k2_rows_r2c": 4 * N * N + 8 * N * N,
+        "k2_cols_conv": 8 * N * N + 8 * N * (N + 1) + 8 * N * N,
+        "k2_rows_c2r": 8 * N * N + 4 * N * N,
     }
     names = list(kernel_bytes)
     dom = int(np.argmax(kt))
@@ -534,6 +535,32 @@ def run_ours(args):
         t["backproject_flop_per_pair"] = "70, algorithmic: <= 7 bins x degree-5 Horner per pixel-view pair"
         extras["hot_path_pass"] = t
         g2.close()
+        # detector kernel of two boxes (widths 1.0 and 0.5) on the 512 x 512 / 720-view
+        # geometry: filter build, back projection and forward projection, FP32, each timed
+        # once after one untimed call
+        cm = get_config("learned_eval_n512")
+        am = np.arange(cm["n_angles"], dtype=np.float64) / cm["n_angles"]
+        mb = {"workload": f"N={cm['N']}, {cm['n_angles']} views, {cm['n_bins']} bins, lambda_y={cm['lambda_y']}, "
+                          "detector boxes of widths 1.0 and 0.5"}
+        for widths, key in (((1.0, 0.5), "two_boxes"), (1.5, "one_box_1.5")):
+            gm = bsct.Geometry(cm["N"], am, cm["n_bins"], cm["lambda_y"], widths)
+            xm = torch.rand((cm["N"], cm["N"]), device=dev)
+            sm = bsct.forward_project(gm, xm, bsct.F32)
+            bsct.backproject(gm, sm, bsct.F32)
+            bsct.gram_build(gm, bsct.F32).close()
+            em = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            em[0].record(stream)
+            gg = bsct.gram_build(gm, bsct.F32)
+            em[1].record(stream)
+            bsct.backproject(gm, sm, bsct.F32)
+            em[2].record(stream)
+            bsct.forward_project(gm, xm, bsct.F32)
+            em[3].record(stream)
+            torch.cuda.synchronize()
+            gg.close()
+            mb[key] = {"gram_build_ms": em[0].elapsed_time(em[1]), "backproject_ms": em[1].elapsed_time(em[2]),
+                       "forward_project_ms": em[2].elapsed_time(em[3])}
+        extras["multibox"] = mb
         # time to a 1e-4 relative residual on the learned-evaluation geometry: 20 held-out
         # seeds (phantoms generated on the device), medians and iteration counts
         from workloads.phantom import ellipse_params, ellipse_sinogram_torch, poisson_log_sinogram_torch

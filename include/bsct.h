@@ -145,7 +145,9 @@ int bsct_gram_spectrum(const bsct_gram* g, double* d_out, void* stream);
  * with every length-2N DFT as two split-BF16 GEMMs on the tensor cores (operands split
  * into BF16 high + low parts, FP32 accumulation; relative error ~5e-6 to 1e-5); its
  * ~12 (2N)^2-float scratch is allocated in the handle on the first such call.
- * d_x and d_y: N*N elements, may not alias. */
+ * d_x and d_y: N*N elements, may not alias; for the FP32 FFT apply both must be 8-byte
+ * aligned (as every cudaMalloc'd buffer is), else BSCT_ERR_INVALID_ARG.  The solvers
+ * below apply G to their caller's x0 / x as well and carry the same requirement. */
 int bsct_gram_apply(const bsct_gram* g, const void* d_x, void* d_y, int mode, void* stream);
 
 /* y_k = G x_k for n images held in HOST memory: h_x and h_y hold n consecutive [N][N]

@@ -1046,6 +1046,11 @@ static int run_apply2(const float* in, float* p, float* out, double* sc, double*
     BSCT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc, TC, smc));
     per_sm_max[d] = per_sm < 1 ? 1 : per_sm;
   }
+  // the row passes load and store the rows as 8-byte complex pairs
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(p)) & 7) {
+    bsct_set_last_message("FP32 Gram apply: x, y (and the CG direction) must be 8-byte aligned");
+    return BSCT_ERR_INVALID_ARG;
+  }
   const int per_sm = cols == 1 ? 1 : per_sm_max[d];
   const int tiles = (N / 2) / CC::G;
   const int grid_c = per_sm * sm_count() < tiles ? per_sm * sm_count() : tiles;

@@ -9,7 +9,8 @@ short-direction split carries the accuracy).  Gates (relative to the largest ref
 value): FP64 1e-12; FP32 1e-5 (the tables are fitted in FP64 and rounded once; the
 detector coordinate is formed in FP64).  Two properties that need no oracle: every view
 of the forward projection sums to the sum of the coefficients when lambda_y = 1 (unit
-mass of the footprint, partition of unity of the unit-spaced samples), and on the views
+mass of the footprint; with a unit-width box among its directions the unit-spaced
+samples form a partition of unity), and on the views
 {0, pi/2} with two unit boxes, lambda_y = 1 and even N, M the back projection of the
 projection is exactly G c (the footprint is then the quadratic B-spline, Sec. 5).
 """
@@ -51,8 +52,8 @@ def angles_for(kind, n, seed):
     return np.random.default_rng(seed).uniform(-1.0, 2.0, n)
 
 
-@pytest.mark.parametrize("N,kind,widths", [(8, "uniform", (0.5, 0.8)), (12, "near_axis", (0.7, 1.0)),
-                                           (10, "random", (1.0, 1.0)), (6, "near_axis", (2.5, 0.3))])
+@pytest.mark.parametrize("N,kind,widths", [(16, "uniform", (0.5, 0.8)), (16, "near_axis", (0.7, 1.0)),
+                                           (32, "random", (1.0, 1.0)), (16, "near_axis", (2.5, 0.3))])
 def test_gram_taps_two_boxes(bsct, N, kind, widths):
     angles = angles_for(kind, 9, N)
     geom = bsct.Geometry(N, angles, 2 * N, 1.0, widths)
@@ -103,11 +104,13 @@ def test_forward_two_boxes(bsct, N, M, lam, widths, kind, nv, prec):
 
 
 def test_forward_two_boxes_unit_mass(bsct):
-    # lambda_y = 1 and a detector wide enough for every footprint: each view sums to sum(c)
+    # lambda_y = 1, one box of unit width and a detector wide enough for every footprint:
+    # the unit box makes the unit-spaced samples of every footprint sum to its unit mass,
+    # so each view sums to sum(c)
     N, M = 40, 90
     angles = np.random.default_rng(5).uniform(0.0, 2.0, 23)
     c = np.random.default_rng(6).standard_normal((N, N))
-    geom = bsct.Geometry(N, angles, M, 1.0, (0.9, 1.7))
+    geom = bsct.Geometry(N, angles, M, 1.0, (1.0, 1.7))
     g = bsct.forward_project(geom, torch.tensor(c, device=DEV), bsct.F64).cpu().numpy()
     assert np.max(np.abs(g.sum(axis=1) - c.sum())) < 1e-11 * np.abs(c).sum()
 

@@ -46,6 +46,7 @@ def test_gemm_bf16(bsct, path, ta, tb, M, N, K, batch):
     b = torch.randn((batch, N, K) if tb else (batch, K, N), generator=g).to(torch.bfloat16)
     c0 = torch.randn((batch, M, N), generator=g)
     bsct.set_gemm_path(path)
+    bsct.input_status()  # clear what earlier work on the device left in the (sticky) status
     try:
         c = bsct.gemm_bf16(a.to(DEV), b.to(DEV), c0.clone().to(DEV), trans_a=ta, trans_b=tb, alpha=0.5, beta=2.0)
         torch.cuda.synchronize()

@@ -107,31 +107,47 @@ def make_problem(cfg, slice_id=0, noise=True):
 
 def ellipse_sinogram_torch(params, angles_pi, M, lambda_y, zeta=0.0, device="cuda", dtype=None):
     """Same analytic sinogram as ``ellipse_sinogram`` evaluated with torch on a device
-    (used to synthesise many large batch inputs quickly)."""
+    (used to synthesise many large batch inputs quickly).  The ellipses' chord terms are
+    formed together in blocks (the same FP64 operations, element by element, as one
+    ellipse at a time) and added to the sinogram in the parameters' order."""
     import torch
 
     dtype = dtype or torch.float64
     c_np, s_np = _angles(angles_pi)
-    c = torch.tensor(c_np, dtype=torch.float64, device=device)
-    s = torch.tensor(s_np, dtype=torch.float64, device=device)
+    c = torch.tensor(c_np, dtype=torch.float64, device=device)[None, :]
+    s = torch.tensor(s_np, dtype=torch.float64, device=device)[None, :]
     ym = (torch.arange(M, dtype=torch.float64, device=device) - (M - 1) / 2.0) * lambda_y
     sino = torch.zeros((len(c_np), M), dtype=torch.float64, device=device)
-    for cx, cy, a, b, phi, rho in params:
-        cr = c * math.cos(phi) + s * math.sin(phi)
-        sr = s * math.cos(phi) - c * math.sin(phi)
-        r2 = (a * a * cr * cr + b * b * sr * sr)[:, None]
+    params = [tuple(float(v) for v in p) for p in params]
+    block = max(1, (1 << 25) // max(1, len(c_np) * M))
+    for e0 in range(0, len(params), block):
+        P = params[e0:e0 + block]
+
+        def col(v):
+            return torch.tensor(v, dtype=torch.float64, device=device)[:, None]
+
+        cx, cy = col([p[0] for p in P]), col([p[1] for p in P])
+        a, b, rho = col([p[2] for p in P]), col([p[3] for p in P]), col([p[5] for p in P])
+        cphi, sphi = col([math.cos(p[4]) for p in P]), col([math.sin(p[4]) for p in P])
+        aa, bb = col([p[2] * p[2] for p in P]), col([p[3] * p[3] for p in P])
+        sc2 = col([2.0 * p[5] * p[2] * p[3] for p in P])
+        cr = c * cphi + s * sphi
+        sr = s * cphi - c * sphi
+        r2 = (aa * cr * cr + bb * sr * sr)[:, :, None]
         r = torch.sqrt(r2)
-        t = ym[None, :] - (cx * c + cy * s)[:, None]
-        scale = 2.0 * rho * a * b / r2
+        t = ym[None, None, :] - (cx * c + cy * s)[:, :, None]
+        scale = r2.reciprocal() * sc2[:, :, None]  # as torch evaluates number / tensor
         if zeta == 0.0:
-            sino += torch.where(t.abs() < r, scale * torch.sqrt(torch.clamp(r2 - t * t, min=0.0)),
-                                torch.zeros_like(t))
+            term = torch.where(t.abs() < r, scale * torch.sqrt(torch.clamp(r2 - t * t, min=0.0)),
+                               torch.zeros_like(t))
         else:
             def F(u):
                 u = torch.maximum(torch.minimum(u, r), -r)
                 return 0.5 * (u * torch.sqrt(torch.clamp(r2 - u * u, min=0.0))
                               + r2 * torch.asin(torch.clamp(u / r, -1.0, 1.0)))
-            sino += scale * (F(t + 0.5 * zeta) - F(t - 0.5 * zeta)) / zeta
+            term = scale * (F(t + 0.5 * zeta) - F(t - 0.5 * zeta)) / zeta
+        for k in range(len(P)):
+            sino += term[k]
     return sino.to(dtype)
 
 
