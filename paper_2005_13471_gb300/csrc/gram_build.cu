@@ -1,9 +1,9 @@
 // Gram filter build (Sec. 4) and the FFT-based Gram apply entry points.
 //
-//   k_geometry   : views reduced to half turns in [0, 1) (theta and theta + pi give the
-//                  same Gram kernel), cos/sin by cospi/sinpi (exact zeros on the axes),
-//                  sorted by angle with a rank count so every tap can find its views by
-//                  binary search.
+//   k_view_keys, k_view_rank : views reduced to half turns in [0, 1) (theta and theta + pi
+//                  give the same Gram kernel), cos/sin by cospi/sinpi (exact zeros on the
+//                  axes), sorted by angle with a rank count (64-bit integer keys) so every
+//                  tap can find its views by binary search.
 //   k_gram_tables: per view, the Gram kernel A(t) = M_[c, c, s, s, zeta, zeta](t) as an
 //                  exact piecewise polynomial between its kinks (FP64).
 //   k_gram_taps  : one thread per tap d of the upper half plane:
@@ -109,23 +109,44 @@ template int build_fft_tables<double>(cpx<double>*, int, cudaStream_t);
 // ------------------------------------------------------------------------------------
 // geometry (views sorted by angle in half turns, [0, 1))
 // ------------------------------------------------------------------------------------
-__global__ void k_geometry(const double* __restrict__ ang, int na, double* __restrict__ th_sorted,
-                           double2* __restrict__ cs_sorted) {
+// reduced angle of each view (half turns in [0, 1)) and its bit pattern, which orders
+// non-negative doubles like the values themselves
+__global__ void k_view_keys(const double* __restrict__ ang, int na, double* __restrict__ red,
+                            unsigned long long* __restrict__ key) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= na) return;
   double a = ang[i];
   a = a - floor(a);
-  if (a >= 1.0) a = 0.0;
+  if (a >= 1.0 || !(a > 0.0)) a = 0.0;  // also maps -0 to +0
+  red[i] = a;
+  key[i] = (unsigned long long)__double_as_longlong(a);
+}
+// rank of view i = #{j : key_j < key_i or (key_j == key_i and j < i)}, by 64-bit integer
+// compares against key tiles in shared memory; writes the views in angle order (FP32 angle
+// for the taps' window search, FP64 cos / sin)
+constexpr int GEO_T = 256;
+__global__ void __launch_bounds__(GEO_T) k_view_rank(const double* __restrict__ red,
+                                                     const unsigned long long* __restrict__ key, int na,
+                                                     float* __restrict__ thf_sorted, double2* __restrict__ cs_sorted) {
+  __shared__ unsigned long long tile[GEO_T];
+  const int i = blockIdx.x * GEO_T + threadIdx.x;
+  const unsigned long long ki = i < na ? key[i] : 0ull;
   int rank = 0;
-  for (int j = 0; j < na; ++j) {
-    double b = ang[j];
-    b = b - floor(b);
-    if (b >= 1.0) b = 0.0;
-    rank += (b < a) || (b == a && j < i);
+  for (int t0 = 0; t0 < na; t0 += GEO_T) {
+    __syncthreads();
+    if (t0 + threadIdx.x < na) tile[threadIdx.x] = key[t0 + threadIdx.x];
+    __syncthreads();
+    const int n = na - t0 < GEO_T ? na - t0 : GEO_T;
+    for (int k = 0; k < n; ++k) {
+      const unsigned long long kj = tile[k];
+      rank += (kj < ki) || (kj == ki && t0 + k < i);
+    }
   }
+  if (i >= na) return;
+  const double a = red[i];
   double s, c;
   sincospi(a, &s, &c);
-  th_sorted[rank] = a;
+  thf_sorted[rank] = (float)a;
   cs_sorted[rank] = make_double2(c, s);
 }
 
@@ -145,7 +166,7 @@ __device__ __forceinline__ double gram_kernel(double t, double a, double b, doub
   return box_eval(t, D, small);
 }
 
-__device__ __forceinline__ int lower_bound_d(const double* __restrict__ v, int n, double x) {
+__device__ __forceinline__ int lower_bound_f(const float* __restrict__ v, int n, float x) {
   int lo = 0, hi = n;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
@@ -170,18 +191,62 @@ template <int KMAX_, int NC_> struct GTab {
 };
 typedef GTab<16, 6> GT1;
 typedef GTab<64, 8> GT2;
-constexpr int GT_KMAX = GT1::KMAX;
-constexpr int GT_S = GT1::S, GT_NK = GT1::NK, GT_KN = GT1::KN, GT_MID = GT1::MID, GT_IHW = GT1::IHW,
-              GT_COEF = GT1::COEF, GT_STRIDE = GT1::STRIDE;
 
-__global__ void __launch_bounds__(32) k_gram_tables(const double2* __restrict__ cs, double zeta, double merge_tol,
+// Pieces [kn[q], kn[q+1]] (q < nk - 1) of a per-view table: the kernel values at the NC
+// Chebyshev nodes of every piece are spread over all threads of the CTA (the near-axis
+// views' short-direction evaluations are the costly ones), then one thread per piece turns
+// its values into monomial coefficients.  fv: shared scratch of KMAX * NC doubles.
+template <typename L, typename F>
+__device__ void fit_table_pieces(double* __restrict__ T, const double* kn, int nk, double* fv, F kernel) {
+  const int items = (nk - 1) * L::NC;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int q = it / L::NC, i = it - q * L::NC;
+    const double mid = 0.5 * (kn[q] + kn[q + 1]), hw = 0.5 * (kn[q + 1] - kn[q]);
+    fv[it] = kernel(mid + hw * cospi((2.0 * i + 1.0) / (2.0 * L::NC)));
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < L::KMAX; q += blockDim.x) {
+    double* c = T + L::COEF + L::NC * q;
+    if (q >= nk - 1) {
+      T[L::MID + q] = 0.0;
+      T[L::IHW + q] = 0.0;
+      for (int i = 0; i < L::NC; ++i) c[i] = 0.0;
+      continue;
+    }
+    const double* v = fv + q * L::NC;
+    if constexpr (L::NC == 8) {
+      cheb8_monomials(v, c);
+    } else {
+      static_assert(L::NC == 6, "6 or 8 coefficients");
+      double ch[6];
+      for (int k = 0; k < 6; ++k) {
+        double acc = 0.0;
+        for (int i = 0; i < 6; ++i) acc += v[i] * cospi(k * (2.0 * i + 1.0) / 12.0);
+        ch[k] = acc * (k == 0 ? 1.0 / 6.0 : 2.0 / 6.0);
+      }
+      // Chebyshev -> monomial: T0=1, T1=v, T2=2v^2-1, T3=4v^3-3v, T4=8v^4-8v^2+1, T5=16v^5-20v^3+5v
+      c[0] = ch[0] - ch[2] + ch[4];
+      c[1] = ch[1] - 3.0 * ch[3] + 5.0 * ch[5];
+      c[2] = 2.0 * ch[2] - 8.0 * ch[4];
+      c[3] = 4.0 * ch[3] - 20.0 * ch[5];
+      c[4] = 8.0 * ch[4];
+      c[5] = 16.0 * ch[5];
+    }
+    T[L::MID + q] = 0.5 * (kn[q] + kn[q + 1]);
+    T[L::IHW + q] = 2.0 / (kn[q + 1] - kn[q]);
+  }
+}
+
+__global__ void __launch_bounds__(64) k_gram_tables(const double2* __restrict__ cs, double zeta, double merge_tol,
                                                     double* __restrict__ tab) {
+  typedef GT1 L;
   const int j = blockIdx.x;
   const double a = fabs(cs[j].x), b = fabs(cs[j].y);
   const double S = a + b + zeta;
   __shared__ double kn[32];
+  __shared__ double fv[L::KMAX * L::NC];
   __shared__ int nk_s;
-  double* T = tab + (long)j * GT_STRIDE;
+  double* T = tab + (long)j * L::STRIDE;
   if (threadIdx.x == 0) {
     int n = 0;
     kn[n++] = 0.0;
@@ -203,38 +268,12 @@ __global__ void __launch_bounds__(32) k_gram_tables(const double2* __restrict__ 
       if (kn[i] - kn[m - 1] > merge_tol) kn[m++] = kn[i];
       else if (i == n - 1) kn[m - 1] = kn[i];
     nk_s = m;
-    T[GT_S] = S;
-    T[GT_NK] = m;
-    for (int i = 0; i < GT_KMAX; ++i) T[GT_KN + i] = i < m ? kn[i] : 1e300;
+    T[L::S] = S;
+    T[L::NK] = m;
+    for (int i = 0; i < L::KMAX; ++i) T[L::KN + i] = i < m ? kn[i] : 1e300;
   }
   __syncthreads();
-  const int nk = nk_s;
-  const int q = threadIdx.x;
-  if (q >= GT_KMAX) return;
-  if (q >= nk - 1) {
-    T[GT_MID + q] = 0.0;
-    T[GT_IHW + q] = 0.0;
-    for (int i = 0; i < 6; ++i) T[GT_COEF + 6 * q + i] = 0.0;
-    return;
-  }
-  const double lo = kn[q], hi = kn[q + 1];
-  const double mid = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
-  double fv[6], ch[6];
-  for (int i = 0; i < 6; ++i) fv[i] = gram_kernel(mid + hw * cospi((2.0 * i + 1.0) / 12.0), a, b, zeta);
-  for (int k = 0; k < 6; ++k) {
-    double acc = 0.0;
-    for (int i = 0; i < 6; ++i) acc += fv[i] * cospi(k * (2.0 * i + 1.0) / 12.0);
-    ch[k] = acc * (k == 0 ? 1.0 / 6.0 : 2.0 / 6.0);
-  }
-  double* c = T + GT_COEF + 6 * q;
-  c[0] = ch[0] - ch[2] + ch[4];
-  c[1] = ch[1] - 3.0 * ch[3] + 5.0 * ch[5];
-  c[2] = 2.0 * ch[2] - 8.0 * ch[4];
-  c[3] = 4.0 * ch[3] - 20.0 * ch[5];
-  c[4] = 8.0 * ch[4];
-  c[5] = 16.0 * ch[5];
-  T[GT_MID + q] = mid;
-  T[GT_IHW + q] = 1.0 / hw;
+  fit_table_pieces<L>(T, kn, nk_s, fv, [&](double t) { return gram_kernel(t, a, b, zeta); });
 }
 
 template <typename L = GT1>
@@ -280,6 +319,7 @@ __global__ void __launch_bounds__(64) k_gram_tables2(const double2* __restrict__
   const double a = fabs(cs[j].x), b = fabs(cs[j].y);
   const double S = a + b + w1 + w2;
   __shared__ double kn[96];
+  __shared__ double fv[L::KMAX * L::NC];
   __shared__ int nk_s;
   double* T = tab + (long)j * L::STRIDE;
   if (threadIdx.x == 0) {
@@ -310,27 +350,12 @@ __global__ void __launch_bounds__(64) k_gram_tables2(const double2* __restrict__
     for (int i = 0; i < L::KMAX; ++i) T[L::KN + i] = i < m ? kn[i] : 1e300;
   }
   __syncthreads();
-  const int nk = nk_s;
-  const int q = threadIdx.x;
-  if (q >= L::KMAX) return;
-  if (q >= nk - 1) {
-    T[L::MID + q] = 0.0;
-    T[L::IHW + q] = 0.0;
-    for (int i = 0; i < L::NC; ++i) T[L::COEF + L::NC * q + i] = 0.0;
-    return;
-  }
-  const double lo = kn[q], hi = kn[q + 1];
-  const double mid = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
-  double fv[8];
-  for (int i = 0; i < 8; ++i) fv[i] = gram_kernel2(mid + hw * cospi((2.0 * i + 1.0) / 16.0), a, b, w1, w2);
-  cheb8_monomials(fv, T + L::COEF + L::NC * q);
-  T[L::MID + q] = mid;
-  T[L::IHW + q] = 1.0 / hw;
+  fit_table_pieces<L>(T, kn, nk_s, fv, [&](double t) { return gram_kernel2(t, a, b, w1, w2); });
 }
 
 // zeta: the sum of the detector box widths (bounds the strip of views that reach a tap)
 template <typename L>
-__global__ void k_gram_taps(int N, int na, const double* __restrict__ th, const double2* __restrict__ cs,
+__global__ void k_gram_taps(int N, int na, const float* __restrict__ th, const double2* __restrict__ cs,
                             const double* __restrict__ tab, double zeta, double* __restrict__ G) {
   const long H = (long)(2 * N - 1) * (N - 1) + N;
   const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -346,7 +371,9 @@ __global__ void k_gram_taps(int N, int na, const double* __restrict__ th, const 
   // the window |theta - (phi_d + pi/2)| <= asin(wmax / |d|).  The window only has to
   // contain them (views outside the support are skipped below), so it is computed in
   // FP32 and widened by 1e-4 half turns - far more than the FP32 error, which is at most
-  // ~1e-5 here because asin's argument stays below 0.9999 - while the taps stay FP64.
+  // ~1e-5 here because asin's argument stays below 0.9999 - and found by binary search
+  // in the FP32 copy of the sorted angles (each within 6e-8 of its FP64 value), while
+  // the taps stay FP64.
   const float wmax = 1.41421356f + (float)zeta;  // >= |c| + |s| + zeta for every view
   const float r = hypotf((float)d1, (float)d2);
   double acc = 0.0;
@@ -372,22 +399,22 @@ __global__ void k_gram_taps(int N, int na, const double* __restrict__ th, const 
       if (t < T[L::S]) acc += gram_table_eval<L>(T, t);
     }
   };
-  const double hw = (r > 1.0001f * wmax) ? (double)(asinf(wmax / r) * 0.318309886f) + 1e-4 : 1.0;
-  if (hw >= 0.5) {
+  const float hw = (r > 1.0001f * wmax) ? asinf(wmax / r) * 0.318309886f + 1e-4f : 1.0f;
+  if (hw >= 0.5f) {
     visit(0, na);
   } else {
-    const double phi = (double)(atan2f((float)d2, (float)d1) * 0.318309886f);  // / pi, in [0, 1]
-    double centre = phi + 0.5;
-    if (centre >= 1.0) centre -= 1.0;
-    const double lo = centre - hw, hi = centre + hw;
-    if (lo < 0.0) {
-      visit(lower_bound_d(th, na, lo + 1.0), na);
-      visit(0, lower_bound_d(th, na, hi));
-    } else if (hi > 1.0) {
-      visit(lower_bound_d(th, na, lo), na);
-      visit(0, lower_bound_d(th, na, hi - 1.0));
+    const float phi = atan2f((float)d2, (float)d1) * 0.318309886f;  // / pi, in [0, 1]
+    float centre = phi + 0.5f;
+    if (centre >= 1.0f) centre -= 1.0f;
+    const float lo = centre - hw, hi = centre + hw;
+    if (lo < 0.0f) {
+      visit(lower_bound_f(th, na, lo + 1.0f), na);
+      visit(0, lower_bound_f(th, na, hi));
+    } else if (hi > 1.0f) {
+      visit(lower_bound_f(th, na, lo), na);
+      visit(0, lower_bound_f(th, na, hi - 1.0f));
     } else {
-      visit(lower_bound_d(th, na, lo), lower_bound_d(th, na, hi));
+      visit(lower_bound_f(th, na, lo), lower_bound_f(th, na, hi));
     }
   }
   const int W = 2 * N - 1;
@@ -586,18 +613,22 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
     g->zeta = w[0] + w[1];  // total detector width (informational)
   }
   g->lambda = geom->lambda_y;
-  double *d_ang = nullptr, *d_th = nullptr, *d_emb = nullptr, *d_gtab = nullptr;
+  double *d_ang = nullptr, *d_emb = nullptr, *d_gtab = nullptr, *d_red = nullptr;
+  float* d_thf = nullptr;
+  unsigned long long* d_key = nullptr;
   double2* d_cs = nullptr;
   void* d_S2 = nullptr;
   cpx<double>* tw64 = nullptr;
   auto cleanup = [&]() {
-    cudaFree(d_ang); cudaFree(d_th); cudaFree(d_cs); cudaFree(d_emb); cudaFree(d_S2);
-    cudaFree(tw64); cudaFree(d_gtab);
+    cudaFree(d_ang); cudaFree(d_cs); cudaFree(d_emb); cudaFree(d_S2);
+    cudaFree(tw64); cudaFree(d_gtab); cudaFree(d_red); cudaFree(d_thf); cudaFree(d_key);
     if (g) { bsct_gram_free(g); g = nullptr; }
   };
   const size_t T = precision == BSCT_F32 ? sizeof(float) : sizeof(double);
   CTRY(cudaMalloc(&d_ang, na * sizeof(double)));
-  CTRY(cudaMalloc(&d_th, na * sizeof(double)));
+  CTRY(cudaMalloc(&d_red, na * sizeof(double)));
+  CTRY(cudaMalloc(&d_thf, na * sizeof(float)));
+  CTRY(cudaMalloc(&d_key, na * sizeof(unsigned long long)));
   CTRY(cudaMalloc(&d_cs, na * sizeof(double2)));
   double wb[2];
   const int nbox = bsct_blur_boxes(geom, wb);
@@ -609,17 +640,18 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
   CTRY(cudaMalloc(&tw64, (size_t)fft_table_elems(N) * sizeof(cpx<double>)));
   CTRY(cudaMemcpyAsync(d_ang, geom->angles_pi, na * sizeof(double), cudaMemcpyHostToDevice, st));
 
-  k_geometry<<<(na + 127) / 128, 128, 0, st>>>(d_ang, na, d_th, d_cs);
+  k_view_keys<<<(na + 255) / 256, 256, 0, st>>>(d_ang, na, d_red, d_key);
+  k_view_rank<<<(na + GEO_T - 1) / GEO_T, GEO_T, 0, st>>>(d_red, d_key, na, d_thf, d_cs);
   const long H = (long)(2 * N - 1) * (N - 1) + N;
   if (nbox == 2) {
     k_gram_tables2<<<na, 64, 0, st>>>(d_cs, wb[0], wb[1], 1e-13, d_gtab);
-    k_gram_taps<GT2><<<(unsigned)((H + 127) / 128), 128, 0, st>>>(N, na, d_th, d_cs, d_gtab, wb[0] + wb[1], g->taps);
+    k_gram_taps<GT2><<<(unsigned)((H + 127) / 128), 128, 0, st>>>(N, na, d_thf, d_cs, d_gtab, wb[0] + wb[1], g->taps);
   } else {
-    k_gram_tables<<<na, 32, 0, st>>>(d_cs, wb[0], 1e-13, d_gtab);
-    k_gram_taps<GT1><<<(unsigned)((H + 127) / 128), 128, 0, st>>>(N, na, d_th, d_cs, d_gtab, wb[0], g->taps);
+    k_gram_tables<<<na, 64, 0, st>>>(d_cs, wb[0], 1e-13, d_gtab);
+    k_gram_taps<GT1><<<(unsigned)((H + 127) / 128), 128, 0, st>>>(N, na, d_thf, d_cs, d_gtab, wb[0], g->taps);
   }
   k_embed<<<(unsigned)(((long)L * L + 255) / 256), 256, 0, st>>>(g->taps, N, d_emb);
-  count_launch(4);
+  count_launch(5);
   CTRY(cudaGetLastError());
   TRY(build_fft_tables<double>(tw64, N, st));
   TRY(o64.spectrum(d_emb, (cpx<double>*)d_S2, g->Gt64, tw64, st));
@@ -646,8 +678,8 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
   }
   CTRY(cudaGetLastError());
   CTRY(cudaStreamSynchronize(st));
-  cudaFree(d_ang); cudaFree(d_th); cudaFree(d_cs); cudaFree(d_emb); cudaFree(d_S2);
-  cudaFree(tw64); cudaFree(d_gtab);
+  cudaFree(d_ang); cudaFree(d_cs); cudaFree(d_emb); cudaFree(d_S2);
+  cudaFree(tw64); cudaFree(d_gtab); cudaFree(d_red); cudaFree(d_thf); cudaFree(d_key);
   *out = g;
   return BSCT_OK;
 }
