@@ -742,7 +742,18 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         bms = e0.elapsed_time(e1) / nrep
+        launches_per_batch = (bsct.launch_count() - l0) / nrep
         info = batch.info()
+        # time split: the same batch without CG iterations (prefilter, back projection and
+        # CG start of every slice); the rest of the batch is the CG iterations
+        batch.solve(sinos, xs=xs, cg_iters=0)  # records the shorter graph
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(nrep):
+            batch.solve(sinos, xs=xs, cg_iters=0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bms0 = e0.elapsed_time(e1) / nrep
         extras["batched"] = {
             "workload": f"{len(sl)} slices, N in {wcfg.BATCH_SIZES_N}, views in {wcfg.BATCH_ANGLES}, "
                         f"bins=ceil(1.42N), zeta in {{0,1}}, {wcfg.BATCH_CG_ITERS} CG iterations each",
@@ -750,7 +761,8 @@ def run_ours(args):
             "cg_iters_per_s_aggregate": len(sl) * wcfg.BATCH_CG_ITERS / (bms * 1e-3),
             "geometries": info["geometries"], "graph_nodes": info["graph_nodes"],
             "kernels_per_launch": info["kernels_per_launch"], "create_s": t_create,
-            "launches_counted": (bsct.launch_count() - l0) / nrep}
+            "launches_counted": launches_per_batch,
+            "split_ms": {"backprojection_and_cg_start": bms0, "cg_iterations": bms - bms0}}
         batch.close()
         del sinos, xs
 

@@ -156,6 +156,17 @@ __global__ void __launch_bounds__(256) k_bp_tables(const double* __restrict__ an
     if (i < BP_QMAX * 4) h[BP_CA + (i / 4) * BP_QA + BP_NJMAX * 4 + i % 4] = T(0);
     else h[BP_CB + ((i - BP_QMAX * 4) / 2) * BP_QB + BP_NJMAX * 2 + i % 2] = T(0);
   }
+  // kernel values at the 6 Chebyshev nodes x_i = cos(pi (2i+1) / 12) of every (piece,
+  // offset), spread over all threads (the near-axis views' split evaluations are costly)
+  __shared__ double fvs[BP_QMAX * BP_NJMAX * 6];
+  for (int it = threadIdx.x; it < Q * nJ * 6; it += blockDim.x) {
+    const int i = it % 6, w = it / 6, q = w / nJ, j = w - q * nJ;
+    const double mid = 0.5 * (sig[q] + sig[q + 1]), hw = 0.5 * (sig[q + 1] - sig[q]);
+    const double f = mid + hw * cospi((2.0 * i + 1.0) / 12.0);
+    const double u = (J0 + j - f) * lam;
+    fvs[it] = (fabs(u) < 0.5 * W) ? lam * box_eval(u, D, small) : 0.0;
+  }
+  __syncthreads();
   for (int w = threadIdx.x; w < BP_QMAX * BP_NJMAX; w += blockDim.x) {
     const int q = w / BP_NJMAX, j = w % BP_NJMAX;
     T* ca = h + BP_CA + q * BP_QA + j * 4;
@@ -170,14 +181,7 @@ __global__ void __launch_bounds__(256) k_bp_tables(const double* __restrict__ an
     const double lo = sig[q], hi = sig[q + 1];
     const double mid = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
     if (j == 0) { h[BP_MID + q] = T(mid); h[BP_IHW + q] = T(1.0 / hw); }
-    // Chebyshev interpolation at x_i = cos(pi (2i+1) / 12)
-    double fv[6];
-    for (int i = 0; i < 6; ++i) {
-      const double xi = cospi((2.0 * i + 1.0) / 12.0);
-      const double f = mid + hw * xi;
-      const double u = (J0 + j - f) * lam;
-      fv[i] = (fabs(u) < 0.5 * W) ? lam * box_eval(u, D, small) : 0.0;
-    }
+    const double* fv = fvs + (q * nJ + j) * 6;
     double ch[6];
     for (int k = 0; k < 6; ++k) {
       double acc = 0.0;

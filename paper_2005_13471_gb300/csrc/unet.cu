@@ -137,8 +137,9 @@ inline void launch_bias_relu(float* a, const float* b, int C, long P, int relu, 
   k_bias_relu<<<dim3((unsigned)bx, (unsigned)C), TPB, 0, st>>>(a, b, C, P, relu);
 }
 
-// dpre = g * (out > 0) (BF16 for the GEMMs); db[c] += sum over the channel
-// (grid: x = chunks of the channel, y = channel; one atomic add per block)
+// dpre = g * (out > 0) (BF16 for the GEMMs); the channel sums go to per-block partials
+// part[c][chunk] (grid: x = chunks of the channel, y = channel), added to db[c] in chunk
+// order by k_chan_finish, so every run gives the same bits
 __device__ __forceinline__ float block_reduce(float v) {
   __shared__ float red[TPB / 32];
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -154,7 +155,7 @@ __device__ __forceinline__ float block_reduce(float v) {
 constexpr int CHUNK = 8192;
 // relu = 0: no mask (a layer without its ReLU)
 __global__ void k_relu_bwd(const float* __restrict__ g, const float* __restrict__ out, long P, bf16* __restrict__ dpre,
-                           float* __restrict__ db, int relu = 1) {
+                           float* __restrict__ part, int relu = 1) {
   const int c = blockIdx.y;
   const long p0 = (long)blockIdx.x * CHUNK, p1 = p0 + CHUNK < P ? p0 + CHUNK : P;
   float acc = 0.f;
@@ -165,19 +166,34 @@ __global__ void k_relu_bwd(const float* __restrict__ g, const float* __restrict_
     acc += d;
   }
   acc = block_reduce(acc);
-  if (threadIdx.x == 0) atomicAdd(db + c, acc);
+  if (threadIdx.x == 0) part[(long)c * gridDim.x + blockIdx.x] = acc;
 }
 
-// db[c] += sum_p g[c][p]
-__global__ void k_chan_sum(const float* __restrict__ g, long P, float* __restrict__ db) {
+// part[c][chunk] = sum over the chunk of g[c][p]
+__global__ void k_chan_sum(const float* __restrict__ g, long P, float* __restrict__ part) {
   const int c = blockIdx.y;
   const long p0 = (long)blockIdx.x * CHUNK, p1 = p0 + CHUNK < P ? p0 + CHUNK : P;
   float acc = 0.f;
   for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) acc += g[(long)c * P + p];
   acc = block_reduce(acc);
-  if (threadIdx.x == 0) atomicAdd(db + c, acc);
+  if (threadIdx.x == 0) part[(long)c * gridDim.x + blockIdx.x] = acc;
+}
+// db[c] += sum over chunks of part[c][chunk] (one warp per channel: each lane sums a
+// strided subset in order, then a fixed shuffle tree); with db_last, channel C goes to
+// db_last[0] instead
+__global__ void k_chan_finish(const float* __restrict__ part, int nchunks, float* __restrict__ db,
+                              float* __restrict__ db_last = nullptr, int C = 0) {
+  const int c = blockIdx.x;
+  float acc = 0.f;
+  for (int k = threadIdx.x; k < nchunks; k += 32) acc += part[(long)c * nchunks + k];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (threadIdx.x == 0) {
+    if (db_last && c == C) db_last[0] += acc;
+    else db[c] += acc;
+  }
 }
 inline dim3 chan_grid(long P, int C) { return dim3((unsigned)((P + CHUNK - 1) / CHUNK), (unsigned)C); }
+inline long chan_parts(long P, int C) { return (long)C * ((P + CHUNK - 1) / CHUNK); }
 
 __global__ void k_maxpool2(const float* __restrict__ in, int C, int NB, int H, int W, float* __restrict__ out) {
   const int Ho = H / 2, Wo = W / 2;
@@ -250,15 +266,16 @@ __global__ void k_head_bwd_data(const float* __restrict__ gout, const float* __r
   if (i >= (long)C * P) return;
   ga[i] = w[i / P] * gout[i % P];
 }
-// dw[c] += sum_p a[c][p] g[p] (grid y = channel; y == C accumulates db)
+// part[c][chunk] = sum over the chunk of a[c][p] g[p] (grid y = channel; y == C: of g[p],
+// for db); k_chan_finish then adds them to dw[c] / db
 __global__ void k_head_bwd_w(const float* __restrict__ a, const float* __restrict__ g, int C, long P,
-                             float* __restrict__ dw, float* __restrict__ db) {
+                             float* __restrict__ part) {
   const int c = blockIdx.y;
   const long p0 = (long)blockIdx.x * CHUNK, p1 = p0 + CHUNK < P ? p0 + CHUNK : P;
   float acc = 0.f;
   for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) acc += (c < C ? a[(long)c * P + p] : 1.f) * g[p];
   acc = block_reduce(acc);
-  if (threadIdx.x == 0) atomicAdd(c < C ? dw + c : db, acc);
+  if (threadIdx.x == 0) part[(long)c * gridDim.x + blockIdx.x] = acc;
 }
 
 __global__ void k_adam(float* __restrict__ w, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
@@ -324,6 +341,7 @@ struct bsct_unet {
   float *g00, *gcat0, *gp0, *g10, *gcat1, *gp1, *g20, *gcat2, *gp2, *g30, *g31, *gu2a, *gu2b, *gu1a, *gu1b, *gu0a,
       *gu0b;
   bf16 *col, *dpre;
+  float* red = nullptr;  // per-block partials of the channel sums (bias and head gradients)
   float* out = nullptr;
 };
 
@@ -399,6 +417,14 @@ int alloc_acts(bsct_unet* u, int NB, int H, int W) {
   if (2L * B * P2 * 4 > tmpmax) tmpmax = 2L * B * P2 * 4;
   u->col = (bf16*)mk(colmax, 2);
   u->dcol = f(colmax);
+  {
+    long redmax = chan_parts(P0, B + 1);  // head
+    for (int i = 0; i < 14; ++i) redmax = redmax > chan_parts(Ps[i], cs[i]->cout) ? redmax : chan_parts(Ps[i], cs[i]->cout);
+    const TConv* ts[] = {&u->t3, &u->t2, &u->t1};
+    const long Pt[] = {P3, P2, P1};  // input pixels of the transposed convolutions
+    for (int i = 0; i < 3; ++i) redmax = redmax > chan_parts(4 * Pt[i], ts[i]->cout) ? redmax : chan_parts(4 * Pt[i], ts[i]->cout);
+    u->red = f(redmax);
+  }
   u->tmp = f(tmpmax > 8L * B * P0 ? tmpmax : 8L * B * P0);
   u->dpre = (bf16*)mk(tmpmax > 8L * B * P0 ? tmpmax : 8L * B * P0, 2);
   ok = ok && u->col && u->dpre;
@@ -435,9 +461,11 @@ int conv_fwd(bsct_unet* u, const Conv3& c, const float* in, int NB, int H, int W
 int conv_bwd(bsct_unet* u, const Conv3& c, const float* in, const float* out, const float* gout, int NB, int H, int W,
              float* gin, cudaStream_t st) {
   const long P = (long)NB * H * W;
-  k_relu_bwd<<<chan_grid(P, c.cout), TPB, 0, st>>>(gout, out, P, u->dpre, u->g + c.b);
+  const dim3 cg = chan_grid(P, c.cout);
+  k_relu_bwd<<<cg, TPB, 0, st>>>(gout, out, P, u->dpre, u->red);
+  k_chan_finish<<<c.cout, 32, 0, st>>>(u->red, (int)cg.x, u->g + c.b);
   launch_im2col3(in, c.cin, NB, H, W, c.kpad, u->col, st);
-  count_launch(2);
+  count_launch(3);
   // dW[cout][kpad] += dpre[cout][P] col[kpad][P]^T
   UTRY(bsct::gemm_bf16(false, true, c.cout, c.kpad, (int)P, 1.f, u->dpre, P, 0, u->col, P, 0, 1.f, u->g + c.w, c.kpad,
                        0, 1, st));
@@ -472,8 +500,10 @@ int tconv_bwd(bsct_unet* u, const TConv& t, const float* in, const float* gout, 
   bf16* inb = u->col;                          // BF16 copy of the input [cin][P]
   launch_tconv_gather(gout, t.cout, NB, H, W, gg, st);
   k_to_bf16<<<nblk((long)t.cin * P), TPB, 0, st>>>(in, inb, (long)t.cin * P);
-  k_chan_sum<<<chan_grid(4 * P, t.cout), TPB, 0, st>>>(gout, 4 * P, u->g + t.b);
-  count_launch(3);
+  const dim3 cg = chan_grid(4 * P, t.cout);
+  k_chan_sum<<<cg, TPB, 0, st>>>(gout, 4 * P, u->red);
+  k_chan_finish<<<t.cout, 32, 0, st>>>(u->red, (int)cg.x, u->g + t.b);
+  count_launch(4);
   // dW[(cout*4)][cin] += gg[(cout*4)][P] in[cin][P]^T
   UTRY(bsct::gemm_bf16(false, true, t.cout * 4, t.cin, (int)P, 1.f, gg, P, 0, inb, P, 0, 1.f, u->g + t.w, t.cin, 0, 1,
                        st));
@@ -632,9 +662,11 @@ extern "C" int bsct_unet_backward(bsct_unet* u, const float* d_gout, void* strea
   cudaStream_t st = (cudaStream_t)stream;
   const int B = u->base, NB = u->NB, H = u->H, W = u->W;
   const long P0 = (long)NB * H * W, P1 = P0 / 4, P2 = P0 / 16;
-  k_head_bwd_w<<<chan_grid(P0, B + 1), TPB, 0, st>>>(u->u0b, d_gout, B, P0, u->g + u->hw, u->g + u->hb);
+  const dim3 hg = chan_grid(P0, B + 1);
+  k_head_bwd_w<<<hg, TPB, 0, st>>>(u->u0b, d_gout, B, P0, u->red);
+  k_chan_finish<<<B + 1, 32, 0, st>>>(u->red, (int)hg.x, u->g + u->hw, u->g + u->hb, B);
   k_head_bwd_data<<<nblk(B * P0), TPB, 0, st>>>(d_gout, u->w + u->hw, B, P0, u->gu0b);
-  count_launch(2);
+  count_launch(3);
   UTRY(conv_bwd(u, u->d0b, u->u0a, u->u0b, u->gu0b, NB, H, W, u->gu0a, st));
   UTRY(conv_bwd(u, u->d0a, u->cat0, u->u0a, u->gu0a, NB, H, W, u->gcat0, st));
   UTRY(tconv_bwd(u, u->t1, u->u1b, u->gcat0, NB, H / 2, W / 2, u->gu1b, st));
@@ -682,21 +714,45 @@ __global__ void k_scale_copy(const float* __restrict__ a, float s, float* __rest
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = s * a[i];
 }
-__global__ void k_dot2(const float* __restrict__ a, const float* __restrict__ b, const float* __restrict__ c, long n,
-                       double* __restrict__ out) {
-  // out[0] += <a, b>, out[1] += <a, c>
+// Reproducible FP64 sums: every block reduces its values in a fixed order and writes one
+// partial per sum, part[k * gridDim.x + block]; k_sum_parts then adds the partials of each
+// sum in block order (the results do not depend on scheduling).
+__device__ __forceinline__ double block_sum_d(double v) {
+  __shared__ double red_d[TPB / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();  // red_d may still be read from a previous call
+  if ((threadIdx.x & 31) == 0) red_d[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < TPB / 32; ++w) t += red_d[w];
+  return t;
+}
+// out[k] = (accumulate ? out[k] : 0) + scale * sum_b part[k * nb + b], k < nsum (one warp each)
+__global__ void k_sum_parts(const double* __restrict__ part, int nb, int nsum, double scale, int accumulate,
+                            double* __restrict__ out) {
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (k >= nsum) return;
+  double acc = 0.0;
+  for (int b = lane; b < nb; b += 32) acc += part[(long)k * nb + b];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[k] = (accumulate ? out[k] : 0.0) + scale * acc;
+}
+constexpr int DOT_BLOCKS = 512;
+
+// part: [2][gridDim.x]; sums <a, b> and <a, c>
+__global__ void __launch_bounds__(TPB) k_dot2(const float* __restrict__ a, const float* __restrict__ b,
+                                              const float* __restrict__ c, long n, double* __restrict__ part) {
   double s0 = 0.0, s1 = 0.0;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     s0 += (double)a[i] * b[i];
     s1 += (double)a[i] * c[i];
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    s0 += __shfl_down_sync(0xffffffffu, s0, o);
-    s1 += __shfl_down_sync(0xffffffffu, s1, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(out, s0);
-    atomicAdd(out + 1, s1);
+  s0 = block_sum_d(s0);
+  s1 = block_sum_d(s1);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s0;
+    part[gridDim.x + blockIdx.x] = s1;
   }
 }
 }  // namespace
@@ -716,10 +772,11 @@ static int learned_warm_start(bsct_gram* g, bsct_unet* net, const void* d_b, voi
   UTRY(bsct_unet_forward(net, xin, xhat, 1, N, N, stream));
   float* Gx = (float*)g->r;
   UTRY(bsct_gram_apply(g, xhat, Gx, BSCT_APPLY_FFT32, stream));
-  double* acc = g->partials;  // two doubles
-  BSCT_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
-  k_dot2<<<1024, TPB, 0, st>>>(xhat, (const float*)d_b, Gx, n, acc);
-  count_launch();
+  double* acc = g->partials;            // two doubles
+  double* part = g->partials + 8;       // 2 x DOT_BLOCKS partials (g->partials holds 2048)
+  k_dot2<<<DOT_BLOCKS, TPB, 0, st>>>(xhat, (const float*)d_b, Gx, n, part);
+  k_sum_parts<<<1, 64, 0, st>>>(part, DOT_BLOCKS, 2, 1.0, 0, acc);
+  count_launch(2);
   double h[2];
   BSCT_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
   BSCT_CUDA_TRY(cudaStreamSynchronize(st));
@@ -752,25 +809,24 @@ extern "C" int bsct_pcg_solve_learned(bsct_gram* g, bsct_unet* net, double eps, 
 }
 
 namespace {
-// out[k] += <a_k, b_k> for k < 3 (null a_k skipped)
-__global__ void k_dots3(const float* __restrict__ a0, const float* __restrict__ b0, const float* __restrict__ a1,
-                        const float* __restrict__ b1, const float* __restrict__ a2, const float* __restrict__ b2, long n,
-                        double* __restrict__ out) {
+// part[k][block] = block partial of <a_k, b_k> for k < 3 (0 for a null a_k)
+__global__ void __launch_bounds__(TPB) k_dots3(const float* __restrict__ a0, const float* __restrict__ b0,
+                                               const float* __restrict__ a1, const float* __restrict__ b1,
+                                               const float* __restrict__ a2, const float* __restrict__ b2, long n,
+                                               double* __restrict__ part) {
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     if (a0) s0 += (double)a0[i] * b0[i];
     if (a1) s1 += (double)a1[i] * b1[i];
     if (a2) s2 += (double)a2[i] * b2[i];
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    s0 += __shfl_down_sync(0xffffffffu, s0, o);
-    s1 += __shfl_down_sync(0xffffffffu, s1, o);
-    s2 += __shfl_down_sync(0xffffffffu, s2, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    if (a0) atomicAdd(out, s0);
-    if (a1) atomicAdd(out + 1, s1);
-    if (a2) atomicAdd(out + 2, s2);
+  s0 = block_sum_d(s0);
+  s1 = block_sum_d(s1);
+  s2 = block_sum_d(s2);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s0;
+    part[gridDim.x + blockIdx.x] = s1;
+    part[2 * gridDim.x + blockIdx.x] = s2;
   }
 }
 // x += alpha p; r -= alpha q
@@ -786,15 +842,16 @@ __global__ void k_fcg_dir(float* __restrict__ p, const float* __restrict__ z, fl
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     p[i] = fmaf(beta, p[i], z[i]);
 }
-// out[0] += sum (b - y)^2
-__global__ void k_resid2(const float* __restrict__ b, const float* __restrict__ y, long n, double* __restrict__ out) {
+// part[block] = block partial of sum (b - y)^2
+__global__ void __launch_bounds__(TPB) k_resid2(const float* __restrict__ b, const float* __restrict__ y, long n,
+                                                double* __restrict__ part) {
   double s = 0.0;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const double d = (double)b[i] - y[i];
     s += d * d;
   }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+  s = block_sum_d(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 }  // namespace
 
@@ -811,21 +868,22 @@ extern "C" int bsct_fcg_solve_learned(bsct_gram* g, bsct_unet* net, const void* 
   cudaStream_t st = (cudaStream_t)stream;
   const int N = g->N;
   const long n = (long)N * N;
-  const unsigned nb = 1024;
+  const unsigned nb = DOT_BLOCKS;
   const float* b = (const float*)d_b;
   float* x = (float*)d_x;
   float* r = (float*)g->r;
   float* p = (float*)g->p;
   float* q = (float*)g->q;
   float *z = nullptr, *xin = nullptr;
-  double* acc = g->partials;  // >= 3 doubles
+  double* acc = g->partials;             // 3 doubles
+  double* part = g->partials + 8;        // 3 x DOT_BLOCKS block partials (g->partials holds 2048)
   int rc = BSCT_OK, npre = 0, nfb = 0, it = 0, conv = 0;
   double h[3], bb = 0.0, rr = 0.0;
   auto dots = [&](const float* a0, const float* b0, const float* a1, const float* b1, const float* a2,
                   const float* b2) -> int {
-    BSCT_CUDA_TRY(cudaMemsetAsync(acc, 0, 3 * sizeof(double), st));
-    k_dots3<<<nb, TPB, 0, st>>>(a0, b0, a1, b1, a2, b2, n, acc);
-    count_launch();
+    k_dots3<<<nb, TPB, 0, st>>>(a0, b0, a1, b1, a2, b2, n, part);
+    k_sum_parts<<<1, 96, 0, st>>>(part, (int)nb, 3, 1.0, 0, acc);
+    count_launch(2);
     BSCT_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
     BSCT_CUDA_TRY(cudaStreamSynchronize(st));
     return BSCT_OK;
@@ -896,13 +954,12 @@ extern "C" int bsct_fcg_solve_learned(bsct_gram* g, bsct_unet* net, const void* 
     report->true_rel_residual = -1.0;
     // true residual ||b - G x|| / ||b||
     if ((rc = bsct_gram_apply(g, x, q, BSCT_APPLY_FFT32, stream)) == BSCT_OK) {
-      if (cudaMemsetAsync(acc, 0, sizeof(double), st) == cudaSuccess) {
-        k_resid2<<<nb, TPB, 0, st>>>(b, q, n, acc);
-        count_launch();
-        if (cudaMemcpyAsync(h, acc, sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
-            cudaStreamSynchronize(st) == cudaSuccess)
-          report->true_rel_residual = bb > 0.0 ? sqrt(h[0] / bb) : 0.0;
-      }
+      k_resid2<<<nb, TPB, 0, st>>>(b, q, n, part);
+      k_sum_parts<<<1, 32, 0, st>>>(part, (int)nb, 1, 1.0, 0, acc);
+      count_launch(2);
+      if (cudaMemcpyAsync(h, acc, sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+          cudaStreamSynchronize(st) == cudaSuccess)
+        report->true_rel_residual = bb > 0.0 ? sqrt(h[0] / bb) : 0.0;
     }
   }
   if (n_precond) *n_precond = npre;
@@ -914,9 +971,10 @@ extern "C" int bsct_fcg_solve_learned(bsct_gram* g, bsct_unet* net, const void* 
 }
 
 namespace {
-// grad = 2 (pred - target) / n; loss[0] += sum (pred - target)^2 / n
-__global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ target, long n, float* __restrict__ grad,
-                      double* __restrict__ loss) {
+// grad = 2 (pred - target) / n; part[block] = block partial of sum (pred - target)^2
+// (k_sum_parts adds them, times 1/n, to the loss)
+__global__ void __launch_bounds__(TPB) k_mse(const float* __restrict__ pred, const float* __restrict__ target, long n,
+                                             float* __restrict__ grad, double* __restrict__ part) {
   double acc = 0.0;
   const float inv = 1.f / (float)n;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -924,16 +982,21 @@ __global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ 
     grad[i] = 2.f * d * inv;
     acc += (double)d * d;
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc / (double)n);
+  acc = block_sum_d(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 }  // namespace
 
 extern "C" int bsct_mse_loss_grad(const float* d_pred, const float* d_target, int64_t n, float* d_grad, double* d_loss,
                                   void* stream) {
   if (!d_pred || !d_target || !d_grad || !d_loss || n < 1) { bsct_set_last_message("invalid argument"); return BSCT_ERR_INVALID_ARG; }
-  k_mse<<<1024, TPB, 0, (cudaStream_t)stream>>>(d_pred, d_target, n, d_grad, d_loss);
-  count_launch();
+  cudaStream_t st = (cudaStream_t)stream;
+  LayerScratch sc{st};
+  double* part = sc.get<double>(DOT_BLOCKS);
+  if (!sc.ok) { bsct_set_last_message("out of device memory"); return BSCT_ERR_CUDA; }
+  k_mse<<<DOT_BLOCKS, TPB, 0, st>>>(d_pred, d_target, n, d_grad, part);
+  k_sum_parts<<<1, 32, 0, st>>>(part, DOT_BLOCKS, 1, 1.0 / (double)n, 1, d_loss);
+  count_launch(2);
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
 }
@@ -1061,12 +1124,15 @@ extern "C" int bsct_conv3x3_backward(int32_t n, int32_t cin, int32_t cout, int32
   bf16* col = sc.get<bf16>((long)kpad * P);
   bf16* dpre = sc.get<bf16>((long)cout * P);
   float* dcol = d_gin ? sc.get<float>((long)kpad * P) : nullptr;
+  float* red = sc.get<float>(chan_parts(P, cout));
   if (!sc.ok) { bsct_set_last_message("out of device memory"); return BSCT_ERR_CUDA; }
   BSCT_CUDA_TRY(cudaMemsetAsync(d_gb, 0, (size_t)cout * sizeof(float), st));
   k_to_bf16<<<nblk((long)cout * kpad), TPB, 0, st>>>(d_w, wb, (long)cout * kpad);
-  k_relu_bwd<<<chan_grid(P, cout), TPB, 0, st>>>(d_gout, relu ? d_out : d_gout, P, dpre, d_gb, relu ? 1 : 0);
+  const dim3 cg = chan_grid(P, cout);
+  k_relu_bwd<<<cg, TPB, 0, st>>>(d_gout, relu ? d_out : d_gout, P, dpre, red, relu ? 1 : 0);
+  k_chan_finish<<<cout, 32, 0, st>>>(red, (int)cg.x, d_gb);
   launch_im2col3(d_in, cin, n, H, W, kpad, col, st);
-  count_launch(3);
+  count_launch(4);
   UTRY(bsct::gemm_bf16(false, true, cout, kpad, (int)P, 1.f, dpre, P, 0, col, P, 0, 0.f, d_gw, kpad, 0, 1, st));
   if (d_gin) {
     UTRY(bsct::gemm_bf16(true, false, kpad, (int)P, cout, 1.f, wb, kpad, 0, dpre, P, 0, 0.f, dcol, P, 0, 1, st));
@@ -1113,13 +1179,16 @@ extern "C" int bsct_tconv2x2_backward(int32_t n, int32_t cin, int32_t cout, int3
   bf16* wb = sc.get<bf16>((long)cout * 4 * cin);
   bf16* gg = sc.get<bf16>((long)cout * 4 * P);
   bf16* inb = sc.get<bf16>((long)cin * P);
+  float* red = sc.get<float>(chan_parts(4 * P, cout));
   if (!sc.ok) { bsct_set_last_message("out of device memory"); return BSCT_ERR_CUDA; }
   BSCT_CUDA_TRY(cudaMemsetAsync(d_gb, 0, (size_t)cout * sizeof(float), st));
   k_to_bf16<<<nblk((long)cout * 4 * cin), TPB, 0, st>>>(d_w, wb, (long)cout * 4 * cin);
   launch_tconv_gather(d_gout, cout, n, H, W, gg, st);
   k_to_bf16<<<nblk((long)cin * P), TPB, 0, st>>>(d_in, inb, (long)cin * P);
-  k_chan_sum<<<chan_grid(4 * P, cout), TPB, 0, st>>>(d_gout, 4 * P, d_gb);
-  count_launch(4);
+  const dim3 cg = chan_grid(4 * P, cout);
+  k_chan_sum<<<cg, TPB, 0, st>>>(d_gout, 4 * P, red);
+  k_chan_finish<<<cout, 32, 0, st>>>(red, (int)cg.x, d_gb);
+  count_launch(5);
   UTRY(bsct::gemm_bf16(false, true, cout * 4, cin, (int)P, 1.f, gg, P, 0, inb, P, 0, 0.f, d_gw, cin, 0, 1, st));
   if (d_gin)
     UTRY(bsct::gemm_bf16(true, false, cin, (int)P, cout * 4, 1.f, wb, cin, 0, gg, P, 0, 0.f, d_gin, P, 0, 1, st));

@@ -173,3 +173,41 @@ def test_gnorm_loss_against_oracle(bsct):
     bsct.gnorm_loss_grad(g, pred.to(DEV), target.to(DEV), grad, loss, w.to(DEV))
     assert float(loss.item()) == 2 * first
     g.close()
+
+
+def test_training_and_solvers_are_bit_reproducible(bsct):
+    # every reduction of the CNN and of the learned solvers sums in a fixed order (per-block
+    # partials added in block order), so the same inputs give the same bits on every run:
+    # two networks from the same seed after a forward / backward / Adam step, the MSE loss,
+    # the warm start and flexible CG
+    def step():
+        net = bsct.UNet(base_channels=8, seed=11)
+        g = torch.Generator().manual_seed(4)
+        x = torch.randn((4, 64, 64), generator=g).to(DEV)
+        target = torch.randn((4, 64, 64), generator=g).to(DEV)
+        pred = net.forward(x)
+        grad = torch.empty_like(pred)
+        loss = torch.zeros(1, dtype=torch.float64, device=DEV)
+        bsct.mse_loss_grad(pred, target, grad, loss)
+        net.backward(grad)
+        grads = net.get_grads().clone()
+        net.adam_step(1e-3, 1)
+        params = net.get_params().clone()
+        return net, grads, params, loss.clone()
+
+    net1, g1, p1, l1 = step()
+    net2, g2, p2, l2 = step()
+    assert torch.equal(g1, g2) and torch.equal(p1, p2) and torch.equal(l1, l2)
+    N, na = 64, 90
+    geom = bsct.Geometry(N, np.arange(na) / na, 92, 1.0, 1.0)
+    gm = bsct.gram_build(geom, bsct.F32)
+    b = gm.apply(torch.randn((N, N), generator=torch.Generator().manual_seed(7)).to(DEV))
+    xa, ra = gm.cg_solve_learned(net1, b, 1.0 / na, max_iter=60, rel_tol=0.0, check_every=5)
+    xb, rb = gm.cg_solve_learned(net2, b, 1.0 / na, max_iter=60, rel_tol=0.0, check_every=5)
+    assert ra["alpha"] == rb["alpha"] and torch.equal(xa, xb)
+    fa, _ = gm.fcg_solve_learned(net1, b, 1.0 / na, max_iter=40, rel_tol=0.0, precond_every=2)
+    fb, _ = gm.fcg_solve_learned(net2, b, 1.0 / na, max_iter=40, rel_tol=0.0, precond_every=2)
+    assert torch.equal(fa, fb)
+    gm.close()
+    net1.close()
+    net2.close()

@@ -83,3 +83,22 @@ def test_layer_arguments_checked(bsct):
     w = torch.zeros((6, 32), device=DEV)  # cout = 6 is not a multiple of 8
     with pytest.raises(RuntimeError, match="invalid argument"):
         bsct.conv3x3_layer(x, w, torch.zeros(6, device=DEV))
+
+
+def test_layer_gradients_are_bit_reproducible(bsct):
+    # the bias gradients are channel sums over ~10^4 outputs, formed as per-block partials
+    # added in block order: the same call twice gives the same bits
+    g = torch.Generator().manual_seed(21)
+    x = torch.randn((16, 2, 64, 64), generator=g).to(DEV)
+    w = (torch.randn((32, 144), generator=g) * 0.1).to(DEV)
+    b = torch.randn(32, generator=g).to(DEV)
+    gout = torch.randn((32, 2, 64, 64), generator=g).to(DEV)
+    r1 = bsct.conv3x3_layer(x, w, b, relu=True, gout=gout)
+    r2 = bsct.conv3x3_layer(x, w, b, relu=True, gout=gout)
+    assert all(torch.equal(a, c) for a, c in zip(r1, r2))
+    wt = (torch.randn((64, 16), generator=g) * 0.1).to(DEV)
+    bt = torch.randn(16, generator=g).to(DEV)
+    gt = torch.randn((16, 2, 128, 128), generator=g).to(DEV)
+    t1 = bsct.tconv2x2_layer(x, wt, bt, gout=gt)
+    t2 = bsct.tconv2x2_layer(x, wt, bt, gout=gt)
+    assert all(torch.equal(a, c) for a, c in zip(t1, t2))
