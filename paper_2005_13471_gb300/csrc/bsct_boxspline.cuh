@@ -230,4 +230,150 @@ __device__ inline void cheb8_monomials(const double fv[8], double c[8]) {
   c[7] = 64.0 * ch[7];
 }
 
+// ---------------------------------------------------------------------------------------
+// Footprint of one view with two detector boxes, h = M_[A, B, w1, w2] (A, B = |cos|, |sin|),
+// as exact cubic pieces between its kinks -W/2 + k0 A + k1 B + k2 w1 + k3 w2 (W = A + B +
+// w1 + w2; <= 15 pieces).  Each piece is fitted by Chebyshev interpolation at 4 nodes of
+// FP64 values of box_conv(M_[A, B], M_[w1, w2]) (short-direction split near the axes), which
+// reproduces the cubic exactly up to rounding.  Held in shared memory by one CTA, it turns
+// the kernels built on h into single convolutions of piecewise polynomials:
+//   back projection  lambda M_[A, B, w1, w2, lambda x (d+1)] = lambda (h * beta_d),
+//   Gram kernel      M_[A, A, B, B, w1, w1, w2, w2]          = h * h   (h is even),
+// integrated exactly by 4-point Gauss-Legendre between the kinks of both factors
+// (degree <= 3 + 3).
+struct FootPoly {
+  int K;               // pieces
+  double hw;           // half support W / 2
+  double kn[17];       // piece starts, kn[K] = W / 2
+  double mid[16], ihw[16];
+  double c[16][4];     // monomials in v = (x - mid) * ihw
+  double fv[16][4];    // node values while building
+};
+
+__device__ inline double foot_box_conv(double x, double A, double B, double w1, double w2) {
+  BoxDirs P, Q;
+  P.ng = 0;
+  if (A > 0.0) { P.a[P.ng] = A; P.m[P.ng] = 1; ++P.ng; }
+  if (B > 0.0) { P.a[P.ng] = B; P.m[P.ng] = 1; ++P.ng; }
+  for (int g = P.ng; g < 4; ++g) { P.a[g] = 0.0; P.m[g] = 0; }
+  int small = -1;
+  if (A > 0.0 && B > 0.0) {
+    if (B < BSCT_SHORT_DIR * A) small = 1;
+    else if (A < BSCT_SHORT_DIR * B) small = 0;
+  }
+  Q.ng = 0;
+  if (w1 == w2) { Q.a[0] = w1; Q.m[0] = 2; Q.ng = 1; }
+  else { Q.a[0] = w1; Q.m[0] = 1; Q.a[1] = w2; Q.m[1] = 1; Q.ng = 2; }
+  for (int g = Q.ng; g < 4; ++g) { Q.a[g] = 0.0; Q.m[g] = 0; }
+  return box_conv(x, P, small, Q);
+}
+
+// Built by all threads of a CTA (contains barriers).
+__device__ inline void foot_build(FootPoly& F, double A, double B, double w1, double w2, double merge_tol) {
+  if (threadIdx.x == 0) {
+    const double W = A + B + w1 + w2;
+    double k[16];
+    int n = 0;
+    for (int k0 = 0; k0 <= (A > 0.0); ++k0)
+      for (int k1 = 0; k1 <= (B > 0.0); ++k1)
+        for (int k2 = 0; k2 <= 1; ++k2)
+          for (int k3 = 0; k3 <= 1; ++k3) k[n++] = -0.5 * W + k0 * A + k1 * B + k2 * w1 + k3 * w2;
+    for (int i = 1; i < n; ++i) {  // insertion sort
+      const double t = k[i];
+      int j = i - 1;
+      while (j >= 0 && k[j] > t) { k[j + 1] = k[j]; --j; }
+      k[j + 1] = t;
+    }
+    int m = 1;  // merge kinks closer than merge_tol (the ends -W/2 and W/2 stay)
+    for (int i = 1; i < n; ++i)
+      if (k[i] - k[m - 1] > merge_tol) k[m++] = k[i];
+      else if (i == n - 1) k[m - 1] = k[i];
+    for (int i = 0; i < 17; ++i) F.kn[i] = i < m ? k[i] : 1e300;
+    F.K = m - 1;
+    F.hw = 0.5 * W;
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < F.K * 4; it += blockDim.x) {
+    const int q = it >> 2, i = it & 3;
+    const double mid = 0.5 * (F.kn[q] + F.kn[q + 1]), hw = 0.5 * (F.kn[q + 1] - F.kn[q]);
+    F.fv[q][i] = foot_box_conv(mid + hw * cospi((2.0 * i + 1.0) / 8.0), A, B, w1, w2);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < F.K; q += blockDim.x) {
+    double ch[4];
+    for (int k = 0; k < 4; ++k) {
+      double acc = 0.0;
+      for (int i = 0; i < 4; ++i) acc += F.fv[q][i] * cospi(k * (2.0 * i + 1.0) / 8.0);
+      ch[k] = acc * (k == 0 ? 0.25 : 0.5);
+    }
+    // T0 = 1, T1 = v, T2 = 2v^2 - 1, T3 = 4v^3 - 3v
+    F.c[q][0] = ch[0] - ch[2];
+    F.c[q][1] = ch[1] - 3.0 * ch[3];
+    F.c[q][2] = 2.0 * ch[2];
+    F.c[q][3] = 4.0 * ch[3];
+    F.mid[q] = 0.5 * (F.kn[q] + F.kn[q + 1]);
+    F.ihw[q] = 2.0 / (F.kn[q + 1] - F.kn[q]);
+  }
+  __syncthreads();
+}
+
+__device__ inline int foot_piece(const FootPoly& F, double x) {
+  int q = 0;
+  for (int step = 8; step > 0; step >>= 1)
+    if (q + step < F.K && F.kn[q + step] <= x) q += step;
+  return q;
+}
+__device__ inline double foot_piece_eval(const FootPoly& F, int q, double x) {
+  const double v = (x - F.mid[q]) * F.ihw[q];
+  return fma(fma(fma(F.c[q][3], v, F.c[q][2]), v, F.c[q][1]), v, F.c[q][0]);
+}
+__device__ inline double foot_eval(const FootPoly& F, double x) {
+  if (!(x > -F.hw && x < F.hw)) return 0.0;
+  return foot_piece_eval(F, foot_piece(F, x), x);
+}
+
+// int h(x - v) g(v) dv for g supported on [glo, ghi] with kinks gk[0..ng) there; g(v) by
+// the functor.  Cuts at the kinks of both factors inside the overlap of the supports; on
+// every interval h(x - v) is one piece (found at the interval's midpoint) and g one
+// polynomial, so 4-point Gauss-Legendre is exact for total degree <= 7.
+template <typename G>
+__device__ inline double foot_conv(const FootPoly& F, double x, double glo, double ghi, const double* gk, int ng,
+                                   G g) {
+  const double lo = fmax(glo, x - F.hw), hi = fmin(ghi, x + F.hw);
+  if (!(hi > lo)) return 0.0;
+  double cut[40];
+  int nc = 0;
+  cut[nc++] = lo;
+  cut[nc++] = hi;
+  for (int i = 0; i < ng && nc < 40; ++i)
+    if (gk[i] > lo && gk[i] < hi) cut[nc++] = gk[i];
+  for (int i = 0; i <= F.K && nc < 40; ++i) {
+    const double v = x - F.kn[i];
+    if (v > lo && v < hi) cut[nc++] = v;
+  }
+  for (int i = 1; i < nc; ++i) {  // insertion sort
+    const double t = cut[i];
+    int j = i - 1;
+    while (j >= 0 && cut[j] > t) { cut[j + 1] = cut[j]; --j; }
+    cut[j + 1] = t;
+  }
+  const double gx[4] = {0.06943184420297371239, 0.33000947820757186760, 0.66999052179242813240,
+                        0.93056815579702628761};
+  const double gw[4] = {0.17392742256872692869, 0.32607257743127307131, 0.32607257743127307131,
+                        0.17392742256872692869};
+  double acc = 0.0;
+  for (int i = 0; i + 1 < nc; ++i) {
+    const double a = cut[i], w = cut[i + 1] - cut[i];
+    if (w <= 0.0) continue;
+    const int q = foot_piece(F, x - (a + 0.5 * w));
+    double piece = 0.0;
+    for (int k = 0; k < 4; ++k) {
+      const double v = a + gx[k] * w;
+      piece += gw[k] * foot_piece_eval(F, q, x - v) * g(v);
+    }
+    acc += piece * w;
+  }
+  return acc;
+}
+
 }  // namespace bsct

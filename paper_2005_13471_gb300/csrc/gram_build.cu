@@ -290,28 +290,10 @@ __device__ __forceinline__ double gram_table_eval(const double* __restrict__ T, 
   return r;
 }
 
-// Two detector boxes: the per-view Gram kernel A = M_[c,c,s,s,w1,w1,w2,w2] as the convolution
-// of M_[c,c,s,s] (with the short-direction split near the axes) and M_[w1,w1,w2,w2]; its
-// kinks -S + i|c| + j|s| + k w1 + l w2 (i, j, k, l in 0..2) cut [0, S] into <= 41 pieces of
-// degree 7, fitted by Chebyshev interpolation at 8 nodes (one thread per piece).
-__device__ inline double gram_kernel2(double t, double a, double b, double w1, double w2) {
-  BoxDirs P, Q;
-  P.ng = 0;
-  if (a > 0.0) { P.a[P.ng] = a; P.m[P.ng] = 2; ++P.ng; }
-  if (b > 0.0) { P.a[P.ng] = b; P.m[P.ng] = 2; ++P.ng; }
-  for (int g = P.ng; g < 4; ++g) { P.a[g] = 0.0; P.m[g] = 0; }
-  int small = -1;
-  if (a > 0.0 && b > 0.0) {
-    if (b < BSCT_SHORT_DIR * a) small = 1;
-    else if (a < BSCT_SHORT_DIR * b) small = 0;
-  }
-  Q.ng = 0;
-  if (w1 == w2) { Q.a[0] = w1; Q.m[0] = 4; Q.ng = 1; }
-  else { Q.a[0] = w1; Q.m[0] = 2; Q.a[1] = w2; Q.m[1] = 2; Q.ng = 2; }
-  for (int g = Q.ng; g < 4; ++g) { Q.a[g] = 0.0; Q.m[g] = 0; }
-  return box_conv(t, P, small, Q);
-}
-
+// Two detector boxes: the per-view Gram kernel A = M_[c,c,s,s,w1,w1,w2,w2] is the
+// autocorrelation h * h of the footprint h = M_[c,s,w1,w2] (FootPoly: exact cubic pieces);
+// its kinks -S + i|c| + j|s| + k w1 + l w2 (i, j, k, l in 0..2) cut [0, S] into <= 41
+// pieces of degree 7, fitted by Chebyshev interpolation at 8 nodes.
 __global__ void __launch_bounds__(64) k_gram_tables2(const double2* __restrict__ cs, double w1, double w2,
                                                      double merge_tol, double* __restrict__ tab) {
   typedef GT2 L;
@@ -350,7 +332,12 @@ __global__ void __launch_bounds__(64) k_gram_tables2(const double2* __restrict__
     for (int i = 0; i < L::KMAX; ++i) T[L::KN + i] = i < m ? kn[i] : 1e300;
   }
   __syncthreads();
-  fit_table_pieces<L>(T, kn, nk_s, fv, [&](double t) { return gram_kernel2(t, a, b, w1, w2); });
+  // A = h * h with h = M_[a, b, w1, w2] as exact cubic pieces (h is even)
+  __shared__ FootPoly F;
+  foot_build(F, a, b, w1, w2, 1e-13);
+  fit_table_pieces<L>(T, kn, nk_s, fv, [&](double t) {
+    return foot_conv(F, t, -F.hw, F.hw, F.kn, F.K + 1, [&](double v) { return foot_eval(F, v); });
+  });
 }
 
 // zeta: the sum of the detector box widths (bounds the strip of views that reach a tap)

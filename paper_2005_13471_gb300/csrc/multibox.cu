@@ -14,17 +14,19 @@
 //   phi_j(f) = K((J0 + j - f) lambda), K = lambda M_[|c|, |s|, w1, w2, lambda x (d+1)]; each
 //   phi_j is one polynomial of degree <= 7 between consecutive points of
 //   {0} U {frac(-kink(K) / lambda)} (<= 17 pieces).  k_mb_bp_tables fits them in FP64 by
-//   Chebyshev interpolation at 8 nodes of exact kernel values - K is evaluated as the
-//   convolution of the trapezoid M_[|c|, |s|] (short-direction split near the axes) with
-//   M_[w1, w2, lambda x (d+1)] (box_conv) - and k_mb_bp_gather sums, per pixel and view,
-//   sum_j c~[m0 + J0 + j] poly_{q,j}(v).
+//   Chebyshev interpolation at 8 nodes of exact kernel values - K = lambda (h * beta_d),
+//   the footprint h held as exact cubic pieces (FootPoly) convolved with the B-spline
+//   beta_d = M_[lambda x (d+1)] by Gauss-Legendre between the kinks of both - and
+//   k_mb_bp_gather sums, per pixel and view, sum_j c~[m0 + J0 + j] poly_{q,j}(v).
 // Forward projection, per view: h_theta is one cubic between consecutive kinks
-//   -W/2 + k0 |c| + k1 |s| + k2 w1 + k3 w2 (<= 15 pieces, W = |c| + |s| + w1 + w2), fitted in
-//   FP64 at 4 Chebyshev nodes; one thread per (view, sample) walks the image lines along the
-//   view's major axis and sums h(y_m - x_k . u) c_k over the pixels of each line inside the
+//   -W/2 + k0 |c| + k1 |s| + k2 w1 + k3 w2 (<= 15 pieces, W = |c| + |s| + w1 + w2), the same
+//   FootPoly pieces; one thread per (view, sample) walks the image lines along the view's
+//   major axis and sums h(y_m - x_k . u) c_k over the pixels of each line inside the
 //   support.
-// Detector coordinates are formed in FP64 in both precisions; FP32 evaluates the
-// polynomials and accumulates in FP32, folded into FP64 sums per view block / image line.
+// The back projection forms detector coordinates in FP64 in both precisions; the FP32
+// forward projection forms each line's first footprint argument in FP64 and steps it in
+// FP32.  FP32 evaluates the polynomials and accumulates in FP32, folded into FP64 sums per
+// view block / image line.
 #include <math.h>
 
 #include "bsct_boxspline.cuh"
@@ -38,10 +40,16 @@ constexpr int MB_NC = 8;      // coefficients per (piece, offset): degree <= 7
 // per-view FP64 header: p00, c/lambda, s/lambda, Q, J0, nJ, degree, pad; piece starts
 // sigma[0..Q] (padded to 24 with 2.0); centres mid[QMAX]; inverse half widths ihw[QMAX]
 constexpr int MB_P00 = 0, MB_CL = 1, MB_SL = 2, MB_Q = 3, MB_J0 = 4, MB_NJ = 5, MB_DEG = 6;
-constexpr int MB_SIG = 8, MB_MID = MB_SIG + 24, MB_IHW = MB_MID + MB_QMAX, MB_DH = MB_IHW + MB_QMAX;
+constexpr int MB_SIG = 8, MB_MID = MB_SIG + 24, MB_IHW = MB_MID + MB_QMAX, MB_F = MB_IHW + MB_QMAX;
+// then FP32 copies for the FP32 gather (72 floats in 36 doubles): floor(p00), frac(p00),
+// c/lambda = c_hi + c_lo, s/lambda = s_hi + s_lo (hi parts short enough that X c_hi and
+// Y s_hi are exact in FP32 for every pixel index), 2 pads, sigma[24], mid[20], 1/hw[20]
+constexpr int MBF_P0 = 0, MBF_SIGF = 8, MBF_MIDF = MBF_SIGF + 24, MBF_IHWF = MBF_MIDF + MB_QMAX;
+constexpr int MB_DH = MB_F + 36;
 constexpr long MB_CSTRIDE = (long)MB_QMAX * MB_NJMAX * MB_NC;  // T coefficients per view
 constexpr int MB_PF_T = 256, MB_PF_H = 40;
 constexpr int MB_TX = 16, MB_TY = 16;
+constexpr int MB_CHUNK = 128;  // (piece, offset) pairs fitted per round of the table kernel
 
 __host__ __device__ inline void mb_jrange(double W, double lam, int* J0, int* nJ) {
   const double h = 0.5 * W / lam;
@@ -49,25 +57,6 @@ __host__ __device__ inline void mb_jrange(double W, double lam, int* J0, int* nJ
   const int j1 = (int)ceil(h + 1.0) - 1;
   *J0 = j0;
   *nJ = j1 - j0 + 1;
-}
-
-// P = {|c|, |s|} (non-zero ones, with the short-direction split), Q = {w1, w2, lambda x (d+1)}
-__device__ inline void mb_bp_dirs(double A, double B, double w1, double w2, double lam, int d, BoxDirs* P,
-                                  int* small, BoxDirs* Q) {
-  P->ng = 0;
-  if (A > 0.0) { P->a[P->ng] = A; P->m[P->ng] = 1; ++P->ng; }
-  if (B > 0.0) { P->a[P->ng] = B; P->m[P->ng] = 1; ++P->ng; }
-  for (int g = P->ng; g < 4; ++g) { P->a[g] = 0.0; P->m[g] = 0; }
-  *small = -1;
-  if (A > 0.0 && B > 0.0) {
-    if (B < BSCT_SHORT_DIR * A) *small = 1;
-    else if (A < BSCT_SHORT_DIR * B) *small = 0;
-  }
-  Q->ng = 0;
-  if (w1 == w2) { Q->a[0] = w1; Q->m[0] = 2; Q->ng = 1; }
-  else { Q->a[0] = w1; Q->m[0] = 1; Q->a[1] = w2; Q->m[1] = 1; Q->ng = 2; }
-  Q->a[Q->ng] = lam; Q->m[Q->ng] = d + 1; ++Q->ng;
-  for (int g = Q->ng; g < 4; ++g) { Q->a[g] = 0.0; Q->m[g] = 0; }
 }
 
 // one CTA (256 threads) per view
@@ -79,13 +68,18 @@ __global__ void __launch_bounds__(256) k_mb_bp_tables(const double* __restrict__
   const int a = blockIdx.x;
   __shared__ double sig[MB_QMAX + 4];
   __shared__ int s_q;
+  __shared__ FootPoly F;
   double s_, c_;
   sincospi(ang[a], &s_, &c_);
   const double A = fabs(c_), B = fabs(s_);
   const int d = (A > 0.0) + (B > 0.0) + 1;  // directions |c|, |s|, w1, w2 (non-zero) - 1
-  BoxDirs P, Q;
-  int small;
-  mb_bp_dirs(A, B, w1, w2, lam, d, &P, &small, &Q);
+  foot_build(F, A, B, w1, w2, 1e-13);       // the view's footprint h as exact cubic pieces
+  BoxDirs Q;                                // beta_d = M_[lambda x (d+1)]
+  Q.a[0] = lam; Q.m[0] = d + 1; Q.ng = 1;
+  for (int g = 1; g < 4; ++g) { Q.a[g] = 0.0; Q.m[g] = 0; }
+  const double bh = 0.5 * (d + 1) * lam;
+  double bk[5];
+  for (int k = 0; k <= d + 1; ++k) bk[k] = -bh + k * lam;
   const double W = A + B + w1 + w2 + (d + 1) * lam;
   int J0, nJ;
   mb_jrange(W, lam, &J0, &nJ);
@@ -129,30 +123,64 @@ __global__ void __launch_bounds__(256) k_mb_bp_tables(const double* __restrict__
     h[7] = 0.0;
     for (int i = 0; i < 24; ++i) h[MB_SIG + i] = i <= q ? sig[i] : 2.0;
     if (nJ > MB_NJMAX) atomicExch(status, 1);
+    float* hf = reinterpret_cast<float*>(h + MB_F);
+    const double pz = h[MB_P00], nz = floor(pz);
+    hf[MBF_P0 + 0] = (float)nz;
+    hf[MBF_P0 + 1] = (float)(pz - nz);
+    int nb = 1;  // pixel indices < 2^nb
+    while ((1 << nb) < N) ++nb;
+    const double cs[2] = {c_ / lam, s_ / lam};
+    for (int k = 0; k < 2; ++k) {
+      int e;
+      const double mm = frexp(cs[k], &e);
+      const double hi = ldexp(trunc(ldexp(mm, 24 - nb)), e - (24 - nb));
+      hf[MBF_P0 + 2 + 2 * k] = (float)hi;
+      hf[MBF_P0 + 3 + 2 * k] = (float)(cs[k] - hi);
+    }
+    hf[6] = hf[7] = 0.f;
+    for (int i = 0; i < 24; ++i) hf[MBF_SIGF + i] = i <= q ? (float)sig[i] : 2.f;
   }
   __syncthreads();
   const int Qn = s_q;
   for (int i = threadIdx.x; i < MB_QMAX; i += blockDim.x) {
     h[MB_MID + i] = i < Qn ? 0.5 * (sig[i] + sig[i + 1]) : 0.0;
     h[MB_IHW + i] = i < Qn ? 2.0 / (sig[i + 1] - sig[i]) : 0.0;
+    float* hf = reinterpret_cast<float*>(h + MB_F);
+    hf[MBF_MIDF + i] = (float)h[MB_MID + i];
+    hf[MBF_IHWF + i] = (float)h[MB_IHW + i];
   }
   T* cv = coef + (long)a * MB_CSTRIDE;
+  // unused (piece, offset) slots are zero
   for (int w = threadIdx.x; w < MB_QMAX * MB_NJMAX; w += blockDim.x) {
     const int q = w / MB_NJMAX, j = w % MB_NJMAX;
-    T* c = cv + (long)w * MB_NC;
-    if (q >= Qn || j >= nJ || nJ > MB_NJMAX) {
-      for (int i = 0; i < MB_NC; ++i) c[i] = T(0);
-      continue;
-    }
-    const double mid = 0.5 * (sig[q] + sig[q + 1]), hw = 0.5 * (sig[q + 1] - sig[q]);
-    double fv[8], mono[8];
-    for (int i = 0; i < 8; ++i) {
+    if (q >= Qn || j >= nJ || nJ > MB_NJMAX)
+      for (int i = 0; i < MB_NC; ++i) cv[(long)w * MB_NC + i] = T(0);
+  }
+  if (nJ > MB_NJMAX) return;  // uniform over the CTA (rejected on the host)
+  // the used slots in chunks of MB_CHUNK (piece, offset) pairs: the 8 node values of every
+  // pair of the chunk spread over all threads, then one thread per pair fits them
+  __shared__ double fvs[MB_CHUNK * 8];
+  const int items = Qn * nJ;
+  for (int c0 = 0; c0 < items; c0 += MB_CHUNK) {
+    const int nc = items - c0 < MB_CHUNK ? items - c0 : MB_CHUNK;
+    __syncthreads();  // the previous chunk's values have been fitted
+    for (int it = threadIdx.x; it < nc * 8; it += blockDim.x) {
+      const int w = c0 + (it >> 3), i = it & 7, q = w / nJ, j = w - q * nJ;
+      const double mid = 0.5 * (sig[q] + sig[q + 1]), hw = 0.5 * (sig[q + 1] - sig[q]);
       const double f = mid + hw * cospi((2.0 * i + 1.0) / 16.0);
       const double u = (J0 + j - f) * lam;
-      fv[i] = fabs(u) < 0.5 * W ? lam * box_conv(u, P, small, Q) : 0.0;
+      fvs[it] = fabs(u) < 0.5 * W
+                    ? lam * foot_conv(F, u, -bh, bh, bk, d + 2, [&](double v) { return box_tp(-fabs(v), Q); })
+                    : 0.0;
     }
-    cheb8_monomials(fv, mono);
-    for (int i = 0; i < MB_NC; ++i) c[i] = T(mono[i]);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+      const int w = c0 + k, q = w / nJ, j = w - q * nJ;
+      double mono[8];
+      cheb8_monomials(fvs + 8 * k, mono);
+      T* c = cv + ((long)q * MB_NJMAX + j) * MB_NC;
+      for (int i = 0; i < MB_NC; ++i) c[i] = T(mono[i]);
+    }
   }
 }
 
@@ -183,58 +211,76 @@ __global__ void __launch_bounds__(MB_PF_T) k_mb_prefilter(const double* __restri
   ct[(long)a * M + m] = fma(qs[0], c[0], acc);
 }
 
-template <typename T> struct MbVec;
-template <> struct MbVec<float> {
-  static __device__ __forceinline__ void load8(const float* p, float c[8]) {
-    const float4 x = __ldg(reinterpret_cast<const float4*>(p)), y = __ldg(reinterpret_cast<const float4*>(p + 4));
-    c[0] = x.x; c[1] = x.y; c[2] = x.z; c[3] = x.w; c[4] = y.x; c[5] = y.y; c[6] = y.z; c[7] = y.w;
-  }
-};
-template <> struct MbVec<double> {
-  static __device__ __forceinline__ void load8(const double* p, double c[8]) {
-    for (int i = 0; i < 4; ++i) {
-      const double2 x = __ldg(reinterpret_cast<const double2*>(p) + i);
-      c[2 * i] = x.x;
-      c[2 * i + 1] = x.y;
-    }
-  }
-};
-
-// one thread per pixel, every view
+// one thread per pixel, every view; each view's used coefficients (Q x nJ rows of 8) are
+// staged in shared memory by the whole CTA, so the pixels' data-dependent row reads hit
+// shared memory instead of L1
+template <typename T> __host__ __device__ constexpr size_t mb_gather_smem() {
+  return (size_t)(MB_QMAX - 3) * (MB_NJMAX * MB_NC + 1) * sizeof(T);  // <= 17 pieces occur
+}
 template <typename T>
 __global__ void __launch_bounds__(MB_TX* MB_TY) k_mb_bp_gather(const double* __restrict__ hdr,
                                                                const T* __restrict__ coef, const T* __restrict__ ct,
                                                                int na, int N, int M, T* __restrict__ b) {
+  extern __shared__ __align__(16) unsigned char mb_raw[];
+  T* sc = reinterpret_cast<T*>(mb_raw);  // [q][j][8], j < nJ; piece rows padded by one (banks)
+  const int tid = threadIdx.y * MB_TX + threadIdx.x;
   const int k1 = blockIdx.x * MB_TX + threadIdx.x, k2 = blockIdx.y * MB_TY + threadIdx.y;
-  if (k1 >= N || k2 >= N) return;
+  const bool inside = k1 < N && k2 < N;
   double total = 0.0;
   T part = T(0);
   for (int a = 0; a < na; ++a) {
     const double* h = hdr + (long)a * MB_DH;
-    const double p = h[MB_P00] + (double)k1 * h[MB_CL] + (double)k2 * h[MB_SL];
-    const double mf = floor(p);
-    const double f = p - mf;
     const int Q = (int)h[MB_Q], J0 = (int)h[MB_J0], nJ = (int)h[MB_NJ];
-    int q = 0;
-    while (q + 1 < Q && h[MB_SIG + q + 1] <= f) ++q;
-    const T v = T((f - h[MB_MID + q]) * h[MB_IHW + q]);
-    const T* cq = coef + (long)a * MB_CSTRIDE + (long)q * MB_NJMAX * MB_NC;
-    const T* cr = ct + (long)a * M;
-    const int mb = (int)mf + J0;
-    for (int j = 0; j < nJ; ++j) {
-      const int m = mb + j;
-      if ((unsigned)m >= (unsigned)M) continue;
-      T c[8];
-      MbVec<T>::load8(cq + j * MB_NC, c);
-      T w = c[7];
+    const int row = nJ * MB_NC, rs = row + 1;
+    __syncthreads();  // the previous view's coefficients have been read
+    const T* src = coef + (long)a * MB_CSTRIDE;
+    for (int e = tid; e < Q * row; e += MB_TX * MB_TY) {
+      const int q = e / row, r = e - q * row;
+      sc[q * rs + r] = src[(long)q * MB_NJMAX * MB_NC + r];
+    }
+    __syncthreads();
+    if (inside) {
+      int q = 0, mb;
+      T v;
+      if constexpr (sizeof(T) == 8) {
+        const double p = h[MB_P00] + (double)k1 * h[MB_CL] + (double)k2 * h[MB_SL];
+        const double mf = floor(p);
+        const double f = p - mf;
+        for (int step = 16; step > 0; step >>= 1)
+          if (q + step < Q && h[MB_SIG + q + step] <= f) q += step;
+        v = (f - h[MB_MID + q]) * h[MB_IHW + q];
+        mb = (int)mf + J0;
+      } else {
+        // p = floor(p00) + frac(p00) + X c_hi + Y s_hi + (X c_lo + Y s_lo): the hi products
+        // are exact, so their integer and fractional parts separate exactly in FP32
+        const float* hf = reinterpret_cast<const float*>(h + MB_F);
+        const float X = (float)k1, Y = (float)k2;
+        const float a1 = X * hf[MBF_P0 + 2], a2 = Y * hf[MBF_P0 + 4];
+        const float n1 = floorf(a1), n2 = floorf(a2);
+        const float fr = (hf[MBF_P0 + 1] + (a1 - n1)) + ((a2 - n2) + fmaf(Y, hf[MBF_P0 + 5], X * hf[MBF_P0 + 3]));
+        const float n3 = floorf(fr);
+        const float f = fr - n3;
+        for (int step = 16; step > 0; step >>= 1)
+          if (q + step < Q && hf[MBF_SIGF + q + step] <= f) q += step;
+        v = (f - hf[MBF_MIDF + q]) * hf[MBF_IHWF + q];
+        mb = (int)hf[MBF_P0] + (int)n1 + (int)n2 + (int)n3 + J0;
+      }
+      const T* cq = sc + q * rs;
+      const T* cr = ct + (long)a * M;
+      for (int j = 0; j < nJ; ++j) {
+        const int m = mb + j;
+        if ((unsigned)m >= (unsigned)M) continue;
+        const T* c = cq + j * MB_NC;
+        T w = c[7];
 #pragma unroll
-      for (int i = 6; i >= 0; --i) w = fma(w, v, c[i]);
-      part = fma(w, cr[m], part);
+        for (int i = 6; i >= 0; --i) w = fma(w, v, c[i]);
+        part = fma(w, cr[m], part);
+      }
     }
     if ((a & 31) == 31) { total += (double)part; part = T(0); }
   }
   total += (double)part;
-  b[(long)k2 * N + k1] = T(total);
+  if (inside) b[(long)k2 * N + k1] = T(total);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -249,91 +295,35 @@ constexpr int MBF_KN = 8, MBF_MID = MBF_KN + 20, MBF_IHW = MBF_MID + MBF_KMAX, M
 constexpr int MBF_CSTRIDE = MBF_KMAX * 4;
 constexpr int MBF_THREADS = 128;
 
-__device__ inline double mb_footprint(double u, double A, double B, double w1, double w2) {
-  BoxDirs P, Q;
-  P.ng = 0;
-  if (A > 0.0) { P.a[P.ng] = A; P.m[P.ng] = 1; ++P.ng; }
-  if (B > 0.0) { P.a[P.ng] = B; P.m[P.ng] = 1; ++P.ng; }
-  for (int g = P.ng; g < 4; ++g) { P.a[g] = 0.0; P.m[g] = 0; }
-  int small = -1;
-  if (A > 0.0 && B > 0.0) {
-    if (B < BSCT_SHORT_DIR * A) small = 1;
-    else if (A < BSCT_SHORT_DIR * B) small = 0;
-  }
-  Q.ng = 0;
-  if (w1 == w2) { Q.a[0] = w1; Q.m[0] = 2; Q.ng = 1; }
-  else { Q.a[0] = w1; Q.m[0] = 1; Q.a[1] = w2; Q.m[1] = 1; Q.ng = 2; }
-  for (int g = Q.ng; g < 4; ++g) { Q.a[g] = 0.0; Q.m[g] = 0; }
-  return box_conv(u, P, small, Q);
-}
-
-// one CTA (32 threads) per view; thread q fits piece q
+// one CTA (32 threads) per view: the footprint's exact cubic pieces (foot_build), stored
+// for the gather (coefficients in T)
 template <typename T>
 __global__ void __launch_bounds__(32) k_mb_fp_tables(const double* __restrict__ ang, double w1, double w2,
                                                      double merge_tol, double* __restrict__ hdr,
                                                      T* __restrict__ coef) {
   const int a = blockIdx.x;
-  __shared__ double kn[20];
-  __shared__ int s_k;
+  __shared__ FootPoly F;
   double s_, c_;
   sincospi(ang[a], &s_, &c_);
   const double A = fabs(c_), B = fabs(s_);
-  const double W = A + B + w1 + w2;
+  foot_build(F, A, B, w1, w2, merge_tol);
   double* h = hdr + (long)a * MBF_DH;
   if (threadIdx.x == 0) {
-    double k[16];
-    int n = 0;
-    for (int k0 = 0; k0 <= (A > 0.0); ++k0)
-      for (int k1 = 0; k1 <= (B > 0.0); ++k1)
-        for (int k2 = 0; k2 <= 1; ++k2)
-          for (int k3 = 0; k3 <= 1; ++k3) k[n++] = -0.5 * W + k0 * A + k1 * B + k2 * w1 + k3 * w2;
-    for (int i = 1; i < n; ++i) {  // insertion sort
-      const double t = k[i];
-      int j = i - 1;
-      while (j >= 0 && k[j] > t) { k[j + 1] = k[j]; --j; }
-      k[j + 1] = t;
-    }
-    // merge kinks closer than merge_tol (the ends -W/2 and W/2 stay)
-    int m = 1;
-    for (int i = 1; i < n; ++i)
-      if (k[i] - k[m - 1] > merge_tol) k[m++] = k[i];
-      else if (i == n - 1) k[m - 1] = k[i];
-    for (int i = 0; i < 20; ++i) kn[i] = i < m ? k[i] : 1e300;
-    s_k = m - 1;
-    const bool rows = A >= B;
     h[MBF_C] = c_;
     h[MBF_S] = s_;
-    h[MBF_ROWS] = rows ? 1.0 : 0.0;
-    h[MBF_HW] = 0.5 * W;
-    h[MBF_K] = m - 1;
+    h[MBF_ROWS] = A >= B ? 1.0 : 0.0;
+    h[MBF_HW] = F.hw;
+    h[MBF_K] = F.K;
     for (int i = 5; i < MBF_KN; ++i) h[i] = 0.0;
-    for (int i = 0; i < 20; ++i) h[MBF_KN + i] = kn[i];
+    for (int i = 0; i < 20; ++i) h[MBF_KN + i] = i < 17 ? F.kn[i] : 1e300;
   }
-  __syncthreads();
-  const int K = s_k, q = threadIdx.x;
+  const int q = threadIdx.x;
   if (q >= MBF_KMAX) return;
   T* c = coef + (long)a * MBF_CSTRIDE + 4 * q;
-  if (q >= K) {
-    h[MBF_MID + q] = 0.0;
-    h[MBF_IHW + q] = 0.0;
-    for (int i = 0; i < 4; ++i) c[i] = T(0);
-    return;
-  }
-  const double mid = 0.5 * (kn[q] + kn[q + 1]), hw = 0.5 * (kn[q + 1] - kn[q]);
-  // cubic through the 4 Chebyshev nodes cos(pi (2i + 1) / 8), then monomials in v
-  double fv[4], ch[4];
-  for (int i = 0; i < 4; ++i) fv[i] = mb_footprint(mid + hw * cospi((2.0 * i + 1.0) / 8.0), A, B, w1, w2);
-  for (int k = 0; k < 4; ++k) {
-    double acc = 0.0;
-    for (int i = 0; i < 4; ++i) acc += fv[i] * cospi(k * (2.0 * i + 1.0) / 8.0);
-    ch[k] = acc * (k == 0 ? 0.25 : 0.5);
-  }
-  c[0] = T(ch[0] - ch[2]);
-  c[1] = T(ch[1] - 3.0 * ch[3]);
-  c[2] = T(2.0 * ch[2]);
-  c[3] = T(4.0 * ch[3]);
-  h[MBF_MID + q] = mid;
-  h[MBF_IHW + q] = 1.0 / hw;
+  const bool on = q < F.K;
+  h[MBF_MID + q] = on ? F.mid[q] : 0.0;
+  h[MBF_IHW + q] = on ? F.ihw[q] : 0.0;
+  for (int i = 0; i < 4; ++i) c[i] = on ? T(F.c[q][i]) : T(0);
 }
 
 template <typename T>
@@ -348,42 +338,73 @@ __global__ void k_mb_transpose(const T* __restrict__ a, int N, T* __restrict__ a
     if (xo < N && yo < N) at[(long)yo * N + xo] = t[threadIdx.x][r];
 }
 
-// one thread per (view, detector sample)
+// one thread per (view, detector sample); the view's pieces are staged in shared memory.
+// FP64: every footprint argument u = y - x . u_theta in FP64.  FP32: u in FP64 at the first
+// pixel of each line, then stepped by the FP32 pixel increment (<= ~6 steps: |error| below
+// 1e-6 of a pixel), piece search and Horner in FP32.
 template <typename T>
 __global__ void __launch_bounds__(MBF_THREADS) k_mb_fp_gather(const T* __restrict__ img, const T* __restrict__ imgT,
                                                               const double* __restrict__ hdr,
                                                               const T* __restrict__ coef, int N, int M, double lam,
                                                               T* __restrict__ sino) {
   const int a = blockIdx.y, m = blockIdx.x * MBF_THREADS + threadIdx.x;
-  if (m >= M) return;
+  __shared__ double s_kn[MBF_KMAX + 1], s_mid[MBF_KMAX], s_ihw[MBF_KMAX];
+  __shared__ T s_c[MBF_KMAX][4];
+  __shared__ T s_knt[MBF_KMAX + 1], s_midt[MBF_KMAX], s_ihwt[MBF_KMAX];
   const double* h = hdr + (long)a * MBF_DH;
+  const int K = (int)h[MBF_K];
+  for (int i = threadIdx.x; i <= MBF_KMAX; i += blockDim.x) {
+    const double kn = i <= K ? h[MBF_KN + i] : 1e300;
+    s_kn[i] = kn;
+    s_knt[i] = i <= K ? T(kn) : T(3.0e38);
+    if (i < MBF_KMAX) {
+      s_mid[i] = h[MBF_MID + i];
+      s_ihw[i] = h[MBF_IHW + i];
+      s_midt[i] = T(h[MBF_MID + i]);
+      s_ihwt[i] = T(h[MBF_IHW + i]);
+      for (int k = 0; k < 4; ++k) s_c[i][k] = coef[(long)a * MBF_CSTRIDE + 4 * i + k];
+    }
+  }
+  __syncthreads();
+  if (m >= M) return;
   const bool rows = h[MBF_ROWS] != 0.0;
   const double major = rows ? h[MBF_C] : h[MBF_S], minor = rows ? h[MBF_S] : h[MBF_C];
   const double hW = h[MBF_HW];
-  const int K = (int)h[MBF_K];
   const T* src = rows ? img : imgT;  // line L, position X: src[L N + X]
-  const T* cf = coef + (long)a * MBF_CSTRIDE;
   const double hN = 0.5 * (N - 1);
   const double y = (m - 0.5 * (M - 1)) * lam;
-  const double ihalf = hW / fabs(major);
+  const double ihalf = hW / fabs(major), imaj = 1.0 / major;
+  const T majt = T(major), hWt = T(hW);
   double total = 0.0;
   for (int L = 0; L < N; ++L) {
     // |y - (X - hN) major - (L - hN) minor| < W / 2
     const double base = y - (L - hN) * minor;
-    const double ctr = base / major + hN;
+    const double ctr = base * imaj + hN;  // the pixels at the support's ends carry h ~ 0
     int x0 = (int)ceil(ctr - ihalf), x1 = (int)floor(ctr + ihalf);
     x0 = x0 < 0 ? 0 : x0;
     x1 = x1 > N - 1 ? N - 1 : x1;
     T part = T(0);
     const T* line = src + (long)L * N;
+    const T u0 = T(base - (x0 - hN) * major);
     for (int X = x0; X <= x1; ++X) {
-      const double u = base - (X - hN) * major;
-      if (!(fabs(u) < hW)) continue;
-      int q = 0;
-      while (q + 1 < K && h[MBF_KN + q + 1] <= u) ++q;
-      const T v = T((u - h[MBF_MID + q]) * h[MBF_IHW + q]);
-      const T* c = cf + 4 * q;
-      T w = fma(fma(fma(c[3], v, c[2]), v, c[1]), v, c[0]);
+      T w;
+      if constexpr (sizeof(T) == 8) {
+        const double u = base - (X - hN) * major;
+        if (!(fabs(u) < hW)) continue;
+        int q = 0;
+        for (int step = 8; step > 0; step >>= 1)
+          if (q + step < K && s_kn[q + step] <= u) q += step;
+        const double v = (u - s_mid[q]) * s_ihw[q];
+        w = fma(fma(fma(s_c[q][3], v, s_c[q][2]), v, s_c[q][1]), v, s_c[q][0]);
+      } else {
+        const T u = u0 - T(X - x0) * majt;
+        if (!(fabsf(u) < hWt)) continue;
+        int q = 0;
+        for (int step = 8; step > 0; step >>= 1)
+          if (q + step < K && s_knt[q + step] <= u) q += step;
+        const T v = (u - s_midt[q]) * s_ihwt[q];
+        w = fmaf(fmaf(fmaf(s_c[q][3], v, s_c[q][2]), v, s_c[q][1]), v, s_c[q][0]);
+      }
       part = fma(w, line[X], part);
     }
     total += (double)part;
@@ -436,7 +457,9 @@ template <typename T> int mb_bp_run(const bsct_geom* g, const T* sino, T* b, cha
   dim3 gp((M + MB_PF_T - 1) / MB_PF_T, na);
   k_mb_prefilter<T><<<gp, MB_PF_T, 0, st>>>(hdr, sino, M, ct);
   dim3 gg((N + MB_TX - 1) / MB_TX, (N + MB_TY - 1) / MB_TY), tb(MB_TX, MB_TY);
-  k_mb_bp_gather<T><<<gg, tb, 0, st>>>(hdr, coef, ct, na, N, M, b);
+  BSCT_CUDA_TRY(cudaFuncSetAttribute(k_mb_bp_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)mb_gather_smem<T>()));
+  k_mb_bp_gather<T><<<gg, tb, mb_gather_smem<T>(), st>>>(hdr, coef, ct, na, N, M, b);
   count_launch(3);
   BSCT_CUDA_TRY(cudaGetLastError());
   return BSCT_OK;
