@@ -708,7 +708,7 @@ def run_ours(args):
             "gemm_flop_per_apply": gemm_flop, "gemm_tflops_effective": gemm_flop / (dms * 1e-3) / 1e12,
             "frac_of_bf16_peak": gemm_flop / (dms * 1e-3) / 1e12 / measured_bf16_tflops()[0],
             "bf16_peak_source": measured_bf16_tflops()[1] + " bf16_tflops (burst)",
-            "note": "4 DFTs of 4096^2 as 8 split-BF16 GEMMs (mma.sync m16n8k16, FP32 accumulate) + split/twiddle kernels"}
+            "note": "4 DFTs of 4096^2 as 8 split-BF16 GEMMs (tcgen05 kind::f16, FP32 accumulate in tensor memory) + split/twiddle kernels"}
 
     # ---------------------------------------------------------------- batched slices (one graph launch)
     if not args.quick and not args.no_batch:
