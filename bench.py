@@ -546,6 +546,11 @@ def run_ours(args):
                                 "how": "bsct_fma_peak: 8 independent FMA chains per thread, best of 3"}
         t["backproject_fp32_frac"] = N * N * cfg["n_angles"] * 70.0 / (t["backproject_ms"] * 1e-3) / fp32
         t["backproject_flop_per_pair"] = "70, algorithmic: <= 7 bins x degree-5 Horner per pixel-view pair"
+        # the filter build against the FP64 pipe: 3.8e7 strip evaluations of the Gram kernel
+        # at N = 2048 / 1800 views (each a degree-5 polynomial piece, ~10 FP64 FMA)
+        if N == 2048 and cfg["n_angles"] == 1800:
+            t["gram_build_fp64_frac"] = 3.8e7 * 20.0 / (t["gram_build_ms"] * 1e-3) / fp64
+            t["gram_build_flop"] = "3.8e7 strip evaluations x 20 FP64 flop (whole build, spectrum included)"
         extras["hot_path_pass"] = t
         g2.close()
         # detector kernel of two boxes (widths 1.0 and 0.5) on the 512 x 512 / 720-view
