@@ -461,26 +461,42 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bp_spline(const float* __restrict_
       if (threadIdx.x == 0) header(a + 1, hdr[buf ^ 1]);
       stage_table(a + 1, buf ^ 1);
     }
-    // coefficient window: F on (slot s, piece q) = sum_j c~[m0lo + s + J0 + j] coef_{q,j}
+    // coefficient window: F on (slot s, piece q) = sum_j c~[m0lo + s + J0 + j] coef_{q,j}.
+    // A work item is 2 consecutive slots of one piece: the coefficients are read once per j
+    // for both, the samples slide through registers (one shared load per j), and the six
+    // sums of a slot are three packed FP32 pairs (fma.rn.f32x2: per element the same
+    // rounding and order as scalar FMAs, so the window is bit-identical to one slot an item)
     {
       const BsHeader& h = hdr[buf];
       const float* t = tb + buf * BP_STRIDE;
       const float* cw = ctw + buf * BS_CW;
-      const int W = h.W, nJ = h.nJ, items = h.Q * W;
+      const int W = h.W, nJ = h.nJ, groups = (W + 1) >> 1, items = h.Q * groups;
       for (int it = threadIdx.x; it < items; it += BS_NT) {
-        const int q = it / W, sl = it - q * W;
+        const int q = it / groups, s0 = (it - q * groups) << 1;
         const float* ca = t + BP_CA + q * BP_QA;
         const float* cb = t + BP_CB + q * BP_QB;
-        float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f, r4 = 0.f, r5 = 0.f;
+        float2 a01 = make_float2(0.f, 0.f), a23 = a01, a45 = a01, b01 = a01, b23 = a01, b45 = a01;
+        float c0 = cw[s0];
         for (int j = 0; j < nJ; ++j) {
-          const float cv = cw[sl + j];
+          const float c1 = cw[s0 + j + 1];
           const float4 x = *reinterpret_cast<const float4*>(ca + 4 * j);
           const float2 y = *reinterpret_cast<const float2*>(cb + 2 * j);
-          r0 = fmaf(cv, x.x, r0); r1 = fmaf(cv, x.y, r1); r2 = fmaf(cv, x.z, r2); r3 = fmaf(cv, x.w, r3);
-          r4 = fmaf(cv, y.x, r4); r5 = fmaf(cv, y.y, r5);
+          const float2 x01 = make_float2(x.x, x.y), x23 = make_float2(x.z, x.w);
+          const float2 p0 = make_float2(c0, c0), p1 = make_float2(c1, c1);
+          a01 = __ffma2_rn(p0, x01, a01);
+          a23 = __ffma2_rn(p0, x23, a23);
+          a45 = __ffma2_rn(p0, y, a45);
+          b01 = __ffma2_rn(p1, x01, b01);
+          b23 = __ffma2_rn(p1, x23, b23);
+          b45 = __ffma2_rn(p1, y, b45);
+          c0 = c1;
         }
-        FcA[q * BS_WS + bs_slot(sl)] = make_float4(r0, r1, r2, r3);
-        FcB[q * BS_WS + bs_slot(sl)] = make_float2(r4, r5);
+        FcA[q * BS_WS + bs_slot(s0)] = make_float4(a01.x, a01.y, a23.x, a23.y);
+        FcB[q * BS_WS + bs_slot(s0)] = a45;
+        if (s0 + 1 < W) {
+          FcA[q * BS_WS + bs_slot(s0 + 1)] = make_float4(b01.x, b01.y, b23.x, b23.y);
+          FcB[q * BS_WS + bs_slot(s0 + 1)] = b45;
+        }
       }
     }
     __syncthreads();  // window ready; next header visible
