@@ -340,6 +340,43 @@ __global__ void __launch_bounds__(64) k_gram_tables2(const double2* __restrict__
   });
 }
 
+// Views that can reach tap d: those whose strip |d . u| < |c| + |s| + zeta contains d, bounded
+// by the window |theta - (phi_d + pi/2)| <= asin(wmax / |d|).  The window only has to contain
+// them (views outside the support are skipped by the caller), so it is computed in FP32 and
+// widened by 1e-4 half turns - far more than the FP32 error, which is at most ~1e-5 here
+// because asin's argument stays below 0.9999 - and found by binary search in the FP32 copy
+// of the sorted angles (each within 6e-8 of its FP64 value), while the taps stay FP64.
+// Writes up to two index ranges [lo, hi) of views; returns how many.
+__device__ inline int tap_window(int d1, int d2, float r, int na, const float* __restrict__ th, float wmax,
+                                 int rg[2][2]) {
+  const float hw = (r > 1.0001f * wmax) ? asinf(wmax / r) * 0.318309886f + 1e-4f : 1.0f;
+  if (hw >= 0.5f) {
+    rg[0][0] = 0; rg[0][1] = na;
+    return 1;
+  }
+  const float phi = atan2f((float)d2, (float)d1) * 0.318309886f;  // / pi, in [0, 1]
+  float centre = phi + 0.5f;
+  if (centre >= 1.0f) centre -= 1.0f;
+  const float lo = centre - hw, hi = centre + hw;
+  if (lo < 0.0f) {
+    rg[0][0] = lower_bound_f(th, na, lo + 1.0f); rg[0][1] = na;
+    rg[1][0] = 0; rg[1][1] = lower_bound_f(th, na, hi);
+    return 2;
+  }
+  if (hi > 1.0f) {
+    rg[0][0] = lower_bound_f(th, na, lo); rg[0][1] = na;
+    rg[1][0] = 0; rg[1][1] = lower_bound_f(th, na, hi - 1.0f);
+    return 2;
+  }
+  rg[0][0] = lower_bound_f(th, na, lo); rg[0][1] = lower_bound_f(th, na, hi);
+  return 1;
+}
+
+// Taps closer to the origin than TAP_NEAR see up to all views (1800 at |d| < 2.4, ~40 at
+// |d| = 64) and would hold a single thread for milliseconds, leaving the GPU idle around a few
+// blocks; they are summed by k_gram_taps_near, one warp per tap, instead.
+constexpr float TAP_NEAR = 64.0f;
+
 // zeta: the sum of the detector box widths (bounds the strip of views that reach a tap)
 template <typename L>
 __global__ void k_gram_taps(int N, int na, const float* __restrict__ th, const double2* __restrict__ cs,
@@ -354,19 +391,13 @@ __global__ void k_gram_taps(int N, int na, const float* __restrict__ th, const d
     d2 = 1 + (int)(q / (2 * N - 1));
     d1 = (int)(q % (2 * N - 1)) - (N - 1);
   }
-  // Views visited: those whose strip |d . u| < |c| + |s| + zeta can reach d, bounded by
-  // the window |theta - (phi_d + pi/2)| <= asin(wmax / |d|).  The window only has to
-  // contain them (views outside the support are skipped below), so it is computed in
-  // FP32 and widened by 1e-4 half turns - far more than the FP32 error, which is at most
-  // ~1e-5 here because asin's argument stays below 0.9999 - and found by binary search
-  // in the FP32 copy of the sorted angles (each within 6e-8 of its FP64 value), while
-  // the taps stay FP64.
   const float wmax = 1.41421356f + (float)zeta;  // >= |c| + |s| + zeta for every view
   const float r = hypotf((float)d1, (float)d2);
+  if (r < TAP_NEAR) return;  // k_gram_taps_near
   double acc = 0.0;
   // two views per step as independent FP64 chains (the kernel waits on FP64 results,
   // not on issue); a view outside its support is evaluated at the support edge and
-  // masked, and the sum keeps the view order, so the taps are unchanged
+  // masked, and the sum keeps the view order
   auto visit = [&](int j0, int j1) {
     int j = j0;
     for (; j + 1 < j1; j += 2) {
@@ -386,27 +417,47 @@ __global__ void k_gram_taps(int N, int na, const float* __restrict__ th, const d
       if (t < T[L::S]) acc += gram_table_eval<L>(T, t);
     }
   };
-  const float hw = (r > 1.0001f * wmax) ? asinf(wmax / r) * 0.318309886f + 1e-4f : 1.0f;
-  if (hw >= 0.5f) {
-    visit(0, na);
-  } else {
-    const float phi = atan2f((float)d2, (float)d1) * 0.318309886f;  // / pi, in [0, 1]
-    float centre = phi + 0.5f;
-    if (centre >= 1.0f) centre -= 1.0f;
-    const float lo = centre - hw, hi = centre + hw;
-    if (lo < 0.0f) {
-      visit(lower_bound_f(th, na, lo + 1.0f), na);
-      visit(0, lower_bound_f(th, na, hi));
-    } else if (hi > 1.0f) {
-      visit(lower_bound_f(th, na, lo), na);
-      visit(0, lower_bound_f(th, na, hi - 1.0f));
-    } else {
-      visit(lower_bound_f(th, na, lo), lower_bound_f(th, na, hi));
-    }
-  }
+  int rg[2][2];
+  const int nr = tap_window(d1, d2, r, na, th, wmax, rg);
+  for (int k = 0; k < nr; ++k) visit(rg[k][0], rg[k][1]);
   const int W = 2 * N - 1;
   G[(long)(d2 + N - 1) * W + (d1 + N - 1)] = acc;
   G[(long)(-d2 + N - 1) * W + (-d1 + N - 1)] = acc;
+}
+
+// The taps with |d| < TAP_NEAR (upper half plane, as k_gram_taps): one warp per candidate
+// d of the square [-R0, R0) x [0, R0) (R0 = min(TAP_NEAR, N)); the lanes take the window's
+// views in a strided order and the 32 partial sums are added by a fixed shuffle tree.
+template <typename L>
+__global__ void __launch_bounds__(128) k_gram_taps_near(int N, int R0, int na, const float* __restrict__ th,
+                                                        const double2* __restrict__ cs, const double* __restrict__ tab,
+                                                        double zeta, double* __restrict__ G) {
+  const int lane = threadIdx.x & 31;
+  const long w = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= (long)(2 * R0 - 1) * R0) return;
+  const int d2 = (int)(w / (2 * R0 - 1)), d1 = (int)(w % (2 * R0 - 1)) - (R0 - 1);
+  if (d2 == 0 && d1 < 0) return;  // lower half of the centre row: the mirror of d1 > 0
+  const float r = hypotf((float)d1, (float)d2);
+  if (!(r < TAP_NEAR)) return;   // the far kernel's taps
+  const float wmax = 1.41421356f + (float)zeta;
+  int rg[2][2];
+  const int nr = tap_window(d1, d2, r, na, th, wmax, rg);
+  double acc = 0.0;
+  for (int k = 0; k < nr; ++k)
+    for (int j = rg[k][0] + lane; j < rg[k][1]; j += 32) {
+      const double2 u = cs[j];
+      const double t = fabs(d1 * u.x + d2 * u.y);
+      const double* T = tab + (long)j * L::STRIDE;
+      const double s = T[L::S];
+      const double e = gram_table_eval<L>(T, fmin(t, s));
+      if (t < s) acc += e;
+    }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    const int W = 2 * N - 1;
+    G[(long)(d2 + N - 1) * W + (d1 + N - 1)] = acc;
+    G[(long)(-d2 + N - 1) * W + (-d1 + N - 1)] = acc;
+  }
 }
 
 __global__ void k_embed(const double* __restrict__ G, int N, double* __restrict__ E) {
@@ -630,15 +681,20 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
   k_view_keys<<<(na + 255) / 256, 256, 0, st>>>(d_ang, na, d_red, d_key);
   k_view_rank<<<(na + GEO_T - 1) / GEO_T, GEO_T, 0, st>>>(d_red, d_key, na, d_thf, d_cs);
   const long H = (long)(2 * N - 1) * (N - 1) + N;
+  const int R0 = N < (int)TAP_NEAR ? N : (int)TAP_NEAR;  // near taps: |d1|, d2 < R0
   if (nbox == 2) {
     k_gram_tables2<<<na, 64, 0, st>>>(d_cs, wb[0], wb[1], 1e-13, d_gtab);
     k_gram_taps<GT2><<<(unsigned)((H + 127) / 128), 128, 0, st>>>(N, na, d_thf, d_cs, d_gtab, wb[0] + wb[1], g->taps);
+    k_gram_taps_near<GT2><<<(unsigned)(((long)(2 * R0 - 1) * R0 + 3) / 4), 128, 0, st>>>(N, R0, na, d_thf, d_cs, d_gtab,
+                                                                                      wb[0] + wb[1], g->taps);
   } else {
     k_gram_tables<<<na, 64, 0, st>>>(d_cs, wb[0], 1e-13, d_gtab);
     k_gram_taps<GT1><<<(unsigned)((H + 127) / 128), 128, 0, st>>>(N, na, d_thf, d_cs, d_gtab, wb[0], g->taps);
+    k_gram_taps_near<GT1><<<(unsigned)(((long)(2 * R0 - 1) * R0 + 3) / 4), 128, 0, st>>>(N, R0, na, d_thf, d_cs, d_gtab,
+                                                                                      wb[0], g->taps);
   }
   k_embed<<<(unsigned)(((long)L * L + 255) / 256), 256, 0, st>>>(g->taps, N, d_emb);
-  count_launch(5);
+  count_launch(6);
   CTRY(cudaGetLastError());
   TRY(build_fft_tables<double>(tw64, N, st));
   TRY(o64.spectrum(d_emb, (cpx<double>*)d_S2, g->Gt64, tw64, st));
