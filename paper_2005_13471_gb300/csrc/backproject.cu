@@ -566,20 +566,48 @@ __global__ void k_bp_reduce(const float* __restrict__ part, int S, long n, float
   b[i] = (float)acc;
 }
 
-// views per spline-gather CTA: enough view splits that a small image still fills about
-// 1024 CTAs, at least 16 views each (the split is fixed by N and the view count only)
-int bp_view_split(int N, int na, double lambda, int precision) {
-  if (precision != BSCT_F32 || lambda < BS_LAMBDA_MIN) return 1;
+// View splits of the spline gather: blockIdx.z takes 1 / S of the views, and the S partial
+// images are summed in order by k_bp_reduce.  At least enough splits that a small image
+// still fills about 1024 CTAs, at most four times that (and >= 16 views per split); within
+// that range the split is chosen so that the CTAs fill the resident slots of the current
+// GPU (3 per SM) in whole waves (the last wave of 1024 tiles on 456 slots would otherwise run
+// a quarter full).  The workspace is sized for the largest split of the range, so it does
+// not depend on the device.
+static void bp_split_range(int N, int na, double lambda, int precision, int* smin, int* smax) {
+  *smin = *smax = 1;
+  if (precision != BSCT_F32 || lambda < BS_LAMBDA_MIN) return;
   const int t = (N + BS_TS - 1) / BS_TS;
-  int S = (1024 + t * t - 1) / (t * t);
-  const int smax = na / 16 > 1 ? na / 16 : 1;
-  return S < smax ? S : smax;
+  const int lim = na / 16 > 1 ? na / 16 : 1;
+  const int s0 = (1024 + t * t - 1) / (t * t);
+  *smin = s0 < lim ? s0 : lim;
+  *smax = 4 * s0 < lim ? 4 * s0 : lim;
+}
+int bp_view_split(int N, int na, double lambda, int precision) {
+  int smin, smax;
+  bp_split_range(N, na, lambda, precision, &smin, &smax);
+  if (smax == smin) return smin;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1) {
+    cudaGetLastError();
+    return smin;
+  }
+  const int t = (N + BS_TS - 1) / BS_TS;
+  const double slots = 3.0 * sms;
+  int best = smin;
+  double best_score = -1.0;
+  for (int S = smin; S <= smax; ++S) {
+    const double waves = (double)t * t * S / slots;
+    const double score = waves / ceil(waves) - 0.002 * (S - smin);  // fill, then fewer splits
+    if (score > best_score + 1e-12) { best_score = score; best = S; }
+  }
+  return best;
 }
 size_t bp_partial_bytes(int N, int na, double lambda, int precision) {
-  const int S = bp_view_split(N, na, lambda, precision);
-  return S > 1 ? (size_t)S * N * N * sizeof(float) : 0;
+  int smin, smax;
+  bp_split_range(N, na, lambda, precision, &smin, &smax);
+  return smax > 1 ? (size_t)smax * N * N * sizeof(float) : 0;
 }
-
 }  // namespace bsct
 
 using namespace bsct;
