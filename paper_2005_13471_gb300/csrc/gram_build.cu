@@ -657,23 +657,33 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
   double2* d_cs = nullptr;
   void* d_S2 = nullptr;
   cpx<double>* tw64 = nullptr;
+  char* d_tmp = nullptr;  // every temporary of the build in one allocation
   auto cleanup = [&]() {
-    cudaFree(d_ang); cudaFree(d_cs); cudaFree(d_emb); cudaFree(d_S2);
-    cudaFree(tw64); cudaFree(d_gtab); cudaFree(d_red); cudaFree(d_thf); cudaFree(d_key);
+    cudaFree(d_tmp);
+    cudaFree(tw64);
     if (g) { bsct_gram_free(g); g = nullptr; }
   };
   const size_t T = precision == BSCT_F32 ? sizeof(float) : sizeof(double);
-  CTRY(cudaMalloc(&d_ang, na * sizeof(double)));
-  CTRY(cudaMalloc(&d_red, na * sizeof(double)));
-  CTRY(cudaMalloc(&d_thf, na * sizeof(float)));
-  CTRY(cudaMalloc(&d_key, na * sizeof(unsigned long long)));
-  CTRY(cudaMalloc(&d_cs, na * sizeof(double2)));
   double wb[2];
   const int nbox = bsct_blur_boxes(geom, wb);
-  CTRY(cudaMalloc(&d_gtab, (size_t)na * (nbox == 2 ? GT2::STRIDE : GT1::STRIDE) * sizeof(double)));
+  {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t b_ang = al(na * sizeof(double)), b_red = al(na * sizeof(double)), b_thf = al(na * sizeof(float)),
+                 b_key = al(na * sizeof(unsigned long long)), b_cs = al(na * sizeof(double2)),
+                 b_gtab = al((size_t)na * (nbox == 2 ? GT2::STRIDE : GT1::STRIDE) * sizeof(double)),
+                 b_emb = al((size_t)L * L * sizeof(double)), b_S2 = al((size_t)L * N * 2 * sizeof(double));
+    CTRY(cudaMalloc(&d_tmp, b_ang + b_red + b_thf + b_key + b_cs + b_gtab + b_emb + b_S2));
+    char* q = d_tmp;
+    d_ang = (double*)q; q += b_ang;
+    d_red = (double*)q; q += b_red;
+    d_thf = (float*)q; q += b_thf;
+    d_key = (unsigned long long*)q; q += b_key;
+    d_cs = (double2*)q; q += b_cs;
+    d_gtab = (double*)q; q += b_gtab;
+    d_emb = (double*)q; q += b_emb;
+    d_S2 = q;
+  }
   CTRY(cudaMalloc(&g->taps, ntap * sizeof(double)));
-  CTRY(cudaMalloc(&d_emb, (size_t)L * L * sizeof(double)));
-  CTRY(cudaMalloc(&d_S2, (size_t)L * N * 2 * sizeof(double)));
   CTRY(cudaMalloc(&g->Gt64, (size_t)(N + 1) * L * sizeof(double)));
   CTRY(cudaMalloc(&tw64, (size_t)fft_table_elems(N) * sizeof(cpx<double>)));
   CTRY(cudaMemcpyAsync(d_ang, geom->angles_pi, na * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -721,8 +731,8 @@ extern "C" int bsct_gram_build(const bsct_geom* geom, int precision, bsct_gram**
   }
   CTRY(cudaGetLastError());
   CTRY(cudaStreamSynchronize(st));
-  cudaFree(d_ang); cudaFree(d_cs); cudaFree(d_emb); cudaFree(d_S2);
-  cudaFree(tw64); cudaFree(d_gtab); cudaFree(d_red); cudaFree(d_thf); cudaFree(d_key);
+  cudaFree(d_tmp);
+  cudaFree(tw64);
   *out = g;
   return BSCT_OK;
 }
