@@ -204,9 +204,20 @@ __global__ void __launch_bounds__(256) k_bp_tables(const double* __restrict__ an
 // each side (zero outside the detector) is staged in shared memory and the symmetric
 // 81-tap filter is summed from the outermost taps inwards in T.
 constexpr int PF_T = 256, PF_H = 40;
+// the filter taps q[0..40], formed once on the host (a pow per tap per CTA kept the FP64
+// pipe of this part busy for most of the kernel)
+struct PfTaps {
+  double q[PF_H + 1];
+};
+static PfTaps pf_taps() {
+  PfTaps t;
+  const double z1 = 2.0 * 1.4142135623730951 - 3.0;
+  for (int i = 0; i <= PF_H; ++i) t.q[i] = 1.4142135623730951 * pow(z1, (double)i);
+  return t;
+}
 template <typename T>
 __global__ void __launch_bounds__(PF_T) k_prefilter(const double* __restrict__ ang, const T* __restrict__ g, int na,
-                                                    int M, double zeta, T* __restrict__ ct) {
+                                                    int M, double zeta, T* __restrict__ ct, PfTaps taps) {
   __shared__ T qs[PF_H + 1];
   __shared__ T seg[PF_T + 2 * PF_H];
   __shared__ int deg2;
@@ -217,10 +228,7 @@ __global__ void __launch_bounds__(PF_T) k_prefilter(const double* __restrict__ a
     sincospi(ang[a], &s_, &c_);
     deg2 = bp_degree(c_, s_, zeta) == 2;
   }
-  if (threadIdx.x <= PF_H) {
-    const double z1 = 2.0 * 1.4142135623730951 - 3.0;
-    qs[threadIdx.x] = T(1.4142135623730951 * pow(z1, (double)threadIdx.x));
-  }
+  if (threadIdx.x <= PF_H) qs[threadIdx.x] = T(taps.q[threadIdx.x]);
   for (int i = threadIdx.x; i < PF_T + 2 * PF_H; i += PF_T) {
     const int mm = m0 - PF_H + i;
     seg[i] = (mm >= 0 && mm < M) ? gr[mm] : T(0);
@@ -652,7 +660,8 @@ template <typename T> int bp_make_tables(const BpPlan& p, cudaStream_t st) {
 // per-sinogram part: prefilter into ct ([na][M] scratch), then gather into b
 template <typename T> int bp_apply(const BpPlan& p, const T* sino, T* ct, T* b, cudaStream_t st) {
   dim3 gp((p.M + PF_T - 1) / PF_T, p.na);
-  k_prefilter<T><<<gp, PF_T, 0, st>>>(p.ang, sino, p.na, p.M, p.zeta, ct);
+  static const PfTaps taps = pf_taps();
+  k_prefilter<T><<<gp, PF_T, 0, st>>>(p.ang, sino, p.na, p.M, p.zeta, ct, taps);
   if constexpr (sizeof(T) == 4) {
     if (p.lambda >= BS_LAMBDA_MIN) {
       const int S = bp_view_split(p.N, p.na, p.lambda, BSCT_F32);

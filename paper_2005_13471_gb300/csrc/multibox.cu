@@ -185,19 +185,27 @@ __global__ void __launch_bounds__(256) k_mb_bp_tables(const double* __restrict__
 }
 
 // c~ = g_s * q (Eq. 5) for the view's degree (2 or 3); one CTA per 256 outputs of one view
+// the taps of both filters, formed once on the host
+struct MbPfTaps {
+  double q2[MB_PF_H + 1], q3[MB_PF_H + 1];
+};
+static MbPfTaps mb_pf_taps() {
+  MbPfTaps t;
+  for (int i = 0; i <= MB_PF_H; ++i) {
+    t.q2[i] = 1.4142135623730951 * pow(2.0 * 1.4142135623730951 - 3.0, (double)i);  // sqrt(2) (2 sqrt(2) - 3)^i
+    t.q3[i] = 1.7320508075688772 * pow(1.7320508075688772 - 2.0, (double)i);        // sqrt(3) (sqrt(3) - 2)^i
+  }
+  return t;
+}
 template <typename T>
 __global__ void __launch_bounds__(MB_PF_T) k_mb_prefilter(const double* __restrict__ hdr, const T* __restrict__ g,
-                                                          int M, T* __restrict__ ct) {
+                                                          int M, T* __restrict__ ct, MbPfTaps taps) {
   __shared__ T qs[MB_PF_H + 1];
   __shared__ T seg[MB_PF_T + 2 * MB_PF_H];
   const int a = blockIdx.y, m0 = blockIdx.x * MB_PF_T;
   const T* gr = g + (long)a * M;
   const int d = (int)hdr[(long)a * MB_DH + MB_DEG];
-  if (threadIdx.x <= MB_PF_H) {
-    const double r = d == 3 ? 1.7320508075688772 : 1.4142135623730951;   // sqrt(3) / sqrt(2)
-    const double z1 = d == 3 ? 1.7320508075688772 - 2.0 : 2.0 * 1.4142135623730951 - 3.0;
-    qs[threadIdx.x] = T(r * pow(z1, (double)threadIdx.x));
-  }
+  if (threadIdx.x <= MB_PF_H) qs[threadIdx.x] = T(d == 3 ? taps.q3[threadIdx.x] : taps.q2[threadIdx.x]);
   for (int i = threadIdx.x; i < MB_PF_T + 2 * MB_PF_H; i += MB_PF_T) {
     const int mm = m0 - MB_PF_H + i;
     seg[i] = (mm >= 0 && mm < M) ? gr[mm] : T(0);
@@ -455,7 +463,8 @@ template <typename T> int mb_bp_run(const bsct_geom* g, const T* sino, T* b, cha
   const double tol = sizeof(T) == 4 ? 1e-6 : 1e-12;
   k_mb_bp_tables<T><<<na, 256, 0, st>>>(ang, N, M, g->lambda_y, wb[0], wb[1], tol, hdr, coef, status);
   dim3 gp((M + MB_PF_T - 1) / MB_PF_T, na);
-  k_mb_prefilter<T><<<gp, MB_PF_T, 0, st>>>(hdr, sino, M, ct);
+  static const MbPfTaps taps = mb_pf_taps();
+  k_mb_prefilter<T><<<gp, MB_PF_T, 0, st>>>(hdr, sino, M, ct, taps);
   dim3 gg((N + MB_TX - 1) / MB_TX, (N + MB_TY - 1) / MB_TY), tb(MB_TX, MB_TY);
   BSCT_CUDA_TRY(cudaFuncSetAttribute(k_mb_bp_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)mb_gather_smem<T>()));
