@@ -32,15 +32,19 @@ constexpr int BP_NJMAX = 16;  // samples touching one pixel (lambda_y >= ~0.2)
 // header: c/lambda, s/lambda, Q, J0, nJ, then the FP32 split of the detector coordinate
 // p = p00 + X c/lambda + Y s/lambda (pixel X, Y): floor(p00), p00 - floor(p00), and
 // c/lambda = c_hi + c_lo, s/lambda = s_hi + s_lo with hi parts short enough that
-// X c_hi and Y s_hi are exact in FP32 for every pixel index of the image
+// X c_hi and Y s_hi are exact in FP32 for every pixel index of the image; last, E (below)
 constexpr int BP_HDR = 12;
 constexpr int BP_SIG = BP_HDR;                      // sigma[16] (padded with 2, for a 4-step search)
-constexpr int BP_MID = BP_SIG + 16;                 // mid[QMAX]
-constexpr int BP_IHW = BP_MID + BP_QMAX;            // 1/halfwidth[QMAX]
+constexpr int BP_MI = BP_SIG + 16;                  // (mid, 1/halfwidth) of piece q at BP_MI + 2 q
+// piece lookup: byte c of the BP_NL bytes at BP_LUT is the piece holding f = c / BP_NL, and
+// E = header[11] is the largest number of kinks strictly inside one cell [c, c + 1) / BP_NL
+// (both in T's comparisons), so with E <= 1 the piece of f is lut[cell] + (sigma[that + 1] <= f)
+constexpr int BP_NL = 128;
+constexpr int BP_LUT = BP_MI + 2 * BP_QMAX;
 // coefficients of piece q, offset j: (c0..c3) at BP_CA + q BP_QA + 4 j, (c4, c5) at
 // BP_CB + q BP_QB + 2 j; the +4 / +2 pads put the pieces one warp touches on different
 // banks for the 16-byte and 8-byte reads
-constexpr int BP_CA = BP_IHW + BP_QMAX;  // 52: 16-byte aligned
+constexpr int BP_CA = BP_LUT + BP_NL / 4;  // 84: 16-byte aligned
 constexpr int BP_QA = BP_NJMAX * 4 + 4;
 constexpr int BP_CB = BP_CA + BP_QMAX * BP_QA;
 constexpr int BP_QB = BP_NJMAX * 2 + 2;
@@ -80,7 +84,11 @@ __global__ void __launch_bounds__(256) k_bp_tables(const double* __restrict__ an
                                                    int* __restrict__ status) {
   const int a = blockIdx.x;
   __shared__ double sig[64];
-  __shared__ int Qs;
+  __shared__ int Qs, Es;
+  // cos(pi k (2i + 1) / 12), k, i < 6: the Chebyshev nodes (k = 1) and the fit's cosines,
+  // formed once per view
+  __shared__ double cosk[36];
+  if (threadIdx.x < 36) cosk[threadIdx.x] = cospi((threadIdx.x / 6) * (2.0 * (threadIdx.x % 6) + 1.0) / 12.0);
   double s_, c_;
   sincospi(ang[a], &s_, &c_);
   const double A = fabs(c_), B = fabs(s_);
@@ -146,12 +154,25 @@ __global__ void __launch_bounds__(256) k_bp_tables(const double* __restrict__ an
       h[7 + 2 * k] = T(hi);
       h[8 + 2 * k] = T(cs[k] - hi);
     }
-    h[11] = T(0);
+    Es = 0;
   }
   __syncthreads();
   const int Q = Qs;
   if (Q > BP_QMAX || nJ > BP_NJMAX) return;
   T* h = tab + (long)a * BP_STRIDE;
+  // piece lookup, one cell a thread, with T's comparisons (those of the gathers): the
+  // piece holding the cell's left end and the kinks strictly inside the cell
+  if (threadIdx.x < BP_NL) {
+    const T x0 = T(threadIdx.x) * T(1.0 / BP_NL), x1 = T(threadIdx.x + 1) * T(1.0 / BP_NL);
+    int q0 = 0, e = 0;
+    for (int r = 1; r < 16; ++r) {
+      const T sr = h[BP_SIG + r];
+      q0 += sr <= x0 ? 1 : 0;
+      e += (x0 < sr && sr < x1) ? 1 : 0;
+    }
+    reinterpret_cast<unsigned char*>(h + BP_LUT)[threadIdx.x] = (unsigned char)q0;
+    atomicMax(&Es, e);
+  }
   for (int i = threadIdx.x; i < BP_QMAX * 6; i += blockDim.x) {  // pads
     if (i < BP_QMAX * 4) h[BP_CA + (i / 4) * BP_QA + BP_NJMAX * 4 + i % 4] = T(0);
     else h[BP_CB + ((i - BP_QMAX * 4) / 2) * BP_QB + BP_NJMAX * 2 + i % 2] = T(0);
@@ -162,11 +183,12 @@ __global__ void __launch_bounds__(256) k_bp_tables(const double* __restrict__ an
   for (int it = threadIdx.x; it < Q * nJ * 6; it += blockDim.x) {
     const int i = it % 6, w = it / 6, q = w / nJ, j = w - q * nJ;
     const double mid = 0.5 * (sig[q] + sig[q + 1]), hw = 0.5 * (sig[q + 1] - sig[q]);
-    const double f = mid + hw * cospi((2.0 * i + 1.0) / 12.0);
+    const double f = mid + hw * cosk[6 + i];
     const double u = (J0 + j - f) * lam;
     fvs[it] = (fabs(u) < 0.5 * W) ? lam * box_eval(u, D, small) : 0.0;
   }
   __syncthreads();
+  if (threadIdx.x == 0) h[11] = T(Es);
   for (int w = threadIdx.x; w < BP_QMAX * BP_NJMAX; w += blockDim.x) {
     const int q = w / BP_NJMAX, j = w % BP_NJMAX;
     T* ca = h + BP_CA + q * BP_QA + j * 4;
@@ -175,17 +197,17 @@ __global__ void __launch_bounds__(256) k_bp_tables(const double* __restrict__ an
       for (int i = 0; i < 4; ++i) ca[i] = T(0);
       cb[0] = T(0);
       cb[1] = T(0);
-      if (j == 0 && q < BP_QMAX) { h[BP_MID + q] = T(0); h[BP_IHW + q] = T(0); }
+      if (j == 0 && q < BP_QMAX) { h[BP_MI + 2 * q] = T(0); h[BP_MI + 2 * q + 1] = T(0); }
       continue;
     }
     const double lo = sig[q], hi = sig[q + 1];
     const double mid = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
-    if (j == 0) { h[BP_MID + q] = T(mid); h[BP_IHW + q] = T(1.0 / hw); }
+    if (j == 0) { h[BP_MI + 2 * q] = T(mid); h[BP_MI + 2 * q + 1] = T(1.0 / hw); }
     const double* fv = fvs + (q * nJ + j) * 6;
     double ch[6];
     for (int k = 0; k < 6; ++k) {
       double acc = 0.0;
-      for (int i = 0; i < 6; ++i) acc += fv[i] * cospi(k * (2.0 * i + 1.0) / 12.0);
+      for (int i = 0; i < 6; ++i) acc += fv[i] * cosk[6 * k + i];
       ch[k] = acc * (k == 0 ? 1.0 / 6.0 : 2.0 / 6.0);
     }
     // Chebyshev -> monomial: T0=1, T1=v, T2=2v^2-1, T3=4v^3-3v, T4=8v^4-8v^2+1, T5=16v^5-20v^3+5v
@@ -353,7 +375,7 @@ __global__ void __launch_bounds__(BP_TX* BP_TY) k_bp_gather(const T* __restrict_
         if (h[BP_SIG + q + step] <= f) q += step;
       const int Qm1 = (int)h[2] - 1;
       q = q < Qm1 ? q : Qm1;  // f rounded up to 1.0: the last piece's right end
-      const T v = (f - h[BP_MID + q]) * h[BP_IHW + q];
+      const T v = (f - h[BP_MI + 2 * q]) * h[BP_MI + 2 * q + 1];
       const T* ca = h + BP_CA + q * BP_QA;
       const T* cb = h + BP_CB + q * BP_QB;
       const T* cw = s_ct + ai * win + moff;
@@ -384,41 +406,49 @@ __global__ void __launch_bounds__(BP_TX* BP_TY) k_bp_gather(const T* __restrict_
 // those coefficients for every bin slot the tile touches (<= 153 slots, ~0.2 extra FMA
 // per pixel-view pair), then every pixel costs one piece search and one Horner step.
 // The next view's piece table (cp.async) and detector-sample window are fetched while
-// the current view is processed.  Each lane owns a 4 x 4 pixel block whose detector
-// coordinate is computed in FP64 per view, so FP32 offsets stay below 4.3 bins; FP32
-// partial sums go into FP64 totals every 32 views.
+// the current view is processed.  A warp owns a 16 x 8 BS_KY block of the tile and one read
+// of the coefficients by its 32 lanes covers a compact 4 x 8 pixel block, whose (slot,
+// piece) records are few and, stored slot-major, mostly on distinct banks; lane (lx, ly)
+// takes the pixels (lx + 4 i, ly + 8 k), i < 4, k < BS_KY.  The detector coordinate of a lane's
+// first pixel comes from the exact FP32 split of the view's steps, and the offsets 4 i c
+// and 8 k s are split the same way into integer and fractional parts, so the FP32 sum
+// that decides the piece stays below 3 bins; FP32 partial sums go into FP64 totals every
+// 32 views.
 // ------------------------------------------------------------------------------------
 constexpr int BS_TS = 64;                          // tile edge (pixels)
-constexpr int BS_NT = 256;                         // 8 warps x 32 lanes x (4 x 4 pixels)
+constexpr int BS_KY = 4;                           // rows (8 apart) of a lane's pixels
+constexpr int BS_NP = 4 * BS_KY;                   // pixels of a lane
+constexpr int BS_NT = BS_TS * BS_TS / BS_NP;       // threads of a tile
+constexpr int BS_MINB = BS_KY == 4 ? 3 : 2;        // CTAs per SM (registers)
 constexpr double BS_LAMBDA_MIN = 0.6;              // window <= 63 sqrt(2) / lambda + 4 <= 153
 constexpr int BS_WMAX = 160;                       // bin slots of the coefficient window
-// bin slot s of piece q lives at q BS_WS + s + s/4: lanes whose slots differ by a
-// multiple of 4 (near-axis views) then fall on different banks
-constexpr int BS_WS = BS_WMAX + BS_WMAX / 4 + 1;
-__device__ __forceinline__ int bs_slot(int s) { return s + (s >> 2); }
+// the record of bin slot s, piece q is entry s Q + q (Q pieces in this view): along a
+// pixel block the (slot, piece) pairs met in order of the detector coordinate are
+// consecutive entries
+constexpr int BS_NREC = BS_WMAX * BP_QMAX;
 constexpr int BS_CW = BS_WMAX + BP_NJMAX + 4;      // detector-sample window
 struct BsHeader {
   double p00, c, s;   // detector coordinate of pixel (0, 0) and its steps, in bins
   int m0lo, W, J0, nJ, Q;
 };
 constexpr size_t bs_smem() {
-  return (size_t)BP_QMAX * BS_WS * (16 + 8) + 2 * (size_t)BP_STRIDE * 4 + 2 * (size_t)BS_CW * 4;
+  return (size_t)BS_NREC * (16 + 8) + 2 * (size_t)BP_STRIDE * 4 + 2 * (size_t)BS_CW * 4;
 }
 
 // blockIdx.z takes views [z vc, min(na, (z + 1) vc)); with more than one z the sums go to
 // the partial image out + z N^2 (summed in order by k_bp_reduce), else to out.
-__global__ void __launch_bounds__(BS_NT, 3) k_bp_spline(const float* __restrict__ tab, const double2* __restrict__ csl,
+__global__ void __launch_bounds__(BS_NT, BS_MINB) k_bp_spline(const float* __restrict__ tab, const double2* __restrict__ csl,
                                                         const double* __restrict__ p00, const float* __restrict__ ct,
                                                         int na, int vc, int N, int M, float* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char bs_raw[];
-  float4* FcA = reinterpret_cast<float4*>(bs_raw);                 // [QMAX][BS_WS]
-  float2* FcB = reinterpret_cast<float2*>(FcA + BP_QMAX * BS_WS);  // [QMAX][BS_WS]
-  float* tb = reinterpret_cast<float*>(FcB + BP_QMAX * BS_WS);     // [2][BP_STRIDE]
+  float4* FcA = reinterpret_cast<float4*>(bs_raw);             // [slot][piece] c0..c3
+  float2* FcB = reinterpret_cast<float2*>(FcA + BS_NREC);      // [slot][piece] c4, c5
+  float* tb = reinterpret_cast<float*>(FcB + BS_NREC);         // [2][BP_STRIDE]
   float* ctw = tb + 2 * BP_STRIDE;                                  // [2][BS_CW]
   __shared__ BsHeader hdr[2];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int TX0 = blockIdx.x * BS_TS, TY0 = blockIdx.y * BS_TS;
-  const int Xb = TX0 + 4 * (lane & 15), Yb = TY0 + 8 * w + 4 * (lane >> 4);
+  const int Xb = TX0 + 16 * (w & 3) + (lane & 3), Yb = TY0 + 8 * BS_KY * (w >> 2) + (lane >> 2);
 
   auto header = [&](int a, BsHeader& h) {
     const double2 u = csl[a];
@@ -457,10 +487,10 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bp_spline(const float* __restrict_
   if (threadIdx.x < BS_CW) ctw[threadIdx.x] = sample(a_begin, hdr[0], threadIdx.x);
   cp_async_wait_bp();
 
-  float acc[16];
-  double tot[16];
+  float acc[BS_NP];
+  double tot[BS_NP];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) { acc[i] = 0.f; tot[i] = 0.0; }
+  for (int i = 0; i < BS_NP; ++i) { acc[i] = 0.f; tot[i] = 0.0; }
 
   for (int a = a_begin; a < a_end; ++a) {
     const int buf = (a - a_begin) & 1;
@@ -478,9 +508,9 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bp_spline(const float* __restrict_
       const BsHeader& h = hdr[buf];
       const float* t = tb + buf * BP_STRIDE;
       const float* cw = ctw + buf * BS_CW;
-      const int W = h.W, nJ = h.nJ, groups = (W + 1) >> 1, items = h.Q * groups;
+      const int W = h.W, nJ = h.nJ, Q = h.Q, items = Q * ((W + 1) >> 1);
       for (int it = threadIdx.x; it < items; it += BS_NT) {
-        const int q = it / groups, s0 = (it - q * groups) << 1;
+        const int g = it / Q, q = it - g * Q, s0 = g << 1;
         const float* ca = t + BP_CA + q * BP_QA;
         const float* cb = t + BP_CB + q * BP_QB;
         float2 a01 = make_float2(0.f, 0.f), a23 = a01, a45 = a01, b01 = a01, b23 = a01, b45 = a01;
@@ -499,11 +529,11 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bp_spline(const float* __restrict_
           b45 = __ffma2_rn(p1, y, b45);
           c0 = c1;
         }
-        FcA[q * BS_WS + bs_slot(s0)] = make_float4(a01.x, a01.y, a23.x, a23.y);
-        FcB[q * BS_WS + bs_slot(s0)] = a45;
+        FcA[s0 * Q + q] = make_float4(a01.x, a01.y, a23.x, a23.y);
+        FcB[s0 * Q + q] = a45;
         if (s0 + 1 < W) {
-          FcA[q * BS_WS + bs_slot(s0 + 1)] = make_float4(b01.x, b01.y, b23.x, b23.y);
-          FcB[q * BS_WS + bs_slot(s0 + 1)] = b45;
+          FcA[(s0 + 1) * Q + q] = make_float4(b01.x, b01.y, b23.x, b23.y);
+          FcB[(s0 + 1) * Q + q] = b45;
         }
       }
     }
@@ -522,24 +552,49 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bp_spline(const float* __restrict_
       const float fr = (t[6] + (a1 - n1)) + ((a2 - n2) + fmaf(Y, t[10], X * t[8]));
       const float n3 = floorf(fr);
       const int mb = (int)t[5] + (int)n1 + (int)n2 + (int)n3 - h.m0lo;
-      const float fb = fr - n3, cl = t[0], sl = t[1];
-      const int Qm1 = h.Q - 1;
+      const float fb = fr - n3;
+      const int Q = h.Q, Qm1 = Q - 1;
+      const unsigned char* lut = reinterpret_cast<const unsigned char*>(t + BP_LUT);
+      // offsets 8 k s of the lane's rows: integer part and fraction (+ the lo part)
+      float gy[BS_KY];
+      int ny[BS_KY];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < BS_KY; ++k) {
+        const float hy = (float)(8 * k) * t[9];  // exact
+        const float fy = floorf(hy);
+        ny[k] = (int)fy;
+        gy[k] = (hy - fy) + (float)(8 * k) * t[10];
+      }
+      // the piece of f: one lookup and one compare where no cell holds two kinks (E <= 1,
+      // the same piece as the search), else a 4-step search; the branch is per view
+      const bool by_lut = t[11] <= 1.f;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float pl = fb + (float)i * cl + (float)k * sl;
+      for (int i = 0; i < 4; ++i) {
+        const float hx = (float)(4 * i) * t[7];  // exact
+        const float fx = floorf(hx);
+        const int nx = mb + (int)fx;
+        const float gx = fb + ((hx - fx) + (float)(4 * i) * t[8]);
+#pragma unroll
+        for (int k = 0; k < BS_KY; ++k) {
+          const float pl = gx + gy[k];
           const float fl = floorf(pl);
           const float f = pl - fl;
-          const int slot = mb + (int)fl;
+          const int slot = nx + ny[k] + (int)fl;
           int q = 0;
+          if (by_lut) {
+            const int cell = (int)(f * (float)BP_NL);
+            q = lut[cell < BP_NL - 1 ? cell : BP_NL - 1];
+            q += t[BP_SIG + q + 1] <= f ? 1 : 0;
+          } else {
 #pragma unroll
-          for (int step = 8; step > 0; step >>= 1)
-            if (t[BP_SIG + q + step] <= f) q += step;
+            for (int step = 8; step > 0; step >>= 1)
+              if (t[BP_SIG + q + step] <= f) q += step;
+          }
           q = q < Qm1 ? q : Qm1;  // f rounded up to 1.0: the last piece's right end
-          const float v = (f - t[BP_MID + q]) * t[BP_IHW + q];
-          const float4 x = FcA[q * BS_WS + bs_slot(slot)];
-          const float2 y = FcB[q * BS_WS + bs_slot(slot)];
+          const float2 mi = *reinterpret_cast<const float2*>(t + BP_MI + 2 * q);
+          const float v = (f - mi.x) * mi.y;
+          const float4 x = FcA[slot * Q + q];
+          const float2 y = FcB[slot * Q + q];
           float r = fmaf(y.y, v, y.x);
           r = fmaf(r, v, x.w);
           r = fmaf(r, v, x.z);
@@ -552,15 +607,15 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bp_spline(const float* __restrict_
     if (a + 1 < a_end && threadIdx.x < BS_CW) ctw[(buf ^ 1) * BS_CW + threadIdx.x] = cnext;
     if (((a - a_begin) & 31) == 31) {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) { tot[i] += (double)acc[i]; acc[i] = 0.f; }
+      for (int i = 0; i < BS_NP; ++i) { tot[i] += (double)acc[i]; acc[i] = 0.f; }
     }
     cp_async_wait_bp();
   }
 #pragma unroll
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < BS_KY; ++k)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int X = Xb + i, Y = Yb + k;
+      const int X = Xb + 4 * i, Y = Yb + 8 * k;
       if (X < N && Y < N) b[(long)Y * N + X] = (float)(tot[4 * k + i] + (double)acc[4 * k + i]);
     }
 }
@@ -578,8 +633,8 @@ __global__ void k_bp_reduce(const float* __restrict__ part, int S, long n, float
 // images are summed in order by k_bp_reduce.  At least enough splits that a small image
 // still fills about 1024 CTAs, at most four times that (and >= 16 views per split); within
 // that range the split is chosen so that the CTAs fill the resident slots of the current
-// GPU (3 per SM) in whole waves (the last wave of 1024 tiles on 456 slots would otherwise run
-// a quarter full).  The workspace is sized for the largest split of the range, so it does
+// GPU (SMs x resident CTAs per SM) in whole waves (the last wave of 1024 tiles on 456 slots
+// would otherwise run a quarter full).  The workspace is sized for the largest split of the range, so it does
 // not depend on the device.
 static void bp_split_range(int N, int na, double lambda, int precision, int* smin, int* smax) {
   *smin = *smax = 1;
@@ -600,8 +655,15 @@ int bp_view_split(int N, int na, double lambda, int precision) {
     cudaGetLastError();
     return smin;
   }
+  int per_sm = 0;
+  if (cudaFuncSetAttribute(k_bp_spline, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs_smem()) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bp_spline, BS_NT, bs_smem()) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = BS_MINB;
+  }
   const int t = (N + BS_TS - 1) / BS_TS;
-  const double slots = 3.0 * sms;
+  const double slots = (double)per_sm * sms;
   int best = smin;
   double best_score = -1.0;
   for (int S = smin; S <= smax; ++S) {
