@@ -210,14 +210,22 @@ __device__ inline double box_conv(double x, const BoxDirs& P, int small_p, const
   return acc;
 }
 
+// cos(pi k (2i + 1) / (2 NC)) for k, i < NC at entry NC k + i: the Chebyshev nodes (k = 1)
+// and the cosines of the discrete Chebyshev transform, formed once by the threads of a CTA
+// (the caller synchronises before reading them)
+template <int NC>
+__device__ inline void cheb_cos_fill(double* t) {
+  for (int e = threadIdx.x; e < NC * NC; e += blockDim.x) t[e] = cospi((e / NC) * (2.0 * (e % NC) + 1.0) / (2.0 * NC));
+}
+
 // Monomial coefficients c[0..7] (in v on [-1, 1]) of the polynomial of degree <= 7 through
 // the values fv[i] at the Chebyshev nodes cos(pi (2i + 1) / 16): the discrete Chebyshev
-// transform, then T_0..T_7 written out in powers of v.
-__device__ inline void cheb8_monomials(const double fv[8], double c[8]) {
+// transform, then T_0..T_7 written out in powers of v.  ck: cheb_cos_fill<8>.
+__device__ inline void cheb8_monomials(const double fv[8], double c[8], const double* ck) {
   double ch[8];
   for (int k = 0; k < 8; ++k) {
     double acc = 0.0;
-    for (int i = 0; i < 8; ++i) acc += fv[i] * cospi(k * (2.0 * i + 1.0) / 16.0);
+    for (int i = 0; i < 8; ++i) acc += fv[i] * ck[8 * k + i];
     ch[k] = acc * (k == 0 ? 1.0 / 8.0 : 2.0 / 8.0);
   }
   c[0] = ch[0] - ch[2] + ch[4] - ch[6];
@@ -270,6 +278,8 @@ __device__ inline double foot_box_conv(double x, double A, double B, double w1, 
 
 // Built by all threads of a CTA (contains barriers).
 __device__ inline void foot_build(FootPoly& F, double A, double B, double w1, double w2, double merge_tol) {
+  __shared__ double ck[16];
+  cheb_cos_fill<4>(ck);
   if (threadIdx.x == 0) {
     const double W = A + B + w1 + w2;
     double k[16];
@@ -296,14 +306,14 @@ __device__ inline void foot_build(FootPoly& F, double A, double B, double w1, do
   for (int it = threadIdx.x; it < F.K * 4; it += blockDim.x) {
     const int q = it >> 2, i = it & 3;
     const double mid = 0.5 * (F.kn[q] + F.kn[q + 1]), hw = 0.5 * (F.kn[q + 1] - F.kn[q]);
-    F.fv[q][i] = foot_box_conv(mid + hw * cospi((2.0 * i + 1.0) / 8.0), A, B, w1, w2);
+    F.fv[q][i] = foot_box_conv(mid + hw * ck[4 + i], A, B, w1, w2);
   }
   __syncthreads();
   for (int q = threadIdx.x; q < F.K; q += blockDim.x) {
     double ch[4];
     for (int k = 0; k < 4; ++k) {
       double acc = 0.0;
-      for (int i = 0; i < 4; ++i) acc += F.fv[q][i] * cospi(k * (2.0 * i + 1.0) / 8.0);
+      for (int i = 0; i < 4; ++i) acc += F.fv[q][i] * ck[4 * k + i];
       ch[k] = acc * (k == 0 ? 0.25 : 0.5);
     }
     // T0 = 1, T1 = v, T2 = 2v^2 - 1, T3 = 4v^3 - 3v

@@ -198,11 +198,14 @@ typedef GTab<64, 8> GT2;
 // its values into monomial coefficients.  fv: shared scratch of KMAX * NC doubles.
 template <typename L, typename F>
 __device__ void fit_table_pieces(double* __restrict__ T, const double* kn, int nk, double* fv, F kernel) {
+  __shared__ double ck[L::NC * L::NC];
+  cheb_cos_fill<L::NC>(ck);
+  __syncthreads();
   const int items = (nk - 1) * L::NC;
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
     const int q = it / L::NC, i = it - q * L::NC;
     const double mid = 0.5 * (kn[q] + kn[q + 1]), hw = 0.5 * (kn[q + 1] - kn[q]);
-    fv[it] = kernel(mid + hw * cospi((2.0 * i + 1.0) / (2.0 * L::NC)));
+    fv[it] = kernel(mid + hw * ck[L::NC + i]);
   }
   __syncthreads();
   for (int q = threadIdx.x; q < L::KMAX; q += blockDim.x) {
@@ -215,13 +218,13 @@ __device__ void fit_table_pieces(double* __restrict__ T, const double* kn, int n
     }
     const double* v = fv + q * L::NC;
     if constexpr (L::NC == 8) {
-      cheb8_monomials(v, c);
+      cheb8_monomials(v, c, ck);
     } else {
       static_assert(L::NC == 6, "6 or 8 coefficients");
       double ch[6];
       for (int k = 0; k < 6; ++k) {
         double acc = 0.0;
-        for (int i = 0; i < 6; ++i) acc += v[i] * cospi(k * (2.0 * i + 1.0) / 12.0);
+        for (int i = 0; i < 6; ++i) acc += v[i] * ck[6 * k + i];
         ch[k] = acc * (k == 0 ? 1.0 / 6.0 : 2.0 / 6.0);
       }
       // Chebyshev -> monomial: T0=1, T1=v, T2=2v^2-1, T3=4v^3-3v, T4=8v^4-8v^2+1, T5=16v^5-20v^3+5v

@@ -160,6 +160,8 @@ __global__ void __launch_bounds__(256) k_mb_bp_tables(const double* __restrict__
   // the used slots in chunks of MB_CHUNK (piece, offset) pairs: the 8 node values of every
   // pair of the chunk spread over all threads, then one thread per pair fits them
   __shared__ double fvs[MB_CHUNK * 8];
+  __shared__ double ck[64];
+  cheb_cos_fill<8>(ck);  // read after the first barrier of the chunk loop
   const int items = Qn * nJ;
   for (int c0 = 0; c0 < items; c0 += MB_CHUNK) {
     const int nc = items - c0 < MB_CHUNK ? items - c0 : MB_CHUNK;
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(256) k_mb_bp_tables(const double* __restrict__
     for (int it = threadIdx.x; it < nc * 8; it += blockDim.x) {
       const int w = c0 + (it >> 3), i = it & 7, q = w / nJ, j = w - q * nJ;
       const double mid = 0.5 * (sig[q] + sig[q + 1]), hw = 0.5 * (sig[q + 1] - sig[q]);
-      const double f = mid + hw * cospi((2.0 * i + 1.0) / 16.0);
+      const double f = mid + hw * ck[8 + i];
       const double u = (J0 + j - f) * lam;
       fvs[it] = fabs(u) < 0.5 * W
                     ? lam * foot_conv(F, u, -bh, bh, bk, d + 2, [&](double v) { return box_tp(-fabs(v), Q); })
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(256) k_mb_bp_tables(const double* __restrict__
     for (int k = threadIdx.x; k < nc; k += blockDim.x) {
       const int w = c0 + k, q = w / nJ, j = w - q * nJ;
       double mono[8];
-      cheb8_monomials(fvs + 8 * k, mono);
+      cheb8_monomials(fvs + 8 * k, mono, ck);
       T* c = cv + ((long)q * MB_NJMAX + j) * MB_NC;
       for (int i = 0; i < MB_NC; ++i) c[i] = T(mono[i]);
     }
