@@ -126,11 +126,15 @@ def test_learned_warm_start_gain(bsct):
     _, rl = g.cg_solve_learned(bad, b, 1.0 / na, max_iter=2000, rel_tol=1e-4, check_every=5)
     assert rl["alpha"] == 0.0 and rl["iterations"] == rp["iterations"]
     # ... and as a preconditioner (<r, z> = 0) falls back to the identity every time, which
-    # makes flexible CG the same method as CG
+    # makes flexible CG the same method as CG in exact arithmetic.  In FP32 the two take
+    # their scalars from different products (flexible: alpha = <p, r> / <p, Gp>, beta =
+    # -<z, Gp> / <p, Gp>; CG: <r, r>-ratios), which lose orthogonality differently on this
+    # ill-conditioned G, so the iterations to 1e-4 differ by a few (32 against 35 seen after
+    # a rounding-level change of b): within 15 %
     _, rp1 = g.cg_solve(b, max_iter=2000, rel_tol=1e-4, check_every=1)
     _, rf = g.fcg_solve_learned(bad, b, 1.0 / na, max_iter=2000, rel_tol=1e-4, precond_every=1)
     assert rf["converged"] and rf["n_fallback"] == rf["n_precond"] == rf["iterations"]
-    assert abs(rf["iterations"] - rp1["iterations"]) <= 2
+    assert abs(rf["iterations"] - rp1["iterations"]) <= max(2, 0.15 * rp1["iterations"])
     # warm start followed by circulant-preconditioned CG: reaches the tolerance; with the
     # useless network it is PCG from x0 = 0 exactly
     b = (Xe[2] * na).contiguous()
