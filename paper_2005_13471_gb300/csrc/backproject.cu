@@ -480,8 +480,12 @@ __global__ void __launch_bounds__(BS_NT, BS_MINB) k_bp_spline(const float* __res
 
   const int a_begin = blockIdx.z * vc, a_end = min(na, a_begin + vc);
   float* b = out + (long)blockIdx.z * N * N;
+  // the next view's header (global loads, FP64) is formed by lane 0 of the last warp: the
+  // window work items go to the low threads first, so that warp is the least loaded and
+  // the loads' latency overlaps the other warps' window work
+  constexpr int HDR_T = BS_NT - 32;
   // prologue: first view
-  if (threadIdx.x == 0) header(a_begin, hdr[0]);
+  if (threadIdx.x == HDR_T) header(a_begin, hdr[0]);
   stage_table(a_begin, 0);
   __syncthreads();
   if (threadIdx.x < BS_CW) ctw[threadIdx.x] = sample(a_begin, hdr[0], threadIdx.x);
@@ -496,7 +500,7 @@ __global__ void __launch_bounds__(BS_NT, BS_MINB) k_bp_spline(const float* __res
     const int buf = (a - a_begin) & 1;
     __syncthreads();  // view a staged; the previous view's pixel phase is done
     if (a + 1 < a_end) {
-      if (threadIdx.x == 0) header(a + 1, hdr[buf ^ 1]);
+      if (threadIdx.x == HDR_T) header(a + 1, hdr[buf ^ 1]);
       stage_table(a + 1, buf ^ 1);
     }
     // coefficient window: F on (slot s, piece q) = sum_j c~[m0lo + s + J0 + j] coef_{q,j}.
