@@ -181,7 +181,7 @@ int bsct_gram_apply_host(bsct_gram* g, const void* h_x, void* h_y, int32_t n, vo
  *                device, read every call);
  *   d_x, d_y   : [N][N] float on the device, may not alias.
  * The first call on a device looks up the device addresses of those arrays (no
- * allocation); make that first call before any stream capture.  All calls share the
+ * allocation).  All calls share the
  * arrays and leave the last call's contents in them; every element a call reads
  * (twiddle tables of its N, packed spectrum, scratch) is written by the same call
  * first, so nothing has to be cleared and calls with different N may follow one
