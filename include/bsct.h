@@ -399,7 +399,7 @@ int bsct_gnorm_loss_grad(const bsct_gram* g, const float* d_pred, const float* d
 /* CG with a learned warm start: x_hat = net(in_scale * b); x0 = alpha x_hat with
  * alpha = <x_hat, b> / <x_hat, G x_hat> (the G-norm-optimal scaling); if alpha is not
  * positive and finite, x0 = 0 (plain CG).  Then bsct_cg_solve from x0 with the given
- * tolerance - plain CG is the judge of the warm start's error.  *alpha_out (may be
+ * tolerance: plain CG removes whatever error the warm start leaves.  *alpha_out (may be
  * NULL) receives alpha.  F32 handle; N a multiple of 64.  Synchronous. */
 int bsct_cg_solve_learned(bsct_gram* g, bsct_unet* net, const void* d_b, void* d_x, float in_scale, int max_iter,
                           double rel_tol, int check_every, bsct_cg_report* report, double* alpha_out, void* stream);

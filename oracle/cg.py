@@ -95,6 +95,6 @@ def steepest_descent(apply_G, b, x0=None, iters=20, tol=0.0):
 
 
 def true_relative_residual(apply_G, b, x):
-    """||b - G x|| / ||b|| recomputed from scratch (the judge of any solver's output)."""
+    """||b - G x|| / ||b|| recomputed from scratch (the measure every solver's output is checked by)."""
     r = b - apply_G(x)
     return float(np.sqrt(np.sum(r * r)) / np.sqrt(np.sum(b * b)))

@@ -85,7 +85,7 @@ def test_adam_step(bsct):
 def test_learned_warm_start_gain(bsct):
     # Trains a small network on pairs the method generates, then measures what its warm
     # start buys: the starting residual (vs 1 for x0 = 0) and the iterations / time to a
-    # 1e-4 relative residual, with plain CG as the judge (both must reach the tolerance
+    # 1e-4 relative residual, with plain CG as the reference (both must reach the tolerance
     # by the FP32 true residual).  An untrained network falls back to plain CG.
     from paper_2005_13471_gb300 import learned
 
