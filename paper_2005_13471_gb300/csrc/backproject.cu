@@ -412,8 +412,10 @@ __global__ void __launch_bounds__(BP_TX* BP_TY) k_bp_gather(const T* __restrict_
 // takes the pixels (lx + 4 i, ly + 8 k), i < 4, k < BS_KY.  The detector coordinate of a lane's
 // first pixel comes from the exact FP32 split of the view's steps, and the offsets 4 i c
 // and 8 k s are split the same way into integer and fractional parts, so the FP32 sum
-// that decides the piece stays below 3 bins; FP32 partial sums go into FP64 totals every
-// 32 views.
+// that decides the piece stays below 3 bins.  Every 32 views the FP32 partial sum acc is
+// moved into the FP32 total th by an exact two-sum, th + acc = th' + e, and the rounding
+// error e stays in acc: th + acc always holds the running sum without loss (as an FP64
+// total would), with no FP64 instruction, which this part issues at 1/64 of the FP32 rate.
 // ------------------------------------------------------------------------------------
 constexpr int BS_TS = 64;                          // tile edge (pixels)
 constexpr int BS_KY = 4;                           // rows (8 apart) of a lane's pixels
@@ -492,9 +494,9 @@ __global__ void __launch_bounds__(BS_NT, BS_MINB) k_bp_spline(const float* __res
   cp_async_wait_bp();
 
   float acc[BS_NP];
-  double tot[BS_NP];
+  float th[BS_NP];  // running sum = th + acc
 #pragma unroll
-  for (int i = 0; i < BS_NP; ++i) { acc[i] = 0.f; tot[i] = 0.0; }
+  for (int i = 0; i < BS_NP; ++i) { acc[i] = 0.f; th[i] = 0.f; }
 
   for (int a = a_begin; a < a_end; ++a) {
     const int buf = (a - a_begin) & 1;
@@ -611,7 +613,13 @@ __global__ void __launch_bounds__(BS_NT, BS_MINB) k_bp_spline(const float* __res
     if (a + 1 < a_end && threadIdx.x < BS_CW) ctw[(buf ^ 1) * BS_CW + threadIdx.x] = cnext;
     if (((a - a_begin) & 31) == 31) {
 #pragma unroll
-      for (int i = 0; i < BS_NP; ++i) { tot[i] += (double)acc[i]; acc[i] = 0.f; }
+      for (int i = 0; i < BS_NP; ++i) {  // two-sum: th + acc = sum + e exactly
+        const float sum = th[i] + acc[i];
+        const float bb = sum - th[i];
+        const float e = (th[i] - (sum - bb)) + (acc[i] - bb);
+        th[i] = sum;
+        acc[i] = e;
+      }
     }
     cp_async_wait_bp();
   }
@@ -620,7 +628,8 @@ __global__ void __launch_bounds__(BS_NT, BS_MINB) k_bp_spline(const float* __res
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int X = Xb + 4 * i, Y = Yb + 8 * k;
-      if (X < N && Y < N) b[(long)Y * N + X] = (float)(tot[4 * k + i] + (double)acc[4 * k + i]);
+      if (X < N && Y < N)
+        b[(long)Y * N + X] = (float)((double)th[4 * k + i] + (double)acc[4 * k + i]);
     }
 }
 
