@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(BP_TX* BP_TY) k_bp_gather(const T* __restrict_
 // one degree-5 polynomial in v = (f - mid_q) / halfwidth_q whose coefficients are
 // sum_j c~[m0 + J0 + j] coef_{q,j}.  A CTA owns a 64 x 64 tile; per view it first forms
 // those coefficients for every bin slot the tile touches (<= 153 slots, ~0.2 extra FMA
-// per pixel-view pair), then every pixel costs one piece search and one Horner step.
+// per pixel-view pair), then every pixel costs one piece lookup and one Horner step.
 // The next view's piece table (cp.async) and detector-sample window are fetched while
 // the current view is processed.  A warp owns a 16 x 8 BS_KY block of the tile and one read
 // of the coefficients by its 32 lanes covers a compact 4 x 8 pixel block, whose (slot,
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(BP_TX* BP_TY) k_bp_gather(const T* __restrict_
 // that decides the piece stays below 3 bins.  Every 32 views the FP32 partial sum acc is
 // moved into the FP32 total th by an exact two-sum, th + acc = th' + e, and the rounding
 // error e stays in acc: th + acc always holds the running sum without loss (as an FP64
-// total would), with no FP64 instruction, which this part issues at 1/64 of the FP32 rate.
+// total would), with no FP64 instruction (GB300 issues FP64 at 1/64 of the FP32 rate).
 // ------------------------------------------------------------------------------------
 constexpr int BS_TS = 64;                          // tile edge (pixels)
 constexpr int BS_KY = 4;                           // rows (8 apart) of a lane's pixels
